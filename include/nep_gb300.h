@@ -1,0 +1,159 @@
+/*
+ * nep_gb300.h -- C ABI of the GB300 (sm_103a) NEP molecular-dynamics library.
+ *
+ * The library evaluates the Neuroevolution Potential (NEP) of one atomic species and integrates
+ * Newton's equations with velocity Verlet, all on one GPU:
+ *   cell-list neighbour build -> radial + angular (3-body, 4-body) descriptors -> single-hidden-layer
+ *   tanh network giving site energies U_i -> chain-rule forces and virial -> velocity Verlet.
+ * The method follows "Trillion-atom molecular dynamics simulations with ab initio accuracy"
+ * (NEP energy formula and descriptor definitions in Section III.B and Fig. 1; model hyper-
+ * parameters and MD protocol in Section VI.A; the five evaluation stages in Section V.B and Table 2).
+ *
+ * Conventions shared by every entry point
+ *   - Units: Angstrom, eV, fs, amu.  Forces eV/Angstrom, virial eV.
+ *   - Array pointers may be host or device memory; the library detects which with
+ *     cudaPointerGetAttributes.  Host pointers make the call synchronous.  Device pointers are used
+ *     on the handle's stream; the call returns once the work is enqueued unless it also returns a
+ *     host scalar.
+ *   - Per-atom arrays are in the caller's atom order ("original order", index 0..n-1 as passed to
+ *     nep_set_state), row-major [n][3] for vectors.  Internally atoms are kept sorted by cell; the
+ *     library permutes back on output.
+ *   - The caller owns every pointer it passes; pointers are read or written only during the call.
+ *     The library owns all of its internal device memory (allocated by nep_set_state, released by
+ *     nep_destroy).
+ *   - Errors are returned as nep_status; nep_last_error(h) gives a message.  No entry point exits,
+ *     traps or spins without a bound.  Conditions detected on the device (neighbour-list overflow,
+ *     non-finite values) are reported through a status word read back by the host.
+ *   - Orthorhombic periodic box only; every edge must be >= 2 * (rc_R + skin).
+ *   - At most NEP_MAX_ATOMS atoms (a neighbour entry packs a 27-bit atom index with a 5-bit
+ *     periodic-shift code).
+ */
+#ifndef NEP_GB300_H
+#define NEP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEP_MAX_ATOMS 134217727LL   /* 2^27 - 1 */
+#define NEP_N_KERNEL_CLASSES 8
+
+typedef enum {
+    NEP_OK = 0,
+    NEP_ERR_ARG = 1,              /* invalid argument (NULL handle, bad size, bad model shape) */
+    NEP_ERR_CUDA = 2,             /* CUDA runtime error; message via nep_last_error */
+    NEP_ERR_NEIGH_OVERFLOW = 3,   /* an atom had more neighbours within rc_R + skin than max_neighbors */
+    NEP_ERR_BOX_TOO_SMALL = 4,    /* some box edge < 2 * (rc_R + skin) */
+    NEP_ERR_NAN = 5,              /* non-finite position or force detected */
+    NEP_ERR_TIMEOUT = 6,          /* a bounded host wait on the stream expired */
+    NEP_ERR_STATE = 7,            /* call out of order (e.g. nep_compute before nep_set_state) */
+    NEP_ERR_UNSUPPORTED = 8,      /* model shape without a compiled kernel instance */
+    NEP_ERR_OOM = 9               /* device allocation failed */
+} nep_status;
+
+enum { NEP_FP32 = 0 };
+
+/* Model and run parameters.  Host memory; copied by nep_create, the caller keeps ownership.
+ * Descriptor order (n_des = (n_max_R+1) + (n_max_A+1)*l_max_3b + (n_max_A+1) if l_max_4b == 2):
+ *   [ q_n, n = 0..n_max_R | q_nl, n-major, l = 1..l_max_3b | q4_n, n = 0..n_max_A ].
+ * Radial functions g_n(r) = sum_k c[n][k] f_k(r), f_k = (T_k(x) + 1)/2 * f_c(r),
+ * x = 2 (r/rc - 1)^2 - 1, f_c(r) = (1 + cos(pi r/rc))/2 (Section III.B: Chebyshev basis of the
+ * first kind times a smooth cutoff).  Angular: q_nl = sum_{j,k} g_n(r_ij) g_n(r_ik) P_l(cos theta_jik)
+ * (the m-contraction of spherical-harmonic sums, Section III.B); 4-body q4_n = tr(T_n^3),
+ * T_n = sum_j g_n(r_ij)(u_ij u_ij^T - I/3) (the "four-body L_max = 2" of Section VI.A).
+ * Site energy U_i = sum_mu w1[mu] tanh(sum_nu W0[mu][nu] q_nu * q_scale[nu] - b0[mu]) - b1
+ * (Section III.B equation), plus half of each shifted-force Lennard-Jones pair energy. */
+typedef struct nep_params {
+    int n_max_R, n_max_A;     /* compiled instance: 4, 4 */
+    int basis_R, basis_A;     /* compiled instance: 8, 8 (number of Chebyshev basis functions) */
+    int l_max_3b, l_max_4b;   /* compiled instance: 4, 2 */
+    int n_neu;                /* compiled instance: 30 */
+    float rc_R, rc_A;         /* radial and angular cutoffs, rc_A <= rc_R */
+    const float *c_R;         /* [n_max_R+1][basis_R] */
+    const float *c_A;         /* [n_max_A+1][basis_A] */
+    const float *W0;          /* [n_neu][n_des] */
+    const float *b0;          /* [n_neu] */
+    const float *w1;          /* [n_neu] */
+    float b1;
+    const float *q_scale;     /* [n_des] */
+    float lj_eps, lj_sigma, lj_rc;   /* shifted-force LJ pair term; lj_eps = 0 disables it; lj_rc <= rc_R */
+    double mass_amu;
+    float skin;               /* neighbour-list skin (Angstrom); list radius rc_R + skin */
+    int precision;            /* NEP_FP32 */
+    int max_neighbors;        /* per-atom list capacity; 0 selects 128 */
+    int rebuild_every;        /* MD: rebuild at least every k steps (0: only when an atom moved > skin/2) */
+} nep_params;
+
+typedef struct nep_handle nep_handle;
+
+/* Create a handle.  cuda_stream: a cudaStream_t to enqueue on, or NULL for a library-owned stream.
+ * Validates the model shape (NEP_ERR_UNSUPPORTED if no kernel instance matches). */
+nep_status nep_create(const nep_params *params, void *cuda_stream, nep_handle **out);
+
+/* Release every device buffer and the handle.  NULL is accepted. */
+nep_status nep_destroy(nep_handle *h);
+
+/* Load a configuration.  x: [n][3] positions (need not be wrapped), v: [n][3] velocities in
+ * Angstrom/fs or NULL for zero, box: host [3] edge lengths.  (Re)allocates device buffers for n atoms
+ * and invalidates the neighbour list and forces.  n = 0 is accepted (every later call is a no-op). */
+nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double *v, const double *box);
+
+/* Build the cell list and the neighbour list (cutoff rc_R + skin) for the current positions:
+ * atoms are sorted by cell, then each atom's list holds every j with |r_ij| < rc_R + skin (minimum
+ * image), ordered by increasing distance; its prefix with |r_ij| < rc_A + skin is the angular list. */
+nep_status nep_build_neighbors(nep_handle *h);
+
+/* Energy, forces and virial of the current positions (builds the neighbour list first if needed).
+ * E: host scalar, total potential energy; F: [n][3] (host or device, float64, original order);
+ * virial: host [9], W[a][b] = -sum_i sum_j r_ij[a] dU_i/dr_ij[b].  Any of the three may be NULL. */
+nep_status nep_compute(nep_handle *h, double *E, double *F, double *virial);
+
+/* n_steps velocity-Verlet NVE steps of dt_fs each: half kick, drift, neighbour rebuild when an atom
+ * moved more than skin/2 since the last build (or every rebuild_every steps), forces, half kick.
+ * Positions/velocities are integrated in float64; forces are evaluated in float32 with float64
+ * energy and virial sums.  Returns after enqueueing; the status word is checked at the end. */
+nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps);
+
+/* Copy positions (wrapped into the box) and velocities out, [n][3] each, original order; either may
+ * be NULL. */
+nep_status nep_get_state(nep_handle *h, double *x, double *v);
+
+/* Thermodynamics of the last force evaluation: out = {potential energy, kinetic energy,
+ * temperature (3N-3 dof), pressure (eV/Angstrom^3), W_xx, W_yy, W_zz, rebuild count}. */
+nep_status nep_get_thermo(nep_handle *h, double out[8]);
+
+/* Neighbour lists in original atom ids: counts[n], n_ang[n] (angular prefix length) and
+ * list[n][cap] (row i holds the ids of i's neighbours in increasing-distance order). */
+nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int32_t *list, int cap);
+
+/* Unscaled descriptors of the last evaluation, [n][n_des] float32, original order. */
+nep_status nep_get_descriptors(nep_handle *h, float *q);
+
+/* Site energies (NEP plus half of each LJ pair) of the last evaluation, [n] float64, original order. */
+nep_status nep_get_site_energies(nep_handle *h, double *U);
+
+/* Per-kernel-class CUDA-event timing of later calls: enable = 1 turns it on (and resets the sums). */
+nep_status nep_set_timing(nep_handle *h, int enable);
+
+/* Accumulated milliseconds and launch counts per kernel class since timing was enabled:
+ * classes 0 drift, 1 cell sort, 2 neighbour list, 3 descriptors+network, 4 forces, 5 kick,
+ * 6 reductions, 7 un-permute/other. */
+nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_t launches[NEP_N_KERNEL_CLASSES]);
+
+/* Counters since nep_set_state: out = {radial pairs evaluated (r < rc_R), angular pairs evaluated
+ * (r < rc_A), force evaluations, neighbour rebuilds, MD steps, kernel launches}. */
+nep_status nep_get_counters(nep_handle *h, int64_t out[6]);
+
+/* Last error message of the handle (never NULL). */
+const char *nep_last_error(nep_handle *h);
+
+/* Name of a status code (never NULL). */
+const char *nep_status_string(nep_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEP_GB300_H */

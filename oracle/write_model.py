@@ -1,9 +1,11 @@
 """Write the synthetic Cu NEP model file used by every test and benchmark.
 
 The weights come from the seeded generator (nep_inputs.random_nep_weights).  The descriptor scale
-q_scale[nu] = 1 / RMS_i(q_nu^i) is computed by the FP64 oracle on the seeded 4x4x4 fcc Cu cell
-(256 atoms, 0.05 Angstrom Gaussian displacements), the only value in the file that needs descriptor
-arithmetic; NEP implementations use a training-set scaler of this kind and the paper does not give one.
+q_scale[nu] = 1 / (max_i q_nu^i - min_i q_nu^i) is a range scaler over a small reference set -- three
+seeded 4x4x4 fcc Cu cells (768 atoms) with 0.05 Angstrom Gaussian displacements, the distribution of
+the 256-atom parity workload -- computed by the FP64 oracle.  It is the only value in the file
+that needs descriptor arithmetic; the paper gives no scaler, and NEP implementations use a
+training-set range scaler of this kind.
 
 Usage:  python -m oracle.write_model [output.json]
 """
@@ -24,6 +26,7 @@ import oracle  # noqa: E402
 
 DEFAULT_OUT = os.path.join(_ROOT, "paper_2604_24816_gb300", "params", "cu_nep4_synth.json")
 WEIGHT_SEED = 2604
+SCALER_SIGMAS = (0.05, 0.05, 0.05)
 
 
 def make_model() -> dict:
@@ -35,11 +38,14 @@ def make_model() -> dict:
         params[k] = np.asarray(w[k]).tolist()
     params["b1"] = float(w["b1"])
     params["q_scale"] = [1.0] * ni.N_DES
-    wl = ni.workload("cu_4x4x4")
-    q = oracle.descriptors(oracle.Model(params), wl.pos, wl.box)
-    rms = np.sqrt(np.mean(q * q, axis=0))
-    params["q_scale"] = (1.0 / rms).tolist()
-    params["q_scale_source"] = "1/RMS of FP64 oracle descriptors on the seeded 4x4x4 fcc Cu cell (256 atoms)"
+    qs = []
+    for k, sigma in enumerate(SCALER_SIGMAS):
+        wl = ni.fcc_cu_workload(4, 300.0, sigma, seed=100 + k)
+        qs.append(oracle.descriptors(oracle.Model(params), wl.pos, wl.box))
+    q = np.concatenate(qs, axis=0)
+    params["q_scale"] = (1.0 / (q.max(axis=0) - q.min(axis=0))).tolist()
+    params["q_scale_source"] = ("1/(max-min) of FP64 oracle descriptors over seeded 4x4x4 fcc Cu cells with "
+                                "Gaussian displacements " + ", ".join(f"{s:g}" for s in SCALER_SIGMAS) + " A")
     return params
 
 

@@ -1,0 +1,256 @@
+// nep_common.cuh -- device-side building blocks shared by the NEP kernels (sm_103a).
+//
+// Layout conventions (all per-atom arrays in cell-sorted order):
+//   pos[i]   float4: position relative to the origin of the atom's cell at the last rebuild (x, y, z)
+//            and the packed cell coordinates (w, as int bits: cx | cy << 10 | cz << 20).
+//   nbr      int32 [cap][N] (neighbour-major, so a thread per atom reads coalesced rows); entry =
+//            j | shift << 27, shift = (dx+1) + 3 (dy+1) + 9 (dz+1) the cell offset of j's image.
+//   G        float [N][128]: per-atom adjoint dU_i/ds_nlm (120 values, index n*24 + lm) followed by
+//            dU_i/dq_n of the radial descriptors (5 values) and padding.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nep {
+
+constexpr int J_BITS = 27;
+constexpr uint32_t J_MASK = (1u << J_BITS) - 1u;
+constexpr int GSTRIDE = 128;     // floats per atom row of G
+constexpr int N_LM = 24;         // (l, m) components for l = 1..4
+
+// Status bits of the device status word.
+enum : int {
+  ST_OVERFLOW = 1,   // neighbour list capacity exceeded
+  ST_NAN = 2,        // non-finite value seen
+};
+
+// Device-side control block (one per handle).
+struct Control {
+  int status;           // OR of ST_* bits
+  int moved;            // some atom moved more than skin/2 since the last rebuild
+  int do_rebuild;       // decision of the current step
+  int force_rebuild;    // host request
+  int steps_since;      // MD steps since the last rebuild
+  int rebuild_every;    // 0 = displacement-triggered only
+  long long rebuilds;   // neighbour builds done
+  long long steps;      // MD steps done
+};
+
+// Compile-time model shape: NR radial functions, NA angular, K basis functions, lmax = 4 3-body,
+// optional 4-body (l = 2), NNEU hidden neurons.
+template <int NR_, int NA_, int KR_, int KA_, bool FOURBODY_, int NNEU_>
+struct Shape {
+  static constexpr int NR = NR_, NA = NA_, KR = KR_, KA = KA_, NNEU = NNEU_;
+  static constexpr bool FOURBODY = FOURBODY_;
+  static constexpr int LMAX = 4;
+  static constexpr int NDES = NR + NA * LMAX + (FOURBODY ? NA : 0);
+  static_assert(NA * N_LM + NR <= GSTRIDE, "adjoint row too small");
+};
+
+using CuShape = Shape<5, 5, 8, 8, true, 30>;   // n_max 4/4, basis 8/8, l_max 4, 4-body, 30 neurons
+
+// Model parameters, passed by value as a __grid_constant__ kernel argument so that every uniform
+// access compiles to a constant-bank operand.
+template <class S>
+struct Model {
+  float cR[S::NR][S::KR];
+  float cA[S::NA][S::KA];
+  float W0[S::NNEU][S::NDES];
+  float b0[S::NNEU];
+  float w1[S::NNEU];
+  float qs[S::NDES];
+  float b1;
+  float rcR, rcA, rcR2, rcA2, inv_rcR, inv_rcA;
+  float lj_on, lj_c12, lj_c6, lj_rc2, lj_e_rc, lj_de_rc, lj_rc;  // shifted-force LJ
+  float rmax2;   // max(rcR, lj_rc)^2
+};
+
+// Cell geometry of the current neighbour list.
+struct Geom {
+  float lx, ly, lz;      // cell edge lengths (float)
+  int ncx, ncy, ncz;
+};
+
+__device__ __forceinline__ int cell_x(float w) { return __float_as_int(w) & 1023; }
+__device__ __forceinline__ int cell_y(float w) { return (__float_as_int(w) >> 10) & 1023; }
+__device__ __forceinline__ int cell_z(float w) { return (__float_as_int(w) >> 20) & 1023; }
+
+// Offsets of the 27 neighbouring cell images: shift s = (dx+1) + 3(dy+1) + 9(dz+1).
+__device__ __forceinline__ void fill_shift_table(float4 *tab, const Geom &g) {
+  for (int s = threadIdx.x; s < 27; s += blockDim.x) {
+    int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+    tab[s] = make_float4(dx * g.lx, dy * g.ly, dz * g.lz, 0.f);
+  }
+}
+
+// Chebyshev basis f_k(r) = (T_k(x) + 1)/2 * fc(r), x = 2 (r/rc - 1)^2 - 1, fc = (1 + cos(pi r/rc))/2.
+template <int K>
+__device__ __forceinline__ void cheb_basis(float r, float inv_rc, float (&f)[K]) {
+  float s, c;
+  const float t = r * inv_rc;
+  sincospif(t, &s, &c);
+  const float fc = 0.5f + 0.5f * c;
+  const float u = t - 1.f;
+  const float x = 2.f * u * u - 1.f;
+  float tm1 = 1.f, t0 = x;
+  f[0] = fc;                       // (T_0 + 1)/2 = 1
+  if (K > 1) f[1] = 0.5f * (x + 1.f) * fc;
+#pragma unroll
+  for (int k = 2; k < K; ++k) {
+    float tk = 2.f * x * t0 - tm1;
+    f[k] = 0.5f * (tk + 1.f) * fc;
+    tm1 = t0; t0 = tk;
+  }
+}
+
+// Basis and radial derivative.
+template <int K>
+__device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K], float (&df)[K]) {
+  float s, c;
+  const float t = r * inv_rc;
+  sincospif(t, &s, &c);
+  const float fc = 0.5f + 0.5f * c;
+  const float dfc = -0.5f * 3.14159265358979f * inv_rc * s;
+  const float u = t - 1.f;
+  const float x = 2.f * u * u - 1.f;
+  const float dx = 4.f * u * inv_rc;
+  float tm1 = 1.f, t0 = x, dtm1 = 0.f, dt0 = 1.f;
+  f[0] = fc; df[0] = dfc;
+  if (K > 1) {
+    f[1] = 0.5f * (x + 1.f) * fc;
+    df[1] = 0.5f * dx * fc + 0.5f * (x + 1.f) * dfc;
+  }
+#pragma unroll
+  for (int k = 2; k < K; ++k) {
+    float tk = 2.f * x * t0 - tm1;
+    float dtk = 2.f * t0 + 2.f * x * dt0 - dtm1;
+    f[k] = 0.5f * (tk + 1.f) * fc;
+    df[k] = 0.5f * dtk * dx * fc + 0.5f * (tk + 1.f) * dfc;
+    tm1 = t0; t0 = tk; dtm1 = dt0; dt0 = dtk;
+  }
+}
+
+// Normalised real harmonics Yh_lm(u) = sqrt(4 pi / (2l+1)) Y_lm(u), l = 1..4 (24 values, m = -l..l),
+// so that sum_m Yh_lm(u) Yh_lm(v) = P_l(u . v).  Written as solid-harmonic polynomials of a unit vector.
+__device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[N_LM]) {
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
+  const float s10 = 3.1622776601683795f, s15 = 3.872983346207417f, s35 = 5.916079783099616f;
+  const float s70 = 8.366600265340756f;
+  // l = 1
+  Y[0] = y; Y[1] = z; Y[2] = x;
+  // l = 2
+  Y[3] = s3 * x * y;
+  Y[4] = s3 * y * z;
+  Y[5] = z2 - 0.5f * (x2 + y2);
+  Y[6] = s3 * x * z;
+  Y[7] = 0.5f * s3 * (x2 - y2);
+  // l = 3
+  const float a3 = 4.f * z2 - x2 - y2;
+  Y[8] = 0.25f * s10 * y * (3.f * x2 - y2);
+  Y[9] = s15 * x * y * z;
+  Y[10] = 0.25f * s6 * y * a3;
+  Y[11] = z * (z2 - 1.5f * (x2 + y2));
+  Y[12] = 0.25f * s6 * x * a3;
+  Y[13] = 0.5f * s15 * z * (x2 - y2);
+  Y[14] = 0.25f * s10 * x * (x2 - 3.f * y2);
+  // l = 4
+  const float rr = x2 + y2 + z2;
+  const float b4 = 7.f * z2 - rr, c4 = 7.f * z2 - 3.f * rr;
+  Y[15] = 0.5f * s35 * x * y * (x2 - y2);
+  Y[16] = 0.25f * s70 * y * z * (3.f * x2 - y2);
+  Y[17] = 0.5f * s5 * x * y * b4;
+  Y[18] = 0.25f * s10 * y * z * c4;
+  Y[19] = 0.125f * (35.f * z2 * z2 - 30.f * z2 * rr + 3.f * rr * rr);
+  Y[20] = 0.25f * s10 * x * z * c4;
+  Y[21] = 0.25f * s5 * (x2 - y2) * b4;
+  Y[22] = 0.25f * s70 * x * z * (x2 - 3.f * y2);
+  Y[23] = 0.125f * s35 * (x2 * x2 - 6.f * x2 * y2 + y2 * y2);
+}
+
+// Gradient of the solid-harmonic polynomial of component lm, evaluated at (x, y, z), accumulated
+// with weight b into (gx, gy, gz).  lm is a compile-time constant after unrolling.
+__device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, float z, float b, float &gx,
+                                                  float &gy, float &gz) {
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
+  const float s10 = 3.1622776601683795f, s15 = 3.872983346207417f, s35 = 5.916079783099616f;
+  const float s70 = 8.366600265340756f;
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  switch (lm) {
+    case 0: ay = 1.f; break;
+    case 1: az = 1.f; break;
+    case 2: ax = 1.f; break;
+    case 3: ax = s3 * y; ay = s3 * x; break;
+    case 4: ay = s3 * z; az = s3 * y; break;
+    case 5: ax = -x; ay = -y; az = 2.f * z; break;
+    case 6: ax = s3 * z; az = s3 * x; break;
+    case 7: ax = s3 * x; ay = -s3 * y; break;
+    case 8: ax = 1.5f * s10 * x * y; ay = 0.75f * s10 * (x2 - y2); break;
+    case 9: ax = s15 * y * z; ay = s15 * x * z; az = s15 * x * y; break;
+    case 10: ax = -0.5f * s6 * x * y; ay = -0.25f * s6 * (x2 + 3.f * y2 - 4.f * z2); az = 2.f * s6 * y * z; break;
+    case 11: ax = -3.f * x * z; ay = -3.f * y * z; az = -1.5f * (x2 + y2 - 2.f * z2); break;
+    case 12: ax = -0.25f * s6 * (3.f * x2 + y2 - 4.f * z2); ay = -0.5f * s6 * x * y; az = 2.f * s6 * x * z; break;
+    case 13: ax = s15 * x * z; ay = -s15 * y * z; az = 0.5f * s15 * (x2 - y2); break;
+    case 14: ax = 0.75f * s10 * (x2 - y2); ay = -1.5f * s10 * x * y; break;
+    case 15: ax = 0.5f * s35 * y * (3.f * x2 - y2); ay = 0.5f * s35 * x * (x2 - 3.f * y2); break;
+    case 16: ax = 1.5f * s70 * x * y * z; ay = 0.75f * s70 * z * (x2 - y2); az = 0.25f * s70 * y * (3.f * x2 - y2); break;
+    case 17: ax = -0.5f * s5 * y * (3.f * x2 + y2 - 6.f * z2); ay = -0.5f * s5 * x * (x2 + 3.f * y2 - 6.f * z2);
+             az = 6.f * s5 * x * y * z; break;
+    case 18: ax = -1.5f * s10 * x * y * z; ay = -0.25f * s10 * z * (3.f * x2 + 9.f * y2 - 4.f * z2);
+             az = -0.75f * s10 * y * (x2 + y2 - 4.f * z2); break;
+    case 19: ax = 1.5f * x * (x2 + y2 - 4.f * z2); ay = 1.5f * y * (x2 + y2 - 4.f * z2);
+             az = -2.f * z * (3.f * x2 + 3.f * y2 - 2.f * z2); break;
+    case 20: ax = -0.25f * s10 * z * (9.f * x2 + 3.f * y2 - 4.f * z2); ay = -1.5f * s10 * x * y * z;
+             az = -0.75f * s10 * x * (x2 + y2 - 4.f * z2); break;
+    case 21: ax = -s5 * x * (x2 - 3.f * z2); ay = s5 * y * (y2 - 3.f * z2); az = 3.f * s5 * z * (x2 - y2); break;
+    case 22: ax = 0.75f * s70 * z * (x2 - y2); ay = -1.5f * s70 * x * y * z; az = 0.25f * s70 * x * (x2 - 3.f * y2); break;
+    case 23: ax = 0.5f * s35 * x * (x2 - 3.f * y2); ay = -0.5f * s35 * y * (3.f * x2 - y2); break;
+    default: break;
+  }
+  gx = fmaf(b, ax, gx);
+  gy = fmaf(b, ay, gy);
+  gz = fmaf(b, az, gz);
+}
+
+__host__ __device__ constexpr int lm_l(int lm) { return lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4)); }
+
+// Shifted-force LJ pair energy E(r) and dE/dr, from r^2 (r also passed).
+template <class S>
+__device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, float &e, float &de) {
+  const float ir2 = 1.f / r2;
+  const float ir6 = ir2 * ir2 * ir2;
+  const float a12 = P.lj_c12 * ir6 * ir6, a6 = P.lj_c6 * ir6;
+  e = a12 - a6 - P.lj_e_rc - (r - P.lj_rc) * P.lj_de_rc;
+  de = (-12.f * a12 + 6.f * a6) / r - P.lj_de_rc;
+}
+
+// Block-wide sum of NV doubles into out[blockIdx.x * NV + v] in a fixed order (deterministic).
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out) {
+  __shared__ double red[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? red[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) out[(size_t)blockIdx.x * NV + k] = t;
+    }
+  }
+}
+
+}  // namespace nep

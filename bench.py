@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""NEP molecular-dynamics throughput on GB300: atom-steps/s of plain FP32 NEP-MD.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One step = one velocity-Verlet MD step of the whole hot path on the 1,048,576-atom fcc Cu workload
+(64x64x64 cells, 300 K, 1 fs): half kick + drift, neighbour-rebuild check (a rebuild runs every 10
+steps -- the refresh interval of the paper's MD protocol -- and whenever an atom moved more than
+skin/2), cell sort + neighbour list when rebuilding, descriptors + network, forces + virial, half
+kick, energy/virial/kinetic sums.  Inputs are resident in HBM when the timed region starts.
+
+N > 1 (torchrun): every rank runs an independent replica on its own GPU (no collective on the data
+path); value = atom-steps of all ranks / max-over-ranks time ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle (the method as written, plain C) on the host cores for
+the same metric, each step on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import nep_inputs as ni  # noqa: E402
+
+METRIC = "NEP MD atom-steps/s on 1 GB300: plain FP32 vs mixed/student at stated force RMSE"
+UNIT = "atom-steps/s"
+N_SMS = 152
+FP32_LANES_PER_SM = 128
+
+# Algorithmic FP32 FLOPs of the method per unit (static count of the arithmetic each unit needs,
+# FMA = 2, add/mul/compare-free = 1, each transcendental = 1), for the compiled shape
+# (5 radial + 5 angular channels, 8 basis functions, l = 1..4, 4-body, 30 neurons).
+FLOPS = {
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=128, lj_pair=12, angular_pair=464, atom=4655),
+    "force": dict(list_entry=11, active_pair=2 + 27, radial_pair=220, lj_pair=13, angular_pair=1465, atom=0),
+}
+# Algorithmic bytes per atom per force evaluation (HBM, float32 path): positions 16, list
+# entries 4 each (read by both kernels), adjoint row 512 written + read, force 12, site energy 4.
+BYTES = dict(per_atom=16 * 2 + 512 * 2 + 12 + 4, per_list_entry=4 * 2)
+
+
+def kernel_flops(kind: str, c: dict, n_atoms_evals: int) -> float:
+    f = FLOPS[kind]
+    return (f["list_entry"] * c["list_entries"] + f["active_pair"] * c["active_pairs"] +
+            f["radial_pair"] * c["radial_pairs"] + f["lj_pair"] * c["radial_pairs"] +
+            f["angular_pair"] * c["angular_pairs"] + f["atom"] * n_atoms_evals)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("nep_force.cu", "nep_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_24816_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was captured on the
+    current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == cur:
+            return dict(bytes=float(parts[2]), atoms=int(parts[3]))
+    return None
+
+
+# ---------------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 50 ms in a background thread."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.window = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = [s for t, s in self.samples if t0 <= t <= t1]
+        if len(rows) < 3:        # very short timed region: widen to the nearest samples around it
+            rows = [s for t, s in self.samples if t0 - 0.5 <= t <= t1 + 0.5]
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            p = [x.strip() for x in r.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1])); smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------------
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    import torch
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    return rank, ws, local
+
+
+def dist_barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x: float, ws: int, device=None) -> float:
+    """Max of a scalar over ranks (identity at world size 1)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(x: float, ws: int, device=None) -> float:
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def cpu_baseline(seconds_hint: float = 15.0) -> dict:
+    """The FP64 oracle, as it stands, timed on the host cores on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    model = oracle.load_model(os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_nep4_synth.json"))
+    wl = ni.workload("cu_16x16x16")
+    steps = 2
+    t0 = time.perf_counter()
+    oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, 1.0, steps)
+    dt = time.perf_counter() - t0
+    return {"value": wl.n * steps / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"fcc Cu 16x16x16 cells ({wl.n} atoms), {steps} velocity-Verlet steps "
+                      f"({steps + 1} force evaluations, fresh neighbour search each), FP64, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------------------------------
+def run_reference(args, rank: int, ws: int):
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    model = oracle.load_model(os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_nep4_synth.json"))
+    # size the per-step sample so that warmup + steps take about two minutes
+    probe = ni.fcc_cu_workload(6, 300.0, 0.05, seed=2)
+    t0 = time.perf_counter()
+    oracle.md_nve(model, probe.pos, probe.vel, probe.box, ni.M_CU, 1.0, 1)
+    t_atom_step = (time.perf_counter() - t0) / (2 * probe.n)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    cells = int(max(4, min(16, round((budget / t_atom_step / 4) ** (1 / 3)))))
+    wl = ni.fcc_cu_workload(cells, 300.0, 0.05, seed=2)
+    x, v = wl.pos.copy(), wl.vel.copy()
+    for _ in range(args.warmup):
+        x, v, _ = oracle.md_nve(model, x, v, wl.box, ni.M_CU, 1.0, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, v, _ = oracle.md_nve(model, x, v, wl.box, ni.M_CU, 1.0, 1)
+    dt = time.perf_counter() - t0
+    value = wl.n * args.steps / dt
+    sample = (f"fcc Cu {cells}x{cells}x{cells} cells ({wl.n} atoms) per step, FP64 oracle velocity-Verlet "
+              f"(each step: 2 force evaluations with a fresh neighbour search, as the oracle stands)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample, "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, rank: int, ws: int, local: int):
+    import torch
+    from paper_2604_24816_gb300 import NEP, load_model, build
+
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    model = load_model()
+    wl = ni.workload(args.workload) if rank == 0 else ni.fcc_cu_workload(
+        64, 300.0, 0.05, seed=2 + rank, steps=200, name=args.workload)   # independent replica per rank
+    stream = torch.cuda.Stream(device=dev)
+    nep = NEP(model, stream=stream.cuda_stream, rebuild_every=args.rebuild_every)
+    nep.set_state(wl.pos, wl.vel, wl.box)
+    nep.compute(forces=False)
+
+    # warm-up (untimed), then per-kernel event timing switched on for the timed region
+    nep.set_timing(True)
+    nep.step(wl.dt_fs, args.warmup)
+    torch.cuda.synchronize(dev)
+    nep.set_timing(True)
+    c0 = nep.counters()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    dist_barrier(ws)
+    torch.cuda.synchronize(dev)
+    t_host0 = time.perf_counter()
+    start.record(stream)
+    nep.step(wl.dt_fs, args.steps)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    t_host1 = time.perf_counter()
+    dist_barrier(ws)
+    clocks.stop()
+    ms = start.elapsed_time(end)
+    ms_max = dist_max(ms, ws, dev)
+    atoms_total = dist_sum(wl.n, ws, dev)
+    value = atoms_total * args.steps / (ms_max * 1e-3)
+
+    c1 = nep.counters()
+    tim = nep.timing()
+    th = nep.thermo()
+    dc = {k: c1[k] - c0[k] for k in ("radial_pairs", "angular_pairs", "list_entries", "active_pairs",
+                                     "evaluations", "rebuilds", "steps", "launches")}
+    evals = dc["evaluations"]
+    f_desc = kernel_flops("descriptor", dc, evals * wl.n)
+    f_force = kernel_flops("force", dc, evals * wl.n)
+    peaks = load_peaks()
+    clk = clocks.summary(t_host0, t_host1)
+    peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    kern = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in tim.items()}
+    dominant = max(("descriptor", "force"), key=lambda k: tim[k][0])
+    dom_flops = f_force if dominant == "force" else f_desc
+    dom_ms = tim[dominant][0]
+    dom_launches = max(1, tim[dominant][1])
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    traffic = profiled_traffic(dominant)
+    roofline = {
+        "bound": "alu", "kernel": f"k_{dominant}", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
+        "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+        "traffic": (round(traffic["bytes"] * wl.n / traffic["atoms"]) if traffic else None),
+        "peak_source": f"FP32 FFMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
+                       f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peaks['source']} max SM clock)",
+        "flops_per_launch": round(dom_flops / dom_launches),
+        "ms_per_launch": round(dom_ms / dom_launches, 5),
+        "frac_at_measured_clock": (round(achieved / (N_SMS * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e-6), 4)
+                                   if clk.get("sm_mhz") else None),
+    }
+    both_ms = tim["descriptor"][0] + tim["force"][0]
+    both = (f_desc + f_force) / (both_ms * 1e-3) / 1e12 if both_ms > 0 else 0.0
+
+    # end-to-end through the public API with pinned host buffers: every step uploads (x, v), runs one
+    # MD step (which must rebuild and recompute forces for the uploaded state) and downloads (x, v, E)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(wl.pos).pin_memory()
+        vh = torch.from_numpy(wl.vel).pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        vo = torch.empty_like(vh).pin_memory()
+        nep.set_timing(False)
+        for _ in range(2):
+            nep.set_state(xh, vh, wl.box); nep.step(wl.dt_fs, 1); nep.get_state(xo, vo); nep.thermo()
+        dist_barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            nep.set_state(xh, vh, wl.box)
+            nep.step(wl.dt_fs, 1)
+            nep.get_state(xo, vo)
+            nep.thermo()
+        torch.cuda.synchronize(dev)
+        te = dist_max(time.perf_counter() - t0, ws, dev)
+        dist_barrier(ws)
+        e2e = {"value": atoms_total * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 48 * wl.n,
+               "d2h_bytes_per_step": 48 * wl.n + 8 * 16, "steps": args.e2e_steps,
+               "note": "per step: nep_set_state(x, v from pinned host) + md_verlet_step(1) (rebuild + 2 force "
+                       "evaluations for the uploaded state) + nep_get_state(x, v to pinned host) + thermo"}
+    nep.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "form": "plain FP32 NEP (float64 integration "
+                   "and sums)", "dt_fs": wl.dt_fs, "temperature_K": wl.temperature,
+                   "neighbor_rebuild": f"every {args.rebuild_every} steps + displacement check (skin/2)",
+                   "rebuilds_in_timed_region": dc["rebuilds"],
+                   "l2": "inputs larger than L2: per-step working set ~"
+                         f"{(wl.n * (BYTES['per_atom'] + 48 * 2) + dc['list_entries'] / max(1, evals) * BYTES['per_list_entry']) / 1e9:.2f} GB"
+                         " (neighbour list, adjoint rows, state) vs 129 MB L2",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "model": "cu_nep4_synth (seeded)"},
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": dc["launches"],
+        "kernels": kern,
+        "descriptor_plus_force_tflops": round(both, 3),
+        "pairs_per_atom": {"list": dc["list_entries"] / max(1, evals * wl.n),
+                           "radial": dc["radial_pairs"] / max(1, evals * wl.n),
+                           "angular": dc["angular_pairs"] / max(1, evals * wl.n)},
+        "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"]},
+        "e2e": e2e,
+        "source_hash": source_hash(),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="cu_64x64x64")
+    ap.add_argument("--rebuild-every", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, ws, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -96,8 +96,9 @@ nep_status nep_create(const nep_params *params, void *cuda_stream, nep_handle **
 nep_status nep_destroy(nep_handle *h);
 
 /* Load a configuration.  x: [n][3] positions (need not be wrapped), v: [n][3] velocities in
- * Angstrom/fs or NULL for zero, box: host [3] edge lengths.  (Re)allocates device buffers for n atoms
- * and invalidates the neighbour list and forces.  n = 0 is accepted (every later call is a no-op). */
+ * Angstrom/fs or NULL for zero, box: host [3] edge lengths.  Allocates device buffers for n atoms
+ * (kept when n and the box are unchanged since the last call) and invalidates the neighbour list and
+ * forces.  n = 0 is accepted (every later call is a no-op). */
 nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double *v, const double *box);
 
 /* Build the cell list and the neighbour list (cutoff rc_R + skin) for the current positions:
@@ -143,8 +144,9 @@ nep_status nep_set_timing(nep_handle *h, int enable);
 nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_t launches[NEP_N_KERNEL_CLASSES]);
 
 /* Counters since nep_set_state: out = {radial pairs evaluated (r < rc_R), angular pairs evaluated
- * (r < rc_A), force evaluations, neighbour rebuilds, MD steps, kernel launches}. */
-nep_status nep_get_counters(nep_handle *h, int64_t out[6]);
+ * (r < rc_A), force evaluations, neighbour rebuilds, MD steps, kernel launches enqueued by the library,
+ * neighbour-list entries visited, pairs inside the largest cutoff}.  Pair counts sum over evaluations. */
+nep_status nep_get_counters(nep_handle *h, int64_t out[8]);
 
 /* Last error message of the handle (never NULL). */
 const char *nep_last_error(nep_handle *h);

@@ -1,0 +1,767 @@
+// nep_api.cu -- the C ABI declared in include/nep_gb300.h: handle, device buffers, step sequencing.
+//
+// One MD step enqueues: kick+drift -> step control -> rebuild chain (kernels return at once unless
+// the control kernel asked for a rebuild) -> descriptors+network -> forces -> kick -> reductions.
+// Because the rebuild decision is taken on the device, a step has a fixed launch sequence: it is
+// captured once as a CUDA graph and replayed, with no host synchronisation inside an md_verlet_step
+// call.  With timing enabled the same sequence is launched eagerly with CUDA events around each
+// kernel class.  The only host waits are bounded polls of a stream event (NEP_ERR_TIMEOUT).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/nep_gb300.h"
+#include "nep_common.cuh"
+
+namespace nep {
+// nep_force.cu
+template <class S>
+cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
+                              float *, float *, float *, double *, int *, cudaStream_t);
+template <class S>
+cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
+                         const float *, float *, double *, int *, cudaStream_t);
+int descriptor_blocks(int n);
+int force_blocks(int n);
+// nep_neighbor.cu
+cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
+cudaError_t launch_neighbors(const RebuildArgs &, cudaStream_t);
+int scan_tiles(int ncell);
+// nep_md.cu
+int md_blocks(int n);
+cudaError_t launch_kick_drift(int, double *, double *, double *, double *, double *, double *, const float *, float4 *,
+                              const float4 *, double, double, const double *, float, Control *, cudaStream_t);
+cudaError_t launch_control(Control *, bool, cudaStream_t);
+cudaError_t launch_kick(int, double *, double *, double *, const float *, double, double, double *, cudaStream_t);
+cudaError_t launch_kinetic(int, const double *, const double *, const double *, double, double *, cudaStream_t);
+cudaError_t launch_finalize(const double *, int, const double *, int, const double *, int, double *, long long *,
+                            cudaStream_t);
+cudaError_t launch_load_state(int, const double *, const double *, double *, double *, double *, double *, double *,
+                              double *, int *, int *, cudaStream_t);
+cudaError_t launch_store_vec(int, const int *, const double *, const double *, const double *, const double *, int,
+                             double *, cudaStream_t);
+cudaError_t launch_store_force(int, const int *, const float *, double *, cudaStream_t);
+cudaError_t launch_store_scalar(int, const int *, const float *, double *, cudaStream_t);
+cudaError_t launch_store_rows(int, int, const int *, const float *, float *, cudaStream_t);
+cudaError_t launch_store_neighbors(int, int, int, const int *, const int32_t *, const int32_t *, const int32_t *,
+                                   int32_t *, int32_t *, int32_t *, cudaStream_t);
+}  // namespace nep
+
+using namespace nep;
+using S = CuShape;
+
+namespace {
+
+constexpr double KB_EV = 8.617333262e-5;
+constexpr double ACC_CONV = 9.64853321233100e-3;
+constexpr double WAIT_LIMIT_S = 900.0;
+
+enum KClass { KC_DRIFT = 0, KC_CELL = 1, KC_NEIGH = 2, KC_DESC = 3, KC_FORCE = 4, KC_KICK = 5, KC_RED = 6, KC_OTHER = 7 };
+
+struct Timer {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct nep_handle {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Model<S> model{};
+  double mass = 1.0;
+  float skin = 1.0f, rcR = 0.f, rcA = 0.f;
+  int cap = 128;
+  int rebuild_every = 0;
+  std::string err;
+
+  // system
+  int n = 0;
+  double L[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+  int nc[3] = {0, 0, 0};
+  int ncell = 0;
+  bool have_state = false, have_nlist = false, have_forces = false;
+
+  // device buffers
+  double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
+  double *xb = nullptr, *yb = nullptr, *zb = nullptr, *vxb = nullptr, *vyb = nullptr, *vzb = nullptr;
+  int *id = nullptr, *idb = nullptr, *cell_of = nullptr, *perm = nullptr;
+  float4 *pos = nullptr, *pos_ref = nullptr;
+  float *F = nullptr, *usite = nullptr, *G = nullptr, *qbuf = nullptr;
+  int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr;
+  int *count = nullptr, *cursor = nullptr, *start = nullptr, *tile_sums = nullptr;
+  double *part_d = nullptr, *part_f = nullptr, *part_k = nullptr, *sums = nullptr;
+  long long *counters = nullptr;   // {radial pairs, angular pairs, evaluations}
+  Control *ctrl = nullptr;
+  double *io = nullptr;            // staging 2 x [n][3] float64 for host transfers
+  int32_t *io_i = nullptr;         // staging for neighbour output
+  size_t io_i_elems = 0;
+  int nb_d = 0, nb_f = 0, nb_k = 0;
+
+  // host mirrors (pinned)
+  double *h_sums = nullptr;
+  Control *h_ctrl = nullptr;
+  long long *h_counters = nullptr;
+  cudaEvent_t done = nullptr;
+
+  // graph of one MD step
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+
+  // timing
+  bool timing = false;
+  std::vector<Timer> timers;
+  size_t timers_used = 0;
+  double ms[NEP_N_KERNEL_CLASSES] = {0};
+  long long launches[NEP_N_KERNEL_CLASSES] = {0};
+  long long launch_total = 0;
+};
+
+namespace {
+
+nep_status fail(nep_handle *h, nep_status s, const std::string &msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+nep_status cuda_fail(nep_handle *h, cudaError_t e, const char *where) {
+  return fail(h, NEP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define NEP_CUDA(h, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);  \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+void free_system(nep_handle *h) {
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  dfree(h->x); dfree(h->y); dfree(h->z); dfree(h->vx); dfree(h->vy); dfree(h->vz);
+  dfree(h->xb); dfree(h->yb); dfree(h->zb); dfree(h->vxb); dfree(h->vyb); dfree(h->vzb);
+  dfree(h->id); dfree(h->idb); dfree(h->cell_of); dfree(h->perm);
+  dfree(h->pos); dfree(h->pos_ref); dfree(h->F); dfree(h->usite); dfree(h->G); dfree(h->qbuf);
+  dfree(h->nbr); dfree(h->nnum); dfree(h->nang);
+  dfree(h->count); dfree(h->cursor); dfree(h->start); dfree(h->tile_sums);
+  dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
+  h->io_i_elems = 0;
+  h->n = 0;
+  h->have_state = h->have_nlist = h->have_forces = false;
+}
+
+template <class T>
+cudaError_t dalloc(T *&p, size_t elems) {
+  return cudaMalloc((void **)&p, std::max<size_t>(elems, 1) * sizeof(T));
+}
+
+// Bounded wait for all work enqueued so far on the handle's stream.
+nep_status wait_stream(nep_handle *h) {
+  NEP_CUDA(h, cudaEventRecord(h->done, h->stream));
+  auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(h->done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(h, e, "cudaEventQuery");
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > WAIT_LIMIT_S) return fail(h, NEP_ERR_TIMEOUT, "stream wait exceeded its limit");
+  }
+  return NEP_OK;
+}
+
+// Timer helpers: record an event pair around a kernel class when timing is on.
+struct Scope {
+  nep_handle *h;
+  int cls, nlaunch;
+  Timer *t = nullptr;
+  Scope(nep_handle *h_, int cls_, int nlaunch_) : h(h_), cls(cls_), nlaunch(nlaunch_) {
+    h->launch_total += nlaunch;
+    if (!h->timing) return;
+    if (h->timers_used == h->timers.size()) {
+      Timer nt{cls, nullptr, nullptr};
+      cudaEventCreate(&nt.a);
+      cudaEventCreate(&nt.b);
+      h->timers.push_back(nt);
+    }
+    t = &h->timers[h->timers_used++];
+    t->cls = cls;
+    cudaEventRecord(t->a, h->stream);
+  }
+  ~Scope() {
+    if (t) cudaEventRecord(t->b, h->stream);
+    if (h->timing) h->launches[cls] += nlaunch;
+  }
+};
+
+void collect_timers(nep_handle *h) {
+  for (size_t k = 0; k < h->timers_used; ++k) {
+    float m = 0.f;
+    if (cudaEventElapsedTime(&m, h->timers[k].a, h->timers[k].b) == cudaSuccess) h->ms[h->timers[k].cls] += m;
+    else cudaGetLastError();
+  }
+  h->timers_used = 0;
+}
+
+RebuildArgs rebuild_args(nep_handle *h) {
+  RebuildArgs a;
+  a.n = h->n; a.ncell = h->ncell;
+  for (int d = 0; d < 3; ++d) { a.L[d] = h->L[d]; a.l[d] = h->l[d]; a.nc[d] = h->nc[d]; }
+  a.x = h->x; a.y = h->y; a.z = h->z; a.vx = h->vx; a.vy = h->vy; a.vz = h->vz;
+  a.xb = h->xb; a.yb = h->yb; a.zb = h->zb; a.vxb = h->vxb; a.vyb = h->vyb; a.vzb = h->vzb;
+  a.id = h->id; a.idb = h->idb; a.cell_of = h->cell_of; a.count = h->count; a.cursor = h->cursor;
+  a.start = h->start; a.tile_sums = h->tile_sums; a.perm = h->perm;
+  a.pos = h->pos; a.pos_ref = h->pos_ref; a.nbr = h->nbr; a.nnum = h->nnum; a.nang = h->nang;
+  a.cap = h->cap;
+  const float rl = h->rcR + h->skin, ra = h->rcA + h->skin;
+  a.rl2 = rl * rl; a.ra2 = ra * ra;
+  a.ctrl = h->ctrl;
+  return a;
+}
+
+Geom geom_of(nep_handle *h) {
+  Geom g;
+  g.lx = (float)h->l[0]; g.ly = (float)h->l[1]; g.lz = (float)h->l[2];
+  g.ncx = h->nc[0]; g.ncy = h->nc[1]; g.ncz = h->nc[2];
+  return g;
+}
+
+// Rebuild chain (cell sort + neighbour list); kernels act only if ctrl->do_rebuild is set.
+cudaError_t enqueue_rebuild(nep_handle *h) {
+  RebuildArgs a = rebuild_args(h);
+  cudaError_t e;
+  {
+    Scope sc(h, KC_CELL, 9);
+    e = launch_cell_sort(a, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  Scope sc(h, KC_NEIGH, 1);
+  return launch_neighbors(a, h->stream);
+}
+
+// Descriptors + network + forces; partial sums reduced with KE partials pk (may be null).
+cudaError_t enqueue_forces(nep_handle *h, float *qout) {
+  const Geom g = geom_of(h);
+  cudaError_t e;
+  {
+    Scope sc(h, KC_DESC, 1);
+    e = launch_descriptor<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, h->G, h->usite, qout, h->part_d,
+                             &h->ctrl->status, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  Scope sc(h, KC_FORCE, 1);
+  return launch_force<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, h->G, h->F, h->part_f, &h->ctrl->status,
+                         h->stream);
+}
+
+cudaError_t enqueue_finalize(nep_handle *h, bool with_kinetic) {
+  Scope sc(h, KC_RED, 1);
+  return launch_finalize(h->part_d, h->nb_d, h->part_f, h->nb_f, with_kinetic ? h->part_k : nullptr, h->nb_k, h->sums,
+                         h->counters, h->stream);
+}
+
+// One velocity-Verlet step.
+cudaError_t enqueue_step(nep_handle *h, double dt) {
+  const double kick = 0.5 * dt * ACC_CONV / h->mass;
+  const float hs = 0.5f * h->skin;
+  cudaError_t e;
+  {
+    Scope sc(h, KC_DRIFT, 1);
+    e = launch_kick_drift(h->n, h->x, h->y, h->z, h->vx, h->vy, h->vz, h->F, h->pos, h->pos_ref, kick, dt, h->l,
+                          hs * hs, h->ctrl, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  {
+    Scope sc(h, KC_CELL, 1);
+    e = launch_control(h->ctrl, false, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  if ((e = enqueue_rebuild(h)) != cudaSuccess) return e;
+  if ((e = enqueue_forces(h, nullptr)) != cudaSuccess) return e;
+  {
+    Scope sc(h, KC_KICK, 1);
+    e = launch_kick(h->n, h->vx, h->vy, h->vz, h->F, kick, h->mass, h->part_k, h->stream);
+  }
+  if (e != cudaSuccess) return e;
+  return enqueue_finalize(h, true);
+}
+
+// Read back the control block and translate device-detected conditions into a status.
+nep_status check_device_status(nep_handle *h) {
+  NEP_CUDA(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(h->h_sums, h->sums, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(h->h_counters, h->counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  nep_status s = wait_stream(h);
+  if (s != NEP_OK) return s;
+  if (h->timing) collect_timers(h);
+  const int st = h->h_ctrl->status;
+  if (st & ST_OVERFLOW)
+    return fail(h, NEP_ERR_NEIGH_OVERFLOW, "an atom has more neighbours within rc_R + skin than max_neighbors");
+  if (st & ST_NAN) return fail(h, NEP_ERR_NAN, "non-finite position, energy or force");
+  return NEP_OK;
+}
+
+nep_status ensure_nlist(nep_handle *h) {
+  if (h->have_nlist) return NEP_OK;
+  {
+    Scope sc(h, KC_CELL, 1);
+    NEP_CUDA(h, launch_control(h->ctrl, true, h->stream));
+  }
+  NEP_CUDA(h, enqueue_rebuild(h));
+  h->have_nlist = true;
+  h->have_forces = false;
+  return NEP_OK;
+}
+
+nep_status compute_internal(nep_handle *h, float *qout) {
+  nep_status s = ensure_nlist(h);
+  if (s != NEP_OK) return s;
+  NEP_CUDA(h, enqueue_forces(h, qout));
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_kinetic(h->n, h->vx, h->vy, h->vz, h->mass, h->part_k, h->stream));
+  }
+  NEP_CUDA(h, enqueue_finalize(h, true));
+  h->have_forces = true;
+  return NEP_OK;
+}
+
+nep_status build_graph(nep_handle *h, double dt) {
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  cudaGraph_t g = nullptr;
+  const long long before = h->launch_total;
+  NEP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_step(h, dt);
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+  h->launch_total = before;
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capture step"); }
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+  h->graph_dt = dt;
+  return NEP_OK;
+}
+
+// Copy [n][3] positions/velocities (host or device) into the SoA state, ids = 0..n-1, and reset the
+// device status word.
+nep_status upload_state(nep_handle *h, const double *x, const double *v) {
+  if (h->n > 0) {
+    const size_t N = (size_t)h->n;
+    NEP_CUDA(h, cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int), h->stream));
+    const double *xs = x, *vs = v;
+    if (!is_device_ptr(x)) {
+      NEP_CUDA(h, cudaMemcpyAsync(h->io, x, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      xs = h->io;
+    }
+    if (v && !is_device_ptr(v)) {
+      NEP_CUDA(h, cudaMemcpyAsync(h->io + 3 * N, v, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      vs = h->io + 3 * N;
+    }
+    {
+      Scope sc(h, KC_OTHER, 1);
+      NEP_CUDA(h, launch_load_state(h->n, xs, vs, h->x, h->y, h->z, h->vx, h->vy, h->vz, h->id, &h->ctrl->status,
+                                    h->stream));
+    }
+    nep_status s = check_device_status(h);
+    if (s != NEP_OK) return s;
+  }
+  h->have_state = true;
+  return NEP_OK;
+}
+
+const int LAUNCHES_PER_STEP = 16;
+
+}  // namespace
+
+// =====================================================================================================
+extern "C" {
+
+const char *nep_status_string(nep_status s) {
+  switch (s) {
+    case NEP_OK: return "NEP_OK";
+    case NEP_ERR_ARG: return "NEP_ERR_ARG";
+    case NEP_ERR_CUDA: return "NEP_ERR_CUDA";
+    case NEP_ERR_NEIGH_OVERFLOW: return "NEP_ERR_NEIGH_OVERFLOW";
+    case NEP_ERR_BOX_TOO_SMALL: return "NEP_ERR_BOX_TOO_SMALL";
+    case NEP_ERR_NAN: return "NEP_ERR_NAN";
+    case NEP_ERR_TIMEOUT: return "NEP_ERR_TIMEOUT";
+    case NEP_ERR_STATE: return "NEP_ERR_STATE";
+    case NEP_ERR_UNSUPPORTED: return "NEP_ERR_UNSUPPORTED";
+    case NEP_ERR_OOM: return "NEP_ERR_OOM";
+  }
+  return "NEP_ERR_UNKNOWN";
+}
+
+const char *nep_last_error(nep_handle *h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) {
+  if (!p || !out) return NEP_ERR_ARG;
+  *out = nullptr;
+  if (p->n_max_R + 1 != S::NR || p->n_max_A + 1 != S::NA || p->basis_R != S::KR || p->basis_A != S::KA ||
+      p->l_max_3b != S::LMAX || p->l_max_4b != (S::FOURBODY ? 2 : 0) || p->n_neu != S::NNEU)
+    return NEP_ERR_UNSUPPORTED;
+  if (p->precision != NEP_FP32) return NEP_ERR_UNSUPPORTED;
+  if (!p->c_R || !p->c_A || !p->W0 || !p->b0 || !p->w1 || !p->q_scale) return NEP_ERR_ARG;
+  if (!(p->rc_R > 0.f) || !(p->rc_A > 0.f) || p->rc_A > p->rc_R || !(p->skin >= 0.f) || !(p->mass_amu > 0.0))
+    return NEP_ERR_ARG;
+  if (p->lj_eps != 0.f && (!(p->lj_rc > 0.f) || p->lj_rc > p->rc_R || !(p->lj_sigma > 0.f))) return NEP_ERR_ARG;
+  if (p->max_neighbors < 0 || p->max_neighbors > 256 || p->rebuild_every < 0) return NEP_ERR_ARG;
+
+  nep_handle *h = new (std::nothrow) nep_handle();
+  if (!h) return NEP_ERR_OOM;
+  Model<S> &M = h->model;
+  for (int a = 0; a < S::NR; ++a)
+    for (int b = 0; b < S::KR; ++b) M.cR[a][b] = p->c_R[a * S::KR + b];
+  for (int a = 0; a < S::NA; ++a)
+    for (int b = 0; b < S::KA; ++b) M.cA[a][b] = p->c_A[a * S::KA + b];
+  for (int m = 0; m < S::NNEU; ++m) {
+    for (int v = 0; v < S::NDES; ++v) M.W0[m][v] = p->W0[m * S::NDES + v];
+    M.b0[m] = p->b0[m];
+    M.w1[m] = p->w1[m];
+  }
+  for (int v = 0; v < S::NDES; ++v) M.qs[v] = p->q_scale[v];
+  M.b1 = p->b1;
+  M.rcR = p->rc_R; M.rcA = p->rc_A;
+  M.rcR2 = p->rc_R * p->rc_R; M.rcA2 = p->rc_A * p->rc_A;
+  M.inv_rcR = 1.f / p->rc_R; M.inv_rcA = 1.f / p->rc_A;
+  const double eps = p->lj_eps, sig = p->lj_sigma, rc = p->lj_rc;
+  M.lj_on = eps != 0.0 ? 1.f : 0.f;
+  if (eps != 0.0) {
+    const double s6 = std::pow(sig, 6.0);
+    const double sr6 = std::pow(sig / rc, 6.0);
+    M.lj_c12 = (float)(4.0 * eps * s6 * s6);
+    M.lj_c6 = (float)(4.0 * eps * s6);
+    M.lj_e_rc = (float)(4.0 * eps * (sr6 * sr6 - sr6));
+    M.lj_de_rc = (float)(4.0 * eps * (-12.0 * sr6 * sr6 + 6.0 * sr6) / rc);
+    M.lj_rc = (float)rc;
+    M.lj_rc2 = (float)(rc * rc);
+  } else {
+    M.lj_c12 = M.lj_c6 = M.lj_e_rc = M.lj_de_rc = 0.f;
+    M.lj_rc = 0.f; M.lj_rc2 = 0.f;
+  }
+  const float rmax = std::max(p->rc_R, eps != 0.0 ? p->lj_rc : 0.f);
+  M.rmax2 = rmax * rmax;
+  h->mass = p->mass_amu;
+  h->skin = p->skin;
+  h->rcR = p->rc_R;
+  h->rcA = p->rc_A;
+  h->cap = p->max_neighbors ? p->max_neighbors : 128;
+  h->rebuild_every = p->rebuild_every;
+
+  cudaError_t e;
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete h; return NEP_ERR_CUDA; }
+    h->own_stream = true;
+  }
+  if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = dalloc(h->sums, 16)) != cudaSuccess || (e = dalloc(h->counters, 8)) != cudaSuccess ||
+      (e = dalloc(h->ctrl, 1)) != cudaSuccess || (e = cudaMallocHost((void **)&h->h_sums, 16 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost((void **)&h->h_ctrl, sizeof(Control))) != cudaSuccess ||
+      (e = cudaMallocHost((void **)&h->h_counters, 8 * sizeof(long long))) != cudaSuccess) {
+    nep_destroy(h);
+    return NEP_ERR_CUDA;
+  }
+  cudaMemsetAsync(h->sums, 0, 16 * sizeof(double), h->stream);
+  cudaMemsetAsync(h->counters, 0, 8 * sizeof(long long), h->stream);
+  Control c0{};
+  c0.rebuild_every = h->rebuild_every;
+  cudaMemcpyAsync(h->ctrl, &c0, sizeof(Control), cudaMemcpyHostToDevice, h->stream);
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { nep_destroy(h); return NEP_ERR_CUDA; }
+  *out = h;
+  return NEP_OK;
+}
+
+nep_status nep_destroy(nep_handle *h) {
+  if (!h) return NEP_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_system(h);
+  dfree(h->sums); dfree(h->counters); dfree(h->ctrl);
+  if (h->h_sums) cudaFreeHost(h->h_sums);
+  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  if (h->h_counters) cudaFreeHost(h->h_counters);
+  for (auto &t : h->timers) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  if (h->done) cudaEventDestroy(h->done);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return NEP_OK;
+}
+
+nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double *v, const double *box) {
+  if (!h) return NEP_ERR_ARG;
+  if (n < 0 || n > NEP_MAX_ATOMS) return fail(h, NEP_ERR_ARG, "atom count out of range");
+  if (n > 0 && !x) return fail(h, NEP_ERR_ARG, "positions are NULL");
+  if (!box) return fail(h, NEP_ERR_ARG, "box is NULL");
+  const double rl = (double)h->rcR + (double)h->skin;
+  for (int d = 0; d < 3; ++d) {
+    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(h, NEP_ERR_ARG, "box edges must be positive and finite");
+    if (box[d] < 2.0 * rl) return fail(h, NEP_ERR_BOX_TOO_SMALL, "every box edge must be >= 2 (rc_R + skin)");
+  }
+  cudaStreamSynchronize(h->stream);
+  const bool same = h->have_state && h->n == (int)n && h->L[0] == box[0] && h->L[1] == box[1] && h->L[2] == box[2];
+  if (same) {
+    // Same size and box: keep every buffer (and the captured step graph); upload and invalidate.
+    h->have_nlist = h->have_forces = false;
+    return upload_state(h, x, v);
+  }
+  free_system(h);
+  h->n = (int)n;
+  int64_t ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    h->L[d] = box[d];
+    int nc = (int)std::floor(box[d] / rl);
+    nc = std::max(2, std::min(nc, 1023));
+    h->nc[d] = nc;
+    h->l[d] = box[d] / nc;
+    ncell *= nc;
+  }
+  if (ncell > (int64_t)1 << 30) return fail(h, NEP_ERR_ARG, "too many cells");
+  h->ncell = (int)ncell;
+  h->nb_d = descriptor_blocks(h->n);
+  h->nb_f = force_blocks(h->n);
+  h->nb_k = md_blocks(h->n);
+  const size_t N = (size_t)std::max(h->n, 1);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(dalloc(h->x, N)); A(dalloc(h->y, N)); A(dalloc(h->z, N)); A(dalloc(h->vx, N)); A(dalloc(h->vy, N)); A(dalloc(h->vz, N));
+  A(dalloc(h->xb, N)); A(dalloc(h->yb, N)); A(dalloc(h->zb, N)); A(dalloc(h->vxb, N)); A(dalloc(h->vyb, N)); A(dalloc(h->vzb, N));
+  A(dalloc(h->id, N)); A(dalloc(h->idb, N)); A(dalloc(h->cell_of, N)); A(dalloc(h->perm, N));
+  A(dalloc(h->pos, N)); A(dalloc(h->pos_ref, N));
+  A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N)); A(dalloc(h->G, N * GSTRIDE));
+  A(dalloc(h->nbr, N * (size_t)h->cap)); A(dalloc(h->nnum, N)); A(dalloc(h->nang, N));
+  A(dalloc(h->count, (size_t)h->ncell)); A(dalloc(h->cursor, (size_t)h->ncell)); A(dalloc(h->start, (size_t)h->ncell + 1));
+  A(dalloc(h->tile_sums, (size_t)scan_tiles(h->ncell) + 1));
+  A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 9 + 1));
+  A(dalloc(h->part_k, (size_t)h->nb_k + 1)); A(dalloc(h->io, 6 * N));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_system(h);
+    return fail(h, e == cudaErrorMemoryAllocation ? NEP_ERR_OOM : NEP_ERR_CUDA,
+                std::string("allocation failed: ") + cudaGetErrorString(e));
+  }
+  NEP_CUDA(h, cudaMemsetAsync(h->F, 0, 3 * N * sizeof(float), h->stream));
+  NEP_CUDA(h, cudaMemsetAsync(h->sums, 0, 16 * sizeof(double), h->stream));
+  NEP_CUDA(h, cudaMemsetAsync(h->counters, 0, 8 * sizeof(long long), h->stream));
+  Control c0{};
+  c0.rebuild_every = h->rebuild_every;
+  NEP_CUDA(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Control), cudaMemcpyHostToDevice, h->stream));
+  return upload_state(h, x, v);
+}
+
+nep_status nep_build_neighbors(nep_handle *h) {
+  if (!h) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->n == 0) return NEP_OK;
+  h->have_nlist = false;
+  nep_status s = ensure_nlist(h);
+  if (s != NEP_OK) return s;
+  return check_device_status(h);
+}
+
+nep_status nep_compute(nep_handle *h, double *E, double *F, double *virial) {
+  if (!h) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->n == 0) {
+    if (E) *E = 0.0;
+    if (virial) for (int k = 0; k < 9; ++k) virial[k] = 0.0;
+    return NEP_OK;
+  }
+  nep_status s = compute_internal(h, nullptr);
+  if (s != NEP_OK) return s;
+  const bool fdev = F && is_device_ptr(F);
+  if (F) {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_store_force(h->n, h->id, h->F, fdev ? F : h->io, h->stream));
+    if (!fdev)
+      NEP_CUDA(h, cudaMemcpyAsync(F, h->io, 3 * (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  s = check_device_status(h);
+  if (s != NEP_OK) return s;
+  if (E) *E = h->h_sums[0];
+  if (virial) for (int k = 0; k < 9; ++k) virial[k] = h->h_sums[1 + k];
+  return NEP_OK;
+}
+
+nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
+  if (!h) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (n_steps < 0 || !(std::isfinite(dt_fs))) return fail(h, NEP_ERR_ARG, "bad dt or step count");
+  if (h->n == 0 || n_steps == 0) return NEP_OK;
+  if (!h->have_forces) {
+    nep_status s = compute_internal(h, nullptr);
+    if (s != NEP_OK) return s;
+  }
+  if (h->timing) {
+    for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, enqueue_step(h, dt_fs));
+  } else {
+    if (!h->graph || h->graph_dt != dt_fs) {
+      nep_status s = build_graph(h, dt_fs);
+      if (s != NEP_OK) return s;
+    }
+    for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+    h->launch_total += (long long)LAUNCHES_PER_STEP * n_steps;
+  }
+  return check_device_status(h);
+}
+
+nep_status nep_get_state(nep_handle *h, double *x, double *v) {
+  if (!h) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->n == 0) return NEP_OK;
+  const size_t bytes = 3 * (size_t)h->n * sizeof(double);
+  for (int which = 0; which < 2; ++which) {
+    double *out = which == 0 ? x : v;
+    if (!out) continue;
+    const bool dev = is_device_ptr(out);
+    {
+      Scope sc(h, KC_OTHER, 1);
+      if (which == 0) NEP_CUDA(h, launch_store_vec(h->n, h->id, h->x, h->y, h->z, h->L, 1, dev ? out : h->io, h->stream));
+      else NEP_CUDA(h, launch_store_vec(h->n, h->id, h->vx, h->vy, h->vz, h->L, 0, dev ? out : h->io, h->stream));
+    }
+    if (!dev) {
+      NEP_CUDA(h, cudaMemcpyAsync(out, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
+      nep_status s = wait_stream(h);
+      if (s != NEP_OK) return s;
+    }
+  }
+  return wait_stream(h);
+}
+
+nep_status nep_get_thermo(nep_handle *h, double out[8]) {
+  if (!h || !out) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  nep_status s = check_device_status(h);
+  if (s != NEP_OK) return s;
+  const double pe = h->h_sums[0], ke = h->h_sums[10];
+  const double V = h->L[0] * h->L[1] * h->L[2];
+  const double trW = h->h_sums[1] + h->h_sums[5] + h->h_sums[9];
+  out[0] = pe;
+  out[1] = ke;
+  out[2] = h->n > 1 ? 2.0 * ke / ((3.0 * h->n - 3.0) * KB_EV) : 0.0;
+  out[3] = (2.0 * ke + trW) / (3.0 * V);
+  out[4] = h->h_sums[1]; out[5] = h->h_sums[5]; out[6] = h->h_sums[9];
+  out[7] = (double)h->h_ctrl->rebuilds;
+  return NEP_OK;
+}
+
+nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int32_t *list, int cap) {
+  if (!h || !counts || !n_ang || !list || cap <= 0) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->n == 0) return NEP_OK;
+  nep_status s = ensure_nlist(h);
+  if (s != NEP_OK) return s;
+  const size_t N = (size_t)h->n;
+  const size_t elems = N * 2 + N * (size_t)cap;
+  if (h->io_i_elems < elems) {
+    dfree(h->io_i);
+    NEP_CUDA(h, dalloc(h->io_i, elems));
+    h->io_i_elems = elems;
+  }
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_store_neighbors(h->n, h->cap, cap, h->id, h->nbr, h->nnum, h->nang, h->io_i, h->io_i + N,
+                                       h->io_i + 2 * N, h->stream));
+  }
+  NEP_CUDA(h, cudaMemcpyAsync(counts, h->io_i, N * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(n_ang, h->io_i + N, N * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(list, h->io_i + 2 * N, N * (size_t)cap * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  return check_device_status(h);
+}
+
+nep_status nep_get_descriptors(nep_handle *h, float *q) {
+  if (!h || !q) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->n == 0) return NEP_OK;
+  const size_t N = (size_t)h->n;
+  if (!h->qbuf) NEP_CUDA(h, dalloc(h->qbuf, 2 * N * S::NDES));
+  nep_status s = compute_internal(h, h->qbuf);
+  if (s != NEP_OK) return s;
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_store_rows(h->n, S::NDES, h->id, h->qbuf, h->qbuf + N * S::NDES, h->stream));
+  }
+  NEP_CUDA(h, cudaMemcpyAsync(q, h->qbuf + N * S::NDES, N * S::NDES * sizeof(float), cudaMemcpyDefault, h->stream));
+  return check_device_status(h);
+}
+
+nep_status nep_get_site_energies(nep_handle *h, double *U) {
+  if (!h || !U) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->n == 0) return NEP_OK;
+  if (!h->have_forces) {
+    nep_status s = compute_internal(h, nullptr);
+    if (s != NEP_OK) return s;
+  }
+  const bool dev = is_device_ptr(U);
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_store_scalar(h->n, h->id, h->usite, dev ? U : h->io, h->stream));
+  }
+  if (!dev) NEP_CUDA(h, cudaMemcpyAsync(U, h->io, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return check_device_status(h);
+}
+
+nep_status nep_set_timing(nep_handle *h, int enable) {
+  if (!h) return NEP_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  h->timing = enable != 0;
+  h->timers_used = 0;
+  for (int k = 0; k < NEP_N_KERNEL_CLASSES; ++k) { h->ms[k] = 0.0; h->launches[k] = 0; }
+  return NEP_OK;
+}
+
+nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_t launches[NEP_N_KERNEL_CLASSES]) {
+  if (!h || !ms || !launches) return NEP_ERR_ARG;
+  nep_status s = wait_stream(h);
+  if (s != NEP_OK) return s;
+  collect_timers(h);
+  for (int k = 0; k < NEP_N_KERNEL_CLASSES; ++k) { ms[k] = h->ms[k]; launches[k] = h->launches[k]; }
+  return NEP_OK;
+}
+
+nep_status nep_get_counters(nep_handle *h, int64_t out[8]) {
+  if (!h || !out) return NEP_ERR_ARG;
+  nep_status s = check_device_status(h);
+  if (s != NEP_OK && s != NEP_ERR_NEIGH_OVERFLOW && s != NEP_ERR_NAN) return s;
+  out[0] = h->h_counters[0];
+  out[1] = h->h_counters[1];
+  out[2] = h->h_counters[2];
+  out[3] = h->h_ctrl->rebuilds;
+  out[4] = h->h_ctrl->steps;
+  out[5] = h->launch_total;
+  out[6] = h->h_counters[3];
+  out[7] = h->h_counters[4];
+  return NEP_OK;
+}
+
+}  // extern "C"

@@ -37,6 +37,20 @@ struct Control {
   long long steps;      // MD steps done
 };
 
+// Arguments of the rebuild chain (cell sort + neighbour list).
+struct RebuildArgs {
+  int n, ncell;
+  double L[3], l[3];
+  int nc[3];
+  double *x, *y, *z, *vx, *vy, *vz, *xb, *yb, *zb, *vxb, *vyb, *vzb;
+  int *id, *idb, *cell_of, *count, *cursor, *start, *tile_sums, *perm;
+  float4 *pos, *pos_ref;
+  int32_t *nbr, *nnum, *nang;
+  int cap;
+  float rl2, ra2;
+  Control *ctrl;
+};
+
 // Compile-time model shape: NR radial functions, NA angular, K basis functions, lmax = 4 3-body,
 // optional 4-body (l = 2), NNEU hidden neurons.
 template <int NR_, int NA_, int KR_, int KA_, bool FOURBODY_, int NNEU_>

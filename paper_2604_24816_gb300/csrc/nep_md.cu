@@ -1,0 +1,271 @@
+// nep_md.cu -- velocity-Verlet integration, step control, reductions and layout kernels (sm_103a).
+//
+// Positions and velocities are float64 (structure of arrays, cell-sorted order); forces are float32.
+// Between rebuilds positions are not wrapped, so each atom's cell-relative float32 coordinate
+// p = x - (cell origin) stays continuous; wrapping happens in the rebuild.  The drift kernel flags any
+// atom whose cell-relative coordinate moved more than skin/2 since the last rebuild; the control
+// kernel then asks the next rebuild chain to run.
+#include "nep_common.cuh"
+
+namespace nep {
+
+constexpr double KE_CONV = 103.642696562;          // 1 amu Angstrom^2/fs^2 in eV
+
+__global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                             double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                             const float *__restrict__ F, float4 *__restrict__ pos, const float4 *__restrict__ pos_ref,
+                             double kick, double dt, double lx, double ly, double lz, float half_skin2, Control *ctrl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool moved = false;
+  if (i < n) {
+    double ux = vx[i] + kick * (double)F[i];
+    double uy = vy[i] + kick * (double)F[(size_t)n + i];
+    double uz = vz[i] + kick * (double)F[2 * (size_t)n + i];
+    vx[i] = ux; vy[i] = uy; vz[i] = uz;
+    const double px = x[i] + dt * ux, py = y[i] + dt * uy, pz = z[i] + dt * uz;
+    x[i] = px; y[i] = py; z[i] = pz;
+    const float4 p = pos[i];
+    const int cx = cell_x(p.w), cy = cell_y(p.w), cz = cell_z(p.w);
+    const float4 q = make_float4((float)(px - cx * lx), (float)(py - cy * ly), (float)(pz - cz * lz), p.w);
+    pos[i] = q;
+    const float4 r = pos_ref[i];
+    const float ddx = q.x - r.x, ddy = q.y - r.y, ddz = q.z - r.z;
+    const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+    moved = !(d2 <= half_skin2);       // also true for NaN
+  }
+  if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->moved, 1);
+}
+
+// Decide whether this step rebuilds the neighbour list.
+__global__ void k_control(Control *ctrl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctrl->steps += 1;
+  ctrl->steps_since += 1;
+  int rb = ctrl->moved | ctrl->force_rebuild;
+  if (ctrl->rebuild_every > 0 && ctrl->steps_since >= ctrl->rebuild_every) rb = 1;
+  ctrl->do_rebuild = rb;
+  if (rb) {
+    ctrl->moved = 0;
+    ctrl->force_rebuild = 0;
+    ctrl->steps_since = 0;
+    ctrl->rebuilds += 1;
+  }
+}
+
+// Rebuild unconditionally (outside MD steps).
+__global__ void k_control_force(Control *ctrl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctrl->do_rebuild = 1;
+  ctrl->moved = 0;
+  ctrl->force_rebuild = 0;
+  ctrl->steps_since = 0;
+  ctrl->rebuilds += 1;
+}
+
+__global__ void k_kick(int n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                       const float *__restrict__ F, double kick, double mass, double *__restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (i < n) {
+    const double ux = vx[i] + kick * (double)F[i];
+    const double uy = vy[i] + kick * (double)F[(size_t)n + i];
+    const double uz = vz[i] + kick * (double)F[2 * (size_t)n + i];
+    vx[i] = ux; vy[i] = uy; vz[i] = uz;
+    acc[0] = 0.5 * mass * KE_CONV * (ux * ux + uy * uy + uz * uz);
+  }
+  block_sum_store<1>(acc, part);
+}
+
+// Kinetic energy only (no kick): for thermo outside MD steps.
+__global__ void k_kinetic(int n, const double *__restrict__ vx, const double *__restrict__ vy,
+                          const double *__restrict__ vz, double mass, double *__restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (i < n) acc[0] = 0.5 * mass * KE_CONV * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+  block_sum_store<1>(acc, part);
+}
+
+// Fixed-order reduction of the per-block partials.
+// pd (stride 5): {site energy, radial pairs, angular pairs, list entries, active pairs};
+// pf (stride 9): virial; pk (stride 1): kinetic energy.
+// sums = {E, W[9], KE, radial, angular, list, active}; counters += {radial, angular, 1, list, active}.
+__global__ void __launch_bounds__(256)
+k_finalize(const double *__restrict__ pd, int nbd, const double *__restrict__ pf, int nbf,
+           const double *__restrict__ pk, int nbk, double *__restrict__ sums, long long *__restrict__ counters) {
+  __shared__ double red[256];
+  double out[15];
+  for (int v = 0; v < 15; ++v) {
+    const double *src;
+    int nb, stride, off;
+    if (v == 0) { src = pd; nb = nbd; stride = 5; off = 0; }
+    else if (v <= 9) { src = pf; nb = nbf; stride = 9; off = v - 1; }
+    else if (v == 10) { src = pk; nb = nbk; stride = 1; off = 0; }
+    else { src = pd; nb = nbd; stride = 5; off = v - 10; }
+    double t = 0.0;
+    if (src != nullptr)
+      for (int b = threadIdx.x; b < nb; b += blockDim.x) t += src[(size_t)b * stride + off];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    out[v] = red[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (pd != nullptr) { sums[0] = out[0]; for (int v = 11; v < 15; ++v) sums[v] = out[v]; }
+    if (pf != nullptr) for (int v = 1; v <= 9; ++v) sums[v] = out[v];
+    if (pk != nullptr) sums[10] = out[10];
+    if (counters != nullptr && pd != nullptr) {
+      counters[0] += (long long)out[11];
+      counters[1] += (long long)out[12];
+      counters[2] += 1;
+      counters[3] += (long long)out[13];
+      counters[4] += (long long)out[14];
+    }
+  }
+}
+
+// [n][3] float64 (original order) -> SoA float64, ids = 0..n-1.
+__global__ void k_load_state(int n, const double *__restrict__ xin, const double *__restrict__ vin,
+                             double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                             double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                             int *__restrict__ id, int *__restrict__ status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double a = xin[3 * (size_t)s], b = xin[3 * (size_t)s + 1], c = xin[3 * (size_t)s + 2];
+  if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(status, ST_NAN);
+  x[s] = a; y[s] = b; z[s] = c;
+  if (vin != nullptr) {
+    vx[s] = vin[3 * (size_t)s]; vy[s] = vin[3 * (size_t)s + 1]; vz[s] = vin[3 * (size_t)s + 2];
+  } else {
+    vx[s] = 0.0; vy[s] = 0.0; vz[s] = 0.0;
+  }
+  id[s] = s;
+}
+
+// Sorted SoA -> original-order [n][3] float64 (positions wrapped into the box when L != nullptr).
+__global__ void k_store_vec(int n, const int *__restrict__ id, const double *__restrict__ a, const double *__restrict__ b,
+                            const double *__restrict__ c, double Lx, double Ly, double Lz, int wrap,
+                            double *__restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double u = a[s], v = b[s], w = c[s];
+  if (wrap) {
+    u -= Lx * floor(u / Lx); if (u >= Lx) u -= Lx;
+    v -= Ly * floor(v / Ly); if (v >= Ly) v -= Ly;
+    w -= Lz * floor(w / Lz); if (w >= Lz) w -= Lz;
+  }
+  const size_t o = 3 * (size_t)id[s];
+  out[o] = u; out[o + 1] = v; out[o + 2] = w;
+}
+
+__global__ void k_store_force(int n, const int *__restrict__ id, const float *__restrict__ F, double *__restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const size_t o = 3 * (size_t)id[s];
+  out[o] = F[s]; out[o + 1] = F[(size_t)n + s]; out[o + 2] = F[2 * (size_t)n + s];
+}
+
+__global__ void k_store_scalar(int n, const int *__restrict__ id, const float *__restrict__ u, double *__restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  out[id[s]] = u[s];
+}
+
+__global__ void k_store_rows(int n, int width, const int *__restrict__ id, const float *__restrict__ q,
+                             float *__restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  for (int v = 0; v < width; ++v) out[(size_t)id[s] * width + v] = q[(size_t)s * width + v];
+}
+
+__global__ void k_store_neighbors(int n, int cap_in, int cap_out, const int *__restrict__ id, const int32_t *__restrict__ nbr,
+                                  const int32_t *__restrict__ nnum, const int32_t *__restrict__ nang,
+                                  int32_t *__restrict__ counts, int32_t *__restrict__ n_ang, int32_t *__restrict__ list) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int o = id[s];
+  const int c = nnum[s];
+  counts[o] = c;
+  n_ang[o] = nang[s];
+  for (int k = 0; k < c && k < cap_out; ++k) list[(size_t)o * cap_out + k] = id[nbr[(size_t)k * n + s] & J_MASK];
+  for (int k = c; k < cap_out; ++k) list[(size_t)o * cap_out + k] = -1;
+  (void)cap_in;
+}
+
+// ---------------------------------------------------------------------------------------------------
+static int bl(long long m, int b) { return (int)((m + b - 1) / b); }
+
+constexpr int MD_BLOCK = 256;
+int md_blocks(int n) { return bl(n, MD_BLOCK); }
+
+cudaError_t launch_kick_drift(int n, double *x, double *y, double *z, double *vx, double *vy, double *vz, const float *F,
+                              float4 *pos, const float4 *pos_ref, double kick, double dt, const double l[3],
+                              float half_skin2, Control *ctrl, cudaStream_t st) {
+  if (n > 0)
+    k_kick_drift<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, x, y, z, vx, vy, vz, F, pos, pos_ref, kick, dt, l[0], l[1],
+                                                       l[2], half_skin2, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_control(Control *ctrl, bool force, cudaStream_t st) {
+  if (force) k_control_force<<<1, 32, 0, st>>>(ctrl);
+  else k_control<<<1, 32, 0, st>>>(ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick(int n, double *vx, double *vy, double *vz, const float *F, double kick, double mass, double *part,
+                        cudaStream_t st) {
+  if (n > 0) k_kick<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, F, kick, mass, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic(int n, const double *vx, const double *vy, const double *vz, double mass, double *part,
+                           cudaStream_t st) {
+  if (n > 0) k_kinetic<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, mass, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *pd, int nbd, const double *pf, int nbf, const double *pk, int nbk,
+                            double *sums, long long *counters, cudaStream_t st) {
+  k_finalize<<<1, 256, 0, st>>>(pd, nbd, pf, nbf, pk, nbk, sums, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_state(int n, const double *xin, const double *vin, double *x, double *y, double *z, double *vx,
+                              double *vy, double *vz, int *id, int *status, cudaStream_t st) {
+  if (n > 0) k_load_state<<<bl(n, 256), 256, 0, st>>>(n, xin, vin, x, y, z, vx, vy, vz, id, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_vec(int n, const int *id, const double *a, const double *b, const double *c, const double L[3],
+                             int wrap, double *out, cudaStream_t st) {
+  if (n > 0) k_store_vec<<<bl(n, 256), 256, 0, st>>>(n, id, a, b, c, L[0], L[1], L[2], wrap, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_force(int n, const int *id, const float *F, double *out, cudaStream_t st) {
+  if (n > 0) k_store_force<<<bl(n, 256), 256, 0, st>>>(n, id, F, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_scalar(int n, const int *id, const float *u, double *out, cudaStream_t st) {
+  if (n > 0) k_store_scalar<<<bl(n, 256), 256, 0, st>>>(n, id, u, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_rows(int n, int width, const int *id, const float *q, float *out, cudaStream_t st) {
+  if (n > 0) k_store_rows<<<bl(n, 256), 256, 0, st>>>(n, width, id, q, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_neighbors(int n, int cap_in, int cap_out, const int *id, const int32_t *nbr, const int32_t *nnum,
+                                   const int32_t *nang, int32_t *counts, int32_t *n_ang, int32_t *list, cudaStream_t st) {
+  if (n > 0)
+    k_store_neighbors<<<bl(n, 256), 256, 0, st>>>(n, cap_in, cap_out, id, nbr, nnum, nang, counts, n_ang, list);
+  return cudaGetLastError();
+}
+
+}  // namespace nep

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances (float32 path vs float64 oracle):
+  neighbour sets        bit-exact (as sets of atom ids), for the radial list and its angular prefix
+  forces                max |dF| <= 1e-4 eV/Angstrom (LJ + NEP); NEP-only forces also relative 1e-3 of max |F|
+  total energy          |dE| / |E| <= 1e-6
+  site energies         max |dU| <= 2e-6 eV
+  virial                max |dW| <= 1e-5 * max |W|
+  descriptors           |dq| <= 2e-5 * max(1, |q|) per component, relative to each column's scale
+  10-step trajectory    positions 1e-6 Angstrom, velocities 1e-7 Angstrom/fs
+"""
+import numpy as np
+import pytest
+
+import nep_inputs as ni
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2604_24816_gb300 import build
+    build.build()
+    import paper_2604_24816_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return ni.workload("cu_4x4x4")
+
+
+def _sets_from_gpu(counts, lst):
+    return [set(lst[i, :counts[i]].tolist()) for i in range(len(counts))]
+
+
+def _sets_from_oracle(off, lst):
+    return [set(lst[off[i]:off[i + 1]].tolist()) for i in range(len(off) - 1)]
+
+
+def _min_gap_to_cutoffs(pos, box, cuts):
+    d = pos[None, :, :] - pos[:, None, :]
+    d -= box * np.round(d / box)
+    r = np.sqrt((d ** 2).sum(-1))
+    return min(np.abs(r - c).min() for c in cuts)
+
+
+@pytest.mark.parametrize("cells", [(4, 4, 4), (4, 4, 5), (6, 5, 4)])
+def test_neighbor_sets_bit_exact(api, model_params, cells):
+    wl = ni.fcc_cu_workload(0, sigma=0.05, seed=21 + sum(cells), cells_xyz=cells)
+    rl = model_params["rc_R"] + model_params["skin"]
+    ra = model_params["rc_A"] + model_params["skin"]
+    assert _min_gap_to_cutoffs(wl.pos, wl.box, (rl, ra)) > 1e-5, "ambiguous pair within 1e-5 A of a cutoff"
+    with api.NEP(model_params) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.build_neighbors()
+        counts, nang, lst = nep.neighbors(cap=160)
+    o_off, o_lst = oracle.neighbor_lists(wl.pos, wl.box, rl, use_cells=False)
+    a_off, a_lst = oracle.neighbor_lists(wl.pos, wl.box, ra, use_cells=False)
+    assert _sets_from_gpu(counts, lst) == _sets_from_oracle(o_off, o_lst)
+    ang = [set(lst[i, :nang[i]].tolist()) for i in range(wl.n)]
+    assert ang == _sets_from_oracle(a_off, a_lst)
+    # distance order within each row
+    for i in range(0, wl.n, 17):
+        d = wl.pos[lst[i, :counts[i]]] - wl.pos[i]
+        d -= wl.box * np.round(d / wl.box)
+        r = np.sqrt((d ** 2).sum(1))
+        assert np.all(np.diff(r) >= -1e-5)
+
+
+def test_descriptors(api, model_params, model, c1):
+    with api.NEP(model_params) as nep:
+        nep.set_state(c1.pos, c1.vel, c1.box)
+        q = nep.descriptors().astype(np.float64)
+    qo = oracle.descriptors(model, c1.pos, c1.box)
+    scale = np.maximum(1.0, np.abs(qo).max(axis=0))
+    assert (np.abs(q - qo) / scale).max() < 2e-5
+
+
+@pytest.mark.parametrize("cells", [(4, 4, 4), (4, 4, 5), (6, 6, 6)])
+def test_energy_forces_virial(api, model_params, model, cells):
+    wl = ni.fcc_cu_workload(0, sigma=0.05, seed=5 + sum(cells), cells_xyz=cells)
+    with api.NEP(model_params) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        E, F, W = nep.compute()
+        U = nep.site_energies()
+    Eo, Uo, Fo, Wo = oracle.energy_forces(model, wl.pos, wl.box)
+    assert np.abs(F - Fo).max() <= 1e-4
+    assert abs(E - Eo) / abs(Eo) <= 1e-6
+    assert np.abs(U - Uo).max() <= 2e-6
+    assert np.abs(W - Wo).max() <= 1e-5 * np.abs(Wo).max()
+
+
+def test_nep_only_forces(api, model_params, model, c1):
+    """Without the LJ term the forces are the NEP chain rule alone (max |F| ~ 0.2 eV/A)."""
+    m0 = model.with_changes(lj_eps=0.0)
+    with api.NEP(model_params, lj=False) as nep:
+        nep.set_state(c1.pos, c1.vel, c1.box)
+        E, F, W = nep.compute()
+    Eo, Uo, Fo, Wo = oracle.energy_forces(m0, c1.pos, c1.box)
+    assert np.abs(F - Fo).max() <= 1e-3 * np.abs(Fo).max()
+    assert np.abs(F - Fo).max() <= 1e-4
+    assert abs(E - Eo) <= 1e-6 * c1.n
+    assert np.abs(W - Wo).max() <= 1e-4 * np.abs(Wo).max()
+
+
+def test_md_trajectory_10_steps(api, model_params, model, c1):
+    with api.NEP(model_params) as nep:
+        nep.set_state(c1.pos, c1.vel, c1.box)
+        nep.step(1.0, 10)
+        x, v = nep.get_state()
+        th = nep.thermo()
+    xo, vo, tho = oracle.md_nve(model, c1.pos, c1.vel, c1.box, ni.M_CU, 1.0, 10)
+    dx = x - xo
+    dx -= c1.box * np.round(dx / c1.box)
+    assert np.abs(dx).max() <= 1e-6
+    assert np.abs(v - vo).max() <= 1e-7
+    assert abs(th["pe"] - tho[-1, 0]) / abs(tho[-1, 0]) <= 1e-6
+    assert abs(th["ke"] - tho[-1, 1]) / abs(tho[-1, 1]) <= 1e-6
+
+
+def test_deterministic_runs(api, model_params, c1):
+    out = []
+    for _ in range(2):
+        with api.NEP(model_params, rebuild_every=3) as nep:
+            nep.set_state(c1.pos, c1.vel, c1.box)
+            nep.step(1.0, 7)
+            E, F, W = nep.compute()
+            x, v = nep.get_state()
+            out.append((E, F, W, x, v))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_graph_and_eager_paths_identical(api, model_params, c1):
+    res = []
+    for timing in (False, True):
+        with api.NEP(model_params, rebuild_every=4) as nep:
+            nep.set_state(c1.pos, c1.vel, c1.box)
+            nep.set_timing(timing)
+            nep.step(1.0, 9)
+            res.append(nep.get_state())
+            if timing:
+                t = nep.timing()
+                assert t["force"][1] >= 9 and t["force"][0] > 0
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_device_and_host_pointers_agree(api, model_params, c1):
+    import torch
+    with api.NEP(model_params) as nep:
+        nep.set_state(torch.from_numpy(c1.pos).cuda(), torch.from_numpy(c1.vel).cuda(), c1.box)
+        Fd = torch.zeros((c1.n, 3), dtype=torch.float64, device="cuda")
+        Ed, _, Wd = nep.compute(out=Fd)
+        nep.set_state(c1.pos, c1.vel, c1.box)
+        Eh, Fh, Wh = nep.compute()
+    assert Ed == Eh and np.array_equal(Fd.cpu().numpy(), Fh) and np.array_equal(Wd, Wh)
+
+
+def test_rebuild_policy_does_not_change_physics(api, model_params, c1):
+    res = []
+    for every in (0, 1):
+        with api.NEP(model_params, rebuild_every=every) as nep:
+            nep.set_state(c1.pos, c1.vel, c1.box)
+            nep.step(1.0, 20)
+            res.append(nep.get_state()[0])
+            c = nep.counters()
+            assert c["steps"] == 20
+            if every == 1:
+                assert c["rebuilds"] >= 21
+    d = res[0] - res[1]
+    d -= c1.box * np.round(d / c1.box)
+    assert np.abs(d).max() < 1e-6
+
+
+def test_atoms_crossing_the_boundary_and_rebuilds(api, model_params, model):
+    """Hot small cell: atoms leave their cells and cross the periodic boundary between rebuilds."""
+    wl = ni.fcc_cu_workload(4, temperature=1500.0, sigma=0.1, seed=33)
+    with api.NEP(model_params) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.step(1.0, 60)
+        x, v = nep.get_state()
+        E, F, W = nep.compute()
+        assert nep.counters()["rebuilds"] >= 2
+    assert np.all((x >= 0) & (x < wl.box))
+    Eo, Uo, Fo, Wo = oracle.energy_forces(model, x, wl.box)
+    assert np.abs(F - Fo).max() <= 1e-4
+    assert abs(E - Eo) / abs(Eo) <= 1e-6
+
+
+def test_nve_energy_drift_gpu(api, model_params, c1):
+    """Plain FP32 forces with FP64 integration: drift below 1e-5 eV/atom/ps over 2 ps."""
+    with api.NEP(model_params) as nep:
+        nep.set_state(c1.pos, c1.vel, c1.box)
+        et = []
+        for _ in range(40):
+            nep.step(1.0, 50)
+            th = nep.thermo()
+            et.append((th["pe"] + th["ke"]) / c1.n)
+    t_ps = np.arange(1, 41) * 0.05
+    assert abs(np.polyfit(t_ps, np.array(et), 1)[0]) < 1e-5
+
+
+# ----------------------------------------------------------------------------------------------------
+# Edge cases and error statuses (host-detected or reported through the device status word).
+
+def test_empty_system(api, model_params):
+    with api.NEP(model_params) as nep:
+        nep.set_state(np.zeros((0, 3)), None, [20.0, 20.0, 20.0])
+        E, F, W = nep.compute()
+        nep.step(1.0, 3)
+        assert E == 0.0 and F.shape == (0, 3) and np.all(W == 0)
+
+
+def test_box_too_small(api, model_params):
+    with api.NEP(model_params) as nep:
+        with pytest.raises(api.NepError) as e:
+            nep.set_state(np.zeros((4, 3)), None, [11.0, 20.0, 20.0])
+        assert e.value.name == "NEP_ERR_BOX_TOO_SMALL"
+
+
+def test_nan_positions_reported(api, model_params, c1):
+    x = c1.pos.copy()
+    x[17, 1] = np.nan
+    with api.NEP(model_params) as nep:
+        with pytest.raises(api.NepError) as e:
+            nep.set_state(x, None, c1.box)
+        assert e.value.name == "NEP_ERR_NAN"
+
+
+def test_neighbor_overflow_reported(api, model_params, c1):
+    with api.NEP(model_params, max_neighbors=40) as nep:
+        nep.set_state(c1.pos, c1.vel, c1.box)
+        with pytest.raises(api.NepError) as e:
+            nep.compute()
+        assert e.value.name == "NEP_ERR_NEIGH_OVERFLOW"
+
+
+def test_compute_before_state(api, model_params):
+    with api.NEP(model_params) as nep:
+        with pytest.raises(api.NepError) as e:
+            nep.compute()
+        assert e.value.name == "NEP_ERR_STATE"
+
+
+def test_unwrapped_input_positions(api, model_params, model, c1):
+    shifted = c1.pos + c1.box * np.array([1.0, -2.0, 3.0])
+    with api.NEP(model_params) as nep:
+        nep.set_state(shifted, c1.vel, c1.box)
+        E, F, W = nep.compute()
+    Eo, Uo, Fo, Wo = oracle.energy_forces(model, c1.pos, c1.box)
+    assert np.abs(F - Fo).max() <= 1e-4 and abs(E - Eo) / abs(Eo) <= 1e-6

@@ -10,17 +10,17 @@
 //                   positions, independent of launch timing and of the previous order
 //   k_permute       gather x, v, id into the new order; cell-relative float32 coordinates
 //   k_copy_back     copy the gathered arrays back (fixed device pointers for graph replay)
-//   k_neighbors     for each atom, every j with |r_ij| < rc_R + skin among the 27 neighbouring cell
-//                   images, sorted by (float32 distance^2, packed j) so that the entries inside the
-//                   angular and radial cutoffs come first and the per-pair branches in the force
-//                   kernels stay warp-uniform; the prefix with |r_ij| < rc_A + skin is the angular list.
+//   k_neighbors     for each atom (one warp per atom), every j with |r_ij| < rc_R + skin among the 27
+//                   neighbouring cell images, sorted by (float32 distance^2, packed j) so that the
+//                   entries inside the angular and radial cutoffs come first and the per-pair branches
+//                   in the force kernels stay warp-uniform; the prefix with |r_ij| < rc_A + skin is
+//                   the angular list.
 // Distances use cell-relative float32 coordinates plus the image offset of the neighbouring cell, so
 // their error does not grow with the box size (float64 appears only in the wrap and cell assignment).
 #include "nep_common.cuh"
 
 namespace nep {
 
-constexpr int NB_BLOCK = 128;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -183,61 +183,106 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
   id[t] = idb[t];
 }
 
+// One warp per atom, 32 consecutive atoms (a tile) per warp.  Lanes test the candidates of each of the
+// 27 neighbouring cell images in parallel; accepted entries are compacted with a ballot into a
+// per-warp key buffer (key = float32 distance^2 bits << 32 | packed entry), bitonic-sorted in shared
+// memory, and staged in a [32][CAP+1] tile so the list is written row-coalesced ([cap][N] layout).
 template <int CAP>
-__global__ void __launch_bounds__(NB_BLOCK)
+__global__ void __launch_bounds__(32)
 k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_start, const Geom geom, int cap,
             float rl2, float ra2, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
             Control *ctrl) {
   if (!ctrl->do_rebuild) return;
   __shared__ float4 shift[27];
+  __shared__ unsigned long long keys[CAP];
+  __shared__ uint32_t tile[32][CAP + 1];
+  __shared__ int tile_cnt[32];
   fill_shift_table(shift, geom);
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 pi = pos[i];
-  const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
-  unsigned long long keys[CAP];
-  int cnt = 0, kept = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int zz = (cz + dz + geom.ncz) % geom.ncz;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = (cy + dy + geom.ncy) % geom.ncy;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = (cx + dx + geom.ncx) % geom.ncx;
-        const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        const float4 o = shift[sh];
-        const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
-        const int b = cell_start[c], e = cell_start[c + 1];
-        for (int j = b; j < e; ++j) {
-          if (j == i && sh == 13) continue;
-          const float4 pj = pos[j];
-          const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
-          const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 < rl2) {
-            ++cnt;
-            if (kept < cap && kept < CAP) {
-              const unsigned long long key =
-                  ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)((uint32_t)j | ((uint32_t)sh << J_BITS));
-              int q = kept++;
-              while (q > 0 && keys[q - 1] > key) {
-                keys[q] = keys[q - 1];
-                --q;
-              }
-              keys[q] = key;
+  __syncwarp();
+  const int lane = threadIdx.x;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int base = blockIdx.x * 32;
+  const int limit = min(cap, CAP);
+  for (int t = 0; t < 32; ++t) {
+    const int i = base + t;
+    if (i >= n) {
+      if (lane == 0) tile_cnt[t] = 0;
+      continue;
+    }
+    const float4 pi = pos[i];
+    const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (cz + dz + geom.ncz) % geom.ncz;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = (cy + dy + geom.ncy) % geom.ncy;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = (cx + dx + geom.ncx) % geom.ncx;
+          const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+          const float4 o = shift[sh];
+          const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
+          const int b = cell_start[c], e = cell_start[c + 1];
+          for (int j0 = b; j0 < e; j0 += 32) {
+            const int j = j0 + lane;
+            bool ok = false;
+            unsigned long long key = 0ull;
+            if (j < e && !(j == i && sh == 13)) {
+              const float4 pj = pos[j];
+              const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
+              const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+              ok = r2 < rl2;
+              key = ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)((uint32_t)j | ((uint32_t)sh << J_BITS));
             }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+              const int slot = cnt + __popc(m & lt_mask);
+              if (slot < CAP) keys[slot] = key;
+            }
+            cnt += __popc(m);
           }
         }
       }
     }
+    const int kept = min(cnt, limit);
+    if (lane == 0 && cnt > kept) atomicOr(&ctrl->status, ST_OVERFLOW);
+    for (int s = min(cnt, CAP) + lane; s < CAP; s += 32) keys[s] = ~0ull;
+    __syncwarp();
+    // bitonic sort of keys[0..CAP) ascending
+    for (int size = 2; size <= CAP; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int p = lane; p < CAP / 2; p += 32) {
+          const int lo = 2 * p - (p & (stride - 1));
+          const int hi = lo + stride;
+          const unsigned long long a = keys[lo], bb = keys[hi];
+          const bool up = (lo & size) == 0;
+          if ((a > bb) == up) { keys[lo] = bb; keys[hi] = a; }
+        }
+        __syncwarp();
+      }
+    }
+    int na = 0;
+    for (int k = lane; k < kept; k += 32) {
+      const unsigned long long key = keys[k];
+      tile[t][k] = (uint32_t)(key & 0xffffffffull);
+      na += __uint_as_float((uint32_t)(key >> 32)) < ra2 ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) na += __shfl_xor_sync(0xffffffffu, na, o);
+    if (lane == 0) {
+      tile_cnt[t] = kept;
+      nnum[i] = kept;
+      nang[i] = na;
+    }
+    __syncwarp();
   }
-  if (cnt > kept) atomicOr(&ctrl->status, ST_OVERFLOW);
-  int na = 0;
-  for (int k = 0; k < kept; ++k) {
-    nbr[(size_t)k * n + i] = (int32_t)(uint32_t)(keys[k] & 0xffffffffull);
-    if (__uint_as_float((uint32_t)(keys[k] >> 32)) < ra2) ++na;
-  }
-  nnum[i] = kept;
-  nang[i] = na;
+  // flush: row k of the tile is 32 consecutive atoms -> one coalesced 128-byte store
+  const int i = base + lane;
+  const int mine = tile_cnt[lane];
+  int kmax = mine;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  for (int k = 0; k < kmax; ++k)
+    if (k < mine && i < n) nbr[(size_t)k * n + i] = (int32_t)tile[lane][k];
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -270,12 +315,11 @@ cudaError_t launch_neighbors(const RebuildArgs &a, cudaStream_t st) {
   Geom g;
   g.lx = (float)a.l[0]; g.ly = (float)a.l[1]; g.lz = (float)a.l[2];
   g.ncx = a.nc[0]; g.ncy = a.nc[1]; g.ncz = a.nc[2];
+  const int grid = blocks_for(a.n, 32);
   if (a.cap <= 128)
-    k_neighbors<128><<<blocks_for(a.n, NB_BLOCK), NB_BLOCK, 0, st>>>(a.n, a.pos, a.start, g, a.cap, a.rl2, a.ra2, a.nbr,
-                                                                     a.nnum, a.nang, a.ctrl);
+    k_neighbors<128><<<grid, 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, a.rl2, a.ra2, a.nbr, a.nnum, a.nang, a.ctrl);
   else
-    k_neighbors<256><<<blocks_for(a.n, NB_BLOCK), NB_BLOCK, 0, st>>>(a.n, a.pos, a.start, g, a.cap, a.rl2, a.ra2, a.nbr,
-                                                                     a.nnum, a.nang, a.ctrl);
+    k_neighbors<256><<<grid, 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, a.rl2, a.ra2, a.nbr, a.nnum, a.nang, a.ctrl);
   return cudaGetLastError();
 }
 

@@ -4,7 +4,8 @@ Tolerances (float32 path vs float64 oracle):
   neighbour sets        bit-exact (as sets of atom ids), for the radial list and its angular prefix
   forces                max |dF| <= 1e-4 eV/Angstrom (LJ + NEP); NEP-only forces also relative 1e-3 of max |F|
   total energy          |dE| / |E| <= 1e-6
-  site energies         max |dU| <= 2e-6 eV
+  site energies         max |dU| <= 1e-5 eV: U_i ~ -2.2 eV is a float32 sum of ~42 LJ pair terms (|e| up to
+                        0.35 eV) plus the network output; n * eps32 * sum|e| ~ 42 * 6e-8 * 4 eV = 1e-5
   virial                max |dW| <= 1e-5 * max |W|
   descriptors           |dq| <= 2e-5 * max(1, |q|) per component, relative to each column's scale
   10-step trajectory    positions 1e-6 Angstrom, velocities 1e-7 Angstrom/fs
@@ -91,7 +92,7 @@ def test_energy_forces_virial(api, model_params, model, cells):
     Eo, Uo, Fo, Wo = oracle.energy_forces(model, wl.pos, wl.box)
     assert np.abs(F - Fo).max() <= 1e-4
     assert abs(E - Eo) / abs(Eo) <= 1e-6
-    assert np.abs(U - Uo).max() <= 2e-6
+    assert np.abs(U - Uo).max() <= 1e-5
     assert np.abs(W - Wo).max() <= 1e-5 * np.abs(Wo).max()
 
 
@@ -178,18 +179,21 @@ def test_rebuild_policy_does_not_change_physics(api, model_params, c1):
 
 
 def test_atoms_crossing_the_boundary_and_rebuilds(api, model_params, model):
-    """Hot small cell: atoms leave their cells and cross the periodic boundary between rebuilds."""
+    """Hot small cell: atoms leave their cells and cross the periodic boundary between rebuilds; the
+    60-step GPU trajectory follows the oracle's trajectory from the same seeded start."""
     wl = ni.fcc_cu_workload(4, temperature=1500.0, sigma=0.1, seed=33)
     with api.NEP(model_params) as nep:
         nep.set_state(wl.pos, wl.vel, wl.box)
         nep.step(1.0, 60)
         x, v = nep.get_state()
-        E, F, W = nep.compute()
+        th = nep.thermo()
         assert nep.counters()["rebuilds"] >= 2
     assert np.all((x >= 0) & (x < wl.box))
-    Eo, Uo, Fo, Wo = oracle.energy_forces(model, x, wl.box)
-    assert np.abs(F - Fo).max() <= 1e-4
-    assert abs(E - Eo) / abs(Eo) <= 1e-6
+    xo, vo, tho = oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, 1.0, 60)
+    dx = x - xo
+    dx -= wl.box * np.round(dx / wl.box)
+    assert np.abs(dx).max() <= 1e-5
+    assert abs(th["pe"] - tho[-1, 0]) / abs(tho[-1, 0]) <= 1e-6
 
 
 def test_nve_energy_drift_gpu(api, model_params, c1):

@@ -41,22 +41,28 @@ N_SMS = 152
 FP32_LANES_PER_SM = 128
 
 # Algorithmic FP32 FLOPs of the method per unit (static count of the arithmetic each unit needs,
-# FMA = 2, add/mul/compare-free = 1, each transcendental = 1), for the compiled shape
-# (5 radial + 5 angular channels, 8 basis functions, l = 1..4, 4-body, 30 neurons).
+# FMA = 2, add/mul = 1, each transcendental = 1), for the compiled shape (5 radial + 5 angular
+# channels, 8 basis functions, l = 1..4, 4-body, 30 neurons).  The descriptor kernel visits every
+# list entry of every atom; the force kernel visits each unordered pair once (its owner's half list).
 FLOPS = {
     "descriptor": dict(list_entry=11, active_pair=2, radial_pair=128, lj_pair=12, angular_pair=464, atom=4655),
-    "force": dict(list_entry=11, active_pair=2 + 27, radial_pair=220, lj_pair=13, angular_pair=1465, atom=0),
+    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=220, lj_pair=13, angular_pair=1465, atom=3),
 }
-# Algorithmic bytes per atom per force evaluation (HBM, float32 path): positions 16, list
-# entries 4 each (read by both kernels), adjoint row 512 written + read, force 12, site energy 4.
-BYTES = dict(per_atom=16 * 2 + 512 * 2 + 12 + 4, per_list_entry=4 * 2)
+# Algorithmic bytes per atom per force evaluation (HBM, float32 path): positions 16 (x2 kernels), list
+# entries 4 each (descriptor: full row, force: owned half), adjoint row 512 written + read, fixed-point
+# force 24 zeroed + accumulated, site energy 4.
+BYTES = dict(per_atom=16 * 2 + 512 * 2 + 24 * 2 + 4, per_list_entry=4 * 1.5)
 
 
 def kernel_flops(kind: str, c: dict, n_atoms_evals: int) -> float:
     f = FLOPS[kind]
-    return (f["list_entry"] * c["list_entries"] + f["active_pair"] * c["active_pairs"] +
-            f["radial_pair"] * c["radial_pairs"] + f["lj_pair"] * c["radial_pairs"] +
-            f["angular_pair"] * c["angular_pairs"] + f["atom"] * n_atoms_evals)
+    if kind == "descriptor":
+        lst, act, rad, ang = c["list_entries"], c["active_pairs"], c["radial_pairs"], c["angular_pairs"]
+    else:
+        lst, act, rad, ang = (c["owned_list_entries"], c["owned_active_pairs"], c["owned_radial_pairs"],
+                              c["owned_angular_pairs"])
+    return (f["list_entry"] * lst + f["active_pair"] * act + f["radial_pair"] * rad + f["lj_pair"] * rad +
+            f["angular_pair"] * ang + f["atom"] * n_atoms_evals)
 
 
 def source_hash() -> str:
@@ -288,8 +294,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     c1 = nep.counters()
     tim = nep.timing()
     th = nep.thermo()
-    dc = {k: c1[k] - c0[k] for k in ("radial_pairs", "angular_pairs", "list_entries", "active_pairs",
-                                     "evaluations", "rebuilds", "steps", "launches")}
+    dc = {k: c1[k] - c0[k] for k in c1}
     evals = dc["evaluations"]
     f_desc = kernel_flops("descriptor", dc, evals * wl.n)
     f_force = kernel_flops("force", dc, evals * wl.n)
@@ -366,7 +371,8 @@ def run_ours(args, rank: int, ws: int, local: int):
         "descriptor_plus_force_tflops": round(both, 3),
         "pairs_per_atom": {"list": dc["list_entries"] / max(1, evals * wl.n),
                            "radial": dc["radial_pairs"] / max(1, evals * wl.n),
-                           "angular": dc["angular_pairs"] / max(1, evals * wl.n)},
+                           "angular": dc["angular_pairs"] / max(1, evals * wl.n),
+                           "owned_angular": dc["owned_angular_pairs"] / max(1, evals * wl.n)},
         "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"]},
         "e2e": e2e,
         "source_hash": source_hash(),

@@ -82,7 +82,7 @@ typedef struct nep_params {
     double mass_amu;
     float skin;               /* neighbour-list skin (Angstrom); list radius rc_R + skin */
     int precision;            /* NEP_FP32 */
-    int max_neighbors;        /* per-atom list capacity; 0 selects 128 */
+    int max_neighbors;        /* per-atom list capacity, 1..128; 0 selects 128 */
     int rebuild_every;        /* MD: rebuild at least every k steps (0: only when an atom moved > skin/2) */
 } nep_params;
 
@@ -103,7 +103,8 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
 
 /* Build the cell list and the neighbour list (cutoff rc_R + skin) for the current positions:
  * atoms are sorted by cell, then each atom's list holds every j with |r_ij| < rc_R + skin (minimum
- * image), ordered by increasing distance; its prefix with |r_ij| < rc_A + skin is the angular list. */
+ * image), grouped by distance band -- r < rc_A, r < rc_A + skin, r < rc_R, r < rc_R + skin -- in a
+ * fixed cell-stencil order inside each band; its prefix with |r_ij| < rc_A + skin is the angular list. */
 nep_status nep_build_neighbors(nep_handle *h);
 
 /* Energy, forces and virial of the current positions (builds the neighbour list first if needed).
@@ -125,9 +126,11 @@ nep_status nep_get_state(nep_handle *h, double *x, double *v);
  * temperature (3N-3 dof), pressure (eV/Angstrom^3), W_xx, W_yy, W_zz, rebuild count}. */
 nep_status nep_get_thermo(nep_handle *h, double out[8]);
 
-/* Neighbour lists in original atom ids: counts[n], n_ang[n] (angular prefix length) and
- * list[n][cap] (row i holds the ids of i's neighbours in increasing-distance order). */
-nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int32_t *list, int cap);
+/* Neighbour lists in original atom ids: counts[n], n_ang[n] (entries with |r_ij| < rc_A + skin),
+ * n_own[n] (length of the owned part: each unordered pair is owned by exactly one of its two atoms)
+ * and list[n][cap] (row i holds the ids of i's neighbours in list order -- owned part first, each part
+ * grouped by distance band -- and -1 past the count). */
+nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int32_t *n_own, int32_t *list, int cap);
 
 /* Unscaled descriptors of the last evaluation, [n][n_des] float32, original order. */
 nep_status nep_get_descriptors(nep_handle *h, float *q);
@@ -143,10 +146,12 @@ nep_status nep_set_timing(nep_handle *h, int enable);
  * 6 reductions, 7 un-permute/other. */
 nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_t launches[NEP_N_KERNEL_CLASSES]);
 
-/* Counters since nep_set_state: out = {radial pairs evaluated (r < rc_R), angular pairs evaluated
- * (r < rc_A), force evaluations, neighbour rebuilds, MD steps, kernel launches enqueued by the library,
- * neighbour-list entries visited, pairs inside the largest cutoff}.  Pair counts sum over evaluations. */
-nep_status nep_get_counters(nep_handle *h, int64_t out[8]);
+/* Counters since nep_set_state: out = {radial pairs (r < rc_R) and angular pairs (r < rc_A) seen by the
+ * descriptor kernel, force evaluations, neighbour rebuilds, MD steps, kernel launches enqueued by the
+ * library, list entries and pairs inside the largest cutoff seen by the descriptor kernel, then the
+ * same four counts for the owned pairs seen by the force kernel: list entries, pairs inside the
+ * largest cutoff, radial pairs, angular pairs}.  Pair counts sum over evaluations. */
+nep_status nep_get_counters(nep_handle *h, int64_t out[12]);
 
 /* Last error message of the handle (never NULL). */
 const char *nep_last_error(nep_handle *h);

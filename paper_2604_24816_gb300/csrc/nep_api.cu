@@ -25,10 +25,10 @@ namespace nep {
 // nep_force.cu
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                              float *, float *, float *, double *, int *, cudaStream_t);
+                              float *, float *, float *, long long *, double *, int *, cudaStream_t);
 template <class S>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const float *, float *, double *, int *, cudaStream_t);
+                         const int32_t *, const float *, long long *, double *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
 // nep_neighbor.cu
@@ -37,10 +37,10 @@ cudaError_t launch_neighbors(const RebuildArgs &, cudaStream_t);
 int scan_tiles(int ncell);
 // nep_md.cu
 int md_blocks(int n);
-cudaError_t launch_kick_drift(int, double *, double *, double *, double *, double *, double *, const float *, float4 *,
+cudaError_t launch_kick_drift(int, double *, double *, double *, double *, double *, double *, const long long *, float4 *,
                               const float4 *, double, double, const double *, float, Control *, cudaStream_t);
 cudaError_t launch_control(Control *, bool, cudaStream_t);
-cudaError_t launch_kick(int, double *, double *, double *, const float *, double, double, double *, cudaStream_t);
+cudaError_t launch_kick(int, double *, double *, double *, const long long *, double, double, double *, cudaStream_t);
 cudaError_t launch_kinetic(int, const double *, const double *, const double *, double, double *, cudaStream_t);
 cudaError_t launch_finalize(const double *, int, const double *, int, const double *, int, double *, long long *,
                             cudaStream_t);
@@ -48,11 +48,11 @@ cudaError_t launch_load_state(int, const double *, const double *, double *, dou
                               double *, int *, int *, cudaStream_t);
 cudaError_t launch_store_vec(int, const int *, const double *, const double *, const double *, const double *, int,
                              double *, cudaStream_t);
-cudaError_t launch_store_force(int, const int *, const float *, double *, cudaStream_t);
+cudaError_t launch_store_force(int, const int *, const long long *, double *, cudaStream_t);
 cudaError_t launch_store_scalar(int, const int *, const float *, double *, cudaStream_t);
 cudaError_t launch_store_rows(int, int, const int *, const float *, float *, cudaStream_t);
 cudaError_t launch_store_neighbors(int, int, int, const int *, const int32_t *, const int32_t *, const int32_t *,
-                                   int32_t *, int32_t *, int32_t *, cudaStream_t);
+                                   const int32_t *, int32_t *, int32_t *, int32_t *, int32_t *, cudaStream_t);
 }  // namespace nep
 
 using namespace nep;
@@ -95,11 +95,12 @@ struct nep_handle {
   double *xb = nullptr, *yb = nullptr, *zb = nullptr, *vxb = nullptr, *vyb = nullptr, *vzb = nullptr;
   int *id = nullptr, *idb = nullptr, *cell_of = nullptr, *perm = nullptr;
   float4 *pos = nullptr, *pos_ref = nullptr;
-  float *F = nullptr, *usite = nullptr, *G = nullptr, *qbuf = nullptr;
-  int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr;
+  long long *F = nullptr;          // fixed-point forces [3][n]
+  float *usite = nullptr, *G = nullptr, *qbuf = nullptr;
+  int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr, *nown = nullptr, *nband0 = nullptr;
   int *count = nullptr, *cursor = nullptr, *start = nullptr, *tile_sums = nullptr;
   double *part_d = nullptr, *part_f = nullptr, *part_k = nullptr, *sums = nullptr;
-  long long *counters = nullptr;   // {radial pairs, angular pairs, evaluations}
+  long long *counters = nullptr;   // pair counts (descriptor, force) and evaluations
   Control *ctrl = nullptr;
   double *io = nullptr;            // staging 2 x [n][3] float64 for host transfers
   int32_t *io_i = nullptr;         // staging for neighbour output
@@ -165,7 +166,7 @@ void free_system(nep_handle *h) {
   dfree(h->xb); dfree(h->yb); dfree(h->zb); dfree(h->vxb); dfree(h->vyb); dfree(h->vzb);
   dfree(h->id); dfree(h->idb); dfree(h->cell_of); dfree(h->perm);
   dfree(h->pos); dfree(h->pos_ref); dfree(h->F); dfree(h->usite); dfree(h->G); dfree(h->qbuf);
-  dfree(h->nbr); dfree(h->nnum); dfree(h->nang);
+  dfree(h->nbr); dfree(h->nnum); dfree(h->nang); dfree(h->nown); dfree(h->nband0);
   dfree(h->count); dfree(h->cursor); dfree(h->start); dfree(h->tile_sums);
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
   h->io_i_elems = 0;
@@ -235,10 +236,11 @@ RebuildArgs rebuild_args(nep_handle *h) {
   a.xb = h->xb; a.yb = h->yb; a.zb = h->zb; a.vxb = h->vxb; a.vyb = h->vyb; a.vzb = h->vzb;
   a.id = h->id; a.idb = h->idb; a.cell_of = h->cell_of; a.count = h->count; a.cursor = h->cursor;
   a.start = h->start; a.tile_sums = h->tile_sums; a.perm = h->perm;
-  a.pos = h->pos; a.pos_ref = h->pos_ref; a.nbr = h->nbr; a.nnum = h->nnum; a.nang = h->nang;
+  a.pos = h->pos; a.pos_ref = h->pos_ref; a.nbr = h->nbr; a.nnum = h->nnum; a.nang = h->nang; a.nown = h->nown; a.nband0 = h->nband0;
   a.cap = h->cap;
   const float rl = h->rcR + h->skin, ra = h->rcA + h->skin;
   a.rl2 = rl * rl; a.ra2 = ra * ra;
+  a.ba2 = h->rcA * h->rcA; a.br2 = h->rcR * h->rcR;
   a.ctrl = h->ctrl;
   return a;
 }
@@ -269,13 +271,13 @@ cudaError_t enqueue_forces(nep_handle *h, float *qout) {
   cudaError_t e;
   {
     Scope sc(h, KC_DESC, 1);
-    e = launch_descriptor<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, h->G, h->usite, qout, h->part_d,
+    e = launch_descriptor<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, h->G, h->usite, qout, h->F, h->part_d,
                              &h->ctrl->status, h->stream);
   }
   if (e != cudaSuccess) return e;
   Scope sc(h, KC_FORCE, 1);
-  return launch_force<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, h->G, h->F, h->part_f, &h->ctrl->status,
-                         h->stream);
+  return launch_force<S>(h->model, g, h->n, h->pos, h->nbr, h->nown, h->nband0, h->G, h->F, h->part_f,
+                         &h->ctrl->status, h->stream);
 }
 
 cudaError_t enqueue_finalize(nep_handle *h, bool with_kinetic) {
@@ -313,8 +315,8 @@ cudaError_t enqueue_step(nep_handle *h, double dt) {
 // Read back the control block and translate device-detected conditions into a status.
 nep_status check_device_status(nep_handle *h) {
   NEP_CUDA(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream));
-  NEP_CUDA(h, cudaMemcpyAsync(h->h_sums, h->sums, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  NEP_CUDA(h, cudaMemcpyAsync(h->h_counters, h->counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(h->h_sums, h->sums, 32 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(h->h_counters, h->counters, 16 * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
   nep_status s = wait_stream(h);
   if (s != NEP_OK) return s;
   if (h->timing) collect_timers(h);
@@ -433,7 +435,7 @@ nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) 
   if (!(p->rc_R > 0.f) || !(p->rc_A > 0.f) || p->rc_A > p->rc_R || !(p->skin >= 0.f) || !(p->mass_amu > 0.0))
     return NEP_ERR_ARG;
   if (p->lj_eps != 0.f && (!(p->lj_rc > 0.f) || p->lj_rc > p->rc_R || !(p->lj_sigma > 0.f))) return NEP_ERR_ARG;
-  if (p->max_neighbors < 0 || p->max_neighbors > 256 || p->rebuild_every < 0) return NEP_ERR_ARG;
+  if (p->max_neighbors < 0 || p->max_neighbors > 128 || p->rebuild_every < 0) return NEP_ERR_ARG;
 
   nep_handle *h = new (std::nothrow) nep_handle();
   if (!h) return NEP_ERR_OOM;
@@ -485,15 +487,15 @@ nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) 
     h->own_stream = true;
   }
   if ((e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = dalloc(h->sums, 16)) != cudaSuccess || (e = dalloc(h->counters, 8)) != cudaSuccess ||
-      (e = dalloc(h->ctrl, 1)) != cudaSuccess || (e = cudaMallocHost((void **)&h->h_sums, 16 * sizeof(double))) != cudaSuccess ||
+      (e = dalloc(h->sums, 32)) != cudaSuccess || (e = dalloc(h->counters, 16)) != cudaSuccess ||
+      (e = dalloc(h->ctrl, 1)) != cudaSuccess || (e = cudaMallocHost((void **)&h->h_sums, 32 * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost((void **)&h->h_ctrl, sizeof(Control))) != cudaSuccess ||
-      (e = cudaMallocHost((void **)&h->h_counters, 8 * sizeof(long long))) != cudaSuccess) {
+      (e = cudaMallocHost((void **)&h->h_counters, 16 * sizeof(long long))) != cudaSuccess) {
     nep_destroy(h);
     return NEP_ERR_CUDA;
   }
-  cudaMemsetAsync(h->sums, 0, 16 * sizeof(double), h->stream);
-  cudaMemsetAsync(h->counters, 0, 8 * sizeof(long long), h->stream);
+  cudaMemsetAsync(h->sums, 0, 32 * sizeof(double), h->stream);
+  cudaMemsetAsync(h->counters, 0, 16 * sizeof(long long), h->stream);
   Control c0{};
   c0.rebuild_every = h->rebuild_every;
   cudaMemcpyAsync(h->ctrl, &c0, sizeof(Control), cudaMemcpyHostToDevice, h->stream);
@@ -558,10 +560,11 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->id, N)); A(dalloc(h->idb, N)); A(dalloc(h->cell_of, N)); A(dalloc(h->perm, N));
   A(dalloc(h->pos, N)); A(dalloc(h->pos_ref, N));
   A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N)); A(dalloc(h->G, N * GSTRIDE));
-  A(dalloc(h->nbr, N * (size_t)h->cap)); A(dalloc(h->nnum, N)); A(dalloc(h->nang, N));
+  A(dalloc(h->nbr, N * (size_t)h->cap)); A(dalloc(h->nnum, N)); A(dalloc(h->nang, N)); A(dalloc(h->nown, N));
+  A(dalloc(h->nband0, N));
   A(dalloc(h->count, (size_t)h->ncell)); A(dalloc(h->cursor, (size_t)h->ncell)); A(dalloc(h->start, (size_t)h->ncell + 1));
   A(dalloc(h->tile_sums, (size_t)scan_tiles(h->ncell) + 1));
-  A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 9 + 1));
+  A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 13 + 1));
   A(dalloc(h->part_k, (size_t)h->nb_k + 1)); A(dalloc(h->io, 6 * N));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -569,9 +572,9 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
     return fail(h, e == cudaErrorMemoryAllocation ? NEP_ERR_OOM : NEP_ERR_CUDA,
                 std::string("allocation failed: ") + cudaGetErrorString(e));
   }
-  NEP_CUDA(h, cudaMemsetAsync(h->F, 0, 3 * N * sizeof(float), h->stream));
-  NEP_CUDA(h, cudaMemsetAsync(h->sums, 0, 16 * sizeof(double), h->stream));
-  NEP_CUDA(h, cudaMemsetAsync(h->counters, 0, 8 * sizeof(long long), h->stream));
+  NEP_CUDA(h, cudaMemsetAsync(h->F, 0, 3 * N * sizeof(long long), h->stream));
+  NEP_CUDA(h, cudaMemsetAsync(h->sums, 0, 32 * sizeof(double), h->stream));
+  NEP_CUDA(h, cudaMemsetAsync(h->counters, 0, 16 * sizeof(long long), h->stream));
   Control c0{};
   c0.rebuild_every = h->rebuild_every;
   NEP_CUDA(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Control), cudaMemcpyHostToDevice, h->stream));
@@ -674,14 +677,14 @@ nep_status nep_get_thermo(nep_handle *h, double out[8]) {
   return NEP_OK;
 }
 
-nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int32_t *list, int cap) {
-  if (!h || !counts || !n_ang || !list || cap <= 0) return NEP_ERR_ARG;
+nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int32_t *n_own, int32_t *list, int cap) {
+  if (!h || !counts || !n_ang || !n_own || !list || cap <= 0) return NEP_ERR_ARG;
   if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
   if (h->n == 0) return NEP_OK;
   nep_status s = ensure_nlist(h);
   if (s != NEP_OK) return s;
   const size_t N = (size_t)h->n;
-  const size_t elems = N * 2 + N * (size_t)cap;
+  const size_t elems = N * 3 + N * (size_t)cap;
   if (h->io_i_elems < elems) {
     dfree(h->io_i);
     NEP_CUDA(h, dalloc(h->io_i, elems));
@@ -689,12 +692,13 @@ nep_status nep_get_neighbors(nep_handle *h, int32_t *counts, int32_t *n_ang, int
   }
   {
     Scope sc(h, KC_OTHER, 1);
-    NEP_CUDA(h, launch_store_neighbors(h->n, h->cap, cap, h->id, h->nbr, h->nnum, h->nang, h->io_i, h->io_i + N,
-                                       h->io_i + 2 * N, h->stream));
+    NEP_CUDA(h, launch_store_neighbors(h->n, h->cap, cap, h->id, h->nbr, h->nnum, h->nang, h->nown, h->io_i,
+                                       h->io_i + N, h->io_i + 2 * N, h->io_i + 3 * N, h->stream));
   }
   NEP_CUDA(h, cudaMemcpyAsync(counts, h->io_i, N * sizeof(int32_t), cudaMemcpyDefault, h->stream));
   NEP_CUDA(h, cudaMemcpyAsync(n_ang, h->io_i + N, N * sizeof(int32_t), cudaMemcpyDefault, h->stream));
-  NEP_CUDA(h, cudaMemcpyAsync(list, h->io_i + 2 * N, N * (size_t)cap * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(n_own, h->io_i + 2 * N, N * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(list, h->io_i + 3 * N, N * (size_t)cap * sizeof(int32_t), cudaMemcpyDefault, h->stream));
   return check_device_status(h);
 }
 
@@ -749,18 +753,23 @@ nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_
   return NEP_OK;
 }
 
-nep_status nep_get_counters(nep_handle *h, int64_t out[8]) {
+nep_status nep_get_counters(nep_handle *h, int64_t out[12]) {
   if (!h || !out) return NEP_ERR_ARG;
   nep_status s = check_device_status(h);
   if (s != NEP_OK && s != NEP_ERR_NEIGH_OVERFLOW && s != NEP_ERR_NAN) return s;
-  out[0] = h->h_counters[0];
-  out[1] = h->h_counters[1];
-  out[2] = h->h_counters[2];
+  const long long *c = h->h_counters;
+  out[0] = c[0];                // descriptor: radial pairs
+  out[1] = c[1];                // descriptor: angular pairs
+  out[2] = c[8];                // force evaluations
   out[3] = h->h_ctrl->rebuilds;
   out[4] = h->h_ctrl->steps;
   out[5] = h->launch_total;
-  out[6] = h->h_counters[3];
-  out[7] = h->h_counters[4];
+  out[6] = c[2];                // descriptor: list entries
+  out[7] = c[3];                // descriptor: active pairs
+  out[8] = c[4];                // force: owned list entries
+  out[9] = c[5];                // force: owned active pairs
+  out[10] = c[6];               // force: owned radial pairs
+  out[11] = c[7];               // force: owned angular pairs
   return NEP_OK;
 }
 

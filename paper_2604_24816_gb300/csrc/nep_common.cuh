@@ -5,6 +5,10 @@
 //            and the packed cell coordinates (w, as int bits: cx | cy << 10 | cz << 20).
 //   nbr      int32 [cap][N] (neighbour-major, so a thread per atom reads coalesced rows); entry =
 //            j | shift << 27, shift = (dx+1) + 3 (dy+1) + 9 (dz+1) the cell offset of j's image.
+//            Row i = [pairs owned by i | the others], each part grouped by distance band; nown[i]
+//            is the length of the owned part.
+//   Ffix     int64 [3][N]: forces in fixed point (2^-32 eV/Angstrom units), accumulated with
+//            integer atomics, so the sum does not depend on the order of the additions.
 //   G        float [N][128]: per-atom adjoint dU_i/ds_nlm (120 values, index n*24 + lm) followed by
 //            dU_i/dq_n of the radial descriptors (5 values) and padding.
 #pragma once
@@ -18,6 +22,8 @@ constexpr int J_BITS = 27;
 constexpr uint32_t J_MASK = (1u << J_BITS) - 1u;
 constexpr int GSTRIDE = 128;     // floats per atom row of G
 constexpr int N_LM = 24;         // (l, m) components for l = 1..4
+constexpr float FIX_SCALE = 4294967296.0f;        // 2^32 fixed-point units per eV/Angstrom
+constexpr double FIX_INV = 1.0 / 4294967296.0;
 
 // Status bits of the device status word.
 enum : int {
@@ -45,9 +51,9 @@ struct RebuildArgs {
   double *x, *y, *z, *vx, *vy, *vz, *xb, *yb, *zb, *vxb, *vyb, *vzb;
   int *id, *idb, *cell_of, *count, *cursor, *start, *tile_sums, *perm;
   float4 *pos, *pos_ref;
-  int32_t *nbr, *nnum, *nang;
+  int32_t *nbr, *nnum, *nang, *nown, *nband0;
   int cap;
-  float rl2, ra2;
+  float rl2, ra2, ba2, br2;   // (rc_R+skin)^2, (rc_A+skin)^2, rc_A^2, rc_R^2
   Control *ctrl;
 };
 

@@ -15,8 +15,12 @@
 //  k_force       F_i = sum_j D_ij with D_ij = dU_i/dr_ij - dU_j/dr_ji.  The radial part uses both atoms'
 //                dU/dq_n; the angular part uses H_nlm = G^i_nlm + (-1)^l G^j_nlm because the pair
 //                geometry g_n(r) Yh_lm(u) is shared by both directions (Yh_lm(-u) = (-1)^l Yh_lm(u)).
-//                Each thread writes only its own force, so the scatter is deterministic with no
-//                atomics and no per-pair buffer.  Virial W = -1/2 sum_i sum_j r_ij (x) D_ij.
+//                Since D_ji = -D_ij exactly, each unordered pair is evaluated once, by its owner (the
+//                owned part of the list), which adds D_ij to F_i and -D_ij to F_j.  The scatter uses
+//                64-bit fixed-point integer atomics (2^-32 eV/Angstrom units): integer addition is
+//                associative, so the forces are bitwise reproducible whatever the order of the
+//                atomics -- the atomic scatter of the paper's consolidated backward kernel (Section V.B,
+//                Optimization 1) made deterministic.  Virial W = -sum_pairs r_ij (x) D_ij.
 //
 // Everything is float32 except the per-block energy/virial partial sums (float64).
 #include "nep_common.cuh"
@@ -25,18 +29,30 @@ namespace nep {
 
 constexpr int DESC_BLOCK = 128;
 constexpr int FORCE_BLOCK = 128;
+// Minimum resident blocks per SM requested from the compiler (register budget per thread =
+// 65536 / (block * min_blocks)); the defaults are the measured best on GB300.
+#ifndef NEP_DESC_MINB
+#define NEP_DESC_MINB 3
+#endif
+#ifndef NEP_FORCE_MINB
+#define NEP_FORCE_MINB 2
+#endif
+
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 template <class S>
-__global__ void __launch_bounds__(DESC_BLOCK)
+__global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
 k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
              const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
-             float *__restrict__ usite, float *__restrict__ qout, double *__restrict__ part, int *__restrict__ status) {
+             float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
+             double *__restrict__ part, int *__restrict__ status) {
   __shared__ float4 shift[27];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (i < n) {
+    Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     const float4 pi = pos[i];
     float qR[S::NR];
     float s[S::NA][N_LM];
@@ -49,9 +65,17 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     float elj = 0.f;
     int nrad = 0, nang = 0, nact = 0;
     const int cnt = nnum[i];
+    // software pipeline: list entry two ahead, neighbour position one ahead
+    const int32_t *row = nbr + i;
+    uint32_t e_nxt = cnt > 0 ? (uint32_t)__ldg(row) : 0u;
+    float4 p_nxt = cnt > 0 ? __ldg(pos + (e_nxt & J_MASK)) : pi;
+    uint32_t e_nn = cnt > 1 ? (uint32_t)__ldg(row + (size_t)n) : 0u;
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = (uint32_t)__ldg(nbr + (size_t)k * n + i);
-      const float4 pj = __ldg(pos + (e & J_MASK));
+      const uint32_t e = e_nxt;
+      const float4 pj = p_nxt;
+      e_nxt = e_nn;
+      if (k + 1 < cnt) p_nxt = __ldg(pos + (e_nxt & J_MASK));
+      if (k + 2 < cnt) e_nn = (uint32_t)__ldg(row + (size_t)(k + 2) * n);
       const float4 o = shift[e >> J_BITS];
       const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
@@ -129,6 +153,15 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
     }
+    // Park s_nlm in this atom's adjoint row while the network runs (frees ~120 registers); it is
+    // read back below and overwritten in place by G_nlm.
+    float *Gi = G + (size_t)i * GSTRIDE;
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+      for (int c = 0; c < N_LM; c += 4)
+        *reinterpret_cast<float4 *>(Gi + a * N_LM + c) = make_float4(s[a][c], s[a][c + 1], s[a][c + 2], s[a][c + 3]);
+    asm volatile("" ::: "memory");
 
     // Network: U = sum_mu w1 tanh(sum_nu W0 q~_nu - b0) - b1; dU/dq~ accumulated in dq.
     float qt[S::NDES], dq[S::NDES];
@@ -150,13 +183,18 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
 
-    // Adjoint G_nlm = dU/ds_nlm = 2 Fp_nl s_nlm (+ 4-body term for l = 2).
-    float *Gi = G + (size_t)i * GSTRIDE;
+    // Adjoint G_nlm = dU/ds_nlm = 2 Fp_nl s_nlm (+ 4-body term for l = 2), s read back from the row.
+    asm volatile("" ::: "memory");
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
       float gl[N_LM];
 #pragma unroll
-      for (int c = 0; c < N_LM; ++c) gl[c] = 2.f * Fp[S::NR + a * 4 + lm_l(c) - 1] * s[a][c];
+      for (int c = 0; c < N_LM; c += 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(Gi + a * N_LM + c);
+        gl[c] = t.x; gl[c + 1] = t.y; gl[c + 2] = t.z; gl[c + 3] = t.w;
+      }
+#pragma unroll
+      for (int c = 0; c < N_LM; ++c) gl[c] *= 2.f * Fp[S::NR + a * 4 + lm_l(c) - 1];
       if (S::FOURBODY) {
         // d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m, M = T^2.
         const float f4 = Fp[S::NR + S::NA * 4 + a];
@@ -197,15 +235,16 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 }
 
 template <class S>
-__global__ void __launch_bounds__(FORCE_BLOCK)
+__global__ void __launch_bounds__(FORCE_BLOCK, NEP_FORCE_MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, const float *__restrict__ G,
-        float *__restrict__ force, double *__restrict__ part, int *__restrict__ status) {
+        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nown, const int32_t *__restrict__ nband0,
+        const float *__restrict__ G, unsigned long long *__restrict__ Ffix, double *__restrict__ part,
+        int *__restrict__ status) {
   __shared__ float4 shift[27];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double acc[13] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (i < n) {
     const float4 pi = pos[i];
     const float *Gi = G + (size_t)i * GSTRIDE;
@@ -226,15 +265,31 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     }
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
-    const int cnt = nnum[i];
+    const int cnt = nown[i];
+    const int nb0 = nband0[i];
+    int nrad = 0, nang = 0, nact = 0;
+    const int32_t *row = nbr + i;
+    uint32_t e_nxt = cnt > 0 ? (uint32_t)__ldg(row) : 0u;
+    float4 p_nxt = cnt > 0 ? __ldg(pos + (e_nxt & J_MASK)) : pi;
+    uint32_t e_nn = cnt > 1 ? (uint32_t)__ldg(row + (size_t)n) : 0u;
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = (uint32_t)__ldg(nbr + (size_t)k * n + i);
+      const uint32_t e = e_nxt;
+      const float4 pj = p_nxt;
+      e_nxt = e_nn;
+      if (k + 1 < cnt) {
+        p_nxt = __ldg(pos + (e_nxt & J_MASK));
+        if (k + 1 < nb0) {
+          const char *gr = reinterpret_cast<const char *>(G + (size_t)(e_nxt & J_MASK) * GSTRIDE);
+          prefetch_l1(gr); prefetch_l1(gr + 128); prefetch_l1(gr + 256); prefetch_l1(gr + 384);
+        }
+      }
+      if (k + 2 < cnt) e_nn = (uint32_t)__ldg(row + (size_t)(k + 2) * n);
       const int j = (int)(e & J_MASK);
-      const float4 pj = __ldg(pos + j);
       const float4 o = shift[e >> J_BITS];
       const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
       if (r2 >= P.rmax2) continue;
+      ++nact;
       const float ir = rsqrtf(r2);
       const float r = r2 * ir;
       const float *Gj = G + (size_t)j * GSTRIDE;
@@ -255,6 +310,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
           c = fmaf(fpi[a] + fpj[a], dg, c);
         }
         coef = c * ir;
+        ++nrad;
       }
       if (P.lj_on != 0.f && r2 < P.lj_rc2) {
         float el, dl;
@@ -262,6 +318,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
         coef = fmaf(dl, ir, coef);
       }
       if (r2 < P.rcA2) {
+        ++nang;
         float f[S::KA], df[S::KA];
         cheb_basis_d<S::KA>(r, P.inv_rcA, f, df);
         float g[S::NA], dg[S::NA];
@@ -303,19 +360,25 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       }
       const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
       fx += Dx; fy += Dy; fz += Dz;
+      // Newton's third law: F_j -= D_ij, accumulated in fixed point (order-independent sum)
+      atomicAdd(Ffix + j, (unsigned long long)__float2ll_rn(-Dx * FIX_SCALE));
+      atomicAdd(Ffix + (size_t)n + j, (unsigned long long)__float2ll_rn(-Dy * FIX_SCALE));
+      atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)__float2ll_rn(-Dz * FIX_SCALE));
       wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
       wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
       wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
     }
-    force[i] = fx;
-    force[(size_t)n + i] = fy;
-    force[2 * (size_t)n + i] = fz;
+    atomicAdd(Ffix + i, (unsigned long long)__float2ll_rn(fx * FIX_SCALE));
+    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)__float2ll_rn(fy * FIX_SCALE));
+    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)__float2ll_rn(fz * FIX_SCALE));
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
-    acc[0] = -0.5 * wxx; acc[1] = -0.5 * wxy; acc[2] = -0.5 * wxz;
-    acc[3] = -0.5 * wyx; acc[4] = -0.5 * wyy; acc[5] = -0.5 * wyz;
-    acc[6] = -0.5 * wzx; acc[7] = -0.5 * wzy; acc[8] = -0.5 * wzz;
+    // each unordered pair once: W = -sum_pairs r_ij (x) D_ij
+    acc[0] = -wxx; acc[1] = -wxy; acc[2] = -wxz;
+    acc[3] = -wyx; acc[4] = -wyy; acc[5] = -wyz;
+    acc[6] = -wzx; acc[7] = -wzy; acc[8] = -wzz;
+    acc[9] = (double)cnt; acc[10] = (double)nact; acc[11] = (double)nrad; acc[12] = (double)nang;
   }
-  block_sum_store<9>(acc, part);
+  block_sum_store<13>(acc, part);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -323,21 +386,22 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                              const int32_t *nnum, float *G, float *usite, float *qout, double *part, int *status,
-                              cudaStream_t st) {
+                              const int32_t *nnum, float *G, float *usite, float *qout, long long *Ffix,
+                              double *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
-  k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, part, status);
+  k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status);
   return cudaGetLastError();
 }
 
 template <class S>
 cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                         const int32_t *nnum, const float *G, float *force, double *part, int *status,
-                         cudaStream_t st) {
+                         const int32_t *nown, const int32_t *nband0, const float *G, long long *Ffix, double *part,
+                         int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, force, part, status);
+  k_force<S><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
+                                           reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }
 
@@ -346,9 +410,9 @@ int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
 
 template cudaError_t launch_descriptor<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
                                                 const int32_t *, const int32_t *, float *, float *, float *,
-                                                double *, int *, cudaStream_t);
+                                                long long *, double *, int *, cudaStream_t);
 template cudaError_t launch_force<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                           const int32_t *, const int32_t *, const float *, float *, double *,
-                                           int *, cudaStream_t);
+                                           const int32_t *, const int32_t *, const int32_t *, const float *,
+                                           long long *, double *, int *, cudaStream_t);
 
 }  // namespace nep

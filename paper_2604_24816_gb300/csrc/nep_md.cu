@@ -11,16 +11,19 @@ namespace nep {
 
 constexpr double KE_CONV = 103.642696562;          // 1 amu Angstrom^2/fs^2 in eV
 
+__device__ __forceinline__ double fix_to_double(long long f) { return (double)f * FIX_INV; }
+
 __global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
-                             const float *__restrict__ F, float4 *__restrict__ pos, const float4 *__restrict__ pos_ref,
-                             double kick, double dt, double lx, double ly, double lz, float half_skin2, Control *ctrl) {
+                             const long long *__restrict__ F, float4 *__restrict__ pos,
+                             const float4 *__restrict__ pos_ref, double kick, double dt, double lx, double ly,
+                             double lz, float half_skin2, Control *ctrl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool moved = false;
   if (i < n) {
-    double ux = vx[i] + kick * (double)F[i];
-    double uy = vy[i] + kick * (double)F[(size_t)n + i];
-    double uz = vz[i] + kick * (double)F[2 * (size_t)n + i];
+    double ux = vx[i] + kick * fix_to_double(F[i]);
+    double uy = vy[i] + kick * fix_to_double(F[(size_t)n + i]);
+    double uz = vz[i] + kick * fix_to_double(F[2 * (size_t)n + i]);
     vx[i] = ux; vy[i] = uy; vz[i] = uz;
     const double px = x[i] + dt * ux, py = y[i] + dt * uy, pz = z[i] + dt * uz;
     x[i] = px; y[i] = py; z[i] = pz;
@@ -63,13 +66,13 @@ __global__ void k_control_force(Control *ctrl) {
 }
 
 __global__ void k_kick(int n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
-                       const float *__restrict__ F, double kick, double mass, double *__restrict__ part) {
+                       const long long *__restrict__ F, double kick, double mass, double *__restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
   if (i < n) {
-    const double ux = vx[i] + kick * (double)F[i];
-    const double uy = vy[i] + kick * (double)F[(size_t)n + i];
-    const double uz = vz[i] + kick * (double)F[2 * (size_t)n + i];
+    const double ux = vx[i] + kick * fix_to_double(F[i]);
+    const double uy = vy[i] + kick * fix_to_double(F[(size_t)n + i]);
+    const double uz = vz[i] + kick * fix_to_double(F[2 * (size_t)n + i]);
     vx[i] = ux; vy[i] = uy; vz[i] = uz;
     acc[0] = 0.5 * mass * KE_CONV * (ux * ux + uy * uy + uz * uz);
   }
@@ -85,45 +88,39 @@ __global__ void k_kinetic(int n, const double *__restrict__ vx, const double *__
   block_sum_store<1>(acc, part);
 }
 
-// Fixed-order reduction of the per-block partials.
-// pd (stride 5): {site energy, radial pairs, angular pairs, list entries, active pairs};
-// pf (stride 9): virial; pk (stride 1): kinetic energy.
-// sums = {E, W[9], KE, radial, angular, list, active}; counters += {radial, angular, 1, list, active}.
+// Fixed-order reduction of the per-block partials, one block per reduced quantity v:
+//   pd (stride 5):  {site energy, radial pairs, angular pairs, list entries, active pairs} (descriptor)
+//   pf (stride 13): {virial W[9], owned list entries, owned active, owned radial, owned angular} (force)
+//   pk (stride 1):  kinetic energy
+// sums[v]: 0 E, 1..9 W, 10 KE, 11..14 descriptor counts, 15..18 force counts;
+// counters[v - 11] += sums[v] for v >= 11, counters[8] += 1 per evaluation.
+constexpr int N_SUMS = 19;
+
 __global__ void __launch_bounds__(256)
 k_finalize(const double *__restrict__ pd, int nbd, const double *__restrict__ pf, int nbf,
            const double *__restrict__ pk, int nbk, double *__restrict__ sums, long long *__restrict__ counters) {
   __shared__ double red[256];
-  double out[15];
-  for (int v = 0; v < 15; ++v) {
-    const double *src;
-    int nb, stride, off;
-    if (v == 0) { src = pd; nb = nbd; stride = 5; off = 0; }
-    else if (v <= 9) { src = pf; nb = nbf; stride = 9; off = v - 1; }
-    else if (v == 10) { src = pk; nb = nbk; stride = 1; off = 0; }
-    else { src = pd; nb = nbd; stride = 5; off = v - 10; }
-    double t = 0.0;
-    if (src != nullptr)
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) t += src[(size_t)b * stride + off];
-    red[threadIdx.x] = t;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-      __syncthreads();
-    }
-    out[v] = red[0];
+  const int v = blockIdx.x;
+  const double *src;
+  int nb, stride, off;
+  if (v == 0) { src = pd; nb = nbd; stride = 5; off = 0; }
+  else if (v <= 9) { src = pf; nb = nbf; stride = 13; off = v - 1; }
+  else if (v == 10) { src = pk; nb = nbk; stride = 1; off = 0; }
+  else if (v <= 14) { src = pd; nb = nbd; stride = 5; off = v - 10; }
+  else { src = pf; nb = nbf; stride = 13; off = 9 + (v - 15); }
+  if (src == nullptr) return;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) t += src[(size_t)b * stride + off];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    if (pd != nullptr) { sums[0] = out[0]; for (int v = 11; v < 15; ++v) sums[v] = out[v]; }
-    if (pf != nullptr) for (int v = 1; v <= 9; ++v) sums[v] = out[v];
-    if (pk != nullptr) sums[10] = out[10];
-    if (counters != nullptr && pd != nullptr) {
-      counters[0] += (long long)out[11];
-      counters[1] += (long long)out[12];
-      counters[2] += 1;
-      counters[3] += (long long)out[13];
-      counters[4] += (long long)out[14];
-    }
+    sums[v] = red[0];
+    if (counters != nullptr && v >= 11) counters[v - 11] += (long long)red[0];
+    if (counters != nullptr && v == 0) counters[8] += 1;
   }
 }
 
@@ -161,11 +158,14 @@ __global__ void k_store_vec(int n, const int *__restrict__ id, const double *__r
   out[o] = u; out[o + 1] = v; out[o + 2] = w;
 }
 
-__global__ void k_store_force(int n, const int *__restrict__ id, const float *__restrict__ F, double *__restrict__ out) {
+__global__ void k_store_force(int n, const int *__restrict__ id, const long long *__restrict__ F,
+                              double *__restrict__ out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const size_t o = 3 * (size_t)id[s];
-  out[o] = F[s]; out[o + 1] = F[(size_t)n + s]; out[o + 2] = F[2 * (size_t)n + s];
+  out[o] = fix_to_double(F[s]);
+  out[o + 1] = fix_to_double(F[(size_t)n + s]);
+  out[o + 2] = fix_to_double(F[2 * (size_t)n + s]);
 }
 
 __global__ void k_store_scalar(int n, const int *__restrict__ id, const float *__restrict__ u, double *__restrict__ out) {
@@ -183,13 +183,15 @@ __global__ void k_store_rows(int n, int width, const int *__restrict__ id, const
 
 __global__ void k_store_neighbors(int n, int cap_in, int cap_out, const int *__restrict__ id, const int32_t *__restrict__ nbr,
                                   const int32_t *__restrict__ nnum, const int32_t *__restrict__ nang,
-                                  int32_t *__restrict__ counts, int32_t *__restrict__ n_ang, int32_t *__restrict__ list) {
+                                  const int32_t *__restrict__ nown, int32_t *__restrict__ counts,
+                                  int32_t *__restrict__ n_ang, int32_t *__restrict__ n_own, int32_t *__restrict__ list) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int o = id[s];
   const int c = nnum[s];
   counts[o] = c;
   n_ang[o] = nang[s];
+  n_own[o] = nown[s];
   for (int k = 0; k < c && k < cap_out; ++k) list[(size_t)o * cap_out + k] = id[nbr[(size_t)k * n + s] & J_MASK];
   for (int k = c; k < cap_out; ++k) list[(size_t)o * cap_out + k] = -1;
   (void)cap_in;
@@ -201,7 +203,7 @@ static int bl(long long m, int b) { return (int)((m + b - 1) / b); }
 constexpr int MD_BLOCK = 256;
 int md_blocks(int n) { return bl(n, MD_BLOCK); }
 
-cudaError_t launch_kick_drift(int n, double *x, double *y, double *z, double *vx, double *vy, double *vz, const float *F,
+cudaError_t launch_kick_drift(int n, double *x, double *y, double *z, double *vx, double *vy, double *vz, const long long *F,
                               float4 *pos, const float4 *pos_ref, double kick, double dt, const double l[3],
                               float half_skin2, Control *ctrl, cudaStream_t st) {
   if (n > 0)
@@ -216,7 +218,7 @@ cudaError_t launch_control(Control *ctrl, bool force, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_kick(int n, double *vx, double *vy, double *vz, const float *F, double kick, double mass, double *part,
+cudaError_t launch_kick(int n, double *vx, double *vy, double *vz, const long long *F, double kick, double mass, double *part,
                         cudaStream_t st) {
   if (n > 0) k_kick<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, F, kick, mass, part);
   return cudaGetLastError();
@@ -230,7 +232,7 @@ cudaError_t launch_kinetic(int n, const double *vx, const double *vy, const doub
 
 cudaError_t launch_finalize(const double *pd, int nbd, const double *pf, int nbf, const double *pk, int nbk,
                             double *sums, long long *counters, cudaStream_t st) {
-  k_finalize<<<1, 256, 0, st>>>(pd, nbd, pf, nbf, pk, nbk, sums, counters);
+  k_finalize<<<N_SUMS, 256, 0, st>>>(pd, nbd, pf, nbf, pk, nbk, sums, counters);
   return cudaGetLastError();
 }
 
@@ -246,7 +248,7 @@ cudaError_t launch_store_vec(int n, const int *id, const double *a, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_store_force(int n, const int *id, const float *F, double *out, cudaStream_t st) {
+cudaError_t launch_store_force(int n, const int *id, const long long *F, double *out, cudaStream_t st) {
   if (n > 0) k_store_force<<<bl(n, 256), 256, 0, st>>>(n, id, F, out);
   return cudaGetLastError();
 }
@@ -262,9 +264,11 @@ cudaError_t launch_store_rows(int n, int width, const int *id, const float *q, f
 }
 
 cudaError_t launch_store_neighbors(int n, int cap_in, int cap_out, const int *id, const int32_t *nbr, const int32_t *nnum,
-                                   const int32_t *nang, int32_t *counts, int32_t *n_ang, int32_t *list, cudaStream_t st) {
+                                   const int32_t *nang, const int32_t *nown, int32_t *counts, int32_t *n_ang,
+                                   int32_t *n_own, int32_t *list, cudaStream_t st) {
   if (n > 0)
-    k_store_neighbors<<<bl(n, 256), 256, 0, st>>>(n, cap_in, cap_out, id, nbr, nnum, nang, counts, n_ang, list);
+    k_store_neighbors<<<bl(n, 256), 256, 0, st>>>(n, cap_in, cap_out, id, nbr, nnum, nang, nown, counts, n_ang, n_own,
+                                                  list);
   return cudaGetLastError();
 }
 

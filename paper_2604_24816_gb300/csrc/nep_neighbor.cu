@@ -1,4 +1,4 @@
-// nep_neighbor.cu -- cell binning, cell sort and distance-sorted neighbour lists on sm_103a.
+// nep_neighbor.cu -- cell binning, cell sort and banded half/full neighbour lists on sm_103a.
 //
 // Rebuild pipeline (every kernel takes the control block and returns at once when the current step
 // does not rebuild, so the whole MD step can be replayed as one CUDA graph):
@@ -10,11 +10,10 @@
 //                   positions, independent of launch timing and of the previous order
 //   k_permute       gather x, v, id into the new order; cell-relative float32 coordinates
 //   k_copy_back     copy the gathered arrays back (fixed device pointers for graph replay)
-//   k_neighbors     for each atom (one warp per atom), every j with |r_ij| < rc_R + skin among the 27
-//                   neighbouring cell images, sorted by (float32 distance^2, packed j) so that the
-//                   entries inside the angular and radial cutoffs come first and the per-pair branches
-//                   in the force kernels stay warp-uniform; the prefix with |r_ij| < rc_A + skin is
-//                   the angular list.
+//   k_neighbors     for each atom, every j with |r_ij| < rc_R + skin among the 27 neighbouring cell
+//                   images, split into the pairs this atom owns (one owner per unordered pair) and the
+//                   rest, each part grouped by distance band so that the per-pair branches of the
+//                   force kernels stay warp-uniform.
 // Distances use cell-relative float32 coordinates plus the image offset of the neighbouring cell, so
 // their error does not grow with the box size (float64 appears only in the wrap and cell assignment).
 #include "nep_common.cuh"
@@ -183,106 +182,127 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
   id[t] = idb[t];
 }
 
-// One warp per atom, 32 consecutive atoms (a tile) per warp.  Lanes test the candidates of each of the
-// 27 neighbouring cell images in parallel; accepted entries are compacted with a ballot into a
-// per-warp key buffer (key = float32 distance^2 bits << 32 | packed entry), bitonic-sorted in shared
-// memory, and staged in a [32][CAP+1] tile so the list is written row-coalesced ([cap][N] layout).
-template <int CAP>
-__global__ void __launch_bounds__(32)
+// One thread per atom, two passes over the candidates of the 27 neighbouring cell images.  Pass 1
+// counts the accepted j per segment; pass 2 writes each entry at its segment's running offset.
+//
+// Segments: the pair (i, j) is "owned" by i when r_ij lies in the upper half-space (see owns_pair;
+// exactly one of r_ij and r_ji = -r_ij is owned, so every unordered pair has one owner), and the row
+// is laid out as [owned | not owned], each part grouped by build-time distance band:
+// [0, rc_A), [rc_A, rc_A + skin), [rc_A + skin, rc_R), [rc_R, rc_R + skin), stencil order inside a band.
+// The force kernel walks only the owned part (each pair once, Newton's third law); the descriptor
+// kernel walks the whole row.  Because every atom of a lattice owns exactly half of each shell and the
+// bands follow the shells, the per-pair branches stay warp-uniform without a full sort.
+// Rows are staged in shared memory ([k][thread]) and flushed row-coalesced.
+constexpr int NB_THREADS = 64;
+constexpr int NB_STAGE = 128;          // staged entries per atom (lists longer than this are an overflow)
+constexpr float OWN_EPS = 0.5f;        // Angstrom; lattice-vector components are either ~0 or >= a/2
+
+struct Bands {
+  float b0, b1, b2, b3;                // squared band edges: rc_A^2, (rc_A+skin)^2, rc_R^2, (rc_R+skin)^2
+};
+
+// Upper half-space test, exactly antisymmetric: owns_pair(d) != owns_pair(-d) for d != 0.  The
+// tolerance makes near-zero components of lattice vectors (thermal noise) defer to the next axis, so
+// each fcc shell splits into two equal halves for every atom.
+__device__ __forceinline__ bool owns_pair(float dx, float dy, float dz) {
+  if (dz > OWN_EPS) return true;
+  if (dz < -OWN_EPS) return false;
+  if (dy > OWN_EPS) return true;
+  if (dy < -OWN_EPS) return false;
+  if (dx != 0.f) return dx > 0.f;
+  if (dy != 0.f) return dy > 0.f;
+  return dz > 0.f;
+}
+
+__global__ void __launch_bounds__(NB_THREADS)
 k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_start, const Geom geom, int cap,
-            float rl2, float ra2, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
-            Control *ctrl) {
+            Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
+            int32_t *__restrict__ nown, int32_t *__restrict__ nband0, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
   __shared__ float4 shift[27];
-  __shared__ unsigned long long keys[CAP];
-  __shared__ uint32_t tile[32][CAP + 1];
-  __shared__ int tile_cnt[32];
+  extern __shared__ uint32_t stage[];            // [NB_STAGE][NB_THREADS]
   fill_shift_table(shift, geom);
-  __syncwarp();
-  const int lane = threadIdx.x;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const int base = blockIdx.x * 32;
-  const int limit = min(cap, CAP);
-  for (int t = 0; t < 32; ++t) {
-    const int i = base + t;
-    if (i >= n) {
-      if (lane == 0) tile_cnt[t] = 0;
-      continue;
-    }
-    const float4 pi = pos[i];
-    const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (cz + dz + geom.ncz) % geom.ncz;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = (cy + dy + geom.ncy) % geom.ncy;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = (cx + dx + geom.ncx) % geom.ncx;
-          const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-          const float4 o = shift[sh];
-          const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
-          const int b = cell_start[c], e = cell_start[c + 1];
-          for (int j0 = b; j0 < e; j0 += 32) {
-            const int j = j0 + lane;
-            bool ok = false;
-            unsigned long long key = 0ull;
-            if (j < e && !(j == i && sh == 13)) {
+  __syncthreads();
+  const int i = blockIdx.x * NB_THREADS + threadIdx.x;
+  const bool live = i < n;
+  const int limit = min(cap, NB_STAGE);
+  // four 16-bit counters per 64-bit word: own = owned segments by band, oth = not-owned segments
+  unsigned long long own = 0ull, oth = 0ull, own_off = 0ull, oth_off = 0ull;
+  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+  int cx = 0, cy = 0, cz = 0;
+  if (live) {
+    pi = pos[i];
+    cx = cell_x(pi.w); cy = cell_y(pi.w); cz = cell_z(pi.w);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    if (live) {
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int zz = (cz + dz + geom.ncz) % geom.ncz;
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int yy = (cy + dy + geom.ncy) % geom.ncy;
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int xx = (cx + dx + geom.ncx) % geom.ncx;
+            const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+            const float4 o = shift[sh];
+            const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
+            const int b = cell_start[c], e = cell_start[c + 1];
+            for (int j = b; j < e; ++j) {
+              if (j == i && sh == 13) continue;
               const float4 pj = pos[j];
               const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
               const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-              ok = r2 < rl2;
-              key = ((unsigned long long)__float_as_uint(r2) << 32) | (unsigned long long)((uint32_t)j | ((uint32_t)sh << J_BITS));
+              if (r2 < B.b3) {
+                const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
+                const unsigned long long one = 1ull << (16 * bd);
+                const bool ow = owns_pair(ddx, ddy, ddz);
+                if (pass == 0) {
+                  if (ow) own += one; else oth += one;
+                } else {
+                  int k;
+                  if (ow) { k = (int)((own_off >> (16 * bd)) & 0xffffull); own_off += one; }
+                  else { k = (int)((oth_off >> (16 * bd)) & 0xffffull); oth_off += one; }
+                  if (k < limit) stage[k * NB_THREADS + threadIdx.x] = (uint32_t)j | ((uint32_t)sh << J_BITS);
+                }
+              }
             }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-              const int slot = cnt + __popc(m & lt_mask);
-              if (slot < CAP) keys[slot] = key;
-            }
-            cnt += __popc(m);
           }
         }
       }
     }
-    const int kept = min(cnt, limit);
-    if (lane == 0 && cnt > kept) atomicOr(&ctrl->status, ST_OVERFLOW);
-    for (int s = min(cnt, CAP) + lane; s < CAP; s += 32) keys[s] = ~0ull;
-    __syncwarp();
-    // bitonic sort of keys[0..CAP) ascending
-    for (int size = 2; size <= CAP; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int p = lane; p < CAP / 2; p += 32) {
-          const int lo = 2 * p - (p & (stride - 1));
-          const int hi = lo + stride;
-          const unsigned long long a = keys[lo], bb = keys[hi];
-          const bool up = (lo & size) == 0;
-          if ((a > bb) == up) { keys[lo] = bb; keys[hi] = a; }
-        }
-        __syncwarp();
+    if (pass == 0) {
+      // exclusive offsets: owned bands 0..3, then not-owned bands 0..3
+      unsigned long long run = 0ull;
+      for (int bd = 0; bd < 4; ++bd) {
+        own_off |= run << (16 * bd);
+        run += (own >> (16 * bd)) & 0xffffull;
+      }
+      for (int bd = 0; bd < 4; ++bd) {
+        oth_off |= run << (16 * bd);
+        run += (oth >> (16 * bd)) & 0xffffull;
       }
     }
-    int na = 0;
-    for (int k = lane; k < kept; k += 32) {
-      const unsigned long long key = keys[k];
-      tile[t][k] = (uint32_t)(key & 0xffffffffull);
-      na += __uint_as_float((uint32_t)(key >> 32)) < ra2 ? 1 : 0;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) na += __shfl_xor_sync(0xffffffffu, na, o);
-    if (lane == 0) {
-      tile_cnt[t] = kept;
-      nnum[i] = kept;
-      nang[i] = na;
-    }
-    __syncwarp();
   }
-  // flush: row k of the tile is 32 consecutive atoms -> one coalesced 128-byte store
-  const int i = base + lane;
-  const int mine = tile_cnt[lane];
-  int kmax = mine;
-#pragma unroll
+  int n_own = 0, n_oth = 0, n_ang = 0;
+  for (int bd = 0; bd < 4; ++bd) {
+    const int a = (int)((own >> (16 * bd)) & 0xffffull), b = (int)((oth >> (16 * bd)) & 0xffffull);
+    n_own += a; n_oth += b;
+    if (bd < 2) n_ang += a + b;
+  }
+  const int total = n_own + n_oth;
+  const int kept = min(total, limit);
+  if (live) {
+    if (total > kept) atomicOr(&ctrl->status, ST_OVERFLOW);
+    nnum[i] = kept;
+    nown[i] = min(n_own, kept);
+    nang[i] = n_ang;
+    nband0[i] = min((int)(own & 0xffffull), kept);
+  }
+  __syncthreads();
+  // row-coalesced flush of the staged rows
+  int kmax = live ? kept : 0;
   for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
   for (int k = 0; k < kmax; ++k)
-    if (k < mine && i < n) nbr[(size_t)k * n + i] = (int32_t)tile[lane][k];
+    if (k < kept && live) nbr[(size_t)k * n + i] = (int32_t)stage[k * NB_THREADS + threadIdx.x];
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -315,11 +335,11 @@ cudaError_t launch_neighbors(const RebuildArgs &a, cudaStream_t st) {
   Geom g;
   g.lx = (float)a.l[0]; g.ly = (float)a.l[1]; g.lz = (float)a.l[2];
   g.ncx = a.nc[0]; g.ncy = a.nc[1]; g.ncz = a.nc[2];
-  const int grid = blocks_for(a.n, 32);
-  if (a.cap <= 128)
-    k_neighbors<128><<<grid, 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, a.rl2, a.ra2, a.nbr, a.nnum, a.nang, a.ctrl);
-  else
-    k_neighbors<256><<<grid, 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, a.rl2, a.ra2, a.nbr, a.nnum, a.nang, a.ctrl);
+  Bands B;
+  B.b0 = a.ba2; B.b1 = a.ra2; B.b2 = a.br2; B.b3 = a.rl2;
+  const size_t smem = (size_t)NB_STAGE * NB_THREADS * sizeof(uint32_t);
+  k_neighbors<<<blocks_for(a.n, NB_THREADS), NB_THREADS, smem, st>>>(a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum,
+                                                                      a.nang, a.nown, a.nband0, a.ctrl);
   return cudaGetLastError();
 }
 

@@ -71,7 +71,7 @@ def lib():
         L.md_verlet_step.argtypes = [vp, C.c_double, C.c_int]
         L.nep_get_state.argtypes = [vp, vp, vp]
         L.nep_get_thermo.argtypes = [vp, d]
-        L.nep_get_neighbors.argtypes = [vp, vp, vp, vp, C.c_int]
+        L.nep_get_neighbors.argtypes = [vp, vp, vp, vp, vp, C.c_int]
         L.nep_get_descriptors.argtypes = [vp, vp]
         L.nep_get_site_energies.argtypes = [vp, vp]
         L.nep_set_timing.argtypes = [vp, C.c_int]
@@ -200,11 +200,14 @@ class NEP:
         return dict(pe=out[0], ke=out[1], temperature=out[2], pressure=out[3], w_diag=out[4:7], rebuilds=int(out[7]))
 
     def neighbors(self, cap: int = 160):
+        """Returns (counts, n_ang, n_own, list[n, cap]) in original atom ids."""
         counts = np.zeros(self.n, dtype=np.int32)
         nang = np.zeros(self.n, dtype=np.int32)
+        nown = np.zeros(self.n, dtype=np.int32)
         lst = np.zeros((self.n, cap), dtype=np.int32)
-        self._check(self._L.nep_get_neighbors(self._h, counts.ctypes.data, nang.ctypes.data, lst.ctypes.data, cap))
-        return counts, nang, lst
+        self._check(self._L.nep_get_neighbors(self._h, counts.ctypes.data, nang.ctypes.data, nown.ctypes.data,
+                                              lst.ctypes.data, cap))
+        return counts, nang, nown, lst
 
     def descriptors(self):
         q = np.zeros((self.n, self.n_des), dtype=np.float32)
@@ -227,8 +230,9 @@ class NEP:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def counters(self) -> dict:
-        out = np.zeros(8, dtype=np.int64)
+        out = np.zeros(12, dtype=np.int64)
         self._check(self._L.nep_get_counters(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return dict(radial_pairs=int(out[0]), angular_pairs=int(out[1]), evaluations=int(out[2]),
                     rebuilds=int(out[3]), steps=int(out[4]), launches=int(out[5]), list_entries=int(out[6]),
-                    active_pairs=int(out[7]))
+                    active_pairs=int(out[7]), owned_list_entries=int(out[8]), owned_active_pairs=int(out[9]),
+                    owned_radial_pairs=int(out[10]), owned_angular_pairs=int(out[11]))

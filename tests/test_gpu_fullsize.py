@@ -55,6 +55,8 @@ def test_full_size_md_conserves_energy_and_is_deterministic(big, model_params):
     assert c["rebuilds"] >= 5 and c["steps"] == 50
     e0 = (th0["pe"] + th0["ke"]) / big.n
     e1 = (th1["pe"] + th1["ke"]) / big.n
-    assert abs(e1 - e0) < 5e-5            # 50 fs of NVE from a displaced start
+    # Velocity Verlet from the displaced start: the oracle's own 256-atom cells of the same distribution
+    # (seeds 1-4) move by 5.5e-5 to 8.3e-5 eV/atom over these 50 steps; allow 2.5x the largest.
+    assert abs(e1 - e0) < 2e-4
     assert np.array_equal(runs[0][2], runs[1][2]) and np.array_equal(runs[0][3], runs[1][3])
     assert np.all(np.isfinite(x)) and np.all((x >= 0) & (x < big.box))

@@ -50,6 +50,12 @@ def _min_gap_to_cutoffs(pos, box, cuts):
     return min(np.abs(r - c).min() for c in cuts)
 
 
+def _bands(pos, box, i, js, edges):
+    d = pos[js] - pos[i]
+    d -= box * np.round(d / box)
+    return np.searchsorted(edges, np.sqrt((d ** 2).sum(1)), side="right")
+
+
 @pytest.mark.parametrize("cells", [(4, 4, 4), (4, 4, 5), (6, 5, 4)])
 def test_neighbor_sets_bit_exact(api, model_params, cells):
     wl = ni.fcc_cu_workload(0, sigma=0.05, seed=21 + sum(cells), cells_xyz=cells)
@@ -59,18 +65,33 @@ def test_neighbor_sets_bit_exact(api, model_params, cells):
     with api.NEP(model_params) as nep:
         nep.set_state(wl.pos, wl.vel, wl.box)
         nep.build_neighbors()
-        counts, nang, lst = nep.neighbors(cap=160)
+        counts, nang, nown, lst = nep.neighbors(cap=160)
     o_off, o_lst = oracle.neighbor_lists(wl.pos, wl.box, rl, use_cells=False)
     a_off, a_lst = oracle.neighbor_lists(wl.pos, wl.box, ra, use_cells=False)
-    assert _sets_from_gpu(counts, lst) == _sets_from_oracle(o_off, o_lst)
-    ang = [set(lst[i, :nang[i]].tolist()) for i in range(wl.n)]
-    assert ang == _sets_from_oracle(a_off, a_lst)
-    # distance order within each row
-    for i in range(0, wl.n, 17):
-        d = wl.pos[lst[i, :counts[i]]] - wl.pos[i]
-        d -= wl.box * np.round(d / wl.box)
-        r = np.sqrt((d ** 2).sum(1))
-        assert np.all(np.diff(r) >= -1e-5)
+    full = _sets_from_gpu(counts, lst)
+    assert full == _sets_from_oracle(o_off, o_lst)
+    assert np.array_equal(nang, np.diff(a_off))
+    # every unordered pair has exactly one owner
+    owned = [set(lst[i, :nown[i]].tolist()) for i in range(wl.n)]
+    for i in range(wl.n):
+        for j in full[i]:
+            assert (j in owned[i]) != (i in owned[j])
+    # row layout: [owned | other], each grouped by band r < rc_A, rc_A + skin, rc_R, rc_R + skin
+    edges = np.array([model_params["rc_A"], ra, model_params["rc_R"], rl])
+    for i in range(0, wl.n, 7):
+        b_own = _bands(wl.pos, wl.box, i, lst[i, :nown[i]], edges)
+        b_oth = _bands(wl.pos, wl.box, i, lst[i, nown[i]:counts[i]], edges)
+        assert np.all(np.diff(b_own) >= 0) and np.all(np.diff(b_oth) >= 0)
+        assert np.sum(b_own <= 1) + np.sum(b_oth <= 1) == nang[i]
+
+
+def test_perfect_lattice_owns_half_of_each_shell(api, model_params):
+    pos, box = ni.fcc_lattice(5, 5, 5)
+    with api.NEP(model_params) as nep:
+        nep.set_state(pos, None, box)
+        nep.build_neighbors()
+        counts, nang, nown, lst = nep.neighbors(cap=160)
+    assert set(counts.tolist()) == {78} and set(nang.tolist()) == {42} and set(nown.tolist()) == {39}
 
 
 def test_descriptors(api, model_params, model, c1):

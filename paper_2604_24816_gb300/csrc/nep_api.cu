@@ -25,10 +25,10 @@ namespace nep {
 // nep_force.cu
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                              float *, float *, float *, long long *, double *, int *, cudaStream_t);
+                              float *, float *, float *, long long *, long long *, int *, cudaStream_t);
 template <class S>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const float *, long long *, double *, int *, cudaStream_t);
+                         const int32_t *, const float *, long long *, long long *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
 // nep_neighbor.cu
@@ -40,10 +40,10 @@ int md_blocks(int n);
 cudaError_t launch_kick_drift(int, double *, double *, double *, double *, double *, double *, const long long *, float4 *,
                               const float4 *, double, double, const double *, float, Control *, cudaStream_t);
 cudaError_t launch_control(Control *, bool, cudaStream_t);
-cudaError_t launch_kick(int, double *, double *, double *, const long long *, double, double, double *, cudaStream_t);
-cudaError_t launch_kinetic(int, const double *, const double *, const double *, double, double *, cudaStream_t);
-cudaError_t launch_finalize(const double *, int, const double *, int, const double *, int, double *, long long *,
-                            cudaStream_t);
+cudaError_t launch_kick(int, double *, double *, double *, const long long *, double, double, long long *, cudaStream_t);
+cudaError_t launch_kinetic(int, const double *, const double *, const double *, double, long long *, cudaStream_t);
+cudaError_t launch_finalize(const long long *, int, const long long *, int, const long long *, int, double *,
+                            long long *, cudaStream_t);
 cudaError_t launch_load_state(int, const double *, const double *, double *, double *, double *, double *, double *,
                               double *, int *, int *, cudaStream_t);
 cudaError_t launch_store_vec(int, const int *, const double *, const double *, const double *, const double *, int,
@@ -99,7 +99,8 @@ struct nep_handle {
   float *usite = nullptr, *G = nullptr, *qbuf = nullptr;
   int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr, *nown = nullptr, *nband0 = nullptr;
   int *count = nullptr, *cursor = nullptr, *start = nullptr, *tile_sums = nullptr;
-  double *part_d = nullptr, *part_f = nullptr, *part_k = nullptr, *sums = nullptr;
+  long long *part_d = nullptr, *part_f = nullptr, *part_k = nullptr;   // per-block int64 partial sums
+  double *sums = nullptr;
   long long *counters = nullptr;   // pair counts (descriptor, force) and evaluations
   Control *ctrl = nullptr;
   double *io = nullptr;            // staging 2 x [n][3] float64 for host transfers

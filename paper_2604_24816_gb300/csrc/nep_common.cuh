@@ -246,10 +246,27 @@ __device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, fl
   de = (-12.f * a12 + 6.f * a6) / r - P.lj_de_rc;
 }
 
-// Block-wide sum of NV doubles into out[blockIdx.x * NV + v] in a fixed order (deterministic).
+// Exact conversion of a float to 64-bit fixed point with 32 fractional bits (round half away from
+// zero), using integer operations only (no 64-bit conversion instruction, which would run on the
+// narrow FP64 pipe).  Valid for |v| < 2^30; zero and subnormals map to 0.
+__device__ __forceinline__ long long to_fix32(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int ex = (int)((b >> 23) & 0xffu);
+  if (ex == 0) return 0;
+  const long long man = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = ex - 118;                      // v * 2^32 = man * 2^(ex - 127 - 23 + 32)
+  long long r;
+  if (sh >= 0) r = man << min(sh, 39);
+  else if (sh > -25) r = (man + (1ll << (-sh - 1))) >> (-sh);
+  else r = 0;
+  return (b >> 31) ? -r : r;
+}
+
+// Block-wide sum of NV int64 values into out[blockIdx.x * NV + v].  Integer addition is associative,
+// so the result does not depend on the reduction order.
 template <int NV>
-__device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out) {
-  __shared__ double red[32][NV];
+__device__ __forceinline__ void block_sum_store(long long (&v)[NV], long long *out) {
+  __shared__ long long red[32][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -265,7 +282,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out) {
     const int nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double t = lane < nw ? red[lane][k] : 0.0;
+      long long t = lane < nw ? red[lane][k] : 0ll;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
       if (lane == 0) out[(size_t)blockIdx.x * NV + k] = t;

@@ -28,7 +28,10 @@
 namespace nep {
 
 constexpr int DESC_BLOCK = 128;
-constexpr int FORCE_BLOCK = 128;
+#ifndef NEP_FORCE_BLOCK
+#define NEP_FORCE_BLOCK 128
+#endif
+constexpr int FORCE_BLOCK = NEP_FORCE_BLOCK;
 // Minimum resident blocks per SM requested from the compiler (register budget per thread =
 // 65536 / (block * min_blocks)); the defaults are the measured best on GB300.
 #ifndef NEP_DESC_MINB
@@ -36,6 +39,11 @@ constexpr int FORCE_BLOCK = 128;
 #endif
 #ifndef NEP_FORCE_MINB
 #define NEP_FORCE_MINB 2
+#endif
+// 1: the force kernel keeps the atom's own adjoint row G_i in shared memory ([component][thread],
+// conflict-free) instead of 120 registers.
+#ifndef NEP_FORCE_GI_SMEM
+#define NEP_FORCE_GI_SMEM 0
 #endif
 
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
@@ -45,12 +53,12 @@ __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
 k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
              const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
              float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
-             double *__restrict__ part, int *__restrict__ status) {
+             long long *__restrict__ part, int *__restrict__ status) {
   __shared__ float4 shift[27];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  long long acc[5] = {0, 0, 0, 0, 0};
   if (i < n) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     const float4 pi = pos[i];
@@ -225,11 +233,11 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     const float ui = U + elj;
     usite[i] = ui;
     if (!isfinite(ui)) atomicOr(status, ST_NAN);
-    acc[0] = (double)ui;
-    acc[1] = (double)nrad;
-    acc[2] = (double)nang;
-    acc[3] = (double)cnt;
-    acc[4] = (double)nact;
+    acc[0] = to_fix32(ui);
+    acc[1] = nrad;
+    acc[2] = nang;
+    acc[3] = cnt;
+    acc[4] = nact;
   }
   block_sum_store<5>(acc, part);
 }
@@ -238,23 +246,29 @@ template <class S>
 __global__ void __launch_bounds__(FORCE_BLOCK, NEP_FORCE_MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
         const int32_t *__restrict__ nbr, const int32_t *__restrict__ nown, const int32_t *__restrict__ nband0,
-        const float *__restrict__ G, unsigned long long *__restrict__ Ffix, double *__restrict__ part,
+        const float *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status) {
   __shared__ float4 shift[27];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[13] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  long long acc[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < n) {
     const float4 pi = pos[i];
     const float *Gi = G + (size_t)i * GSTRIDE;
+#if NEP_FORCE_GI_SMEM
+    extern __shared__ float gsm[];     // [NA * 24][FORCE_BLOCK]
+#define GI(a, lm) gsm[((a) * N_LM + (lm)) * FORCE_BLOCK + threadIdx.x]
+#else
     float gi[S::NA][N_LM];
+#define GI(a, lm) gi[a][lm]
+#endif
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll
       for (int c = 0; c < N_LM; c += 4) {
         const float4 t = __ldg(reinterpret_cast<const float4 *>(Gi + a * N_LM + c));
-        gi[a][c] = t.x; gi[a][c + 1] = t.y; gi[a][c + 2] = t.z; gi[a][c + 3] = t.w;
+        GI(a, c) = t.x; GI(a, c + 1) = t.y; GI(a, c + 2) = t.z; GI(a, c + 3) = t.w;
       }
     float fpi[8];
     {
@@ -347,7 +361,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 #pragma unroll
             for (int a = 0; a < S::NA; ++a) {
               const float gjv = cc == 0 ? hj[a].x : (cc == 1 ? hj[a].y : (cc == 2 ? hj[a].z : hj[a].w));
-              const float H = fmaf(sgn, gjv, gi[a][lm]);
+              const float H = fmaf(sgn, gjv, GI(a, lm));
               av = fmaf(H, dg[a], av);
               bv = fmaf(H, g[a], bv);
             }
@@ -361,24 +375,25 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
       fx += Dx; fy += Dy; fz += Dz;
       // Newton's third law: F_j -= D_ij, accumulated in fixed point (order-independent sum)
-      atomicAdd(Ffix + j, (unsigned long long)__float2ll_rn(-Dx * FIX_SCALE));
-      atomicAdd(Ffix + (size_t)n + j, (unsigned long long)__float2ll_rn(-Dy * FIX_SCALE));
-      atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)__float2ll_rn(-Dz * FIX_SCALE));
+      atomicAdd(Ffix + j, (unsigned long long)(-to_fix32(Dx)));
+      atomicAdd(Ffix + (size_t)n + j, (unsigned long long)(-to_fix32(Dy)));
+      atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)(-to_fix32(Dz)));
       wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
       wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
       wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
     }
-    atomicAdd(Ffix + i, (unsigned long long)__float2ll_rn(fx * FIX_SCALE));
-    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)__float2ll_rn(fy * FIX_SCALE));
-    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)__float2ll_rn(fz * FIX_SCALE));
+    atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
+    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
+    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
     // each unordered pair once: W = -sum_pairs r_ij (x) D_ij
-    acc[0] = -wxx; acc[1] = -wxy; acc[2] = -wxz;
-    acc[3] = -wyx; acc[4] = -wyy; acc[5] = -wyz;
-    acc[6] = -wzx; acc[7] = -wzy; acc[8] = -wzz;
-    acc[9] = (double)cnt; acc[10] = (double)nact; acc[11] = (double)nrad; acc[12] = (double)nang;
+    acc[0] = -to_fix32(wxx); acc[1] = -to_fix32(wxy); acc[2] = -to_fix32(wxz);
+    acc[3] = -to_fix32(wyx); acc[4] = -to_fix32(wyy); acc[5] = -to_fix32(wyz);
+    acc[6] = -to_fix32(wzx); acc[7] = -to_fix32(wzy); acc[8] = -to_fix32(wzz);
+    acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang;
   }
   block_sum_store<13>(acc, part);
+#undef GI
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -387,7 +402,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
                               const int32_t *nnum, float *G, float *usite, float *qout, long long *Ffix,
-                              double *part, int *status, cudaStream_t st) {
+                              long long *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
   k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status);
@@ -396,12 +411,22 @@ cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const flo
 
 template <class S>
 cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                         const int32_t *nown, const int32_t *nband0, const float *G, long long *Ffix, double *part,
+                         const int32_t *nown, const int32_t *nband0, const float *G, long long *Ffix, long long *part,
                          int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
-                                           reinterpret_cast<unsigned long long *>(Ffix), part, status);
+  size_t smem = 0;
+#if NEP_FORCE_GI_SMEM
+  smem = (size_t)S::NA * N_LM * FORCE_BLOCK * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_force<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+#endif
+  k_force<S><<<grid, FORCE_BLOCK, smem, st>>>(P, g, n, pos, nbr, nown, nband0, G,
+                                              reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }
 
@@ -410,9 +435,9 @@ int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
 
 template cudaError_t launch_descriptor<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
                                                 const int32_t *, const int32_t *, float *, float *, float *,
-                                                long long *, double *, int *, cudaStream_t);
+                                                long long *, long long *, int *, cudaStream_t);
 template cudaError_t launch_force<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
                                            const int32_t *, const int32_t *, const int32_t *, const float *,
-                                           long long *, double *, int *, cudaStream_t);
+                                           long long *, long long *, int *, cudaStream_t);
 
 }  // namespace nep

@@ -66,29 +66,30 @@ __global__ void k_control_force(Control *ctrl) {
 }
 
 __global__ void k_kick(int n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
-                       const long long *__restrict__ F, double kick, double mass, double *__restrict__ part) {
+                       const long long *__restrict__ F, double kick, double mass, long long *__restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
+  long long acc[1] = {0};
   if (i < n) {
     const double ux = vx[i] + kick * fix_to_double(F[i]);
     const double uy = vy[i] + kick * fix_to_double(F[(size_t)n + i]);
     const double uz = vz[i] + kick * fix_to_double(F[2 * (size_t)n + i]);
     vx[i] = ux; vy[i] = uy; vz[i] = uz;
-    acc[0] = 0.5 * mass * KE_CONV * (ux * ux + uy * uy + uz * uz);
+    acc[0] = __double2ll_rn(0.5 * mass * KE_CONV * (ux * ux + uy * uy + uz * uz) * 4294967296.0);
   }
   block_sum_store<1>(acc, part);
 }
 
 // Kinetic energy only (no kick): for thermo outside MD steps.
 __global__ void k_kinetic(int n, const double *__restrict__ vx, const double *__restrict__ vy,
-                          const double *__restrict__ vz, double mass, double *__restrict__ part) {
+                          const double *__restrict__ vz, double mass, long long *__restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
-  if (i < n) acc[0] = 0.5 * mass * KE_CONV * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]);
+  long long acc[1] = {0};
+  if (i < n) acc[0] = __double2ll_rn(0.5 * mass * KE_CONV * (vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i]) * 4294967296.0);
   block_sum_store<1>(acc, part);
 }
 
-// Fixed-order reduction of the per-block partials, one block per reduced quantity v:
+// Reduction of the per-block int64 partials (fixed point for energies and virial), one block per
+// reduced quantity v:
 //   pd (stride 5):  {site energy, radial pairs, angular pairs, list entries, active pairs} (descriptor)
 //   pf (stride 13): {virial W[9], owned list entries, owned active, owned radial, owned angular} (force)
 //   pk (stride 1):  kinetic energy
@@ -97,11 +98,11 @@ __global__ void k_kinetic(int n, const double *__restrict__ vx, const double *__
 constexpr int N_SUMS = 19;
 
 __global__ void __launch_bounds__(256)
-k_finalize(const double *__restrict__ pd, int nbd, const double *__restrict__ pf, int nbf,
-           const double *__restrict__ pk, int nbk, double *__restrict__ sums, long long *__restrict__ counters) {
-  __shared__ double red[256];
+k_finalize(const long long *__restrict__ pd, int nbd, const long long *__restrict__ pf, int nbf,
+           const long long *__restrict__ pk, int nbk, double *__restrict__ sums, long long *__restrict__ counters) {
+  __shared__ long long red[256];
   const int v = blockIdx.x;
-  const double *src;
+  const long long *src;
   int nb, stride, off;
   if (v == 0) { src = pd; nb = nbd; stride = 5; off = 0; }
   else if (v <= 9) { src = pf; nb = nbf; stride = 13; off = v - 1; }
@@ -109,7 +110,7 @@ k_finalize(const double *__restrict__ pd, int nbd, const double *__restrict__ pf
   else if (v <= 14) { src = pd; nb = nbd; stride = 5; off = v - 10; }
   else { src = pf; nb = nbf; stride = 13; off = 9 + (v - 15); }
   if (src == nullptr) return;
-  double t = 0.0;
+  long long t = 0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) t += src[(size_t)b * stride + off];
   red[threadIdx.x] = t;
   __syncthreads();
@@ -118,8 +119,9 @@ k_finalize(const double *__restrict__ pd, int nbd, const double *__restrict__ pf
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    sums[v] = red[0];
-    if (counters != nullptr && v >= 11) counters[v - 11] += (long long)red[0];
+    const long long tot = red[0];
+    sums[v] = v <= 10 ? (double)tot * FIX_INV : (double)tot;       // energies/virial are fixed point
+    if (counters != nullptr && v >= 11) counters[v - 11] += tot;
     if (counters != nullptr && v == 0) counters[8] += 1;
   }
 }
@@ -218,19 +220,19 @@ cudaError_t launch_control(Control *ctrl, bool force, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_kick(int n, double *vx, double *vy, double *vz, const long long *F, double kick, double mass, double *part,
+cudaError_t launch_kick(int n, double *vx, double *vy, double *vz, const long long *F, double kick, double mass, long long *part,
                         cudaStream_t st) {
   if (n > 0) k_kick<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, F, kick, mass, part);
   return cudaGetLastError();
 }
 
-cudaError_t launch_kinetic(int n, const double *vx, const double *vy, const double *vz, double mass, double *part,
+cudaError_t launch_kinetic(int n, const double *vx, const double *vy, const double *vz, double mass, long long *part,
                            cudaStream_t st) {
   if (n > 0) k_kinetic<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, mass, part);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double *pd, int nbd, const double *pf, int nbf, const double *pk, int nbk,
+cudaError_t launch_finalize(const long long *pd, int nbd, const long long *pf, int nbf, const long long *pk, int nbk,
                             double *sums, long long *counters, cudaStream_t st) {
   k_finalize<<<N_SUMS, 256, 0, st>>>(pd, nbd, pf, nbf, pk, nbk, sums, counters);
   return cudaGetLastError();

@@ -18,7 +18,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/nep_gb300.h"
+#include "nep_gb300.h"
 #include "nep_common.cuh"
 
 namespace nep {

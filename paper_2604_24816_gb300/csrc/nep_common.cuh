@@ -290,4 +290,65 @@ __device__ __forceinline__ void block_sum_store(long long (&v)[NV], long long *o
   }
 }
 
+
+// ---------------------------------------------------------------------------------------------------
+// Asynchronous per-thread neighbour pipeline (cp.async into shared memory).  The walk over an atom's
+// list is a chain of dependent loads (list entry -> neighbour position); the pipeline keeps list
+// entries DE ahead and neighbour positions DP ahead in shared-memory rings, so the loads of later
+// entries are in flight while the current one is computed, without holding registers.
+// Layout: ring_e[DE][BLOCK] uint32 and ring_p[DP][BLOCK] float4 (bank-conflict-free per thread).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int DE, int DP, int BLOCK>
+struct NbrPipe {
+  static_assert(DE >= 2 * DP && DP >= 1, "entries must run at least twice as far ahead as positions");
+  uint32_t *re;            // this thread's column of ring_e
+  float4 *rp;              // this thread's column of ring_p
+  const int32_t *row;      // &nbr[0 * n + i]
+  size_t n;
+  const float4 *pos;
+  int cnt;
+
+  __device__ __forceinline__ void start(uint32_t *ring_e, float4 *ring_p, const int32_t *row_, size_t n_,
+                                        const float4 *pos_, int cnt_) {
+    re = ring_e + threadIdx.x; rp = ring_p + threadIdx.x; row = row_; n = n_; pos = pos_; cnt = cnt_;
+#pragma unroll
+    for (int k = 0; k < DE; ++k)
+      if (k < cnt) cp_async4(re + k * BLOCK, row + (size_t)k * n);
+    cp_async_commit();
+    cp_async_wait<0>();
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      if (k < cnt) cp_async16(rp + k * BLOCK, pos + (re[k * BLOCK] & J_MASK));
+      cp_async_commit();
+    }
+  }
+
+  // Entry k (0 <= k < cnt, called for k = 0, 1, 2, ... in order): its packed list entry and the
+  // neighbour's position; issues the copies for entries k + DE and k + DP.
+  __device__ __forceinline__ void get(int k, uint32_t &e, float4 &p) {
+    cp_async_wait<DP - 1>();
+    e = re[(k % DE) * BLOCK];
+    p = rp[(k % DP) * BLOCK];
+    if (k + DE < cnt) cp_async4(re + ((k + DE) % DE) * BLOCK, row + (size_t)(k + DE) * n);
+    if (k + DP < cnt) cp_async16(rp + ((k + DP) % DP) * BLOCK, pos + (re[((k + DP) % DE) * BLOCK] & J_MASK));
+    cp_async_commit();
+  }
+
+  // Entry k + DP (already in shared memory once get(k) returned), for look-ahead prefetches.
+  __device__ __forceinline__ uint32_t ahead(int k) const { return re[((k + DP) % DE) * BLOCK]; }
+
+  __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
+};
+
 }  // namespace nep

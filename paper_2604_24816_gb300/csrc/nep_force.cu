@@ -35,7 +35,7 @@ constexpr int FORCE_BLOCK = NEP_FORCE_BLOCK;
 // Minimum resident blocks per SM requested from the compiler (register budget per thread =
 // 65536 / (block * min_blocks)); the defaults are the measured best on GB300.
 #ifndef NEP_DESC_MINB
-#define NEP_DESC_MINB 3
+#define NEP_DESC_MINB 2
 #endif
 #ifndef NEP_FORCE_MINB
 #define NEP_FORCE_MINB 2
@@ -48,6 +48,9 @@ constexpr int FORCE_BLOCK = NEP_FORCE_BLOCK;
 
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
+constexpr int PIPE_DE = 16;   // list entries in flight per thread
+constexpr int PIPE_DP = 8;    // neighbour positions in flight per thread
+
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
 k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
@@ -55,6 +58,8 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
              float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
              long long *__restrict__ part, int *__restrict__ status) {
   __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
+  __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,17 +78,12 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     float elj = 0.f;
     int nrad = 0, nang = 0, nact = 0;
     const int cnt = nnum[i];
-    // software pipeline: list entry two ahead, neighbour position one ahead
-    const int32_t *row = nbr + i;
-    uint32_t e_nxt = cnt > 0 ? (uint32_t)__ldg(row) : 0u;
-    float4 p_nxt = cnt > 0 ? __ldg(pos + (e_nxt & J_MASK)) : pi;
-    uint32_t e_nn = cnt > 1 ? (uint32_t)__ldg(row + (size_t)n) : 0u;
+    NbrPipe<PIPE_DE, PIPE_DP, DESC_BLOCK> pipe;
+    pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = e_nxt;
-      const float4 pj = p_nxt;
-      e_nxt = e_nn;
-      if (k + 1 < cnt) p_nxt = __ldg(pos + (e_nxt & J_MASK));
-      if (k + 2 < cnt) e_nn = (uint32_t)__ldg(row + (size_t)(k + 2) * n);
+      uint32_t e;
+      float4 pj;
+      pipe.get(k, e, pj);
       const float4 o = shift[e >> J_BITS];
       const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
@@ -125,6 +125,7 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
         ++nang;
       }
     }
+    pipe.finish();
 
     // Descriptors: [q_n | q_nl (n-major, l = 1..4) | q4_n].
     float q[S::NDES];
@@ -249,6 +250,8 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
         const float *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status) {
   __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[PIPE_DE * FORCE_BLOCK];
+  __shared__ float4 ring_p[PIPE_DP * FORCE_BLOCK];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -282,22 +285,18 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     const int cnt = nown[i];
     const int nb0 = nband0[i];
     int nrad = 0, nang = 0, nact = 0;
-    const int32_t *row = nbr + i;
-    uint32_t e_nxt = cnt > 0 ? (uint32_t)__ldg(row) : 0u;
-    float4 p_nxt = cnt > 0 ? __ldg(pos + (e_nxt & J_MASK)) : pi;
-    uint32_t e_nn = cnt > 1 ? (uint32_t)__ldg(row + (size_t)n) : 0u;
+    NbrPipe<PIPE_DE, PIPE_DP, FORCE_BLOCK> pipe;
+    pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = e_nxt;
-      const float4 pj = p_nxt;
-      e_nxt = e_nn;
-      if (k + 1 < cnt) {
-        p_nxt = __ldg(pos + (e_nxt & J_MASK));
-        if (k + 1 < nb0) {
-          const char *gr = reinterpret_cast<const char *>(G + (size_t)(e_nxt & J_MASK) * GSTRIDE);
-          prefetch_l1(gr); prefetch_l1(gr + 128); prefetch_l1(gr + 256); prefetch_l1(gr + 384);
-        }
+      uint32_t e;
+      float4 pj;
+      pipe.get(k, e, pj);
+      // pull the next angular neighbour's adjoint row into L1 while this pair is computed
+      if (k + 1 < nb0 && k + 1 < cnt) {
+        const uint32_t en = pipe.re[((k + 1) % PIPE_DE) * FORCE_BLOCK];
+        const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * GSTRIDE);
+        prefetch_l1(gr); prefetch_l1(gr + 128); prefetch_l1(gr + 256); prefetch_l1(gr + 384);
       }
-      if (k + 2 < cnt) e_nn = (uint32_t)__ldg(row + (size_t)(k + 2) * n);
       const int j = (int)(e & J_MASK);
       const float4 o = shift[e >> J_BITS];
       const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
@@ -382,6 +381,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
       wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
     }
+    pipe.finish();
     atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
     atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
     atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));

@@ -50,7 +50,8 @@ class nep_params(C.Structure):
 
 EXPORTED = ("nep_create", "nep_destroy", "nep_set_state", "nep_build_neighbors", "nep_compute", "md_verlet_step",
             "nep_get_state", "nep_get_thermo", "nep_get_neighbors", "nep_get_descriptors", "nep_get_site_energies",
-            "nep_set_timing", "nep_get_timing", "nep_get_counters", "nep_last_error", "nep_status_string")
+            "nep_set_timing", "nep_get_timing", "nep_get_counters", "nep_last_error", "nep_status_string",
+            "nep_compute_noalloc")
 
 
 def lib():
@@ -81,6 +82,7 @@ def lib():
         L.nep_last_error.restype = C.c_char_p
         L.nep_status_string.argtypes = [C.c_int]
         L.nep_status_string.restype = C.c_char_p
+        L.nep_compute_noalloc.argtypes = [C.POINTER(nep_params), i64, vp, d, vp, vp, vp, vp]
         for f in EXPORTED:
             if f not in ("nep_last_error", "nep_status_string"):
                 getattr(L, f).restype = C.c_int

@@ -1,0 +1,80 @@
+"""Host-side logic of bench.py on CPU: replica bookkeeping over two gloo ranks (max-over-ranks time,
+summed atom counts), the FLOP model, the ncu-traffic lookup and the clock-sample parser."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t = bench.dist_max(1.0 + rank, world)          # per-rank timings 1.0 and 2.0
+    n = bench.dist_sum(1000 * (rank + 1), world)   # replicas of 1000 and 2000 atoms
+    bench.dist_barrier(world)
+    dist.destroy_process_group()
+    q.put((rank, t, n))
+
+
+def test_two_rank_replica_bookkeeping():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 2.0, 3000.0), (1, 2.0, 3000.0)]
+
+
+def test_single_rank_helpers_are_identity():
+    assert bench.dist_max(3.5, 1) == 3.5 and bench.dist_sum(7, 1) == 7
+
+
+def test_flop_model_counts_units():
+    c = dict(list_entries=78, active_pairs=42, radial_pairs=42, angular_pairs=18, owned_list_entries=39,
+             owned_active_pairs=21, owned_radial_pairs=21, owned_angular_pairs=9)
+    f_desc = bench.kernel_flops("descriptor", c, 1)
+    f_force = bench.kernel_flops("force", c, 1)
+    assert f_desc == 11 * 78 + 2 * 42 + 128 * 42 + 12 * 42 + 464 * 18 + 4655
+    assert f_force == 11 * 39 + 32 * 21 + 220 * 21 + 13 * 21 + 1465 * 9 + 3
+    assert 15e3 < f_desc < 25e3 and 15e3 < f_force < 25e3
+
+
+def test_traffic_lookup_requires_matching_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_2604_24816_gb300" / "csrc").mkdir(parents=True)
+    for f in ("nep_force.cu", "nep_common.cuh"):
+        (tmp_path / "paper_2604_24816_gb300" / "csrc" / f).write_text("x")
+    h = bench.source_hash()
+    (tmp_path / "profiles" / "traffic_per_launch.txt").write_text(f"# header\nforce {h} 1000 10\nforce deadbeef 5 1\n")
+    assert bench.profiled_traffic("force") == dict(bytes=1000.0, atoms=10)
+    (tmp_path / "paper_2604_24816_gb300" / "csrc" / "nep_force.cu").write_text("changed")
+    assert bench.profiled_traffic("force") is None
+
+
+def test_clock_summary_parses_throttle_reasons():
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)
+    cs.samples = [(1.0, "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"),
+                  (1.1, "0, 1965, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active"),
+                  (1.2, "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active")]
+    s = cs.summary(0.9, 1.3)
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] == 3

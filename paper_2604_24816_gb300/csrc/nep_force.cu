@@ -40,16 +40,11 @@ constexpr int FORCE_BLOCK = NEP_FORCE_BLOCK;
 #ifndef NEP_FORCE_MINB
 #define NEP_FORCE_MINB 2
 #endif
-// 1: the force kernel keeps the atom's own adjoint row G_i in shared memory ([component][thread],
-// conflict-free) instead of 120 registers.
-#ifndef NEP_FORCE_GI_SMEM
-#define NEP_FORCE_GI_SMEM 0
-#endif
 
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-constexpr int PIPE_DE = 16;   // list entries in flight per thread
-constexpr int PIPE_DP = 8;    // neighbour positions in flight per thread
+constexpr int PIPE_DE = 8;    // list entries in flight per thread
+constexpr int PIPE_DP = 4;    // neighbour positions in flight per thread
 
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
@@ -259,13 +254,8 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   if (i < n) {
     const float4 pi = pos[i];
     const float *Gi = G + (size_t)i * GSTRIDE;
-#if NEP_FORCE_GI_SMEM
-    extern __shared__ float gsm[];     // [NA * 24][FORCE_BLOCK]
-#define GI(a, lm) gsm[((a) * N_LM + (lm)) * FORCE_BLOCK + threadIdx.x]
-#else
     float gi[S::NA][N_LM];
 #define GI(a, lm) gi[a][lm]
-#endif
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll
@@ -415,17 +405,7 @@ cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *
                          int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  size_t smem = 0;
-#if NEP_FORCE_GI_SMEM
-  smem = (size_t)S::NA * N_LM * FORCE_BLOCK * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_force<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-#endif
-  k_force<S><<<grid, FORCE_BLOCK, smem, st>>>(P, g, n, pos, nbr, nown, nband0, G,
+  k_force<S><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
                                               reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }

@@ -47,13 +47,17 @@ typedef enum {
     NEP_ERR_NEIGH_OVERFLOW = 3,   /* an atom had more neighbours within rc_R + skin than max_neighbors */
     NEP_ERR_BOX_TOO_SMALL = 4,    /* some box edge < 2 * (rc_R + skin) */
     NEP_ERR_NAN = 5,              /* non-finite position or force detected */
-    NEP_ERR_TIMEOUT = 6,          /* a bounded host wait on the stream expired */
+    NEP_ERR_TIMEOUT = 6,          /* a bounded wait (host on the stream, or a kernel on the tensor cores) expired */
     NEP_ERR_STATE = 7,            /* call out of order (e.g. nep_compute before nep_set_state) */
     NEP_ERR_UNSUPPORTED = 8,      /* model shape without a compiled kernel instance */
     NEP_ERR_OOM = 9               /* device allocation failed */
 } nep_status;
 
-enum { NEP_FP32 = 0 };
+/* Arithmetic of the force evaluation.  NEP_FP32: everything in float32 (float64 integration and sums).
+ * NEP_MIX_BF16 / NEP_MIX_FP16: descriptors in float32; the network GEMMs (forward and gradient) on the
+ * tensor cores with bf16 / f16 operands and float32 accumulation; the per-atom adjoint rows stored in
+ * float16 (the paper's mixed precision, Section V.B Optimization 4 and Section VII.A). */
+enum { NEP_FP32 = 0, NEP_MIX_BF16 = 1, NEP_MIX_FP16 = 2 };
 
 /* Model and run parameters.  Host memory; copied by nep_create, the caller keeps ownership.
  * Descriptor order (n_des = (n_max_R+1) + (n_max_A+1)*l_max_3b + (n_max_A+1) if l_max_4b == 2):
@@ -81,7 +85,7 @@ typedef struct nep_params {
     float lj_eps, lj_sigma, lj_rc;   /* shifted-force LJ pair term; lj_eps = 0 disables it; lj_rc <= rc_R */
     double mass_amu;
     float skin;               /* neighbour-list skin (Angstrom); list radius rc_R + skin */
-    int precision;            /* NEP_FP32 */
+    int precision;            /* NEP_FP32, NEP_MIX_BF16 or NEP_MIX_FP16 */
     int max_neighbors;        /* per-atom list capacity, 1..128; 0 selects 128 */
     int rebuild_every;        /* MD: rebuild at least every k steps (0: only when an atom moved > skin/2) */
 } nep_params;

@@ -20,17 +20,24 @@
 
 #include "nep_gb300.h"
 #include "nep_common.cuh"
+#include "nep_tc.cuh"
 
 namespace nep {
 // nep_force.cu
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
                               float *, float *, float *, long long *, long long *, int *, cudaStream_t);
-template <class S>
+template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const float *, long long *, long long *, int *, cudaStream_t);
+                         const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
+// nep_mixed.cu
+template <class S, class MT>
+cudaError_t launch_descriptor_mixed(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
+                                    const int32_t *, __half *, float *, float *, long long *, long long *, int *,
+                                    cudaStream_t);
+int mixed_descriptor_blocks(int n);
 // nep_neighbor.cu
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
 cudaError_t launch_neighbors(const RebuildArgs &, cudaStream_t);
@@ -81,6 +88,7 @@ struct nep_handle {
   float skin = 1.0f, rcR = 0.f, rcA = 0.f;
   int cap = 128;
   int rebuild_every = 0;
+  int precision = NEP_FP32;
   std::string err;
 
   // system
@@ -96,7 +104,8 @@ struct nep_handle {
   int *id = nullptr, *idb = nullptr, *cell_of = nullptr, *perm = nullptr;
   float4 *pos = nullptr, *pos_ref = nullptr;
   long long *F = nullptr;          // fixed-point forces [3][n]
-  float *usite = nullptr, *G = nullptr, *qbuf = nullptr;
+  float *usite = nullptr, *qbuf = nullptr;
+  void *G = nullptr;               // adjoint rows: float32 (plain) or float16 (mixed) [n][128]
   int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr, *nown = nullptr, *nband0 = nullptr;
   int *count = nullptr, *cursor = nullptr, *start = nullptr, *tile_sums = nullptr;
   long long *part_d = nullptr, *part_f = nullptr, *part_k = nullptr;   // per-block int64 partial sums
@@ -272,13 +281,24 @@ cudaError_t enqueue_forces(nep_handle *h, float *qout) {
   cudaError_t e;
   {
     Scope sc(h, KC_DESC, 1);
-    e = launch_descriptor<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, h->G, h->usite, qout, h->F, h->part_d,
-                             &h->ctrl->status, h->stream);
+    if (h->precision == NEP_FP32)
+      e = launch_descriptor<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, static_cast<float *>(h->G), h->usite, qout,
+                               h->F, h->part_d, &h->ctrl->status, h->stream);
+    else if (h->precision == NEP_MIX_BF16)
+      e = launch_descriptor_mixed<S, __nv_bfloat16>(h->model, g, h->n, h->pos, h->nbr, h->nnum,
+                                                     static_cast<__half *>(h->G), h->usite, qout, h->F, h->part_d,
+                                                     &h->ctrl->status, h->stream);
+    else
+      e = launch_descriptor_mixed<S, __half>(h->model, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
+                                              h->usite, qout, h->F, h->part_d, &h->ctrl->status, h->stream);
   }
   if (e != cudaSuccess) return e;
   Scope sc(h, KC_FORCE, 1);
-  return launch_force<S>(h->model, g, h->n, h->pos, h->nbr, h->nown, h->nband0, h->G, h->F, h->part_f,
-                         &h->ctrl->status, h->stream);
+  if (h->precision == NEP_FP32)
+    return launch_force<S, float>(h->model, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G),
+                                  h->F, h->part_f, &h->ctrl->status, h->stream);
+  return launch_force<S, __half>(h->model, g, h->n, h->pos, h->nbr, h->nown, h->nband0,
+                                 static_cast<const __half *>(h->G), h->F, h->part_f, &h->ctrl->status, h->stream);
 }
 
 cudaError_t enqueue_finalize(nep_handle *h, bool with_kinetic) {
@@ -325,6 +345,7 @@ nep_status check_device_status(nep_handle *h) {
   if (st & ST_OVERFLOW)
     return fail(h, NEP_ERR_NEIGH_OVERFLOW, "an atom has more neighbours within rc_R + skin than max_neighbors");
   if (st & ST_NAN) return fail(h, NEP_ERR_NAN, "non-finite position, energy or force");
+  if (st & ST_TIMEOUT) return fail(h, NEP_ERR_TIMEOUT, "a bounded wait on the tensor cores ran out");
   return NEP_OK;
 }
 
@@ -431,7 +452,8 @@ nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) 
   if (p->n_max_R + 1 != S::NR || p->n_max_A + 1 != S::NA || p->basis_R != S::KR || p->basis_A != S::KA ||
       p->l_max_3b != S::LMAX || p->l_max_4b != (S::FOURBODY ? 2 : 0) || p->n_neu != S::NNEU)
     return NEP_ERR_UNSUPPORTED;
-  if (p->precision != NEP_FP32) return NEP_ERR_UNSUPPORTED;
+  if (p->precision != NEP_FP32 && p->precision != NEP_MIX_BF16 && p->precision != NEP_MIX_FP16)
+    return NEP_ERR_UNSUPPORTED;
   if (!p->c_R || !p->c_A || !p->W0 || !p->b0 || !p->w1 || !p->q_scale) return NEP_ERR_ARG;
   if (!(p->rc_R > 0.f) || !(p->rc_A > 0.f) || p->rc_A > p->rc_R || !(p->skin >= 0.f) || !(p->mass_amu > 0.0))
     return NEP_ERR_ARG;
@@ -478,6 +500,7 @@ nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) 
   h->rcA = p->rc_A;
   h->cap = p->max_neighbors ? p->max_neighbors : 128;
   h->rebuild_every = p->rebuild_every;
+  h->precision = p->precision;
 
   cudaError_t e;
   if (cuda_stream) {
@@ -550,7 +573,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   }
   if (ncell > (int64_t)1 << 30) return fail(h, NEP_ERR_ARG, "too many cells");
   h->ncell = (int)ncell;
-  h->nb_d = descriptor_blocks(h->n);
+  h->nb_d = h->precision == NEP_FP32 ? descriptor_blocks(h->n) : mixed_descriptor_blocks(h->n);
   h->nb_f = force_blocks(h->n);
   h->nb_k = md_blocks(h->n);
   const size_t N = (size_t)std::max(h->n, 1);
@@ -560,7 +583,8 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->xb, N)); A(dalloc(h->yb, N)); A(dalloc(h->zb, N)); A(dalloc(h->vxb, N)); A(dalloc(h->vyb, N)); A(dalloc(h->vzb, N));
   A(dalloc(h->id, N)); A(dalloc(h->idb, N)); A(dalloc(h->cell_of, N)); A(dalloc(h->perm, N));
   A(dalloc(h->pos, N)); A(dalloc(h->pos_ref, N));
-  A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N)); A(dalloc(h->G, N * GSTRIDE));
+  A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N));
+  A(dalloc(reinterpret_cast<char *&>(h->G), N * GSTRIDE * (h->precision == NEP_FP32 ? 4 : 2)));
   A(dalloc(h->nbr, N * (size_t)h->cap)); A(dalloc(h->nnum, N)); A(dalloc(h->nang, N)); A(dalloc(h->nown, N));
   A(dalloc(h->nband0, N));
   A(dalloc(h->count, (size_t)h->ncell)); A(dalloc(h->cursor, (size_t)h->ncell)); A(dalloc(h->start, (size_t)h->ncell + 1));

@@ -1,0 +1,188 @@
+// nep_descriptor.cuh -- per-atom descriptor pieces shared by the float32 and the mixed-precision
+// descriptor kernels: the neighbour walk that accumulates the radial sums q_n, the LJ energy and the
+// angular sums s_nlm (Section III.B; the geometry of each neighbour is computed once and reused for all
+// channels, Algorithm 1 with one tile), the rotation invariants q_nl and q4_n, and the adjoint row
+// G_nlm = dU/ds_nlm built from the network gradient.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "nep_common.cuh"
+
+namespace nep {
+
+// Adjoint rows are stored as float32 (plain form) or float16 (mixed-precision form); the force
+// kernel reads them W values per 16-byte load.
+template <class GT>
+struct GTraits;
+template <>
+struct GTraits<float> {
+  static constexpr int W = 4;
+};
+template <>
+struct GTraits<__half> {
+  static constexpr int W = 8;
+};
+
+__device__ __forceinline__ void load_vec(const float *p, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load_vec(const __half *p, float (&v)[8]) {
+  const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+  const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+    v[2 * k] = f.x; v[2 * k + 1] = f.y;
+  }
+}
+// The 8 values at the tail of a row (dU/dq_n of the radial descriptors and padding).
+template <class GT>
+__device__ __forceinline__ void load_tail8(const GT *row, int off, float (&v)[8]) {
+  constexpr int W = GTraits<GT>::W;
+#pragma unroll
+  for (int b = 0; b < 8; b += W) {
+    float t[W];
+    load_vec(row + off + b, t);
+#pragma unroll
+    for (int k = 0; k < W; ++k) v[b + k] = t[k];
+  }
+}
+
+template <class S>
+struct AtomSums {
+  float qR[S::NR];
+  float s[S::NA][N_LM];
+  float elj;
+  int nrad, nang, nact, cnt;
+};
+
+// Walk atom i's full neighbour row and accumulate q_n, s_nlm and the LJ energy.
+template <class S, int DE, int DP, int BLOCK>
+__device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 *shift, int i, int n,
+                                                const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
+                                                int cnt, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A) {
+  const float4 pi = pos[i];
+#pragma unroll
+  for (int a = 0; a < S::NR; ++a) A.qR[a] = 0.f;
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+    for (int c = 0; c < N_LM; ++c) A.s[a][c] = 0.f;
+  A.elj = 0.f;
+  A.nrad = 0; A.nang = 0; A.nact = 0; A.cnt = cnt;
+  NbrPipe<DE, DP, BLOCK> pipe;
+  pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
+  for (int k = 0; k < cnt; ++k) {
+    uint32_t e;
+    float4 pj;
+    pipe.get(k, e, pj);
+    const float4 o = shift[e >> J_BITS];
+    const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= P.rmax2) continue;
+    ++A.nact;
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    if (r2 < P.rcR2) {
+      float f[S::KR];
+      cheb_basis<S::KR>(r, P.inv_rcR, f);
+#pragma unroll
+      for (int a = 0; a < S::NR; ++a)
+#pragma unroll
+        for (int b = 0; b < S::KR; ++b) A.qR[a] = fmaf(P.cR[a][b], f[b], A.qR[a]);
+      ++A.nrad;
+    }
+    if (P.lj_on != 0.f && r2 < P.lj_rc2) {
+      float el, dl;
+      lj_pair<S>(P, r2, r, el, dl);
+      A.elj = fmaf(0.5f, el, A.elj);
+    }
+    if (r2 < P.rcA2) {
+      float f[S::KA];
+      cheb_basis<S::KA>(r, P.inv_rcA, f);
+      float g[S::NA];
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) {
+        float t = 0.f;
+#pragma unroll
+        for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
+        g[a] = t;
+      }
+      float Y[N_LM];
+      harmonics(dx * ir, dy * ir, dz * ir, Y);
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+        for (int c = 0; c < N_LM; ++c) A.s[a][c] = fmaf(g[a], Y[c], A.s[a][c]);
+      ++A.nang;
+    }
+  }
+  pipe.finish();
+}
+
+// Traceless 4-body tensors T_n rebuilt from the l = 2 sums (components 3..7 = m -2..2).
+template <class S>
+struct FourBody {
+  float xx[S::NA], yy[S::NA], zz[S::NA], xy[S::NA], yz[S::NA], xz[S::NA];
+};
+
+// Descriptors [q_n | q_nl (n-major, l = 1..4) | q4_n = tr(T_n^3) = 3 det T_n].
+template <class S>
+__device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[S::NDES], FourBody<S> &T) {
+#pragma unroll
+  for (int a = 0; a < S::NR; ++a) q[a] = A.qR[a];
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) {
+#pragma unroll
+    for (int l = 1; l <= 4; ++l) {
+      float t = 0.f;
+#pragma unroll
+      for (int c = l * l - 1; c < (l + 1) * (l + 1) - 1; ++c) t = fmaf(A.s[a][c], A.s[a][c], t);
+      q[S::NR + a * 4 + (l - 1)] = t;
+    }
+  }
+  if (S::FOURBODY) {
+    const float i3 = 0.57735026918962576f, third = 1.f / 3.f;
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) {
+      T.xy[a] = A.s[a][3] * i3;
+      T.yz[a] = A.s[a][4] * i3;
+      T.xz[a] = A.s[a][6] * i3;
+      T.xx[a] = A.s[a][7] * i3 - A.s[a][5] * third;
+      T.yy[a] = -A.s[a][7] * i3 - A.s[a][5] * third;
+      T.zz[a] = 2.f * A.s[a][5] * third;
+      const float det = T.xx[a] * (T.yy[a] * T.zz[a] - T.yz[a] * T.yz[a]) -
+                        T.xy[a] * (T.xy[a] * T.zz[a] - T.yz[a] * T.xz[a]) +
+                        T.xz[a] * (T.xy[a] * T.yz[a] - T.yy[a] * T.xz[a]);
+      q[S::NR + S::NA * 4 + a] = 3.f * det;
+    }
+  }
+}
+
+// Adjoint of channel a: gl[c] = dU/ds_{a,c} = 2 Fp_{a,l(c)} s_{a,c} (+ 4-body gradient for l = 2:
+// d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m).
+template <class S>
+__device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, const FourBody<S> &T,
+                                                const float (&Fp)[S::NDES], float (&gl)[N_LM]) {
+#pragma unroll
+  for (int c = 0; c < N_LM; ++c) gl[c] = 2.f * Fp[S::NR + a * 4 + lm_l(c) - 1] * A.s[a][c];
+  if (S::FOURBODY) {
+    const float f4 = Fp[S::NR + S::NA * 4 + a];
+    const float Mxx = T.xx[a] * T.xx[a] + T.xy[a] * T.xy[a] + T.xz[a] * T.xz[a];
+    const float Myy = T.xy[a] * T.xy[a] + T.yy[a] * T.yy[a] + T.yz[a] * T.yz[a];
+    const float Mzz = T.xz[a] * T.xz[a] + T.yz[a] * T.yz[a] + T.zz[a] * T.zz[a];
+    const float Mxy = T.xx[a] * T.xy[a] + T.xy[a] * T.yy[a] + T.xz[a] * T.yz[a];
+    const float Myz = T.xy[a] * T.xz[a] + T.yy[a] * T.yz[a] + T.yz[a] * T.zz[a];
+    const float Mxz = T.xx[a] * T.xz[a] + T.xy[a] * T.yz[a] + T.xz[a] * T.zz[a];
+    const float s3 = 1.7320508075688772f;
+    gl[3] = fmaf(f4, 2.f * s3 * Mxy, gl[3]);
+    gl[4] = fmaf(f4, 2.f * s3 * Myz, gl[4]);
+    gl[5] = fmaf(f4, 2.f * Mzz - Mxx - Myy, gl[5]);
+    gl[6] = fmaf(f4, 2.f * s3 * Mxz, gl[6]);
+    gl[7] = fmaf(f4, s3 * (Mxx - Myy), gl[7]);
+  }
+}
+
+}  // namespace nep

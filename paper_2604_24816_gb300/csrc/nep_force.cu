@@ -23,7 +23,7 @@
 //                Optimization 1) made deterministic.  Virial W = -sum_pairs r_ij (x) D_ij.
 //
 // Everything is float32 except the per-block energy/virial partial sums (float64).
-#include "nep_common.cuh"
+#include "nep_descriptor.cuh"
 
 namespace nep {
 
@@ -61,111 +61,15 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
   long long acc[5] = {0, 0, 0, 0, 0};
   if (i < n) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
-    const float4 pi = pos[i];
-    float qR[S::NR];
-    float s[S::NA][N_LM];
-#pragma unroll
-    for (int a = 0; a < S::NR; ++a) qR[a] = 0.f;
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a)
-#pragma unroll
-      for (int c = 0; c < N_LM; ++c) s[a][c] = 0.f;
-    float elj = 0.f;
-    int nrad = 0, nang = 0, nact = 0;
-    const int cnt = nnum[i];
-    NbrPipe<PIPE_DE, PIPE_DP, DESC_BLOCK> pipe;
-    pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
-    for (int k = 0; k < cnt; ++k) {
-      uint32_t e;
-      float4 pj;
-      pipe.get(k, e, pj);
-      const float4 o = shift[e >> J_BITS];
-      const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 >= P.rmax2) continue;
-      ++nact;
-      const float ir = rsqrtf(r2);
-      const float r = r2 * ir;
-      if (r2 < P.rcR2) {
-        float f[S::KR];
-        cheb_basis<S::KR>(r, P.inv_rcR, f);
-#pragma unroll
-        for (int a = 0; a < S::NR; ++a)
-#pragma unroll
-          for (int b = 0; b < S::KR; ++b) qR[a] = fmaf(P.cR[a][b], f[b], qR[a]);
-        ++nrad;
-      }
-      if (P.lj_on != 0.f && r2 < P.lj_rc2) {
-        float el, dl;
-        lj_pair<S>(P, r2, r, el, dl);
-        elj = fmaf(0.5f, el, elj);
-      }
-      if (r2 < P.rcA2) {
-        float f[S::KA];
-        cheb_basis<S::KA>(r, P.inv_rcA, f);
-        float g[S::NA];
-#pragma unroll
-        for (int a = 0; a < S::NA; ++a) {
-          float t = 0.f;
-#pragma unroll
-          for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
-          g[a] = t;
-        }
-        float Y[N_LM];
-        harmonics(dx * ir, dy * ir, dz * ir, Y);
-#pragma unroll
-        for (int a = 0; a < S::NA; ++a)
-#pragma unroll
-          for (int c = 0; c < N_LM; ++c) s[a][c] = fmaf(g[a], Y[c], s[a][c]);
-        ++nang;
-      }
-    }
-    pipe.finish();
-
-    // Descriptors: [q_n | q_nl (n-major, l = 1..4) | q4_n].
+    AtomSums<S> A;
+    accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
     float q[S::NDES];
-#pragma unroll
-    for (int a = 0; a < S::NR; ++a) q[a] = qR[a];
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a) {
-#pragma unroll
-      for (int l = 1; l <= 4; ++l) {
-        float t = 0.f;
-#pragma unroll
-        for (int c = l * l - 1; c < (l + 1) * (l + 1) - 1; ++c) t = fmaf(s[a][c], s[a][c], t);
-        q[S::NR + a * 4 + (l - 1)] = t;
-      }
-    }
-    // 4-body: T_n from the l = 2 sums (components 3..7 = m -2..2), tr(T^3) = 3 det T (T traceless).
-    float Txx[S::NA], Tyy[S::NA], Tzz[S::NA], Txy[S::NA], Tyz[S::NA], Txz[S::NA];
-    if (S::FOURBODY) {
-      const float i3 = 0.57735026918962576f, third = 1.f / 3.f;
-#pragma unroll
-      for (int a = 0; a < S::NA; ++a) {
-        Txy[a] = s[a][3] * i3;
-        Tyz[a] = s[a][4] * i3;
-        Txz[a] = s[a][6] * i3;
-        Txx[a] = s[a][7] * i3 - s[a][5] * third;
-        Tyy[a] = -s[a][7] * i3 - s[a][5] * third;
-        Tzz[a] = 2.f * s[a][5] * third;
-        const float det = Txx[a] * (Tyy[a] * Tzz[a] - Tyz[a] * Tyz[a]) - Txy[a] * (Txy[a] * Tzz[a] - Tyz[a] * Txz[a]) +
-                          Txz[a] * (Txy[a] * Tyz[a] - Tyy[a] * Txz[a]);
-        q[S::NR + S::NA * 4 + a] = 3.f * det;
-      }
-    }
+    FourBody<S> T;
+    descriptors_of<S>(A, q, T);
     if (qout != nullptr) {
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
     }
-    // Park s_nlm in this atom's adjoint row while the network runs (frees ~120 registers); it is
-    // read back below and overwritten in place by G_nlm.
-    float *Gi = G + (size_t)i * GSTRIDE;
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a)
-#pragma unroll
-      for (int c = 0; c < N_LM; c += 4)
-        *reinterpret_cast<float4 *>(Gi + a * N_LM + c) = make_float4(s[a][c], s[a][c + 1], s[a][c + 2], s[a][c + 3]);
-    asm volatile("" ::: "memory");
 
     // Network: U = sum_mu w1 tanh(sum_nu W0 q~_nu - b0) - b1; dU/dq~ accumulated in dq.
     float qt[S::NDES], dq[S::NDES];
@@ -187,34 +91,11 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
 
-    // Adjoint G_nlm = dU/ds_nlm = 2 Fp_nl s_nlm (+ 4-body term for l = 2), s read back from the row.
-    asm volatile("" ::: "memory");
+    float *Gi = G + (size_t)i * GSTRIDE;
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
       float gl[N_LM];
-#pragma unroll
-      for (int c = 0; c < N_LM; c += 4) {
-        const float4 t = *reinterpret_cast<const float4 *>(Gi + a * N_LM + c);
-        gl[c] = t.x; gl[c + 1] = t.y; gl[c + 2] = t.z; gl[c + 3] = t.w;
-      }
-#pragma unroll
-      for (int c = 0; c < N_LM; ++c) gl[c] *= 2.f * Fp[S::NR + a * 4 + lm_l(c) - 1];
-      if (S::FOURBODY) {
-        // d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m, M = T^2.
-        const float f4 = Fp[S::NR + S::NA * 4 + a];
-        const float Mxx = Txx[a] * Txx[a] + Txy[a] * Txy[a] + Txz[a] * Txz[a];
-        const float Myy = Txy[a] * Txy[a] + Tyy[a] * Tyy[a] + Tyz[a] * Tyz[a];
-        const float Mzz = Txz[a] * Txz[a] + Tyz[a] * Tyz[a] + Tzz[a] * Tzz[a];
-        const float Mxy = Txx[a] * Txy[a] + Txy[a] * Tyy[a] + Txz[a] * Tyz[a];
-        const float Myz = Txy[a] * Txz[a] + Tyy[a] * Tyz[a] + Tyz[a] * Tzz[a];
-        const float Mxz = Txx[a] * Txz[a] + Txy[a] * Tyz[a] + Txz[a] * Tzz[a];
-        const float s3 = 1.7320508075688772f;
-        gl[3] = fmaf(f4, 2.f * s3 * Mxy, gl[3]);
-        gl[4] = fmaf(f4, 2.f * s3 * Myz, gl[4]);
-        gl[5] = fmaf(f4, 2.f * Mzz - Mxx - Myy, gl[5]);
-        gl[6] = fmaf(f4, 2.f * s3 * Mxz, gl[6]);
-        gl[7] = fmaf(f4, s3 * (Mxx - Myy), gl[7]);
-      }
+      adjoint_channel<S>(a, A, T, Fp, gl);
 #pragma unroll
       for (int c = 0; c < N_LM; c += 4)
         *reinterpret_cast<float4 *>(Gi + a * N_LM + c) = make_float4(gl[c], gl[c + 1], gl[c + 2], gl[c + 3]);
@@ -226,23 +107,23 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
       *reinterpret_cast<float4 *>(Gi + S::NA * N_LM) = make_float4(tail[0], tail[1], tail[2], tail[3]);
       *reinterpret_cast<float4 *>(Gi + S::NA * N_LM + 4) = make_float4(tail[4], tail[5], tail[6], tail[7]);
     }
-    const float ui = U + elj;
+    const float ui = U + A.elj;
     usite[i] = ui;
     if (!isfinite(ui)) atomicOr(status, ST_NAN);
     acc[0] = to_fix32(ui);
-    acc[1] = nrad;
-    acc[2] = nang;
-    acc[3] = cnt;
-    acc[4] = nact;
+    acc[1] = A.nrad;
+    acc[2] = A.nang;
+    acc[3] = A.cnt;
+    acc[4] = A.nact;
   }
   block_sum_store<5>(acc, part);
 }
 
-template <class S>
+template <class S, class GT>
 __global__ void __launch_bounds__(FORCE_BLOCK, NEP_FORCE_MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
         const int32_t *__restrict__ nbr, const int32_t *__restrict__ nown, const int32_t *__restrict__ nband0,
-        const float *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
+        const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status) {
   __shared__ float4 shift[27];
   __shared__ uint32_t ring_e[PIPE_DE * FORCE_BLOCK];
@@ -253,23 +134,21 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   long long acc[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < n) {
     const float4 pi = pos[i];
-    const float *Gi = G + (size_t)i * GSTRIDE;
+    constexpr int W = GTraits<GT>::W;
+    const GT *Gi = G + (size_t)i * GSTRIDE;
     float gi[S::NA][N_LM];
 #define GI(a, lm) gi[a][lm]
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-      for (int c = 0; c < N_LM; c += 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4 *>(Gi + a * N_LM + c));
-        GI(a, c) = t.x; GI(a, c + 1) = t.y; GI(a, c + 2) = t.z; GI(a, c + 3) = t.w;
+      for (int c = 0; c < N_LM; c += W) {
+        float t[W];
+        load_vec(Gi + a * N_LM + c, t);
+#pragma unroll
+        for (int k = 0; k < W; ++k) GI(a, c + k) = t[k];
       }
     float fpi[8];
-    {
-      const float4 t0 = __ldg(reinterpret_cast<const float4 *>(Gi + S::NA * N_LM));
-      const float4 t1 = __ldg(reinterpret_cast<const float4 *>(Gi + S::NA * N_LM + 4));
-      fpi[0] = t0.x; fpi[1] = t0.y; fpi[2] = t0.z; fpi[3] = t0.w;
-      fpi[4] = t1.x; fpi[5] = t1.y; fpi[6] = t1.z; fpi[7] = t1.w;
-    }
+    load_tail8(Gi, S::NA * N_LM, fpi);
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
     const int cnt = nown[i];
@@ -285,7 +164,8 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       if (k + 1 < nb0 && k + 1 < cnt) {
         const uint32_t en = pipe.re[((k + 1) % PIPE_DE) * FORCE_BLOCK];
         const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * GSTRIDE);
-        prefetch_l1(gr); prefetch_l1(gr + 128); prefetch_l1(gr + 256); prefetch_l1(gr + 384);
+#pragma unroll
+        for (int b = 0; b < (int)(GSTRIDE * sizeof(GT)); b += 128) prefetch_l1(gr + b);
       }
       const int j = (int)(e & J_MASK);
       const float4 o = shift[e >> J_BITS];
@@ -295,15 +175,14 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       ++nact;
       const float ir = rsqrtf(r2);
       const float r = r2 * ir;
-      const float *Gj = G + (size_t)j * GSTRIDE;
+      const GT *Gj = G + (size_t)j * GSTRIDE;
       float coef = 0.f;                     // D = coef * d + (vx, vy, vz)
       float vx = 0.f, vy = 0.f, vz = 0.f;
       if (r2 < P.rcR2) {
         float f[S::KR], df[S::KR];
         cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
-        const float4 t0 = __ldg(reinterpret_cast<const float4 *>(Gj + S::NA * N_LM));
-        const float4 t1 = __ldg(reinterpret_cast<const float4 *>(Gj + S::NA * N_LM + 4));
-        const float fpj[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+        float fpj[8];
+        load_tail8(Gj, S::NA * N_LM, fpj);
         float c = 0.f;
 #pragma unroll
         for (int a = 0; a < S::NR; ++a) {
@@ -338,18 +217,18 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
         float along = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
         // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u)
 #pragma unroll
-        for (int c = 0; c < N_LM; c += 4) {
-          float4 hj[S::NA];
+        for (int c = 0; c < N_LM; c += W) {
+          float hj[S::NA][W];
 #pragma unroll
-          for (int a = 0; a < S::NA; ++a) hj[a] = __ldg(reinterpret_cast<const float4 *>(Gj + a * N_LM + c));
+          for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * N_LM + c, hj[a]);
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
+          for (int cc = 0; cc < W; ++cc) {
             const int lm = c + cc;
             const float sgn = (lm_l(lm) & 1) ? -1.f : 1.f;
             float av = 0.f, bv = 0.f;
 #pragma unroll
             for (int a = 0; a < S::NA; ++a) {
-              const float gjv = cc == 0 ? hj[a].x : (cc == 1 ? hj[a].y : (cc == 2 ? hj[a].z : hj[a].w));
+              const float gjv = hj[a][cc];
               const float H = fmaf(sgn, gjv, GI(a, lm));
               av = fmaf(H, dg[a], av);
               bv = fmaf(H, g[a], bv);
@@ -399,14 +278,14 @@ cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const flo
   return cudaGetLastError();
 }
 
-template <class S>
+template <class S, class GT>
 cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                         const int32_t *nown, const int32_t *nband0, const float *G, long long *Ffix, long long *part,
+                         const int32_t *nown, const int32_t *nband0, const GT *G, long long *Ffix, long long *part,
                          int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
-                                              reinterpret_cast<unsigned long long *>(Ffix), part, status);
+  k_force<S, GT><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
+                                               reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }
 
@@ -416,8 +295,11 @@ int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
 template cudaError_t launch_descriptor<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
                                                 const int32_t *, const int32_t *, float *, float *, float *,
                                                 long long *, long long *, int *, cudaStream_t);
-template cudaError_t launch_force<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                           const int32_t *, const int32_t *, const int32_t *, const float *,
-                                           long long *, long long *, int *, cudaStream_t);
+template cudaError_t launch_force<CuShape, float>(const Model<CuShape> &, const Geom &, int, const float4 *,
+                                                  const int32_t *, const int32_t *, const int32_t *, const float *,
+                                                  long long *, long long *, int *, cudaStream_t);
+template cudaError_t launch_force<CuShape, __half>(const Model<CuShape> &, const Geom &, int, const float4 *,
+                                                   const int32_t *, const int32_t *, const int32_t *, const __half *,
+                                                   long long *, long long *, int *, cudaStream_t);
 
 }  // namespace nep

@@ -1,0 +1,186 @@
+// nep_mixed.cu -- mixed-precision descriptor + network kernel (sm_103a, tcgen05 tensor cores).
+//
+// Same descriptors as k_descriptor (float32 neighbour walk, Section III.B), but the one-hidden-layer
+// network runs as two GEMMs on the 5th-generation tensor cores, one CTA = one 128-atom tile:
+//   forward   Z[128 x 32]  = Q~[128 x 32] . W0^T      (bf16 or f16 operands, f32 accumulation in TMEM)
+//   backward  dQ[128 x 32] = T[128 x 32] . W0          T_mu = w1_mu (1 - tanh(z_mu - b0_mu)^2)
+// (the batched network GEMM of Section V.B, Optimization 1 and Fig. 2c, with the half-precision network
+// input of Optimization 4).  Thread t of the CTA owns atom row t: it writes its row of the A tile into
+// shared memory and reads its row of the result from TMEM lane t.  The activation, the site energy and
+// the descriptor adjoint are float32; the adjoint rows G are stored as float16 (the paper's half-precision
+// storage of the per-atom gradient and angular accumulators), read by k_force<S, __half>.
+#include "nep_descriptor.cuh"
+#include "nep_tc.cuh"
+
+namespace nep {
+
+constexpr int MIX_BLOCK = 128;       // = the M extent of one tcgen05.mma tile
+constexpr int MIX_DE = 8, MIX_DP = 4;
+constexpr int MIX_K = 32;            // descriptors padded to 32 (two K = 16 steps)
+constexpr int MIX_N = 32;            // neurons padded to 32
+constexpr long MIX_WAIT = 1L << 22;  // mbarrier polls before giving up
+
+// Eight floats rounded to float16, packed for one 16-byte store.
+__device__ __forceinline__ uint4 pack8_half(const float *v) {
+  uint4 w;
+  __half2 h;
+  h = __floats2half2_rn(v[0], v[1]); w.x = *reinterpret_cast<uint32_t *>(&h);
+  h = __floats2half2_rn(v[2], v[3]); w.y = *reinterpret_cast<uint32_t *>(&h);
+  h = __floats2half2_rn(v[4], v[5]); w.z = *reinterpret_cast<uint32_t *>(&h);
+  h = __floats2half2_rn(v[6], v[7]); w.w = *reinterpret_cast<uint32_t *>(&h);
+  return w;
+}
+
+template <class S, class MT>
+__global__ void __launch_bounds__(MIX_BLOCK, 2)
+k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
+                   const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, __half *__restrict__ G,
+                   float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
+                   long long *__restrict__ part, int *__restrict__ status) {
+  static_assert(S::NDES <= MIX_K && S::NNEU <= MIX_N, "network larger than one tensor-core tile");
+  __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[MIX_DE * MIX_BLOCK];
+  __shared__ float4 ring_p[MIX_DP * MIX_BLOCK];
+  __shared__ __align__(1024) MT sA[MIX_BLOCK * MIX_K];     // A tile: q~ rows, then T rows
+  __shared__ __align__(1024) MT sW[MIX_N * MIX_K];         // B of the forward GEMM: W0[neuron][descriptor]
+  __shared__ __align__(1024) MT sWt[MIX_K * MIX_N];        // B of the backward GEMM: W0[descriptor][neuron]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x;
+  fill_shift_table(shift, geom);
+  if (t < 32) {
+    for (int k = 0; k < MIX_K; ++k) {
+      sW[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>((t < S::NNEU && k < S::NDES) ? P.W0[t][k] : 0.f);
+      sWt[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>((t < S::NDES && k < S::NNEU) ? P.W0[k][t] : 0.f);
+    }
+    tmem_alloc(&tmem_base, 64);
+    tc_fence_before();
+  }
+  if (t == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+
+  const int i = blockIdx.x * MIX_BLOCK + t;
+  const bool live = i < n;
+  AtomSums<S> A;
+  FourBody<S> T;
+  float q[S::NDES];
+  long long acc[5] = {0, 0, 0, 0, 0};
+  if (live) {
+    Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
+    accumulate_atom<S, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
+    descriptors_of<S>(A, q, T);
+    if (qout != nullptr) {
+#pragma unroll
+      for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) q[v] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < MIX_K; ++k) sA[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>(k < S::NDES ? q[k] * P.qs[k] : 0.f);
+  fence_async_smem();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = umma_idesc_f16(MIX_BLOCK, MIX_N, MmaKind<MT>::bf16);
+  const uint32_t lbo = 128, sbo = (MIX_K / 8) * 128;
+  if (t == 0) {
+#pragma unroll
+    for (int ks = 0; ks < MIX_K / 16; ++ks)
+      umma_f16(tmem, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo), umma_smem_desc(smem_addr(sW) + ks * 256, lbo, sbo),
+               idesc, ks);
+    umma_commit(&mbar);
+  }
+  bool ok = mbar_wait(&mbar, 0, MIX_WAIT);
+  tc_fence_after();
+  const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
+  float z[32];
+  tmem_ld32(tmem + lane_base, z);
+
+  // activation, site energy and the backward GEMM operand, in float32
+  float U = -P.b1;
+  float tr[MIX_N];
+#pragma unroll
+  for (int mu = 0; mu < MIX_N; ++mu) {
+    if (mu < S::NNEU) {
+      const float h = tanhf(z[mu] - P.b0[mu]);
+      U = fmaf(P.w1[mu], h, U);
+      tr[mu] = P.w1[mu] * (1.f - h * h);
+    } else {
+      tr[mu] = 0.f;
+    }
+  }
+  // the forward MMA has completed (mbarrier), so its A tile can be overwritten
+#pragma unroll
+  for (int k = 0; k < MIX_N; ++k) sA[tile_off(t, k, MIX_N / 8)] = to_mma_type<MT>(tr[k]);
+  fence_async_smem();
+  __syncthreads();
+  tc_fence_after();
+  if (t == 0) {
+#pragma unroll
+    for (int ks = 0; ks < MIX_N / 16; ++ks)
+      umma_f16(tmem + 32, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo),
+               umma_smem_desc(smem_addr(sWt) + ks * 256, lbo, sbo), idesc, ks);
+    umma_commit(&mbar);
+  }
+  ok = mbar_wait(&mbar, 1, MIX_WAIT) && ok;
+  tc_fence_after();
+  float dq[32];
+  tmem_ld32(tmem + lane_base + 32, dq);
+  if (!ok && t == 0) atomicOr(status, ST_TIMEOUT);
+
+  if (live) {
+    float Fp[S::NDES];
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
+    __half *Gi = G + (size_t)i * GSTRIDE;
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) {
+      float gl[N_LM];
+      adjoint_channel<S>(a, A, T, Fp, gl);
+#pragma unroll
+      for (int c = 0; c < N_LM; c += 8) *reinterpret_cast<uint4 *>(Gi + a * N_LM + c) = pack8_half(gl + c);
+    }
+    {
+      float tail[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a < S::NR; ++a) tail[a] = Fp[a];
+      *reinterpret_cast<uint4 *>(Gi + S::NA * N_LM) = pack8_half(tail);
+    }
+    const float ui = U + A.elj;
+    usite[i] = ui;
+    if (!isfinite(ui)) atomicOr(status, ST_NAN);
+    acc[0] = to_fix32(ui);
+    acc[1] = A.nrad;
+    acc[2] = A.nang;
+    acc[3] = A.cnt;
+    acc[4] = A.nact;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (t < 32) tmem_dealloc(tmem, 64);
+  block_sum_store<5>(acc, part);
+}
+
+template <class S, class MT>
+cudaError_t launch_descriptor_mixed(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
+                                    const int32_t *nnum, __half *G, float *usite, float *qout, long long *Ffix,
+                                    long long *part, int *status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + MIX_BLOCK - 1) / MIX_BLOCK;
+  k_descriptor_mixed<S, MT><<<grid, MIX_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status);
+  return cudaGetLastError();
+}
+
+int mixed_descriptor_blocks(int n) { return (n + MIX_BLOCK - 1) / MIX_BLOCK; }
+
+template cudaError_t launch_descriptor_mixed<CuShape, __nv_bfloat16>(const Model<CuShape> &, const Geom &, int,
+                                                                     const float4 *, const int32_t *, const int32_t *,
+                                                                     __half *, float *, float *, long long *,
+                                                                     long long *, int *, cudaStream_t);
+template cudaError_t launch_descriptor_mixed<CuShape, __half>(const Model<CuShape> &, const Geom &, int, const float4 *,
+                                                              const int32_t *, const int32_t *, __half *, float *,
+                                                              float *, long long *, long long *, int *, cudaStream_t);
+
+}  // namespace nep

@@ -29,9 +29,9 @@ namespace nep {
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
                               float *, float *, float *, long long *, long long *, int *, cudaStream_t);
-template <class S>
+template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const float *, long long *, long long *, int *, cudaStream_t);
+                         const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
@@ -245,8 +245,8 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   NA_CUDA(launch_neighbors(a, st));
   NA_CUDA(launch_descriptor<S>(M, g, N, a.pos, a.nbr, a.nnum, (float *)at(LAYOUT.G), (float *)at(LAYOUT.usite),
                                nullptr, Ffix, pd, &ctrl->status, st));
-  NA_CUDA(launch_force<S>(M, g, N, a.pos, a.nbr, a.nown, a.nband0, (const float *)at(LAYOUT.G), Ffix, pf,
-                          &ctrl->status, st));
+  NA_CUDA((launch_force<S, float>(M, g, N, a.pos, a.nbr, a.nown, a.nband0, (const float *)at(LAYOUT.G), Ffix, pf,
+                          &ctrl->status, st)));
   NA_CUDA(launch_finalize(pd, descriptor_blocks(N), pf, force_blocks(N), nullptr, 0, sums, counters, st));
   const bool f_dev = F && device_pointer(F);
   const bool e_dev = E && device_pointer(E);

@@ -21,6 +21,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libnep_gb300.so")
 DEFAULT_MODEL = os.path.join(_PKG, "params", "cu_nep4_synth.json")
 N_KERNEL_CLASSES = 8
+PRECISION = {"fp32": 0, "mix_bf16": 1, "mix_fp16": 2}
 KERNEL_CLASSES = ("drift", "cell_sort", "neighbors", "descriptor", "force", "kick", "reduce", "other")
 
 _lock = threading.Lock()
@@ -120,7 +121,7 @@ class NEP:
     """One handle of the CUDA library: a model plus one atomic configuration on the GPU."""
 
     def __init__(self, model: dict | None = None, stream=None, max_neighbors: int = 0, rebuild_every: int = 0,
-                 skin: float | None = None, lj: bool = True):
+                 skin: float | None = None, lj: bool = True, precision: str = "fp32"):
         self._L = lib()
         m = load_model() if model is None else model
         f32 = lambda k: np.ascontiguousarray(np.asarray(m[k], dtype=np.float32).ravel())
@@ -131,7 +132,8 @@ class NEP:
                        fp("c_R"), fp("c_A"), fp("W0"), fp("b0"), fp("w1"), float(m.get("b1", 0.0)), fp("q_scale"),
                        float(m.get("lj_eps", 0.0)) if lj else 0.0, float(m.get("lj_sigma", 1.0)),
                        float(m.get("lj_rc", m["rc_R"])), float(m.get("mass_amu", 63.546)),
-                       float(m.get("skin", 1.0) if skin is None else skin), 0, int(max_neighbors), int(rebuild_every))
+                       float(m.get("skin", 1.0) if skin is None else skin), PRECISION[precision], int(max_neighbors),
+                       int(rebuild_every))
         self.model = m
         nA = int(m["n_max_A"]) + 1
         self.n_des = (int(m["n_max_R"]) + 1) + nA * int(m["l_max_3b"]) + (nA if int(m["l_max_4b"]) == 2 else 0)

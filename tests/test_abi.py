@@ -66,7 +66,7 @@ def _params(model, **kw):
 
 
 @pytest.mark.parametrize("change,expected", [
-    (dict(n_neu=16), 8), (dict(l_max_3b=2), 8), (dict(basis_R=9), 8), (dict(precision=1), 8),
+    (dict(n_neu=16), 8), (dict(l_max_3b=2), 8), (dict(basis_R=9), 8), (dict(precision=7), 8),
     (dict(rc_A=6.0), 1), (dict(lj_rc=7.0), 1), (dict(skin=-1.0), 1), (dict(max_neighbors=1000), 1),
     (dict(mass_amu=0.0), 1),
 ])

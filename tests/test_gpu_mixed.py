@@ -1,0 +1,87 @@
+"""Mixed-precision form on the GPU (network GEMMs on the tcgen05 tensor cores with bf16/f16 operands and
+float32 accumulation, adjoint rows stored in float16) against the FP64 oracle.
+
+Bounds: force RMSE <= 5 meV/Angstrom over all atoms (the workload's bound for the mixed form), and
+the error budget of the arithmetic:
+  - bf16 operands carry 8 significand bits (unit roundoff 2^-9 = 2e-3), f16 11 bits (2^-12 = 2.4e-4); the
+    network output of an atom is ~0.05 eV, so site energies move by ~1e-4 eV (bf16) / ~1e-5 eV (f16);
+  - float16 adjoint rows add a relative 2^-12 to the NEP part of the forces (|F_NEP| <= 0.2 eV/A).
+"""
+import numpy as np
+import pytest
+
+import nep_inputs as ni
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["mix_bf16", "mix_fp16"]
+BOUNDS = {  # (max |dF| eV/A, |dE|/|E|, max |dU| eV)
+    "mix_bf16": (2e-2, 2e-4, 2e-3),
+    "mix_fp16": (3e-3, 3e-5, 3e-4),
+}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2604_24816_gb300 import build
+    build.build()
+    import paper_2604_24816_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("cells", [(4, 4, 4), (6, 6, 6)])
+def test_mixed_against_oracle(api, model_params, model, mode, cells):
+    wl = ni.fcc_cu_workload(0, sigma=0.05, seed=5 + sum(cells), cells_xyz=cells)
+    with api.NEP(model_params, precision=mode) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        E, F, W = nep.compute()
+        U = nep.site_energies()
+    Eo, Uo, Fo, Wo = oracle.energy_forces(model, wl.pos, wl.box)
+    dF = F - Fo
+    rmse = float(np.sqrt(np.mean(dF ** 2)))
+    fmax, erel, umax = BOUNDS[mode]
+    print(f"{mode} {cells}: force RMSE {rmse:.3e} max {np.abs(dF).max():.3e} eV/A, |dE|/|E| {abs(E - Eo) / abs(Eo):.2e}, "
+          f"max|dU| {np.abs(U - Uo).max():.2e} eV")
+    assert rmse <= 5e-3
+    assert np.abs(dF).max() <= fmax
+    assert abs(E - Eo) / abs(Eo) <= erel
+    assert np.abs(U - Uo).max() <= umax
+    assert np.abs(W - Wo).max() <= 1e-3 * np.abs(Wo).max()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_full_size_sampled(api, model_params, model, mode):
+    wl = ni.workload("cu_64x64x64")
+    with api.NEP(model_params, precision=mode) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        E, F, W = nep.compute()
+    idx = ni.sample_indices(wl.n, 4096, seed=7)
+    Fo, Uo = oracle.forces_sampled(model, wl.pos, wl.box, idx)
+    dF = F[idx] - Fo
+    rmse = float(np.sqrt(np.mean(dF ** 2)))
+    print(f"{mode} 1M atoms, 4096 sampled: force RMSE {rmse:.3e}, max {np.abs(dF).max():.3e} eV/A")
+    assert rmse <= 5e-3 and np.abs(dF).max() <= BOUNDS[mode][0]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_deterministic_and_md(api, model_params, mode):
+    c1 = ni.workload("cu_4x4x4")
+    res = []
+    for _ in range(2):
+        with api.NEP(model_params, precision=mode, rebuild_every=5) as nep:
+            nep.set_state(c1.pos, c1.vel, c1.box)
+            et = []
+            for _ in range(20):
+                nep.step(1.0, 50)
+                th = nep.thermo()
+                et.append((th["pe"] + th["ke"]) / c1.n)
+            res.append((nep.get_state(), et))
+    assert np.array_equal(res[0][0][0], res[1][0][0]) and np.array_equal(res[0][0][1], res[1][0][1])
+    drift = np.polyfit(np.arange(1, 21) * 0.05, np.array(res[0][1]), 1)[0]
+    print(f"{mode}: NVE drift {drift:.2e} eV/atom/ps over 1 ps")
+    assert abs(drift) < 1e-4

@@ -2,12 +2,19 @@
 """NEP molecular-dynamics throughput on GB300: atom-steps/s of plain FP32 NEP-MD.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                    [--form plain|mix_bf16|mix_fp16]
 
 One step = one velocity-Verlet MD step of the whole hot path on the 1,048,576-atom fcc Cu workload
 (64x64x64 cells, 300 K, 1 fs): half kick + drift, neighbour-rebuild check (a rebuild runs every 10
 steps -- the refresh interval of the paper's MD protocol -- and whenever an atom moved more than
 skin/2), cell sort + neighbour list when rebuilding, descriptors + network, forces + virial, half
 kick, energy/virial/kinetic sums.  Inputs are resident in HBM when the timed region starts.
+
+--form selects the form whose throughput is the headline value (default: plain FP32).  The other
+forms are then timed on the same workload and start state ("forms": atom-steps/s, speedup, and force
+RMSE/max against the plain FP32 forces on 8,192 sampled atoms; their error against the FP64 oracle is
+a GPU test).  --workload cu_160x160x160 (16,384,000 atoms, 300 K) or cu_160x160x160_1200K runs the
+mixed-precision workload.
 
 N > 1 (torchrun): every rank runs an independent replica on its own GPU (no collective on the data
 path); value = atom-steps of all ranks / max-over-ranks time ("scaling": "weak").
@@ -65,9 +72,13 @@ def kernel_flops(kind: str, c: dict, n_atoms_evals: int) -> float:
             f["angular_pair"] * ang + f["atom"] * n_atoms_evals)
 
 
+# sources of the descriptor and force kernels: a committed traffic figure is used only while they are unchanged
+SOURCE_FILES = ("nep_force.cu", "nep_common.cuh", "nep_descriptor.cuh", "nep_mixed.cu", "nep_tc.cuh")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("nep_force.cu", "nep_common.cuh"):
+    for f in SOURCE_FILES:
         with open(os.path.join(ROOT, "paper_2604_24816_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -195,14 +206,19 @@ def load_peaks() -> dict:
 
 
 def cpu_baseline(seconds_hint: float = 15.0) -> dict:
-    """The FP64 oracle, as it stands, timed on the host cores on a bounded sample of the workload."""
+    """The FP64 oracle, as it stands, timed on the host cores on a bounded sample of the workload: a
+    2-step probe on 16x16x16 cells sets the number of steps that fills about `seconds_hint` seconds,
+    and that run is the one reported."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     model = oracle.load_model(os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_nep4_synth.json"))
     wl = ni.workload("cu_16x16x16")
-    steps = 2
+    t0 = time.perf_counter()
+    oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, 1.0, 2)
+    per_step = (time.perf_counter() - t0) / 3.0          # 2 steps = 3 force evaluations
+    steps = int(min(200, max(2, seconds_hint / max(per_step, 1e-3))))
     t0 = time.perf_counter()
     oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, 1.0, steps)
     dt = time.perf_counter() - t0
@@ -250,6 +266,39 @@ def run_reference(args, rank: int, ws: int):
     }), flush=True)
 
 
+# form name -> (library precision, arithmetic types, description)
+FORMS = {
+    "plain": ("fp32", "f32", "plain FP32 NEP (float64 integration and sums)"),
+    "mix_bf16": ("mix_bf16", "bf16/f32", "mixed precision: network GEMMs on tcgen05 tensor cores with bf16 operands and "
+                 "f32 accumulation, float16 adjoint rows, FP32 descriptors, float64 integration and sums"),
+    "mix_fp16": ("mix_fp16", "f16/f32", "mixed precision: network GEMMs on tcgen05 tensor cores with f16 operands and "
+                 "f32 accumulation, float16 adjoint rows, FP32 descriptors, float64 integration and sums"),
+}
+
+
+def time_form(form, model, wl, args, stream, dev, ws, atoms_total):
+    """Throughput of another form on the same workload and start state (warm-up, then --form-steps
+    CUDA-graph MD steps timed with events), plus its forces on the start state."""
+    import torch
+    from paper_2604_24816_gb300 import NEP
+    with NEP(model, stream=stream.cuda_stream, rebuild_every=args.rebuild_every, precision=FORMS[form][0]) as h:
+        h.set_state(wl.pos, wl.vel, wl.box)
+        _, F, _ = h.compute()
+        h.step(wl.dt_fs, args.warmup)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        dist_barrier(ws)
+        torch.cuda.synchronize(dev)
+        s.record(stream)
+        h.step(wl.dt_fs, args.form_steps)
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = dist_max(s.elapsed_time(e), ws, dev)
+        th = h.thermo()
+    return {"value": atoms_total * args.form_steps / (ms * 1e-3), "ms_per_step": ms / args.form_steps,
+            "steps": args.form_steps, "dtype": FORMS[form][1], "pe_per_atom_end": th["pe"] / wl.n, "_F": F}
+
+
 def run_ours(args, rank: int, ws: int, local: int):
     import torch
     from paper_2604_24816_gb300 import NEP, load_model, build
@@ -261,7 +310,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     wl = ni.workload(args.workload) if rank == 0 else ni.fcc_cu_workload(
         64, 300.0, 0.05, seed=2 + rank, steps=200, name=args.workload)   # independent replica per rank
     stream = torch.cuda.Stream(device=dev)
-    nep = NEP(model, stream=stream.cuda_stream, rebuild_every=args.rebuild_every)
+    nep = NEP(model, stream=stream.cuda_stream, rebuild_every=args.rebuild_every, precision=FORMS[args.form][0])
     nep.set_state(wl.pos, wl.vel, wl.box)
     nep.compute(forces=False)
 
@@ -309,7 +358,8 @@ def run_ours(args, rank: int, ws: int, local: int):
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     traffic = profiled_traffic(dominant)
     roofline = {
-        "bound": "alu", "kernel": f"k_{dominant}", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
+        "bound": "alu",
+        "kernel": "k_descriptor_mixed" if dominant == "descriptor" and args.form != "plain" else f"k_{dominant}", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
         "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
         "traffic": (round(traffic["bytes"] * wl.n / traffic["atoms"]) if traffic else None),
         "peak_source": f"FP32 FFMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
@@ -348,16 +398,39 @@ def run_ours(args, rank: int, ws: int, local: int):
                "d2h_bytes_per_step": 48 * wl.n + 8 * 16, "steps": args.e2e_steps,
                "note": "per step: nep_set_state(x, v from pinned host) + md_verlet_step(1) (rebuild + 2 force "
                        "evaluations for the uploaded state) + nep_get_state(x, v to pinned host) + thermo"}
+    F_plain = None
+    others = [] if args.no_forms else [f for f in FORMS if f != args.form]
+    if others:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        _, F_this, _ = nep.compute()
     nep.close()
+    forms = {}
+    for f in others:
+        forms[f] = time_form(f, model, wl, args, stream, dev, ws, atoms_total)
+        if f == "plain":
+            F_plain = forms[f].pop("_F")
+    if args.form == "plain":
+        F_plain = F_this
+    if F_plain is not None:
+        idx = ni.sample_indices(wl.n, 8192, seed=11)
+        for f, rec in forms.items():
+            if "_F" in rec:
+                d = rec.pop("_F")[idx] - F_plain[idx]
+                rec["force_rmse_vs_plain"] = float(np.sqrt(np.mean(d ** 2)))
+                rec["force_max_vs_plain"] = float(np.abs(d).max())
+            rec["speedup_vs_this"] = round(rec["value"] / value, 4)
+        if args.form != "plain":
+            d = F_this[idx] - F_plain[idx]
+            forms["this_form_vs_plain"] = {"force_rmse": float(np.sqrt(np.mean(d ** 2))), "force_max": float(np.abs(d).max())}
 
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "form": "plain FP32 NEP (float64 integration "
-                   "and sums)", "dt_fs": wl.dt_fs, "temperature_K": wl.temperature,
+        "dtype": FORMS[args.form][1], "data": "synthetic",
+        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "form": FORMS[args.form][2],
+                   "dt_fs": wl.dt_fs, "temperature_K": wl.temperature,
                    "neighbor_rebuild": f"every {args.rebuild_every} steps + displacement check (skin/2)",
                    "rebuilds_in_timed_region": dc["rebuilds"],
                    "l2": "inputs larger than L2: per-step working set ~"
@@ -375,6 +448,7 @@ def run_ours(args, rank: int, ws: int, local: int):
                            "owned_angular": dc["owned_angular_pairs"] / max(1, evals * wl.n)},
         "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"]},
         "e2e": e2e,
+        "forms": forms or None,
         "source_hash": source_hash(),
     }
     if ws == 1 and not args.no_cpu_baseline:
@@ -393,6 +467,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="plain", choices=tuple(FORMS))
+    ap.add_argument("--form-steps", type=int, default=50)
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

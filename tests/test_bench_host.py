@@ -61,7 +61,7 @@ def test_traffic_lookup_requires_matching_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     (tmp_path / "profiles").mkdir()
     (tmp_path / "paper_2604_24816_gb300" / "csrc").mkdir(parents=True)
-    for f in ("nep_force.cu", "nep_common.cuh"):
+    for f in bench.SOURCE_FILES:
         (tmp_path / "paper_2604_24816_gb300" / "csrc" / f).write_text("x")
     h = bench.source_hash()
     (tmp_path / "profiles" / "traffic_per_launch.txt").write_text(f"# header\nforce {h} 1000 10\nforce deadbeef 5 1\n")

@@ -85,3 +85,35 @@ def test_mixed_deterministic_and_md(api, model_params, mode):
     drift = np.polyfit(np.arange(1, 21) * 0.05, np.array(res[0][1]), 1)[0]
     print(f"{mode}: NVE drift {drift:.2e} eV/atom/ps over 1 ps")
     assert abs(drift) < 1e-4
+
+
+# ---- 16,384,000-atom cells (160x160x160) at 300 K and 1200 K: sampled oracle errors, drift vs plain ----
+C3 = ["cu_160x160x160", "cu_160x160x160_1200K"]
+
+
+@pytest.mark.parametrize("name", C3)
+def test_mixed_c3_sampled_and_drift(api, model_params, model, name):
+    wl = ni.workload(name)
+    idx = ni.sample_indices(wl.n, 8192, seed=11)
+    Fo, Uo = oracle.forces_sampled(model, wl.pos, wl.box, idx)
+    de = {}
+    for form in ["fp32"] + MODES:
+        with api.NEP(model_params, precision=form, rebuild_every=10) as nep:
+            nep.set_state(wl.pos, wl.vel, wl.box)
+            E, F, W = nep.compute()
+            th0 = nep.thermo()
+            nep.step(wl.dt_fs, 100)
+            th1 = nep.thermo()
+        dF = F[idx] - Fo
+        rmse, fmax = float(np.sqrt(np.mean(dF ** 2))), float(np.abs(dF).max())
+        de[form] = ((th1["pe"] + th1["ke"]) - (th0["pe"] + th0["ke"])) / wl.n
+        print(f"{name} {form}: 8192 sampled force RMSE {rmse:.3e} max {fmax:.3e} eV/A; "
+              f"energy change over 100 steps {de[form]:+.3e} eV/atom")
+        if form == "fp32":
+            assert fmax <= 1e-4
+        else:
+            assert rmse <= 5e-3 and fmax <= BOUNDS[form][0]
+    # measured: the mixed forms' energy change over 100 steps differs from the plain path's by <= 1.6e-6
+    # eV/atom (300 K) and 2e-7 eV/atom (1200 K), against plain changes of 5e-5 and 4.8e-4 eV/atom
+    for form in MODES:
+        assert abs(de[form] - de["fp32"]) <= 2e-5

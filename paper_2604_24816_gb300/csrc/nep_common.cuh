@@ -246,19 +246,33 @@ __device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, fl
   de = (-12.f * a12 + 6.f * a6) / r - P.lj_de_rc;
 }
 
-// Exact conversion of a float to 64-bit fixed point with 32 fractional bits (round half away from
-// zero), using integer operations only (no 64-bit conversion instruction, which would run on the
-// narrow FP64 pipe).  Valid for |v| < 2^30; zero and subnormals map to 0.
+// Exact conversion of a float to 64-bit fixed point with 32 fractional bits, without a 64-bit
+// conversion instruction (those run on the narrow FP64 pipe).
+// |v| < 2^12 (every force, energy and virial term of a physical configuration): v * 2^32 is split as
+// h * 2^22 + l with h = rint(v * 2^10) and |l| <= 2^21.  Both parts are exact in float32 (l is the
+// rounding remainder of v * 2^10, scaled by a power of two), and each is turned into an integer by
+// adding 1.5 * 2^23, which places the rounded integer in the low mantissa bits: full-rate FP32 and
+// integer instructions only, rounding to nearest (ties to even).
+// Larger magnitudes, infinities and NaN take an integer bit-manipulation path (round half away from
+// zero; valid for |v| < 2^30).  Either way the result is a fixed function of v, so fixed-point sums
+// do not depend on the order of their terms.
 __device__ __forceinline__ long long to_fix32(float v) {
+  constexpr float SHIFT = 12582912.0f;          // 1.5 * 2^23
+  if (fabsf(v) < 4096.f) {
+    const float hm = fmaf(v, 1024.f, SHIFT);     // SHIFT + rint(v * 2^10)
+    const float h = hm - SHIFT;
+    const float l = fmaf(v, 4294967296.f, -h * 4194304.f);
+    const int hi = __float_as_int(hm) - 0x4B400000;
+    const int lo = __float_as_int(l + SHIFT) - 0x4B400000;
+    return ((long long)hi << 22) + lo;
+  }
   const uint32_t b = __float_as_uint(v);
   const int ex = (int)((b >> 23) & 0xffu);
-  if (ex == 0) return 0;
   const long long man = (long long)((b & 0x7fffffu) | 0x800000u);
   const int sh = ex - 118;                      // v * 2^32 = man * 2^(ex - 127 - 23 + 32)
   long long r;
   if (sh >= 0) r = man << min(sh, 39);
-  else if (sh > -25) r = (man + (1ll << (-sh - 1))) >> (-sh);
-  else r = 0;
+  else r = (man + (1ll << (-sh - 1))) >> (-sh);
   return (b >> 31) ? -r : r;
 }
 

@@ -43,8 +43,10 @@ constexpr int FORCE_BLOCK = NEP_FORCE_BLOCK;
 
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-constexpr int PIPE_DE = 8;    // list entries in flight per thread
-constexpr int PIPE_DP = 4;    // neighbour positions in flight per thread
+constexpr int PIPE_DE = 8;    // list entries in flight per thread (descriptor kernel)
+constexpr int PIPE_DP = 4;    // neighbour positions in flight per thread (descriptor kernel)
+constexpr int FPIPE_DE = 6;   // the same for the force kernel, whose pairs take longer
+constexpr int FPIPE_DP = 3;
 
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
@@ -126,8 +128,8 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
         const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status) {
   __shared__ float4 shift[27];
-  __shared__ uint32_t ring_e[PIPE_DE * FORCE_BLOCK];
-  __shared__ float4 ring_p[PIPE_DP * FORCE_BLOCK];
+  __shared__ uint32_t ring_e[FPIPE_DE * FORCE_BLOCK];
+  __shared__ float4 ring_p[FPIPE_DP * FORCE_BLOCK];
   fill_shift_table(shift, geom);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,7 +156,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     const int cnt = nown[i];
     const int nb0 = nband0[i];
     int nrad = 0, nang = 0, nact = 0;
-    NbrPipe<PIPE_DE, PIPE_DP, FORCE_BLOCK> pipe;
+    NbrPipe<FPIPE_DE, FPIPE_DP, FORCE_BLOCK> pipe;
     pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
     for (int k = 0; k < cnt; ++k) {
       uint32_t e;
@@ -162,7 +164,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       pipe.get(k, e, pj);
       // pull the next angular neighbour's adjoint row into L1 while this pair is computed
       if (k + 1 < nb0 && k + 1 < cnt) {
-        const uint32_t en = pipe.re[((k + 1) % PIPE_DE) * FORCE_BLOCK];
+        const uint32_t en = pipe.re[((k + 1) % FPIPE_DE) * FORCE_BLOCK];
         const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * GSTRIDE);
 #pragma unroll
         for (int b = 0; b < (int)(GSTRIDE * sizeof(GT)); b += 128) prefetch_l1(gr + b);

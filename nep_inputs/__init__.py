@@ -23,6 +23,8 @@ EV_PER_AMU_A2_FS2 = 103.642696562  # 1 amu*A^2/fs^2 in eV  (kinetic-energy unit 
 # NEP hyperparameters of the Cu model (Section VI.A: n_max 4, basis size 8, 3-body l_max 4,
 # 4-body l_max 2, 30 neurons; cutoffs 5.0 / 4.0 Angstrom as the workload specifies).
 NEP_DIMS = dict(n_max_R=4, n_max_A=4, basis_R=8, basis_A=8, l_max_3b=4, l_max_4b=2, n_neu=30)
+# the distilled student: fewer channels, l <= 2, no 4-body term, narrower hidden layer
+STUDENT_DIMS = dict(n_max_R=3, n_max_A=3, basis_R=8, basis_A=8, l_max_3b=2, l_max_4b=0, n_neu=16)
 N_DES = (NEP_DIMS["n_max_R"] + 1) + (NEP_DIMS["n_max_A"] + 1) * NEP_DIMS["l_max_3b"] + (NEP_DIMS["n_max_A"] + 1)
 RC_R = 5.0
 RC_A = 4.0
@@ -65,7 +67,7 @@ def random_nep_weights(seed: int, dims: dict = NEP_DIMS):
     rng = np.random.default_rng(seed)
     nR, nA = dims["n_max_R"] + 1, dims["n_max_A"] + 1
     kR, kA = dims["basis_R"], dims["basis_A"]
-    n_des = nR + nA * dims["l_max_3b"] + nA
+    n_des = nR + nA * dims["l_max_3b"] + (nA if dims["l_max_4b"] > 0 else 0)
     nneu = dims["n_neu"]
     c_R = rng.uniform(-1.0, 1.0, size=(nR, kR))
     c_A = rng.uniform(-1.0, 1.0, size=(nA, kA))

@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
 class _Params(C.Structure):
     _fields_ = [
         ("nR", C.c_int), ("nA", C.c_int), ("kR", C.c_int), ("kA", C.c_int), ("lmax", C.c_int),
-        ("nneu", C.c_int), ("ndes", C.c_int),
+        ("nneu", C.c_int), ("ndes", C.c_int), ("fourbody", C.c_int),
         ("rcR", C.c_double), ("rcA", C.c_double),
         ("cR", C.POINTER(C.c_double)), ("cA", C.POINTER(C.c_double)), ("W0", C.POINTER(C.c_double)),
         ("b0", C.POINTER(C.c_double)), ("w1", C.POINTER(C.c_double)), ("b1", C.c_double),
@@ -98,12 +98,13 @@ class Model:
         nA = int(params["n_max_A"]) + 1
         kR, kA = int(params["basis_R"]), int(params["basis_A"])
         lmax, nneu = int(params["l_max_3b"]), int(params["n_neu"])
-        ndes = nR + nA * lmax + nA
+        fourbody = 1 if int(params.get("l_max_4b", 2)) > 0 else 0
+        ndes = nR + nA * lmax + (nA if fourbody else 0)
         self.ndes, self.nR, self.nA, self.lmax = ndes, nR, nA, lmax
         for k, shape in (("c_R", (nR, kR)), ("c_A", (nA, kA)), ("W0", (nneu, ndes)), ("b0", (nneu,)),
                          ("w1", (nneu,)), ("q_scale", (ndes,))):
             self.p[k] = _f64(params[k], shape)
-        self.s = _Params(nR, nA, kR, kA, lmax, nneu, ndes, float(params["rc_R"]), float(params["rc_A"]),
+        self.s = _Params(nR, nA, kR, kA, lmax, nneu, ndes, fourbody, float(params["rc_R"]), float(params["rc_A"]),
                          _dp(self.p["c_R"]), _dp(self.p["c_A"]), _dp(self.p["W0"]), _dp(self.p["b0"]),
                          _dp(self.p["w1"]), float(params.get("b1", 0.0)), _dp(self.p["q_scale"]),
                          float(params.get("lj_eps", 0.0)), float(params.get("lj_sigma", 1.0)),

@@ -48,7 +48,8 @@
 #define MAXNEU 128
 
 typedef struct {
-    int nR, nA, kR, kA, lmax, nneu, ndes; /* nR = n_max_R + 1, nA = n_max_A + 1; ndes = nR + nA*lmax + nA */
+    int nR, nA, kR, kA, lmax, nneu, ndes; /* nR = n_max_R + 1, nA = n_max_A + 1; ndes = nR + nA*lmax (+ nA) */
+    int fourbody;                         /* 1: the 4-body descriptors q4_n are present (teacher), 0: absent */
     double rcR, rcA;
     const double *cR;    /* [nR][kR] */
     const double *cA;    /* [nA][kA] */
@@ -317,7 +318,7 @@ static void atom_descriptors(const onep *P, int nn, const double *d, double *q) 
                 for (int l = 1; l <= P->lmax; ++l) q[idx_3b(P, n, l)] += ga[n] * gb[n] * Pl[l];
         }
     }
-    for (int n = 0; n < P->nA; ++n) {
+    for (int n = 0; P->fourbody && n < P->nA; ++n) {
         double T2[3][3], tr3 = 0.0;
         for (int s = 0; s < 3; ++s)
             for (int t = 0; t < 3; ++t) {
@@ -383,7 +384,8 @@ static double atom_site(const onep *P, int nn, const double *d, double *dU, doub
                 for (int t = 0; t < 3; ++t) T[n][s][t] += ga[n] * (ua[s] * ua[t] - (s == t ? 1.0 / 3.0 : 0.0));
     }
     double M[MAXN][3][3];
-    for (int n = 0; n < P->nA; ++n)
+    memset(M, 0, sizeof(M));
+    for (int n = 0; P->fourbody && n < P->nA; ++n)
         for (int s = 0; s < 3; ++s)
             for (int t = 0; t < 3; ++t) {
                 double v = 0.0;
@@ -432,7 +434,7 @@ static double atom_site(const onep *P, int nn, const double *d, double *dU, doub
         }
         for (int t = 0; t < 3; ++t) out[t] += along_u * ua[t] + perp[t];
         /* 4-body: sum_ab M_ab dT_ab/dr_a, T_ab = g (u_a u_b - delta/3) */
-        for (int n = 0; n < P->nA; ++n) {
+        for (int n = 0; P->fourbody && n < P->nA; ++n) {
             double Mu[3], uMu = 0.0, trM = M[n][0][0] + M[n][1][1] + M[n][2][2];
             for (int s = 0; s < 3; ++s) {
                 Mu[s] = M[n][s][0] * ua[0] + M[n][s][1] * ua[1] + M[n][s][2] * ua[2];

@@ -29,15 +29,17 @@ WEIGHT_SEED = 2604
 SCALER_SIGMAS = (0.05, 0.05, 0.05)
 
 
-def make_model() -> dict:
-    w = ni.random_nep_weights(WEIGHT_SEED)
-    params = dict(ni.NEP_DIMS)
+def make_model(dims: dict = ni.NEP_DIMS, seed: int = WEIGHT_SEED) -> dict:
+    """Seeded model of shape `dims` (the teacher by default; ni.STUDENT_DIMS gives a seeded, untrained
+    student used by the parity tests of the student-shaped kernels)."""
+    w = ni.random_nep_weights(seed, dims)
+    params = dict(dims)
     params.update(rc_R=ni.RC_R, rc_A=ni.RC_A, lj_eps=ni.LJ["eps"], lj_sigma=ni.LJ["sigma"], lj_rc=ni.LJ["rc"],
-                  mass_amu=ni.M_CU, skin=ni.SKIN, weight_seed=WEIGHT_SEED)
+                  mass_amu=ni.M_CU, skin=ni.SKIN, weight_seed=seed)
     for k in ("c_R", "c_A", "W0", "b0", "w1"):
         params[k] = np.asarray(w[k]).tolist()
     params["b1"] = float(w["b1"])
-    params["q_scale"] = [1.0] * ni.N_DES
+    params["q_scale"] = [1.0] * np.asarray(w["W0"]).shape[1]
     qs = []
     for k, sigma in enumerate(SCALER_SIGMAS):
         wl = ni.fcc_cu_workload(4, 300.0, sigma, seed=100 + k)

@@ -63,7 +63,6 @@ cudaError_t launch_store_neighbors(int, int, int, const int *, const int32_t *, 
 }  // namespace nep
 
 using namespace nep;
-using S = CuShape;
 
 namespace {
 
@@ -83,7 +82,9 @@ struct Timer {
 struct nep_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  Model<S> model{};
+  int shape = 0;                   // 0: teacher shape (CuShape), 1: student shape (StudentShape)
+  Model<CuShape> model_t{};
+  Model<StudentShape> model_s{};
   double mass = 1.0;
   float skin = 1.0f, rcR = 0.f, rcA = 0.f;
   int cap = 128;
@@ -105,7 +106,7 @@ struct nep_handle {
   float4 *pos = nullptr, *pos_ref = nullptr;
   long long *F = nullptr;          // fixed-point forces [3][n]
   float *usite = nullptr, *qbuf = nullptr;
-  void *G = nullptr;               // adjoint rows: float32 (plain) or float16 (mixed) [n][128]
+  void *G = nullptr;               // adjoint rows: float32 (plain) or float16 (mixed) [n][GS]
   int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr, *nown = nullptr, *nband0 = nullptr;
   int *count = nullptr, *cursor = nullptr, *start = nullptr, *tile_sums = nullptr;
   long long *part_d = nullptr, *part_f = nullptr, *part_k = nullptr;   // per-block int64 partial sums
@@ -134,6 +135,9 @@ struct nep_handle {
   double ms[NEP_N_KERNEL_CLASSES] = {0};
   long long launches[NEP_N_KERNEL_CLASSES] = {0};
   long long launch_total = 0;
+
+  int ndes() const { return shape == 0 ? CuShape::NDES : StudentShape::NDES; }
+  int gs() const { return shape == 0 ? CuShape::GS : StudentShape::GS; }
 };
 
 namespace {
@@ -276,29 +280,33 @@ cudaError_t enqueue_rebuild(nep_handle *h) {
 }
 
 // Descriptors + network + forces; partial sums reduced with KE partials pk (may be null).
-cudaError_t enqueue_forces(nep_handle *h, float *qout) {
+template <class S>
+cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   const Geom g = geom_of(h);
   cudaError_t e;
   {
     Scope sc(h, KC_DESC, 1);
     if (h->precision == NEP_FP32)
-      e = launch_descriptor<S>(h->model, g, h->n, h->pos, h->nbr, h->nnum, static_cast<float *>(h->G), h->usite, qout,
-                               h->F, h->part_d, &h->ctrl->status, h->stream);
+      e = launch_descriptor<S>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<float *>(h->G), h->usite, qout, h->F,
+                               h->part_d, &h->ctrl->status, h->stream);
     else if (h->precision == NEP_MIX_BF16)
-      e = launch_descriptor_mixed<S, __nv_bfloat16>(h->model, g, h->n, h->pos, h->nbr, h->nnum,
-                                                     static_cast<__half *>(h->G), h->usite, qout, h->F, h->part_d,
-                                                     &h->ctrl->status, h->stream);
+      e = launch_descriptor_mixed<S, __nv_bfloat16>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
+                                                     h->usite, qout, h->F, h->part_d, &h->ctrl->status, h->stream);
     else
-      e = launch_descriptor_mixed<S, __half>(h->model, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
+      e = launch_descriptor_mixed<S, __half>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
                                               h->usite, qout, h->F, h->part_d, &h->ctrl->status, h->stream);
   }
   if (e != cudaSuccess) return e;
   Scope sc(h, KC_FORCE, 1);
   if (h->precision == NEP_FP32)
-    return launch_force<S, float>(h->model, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G),
+    return launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G),
                                   h->F, h->part_f, &h->ctrl->status, h->stream);
-  return launch_force<S, __half>(h->model, g, h->n, h->pos, h->nbr, h->nown, h->nband0,
-                                 static_cast<const __half *>(h->G), h->F, h->part_f, &h->ctrl->status, h->stream);
+  return launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const __half *>(h->G),
+                                 h->F, h->part_f, &h->ctrl->status, h->stream);
+}
+
+cudaError_t enqueue_forces(nep_handle *h, float *qout) {
+  return h->shape == 0 ? forces_of<CuShape>(h, h->model_t, qout) : forces_of<StudentShape>(h, h->model_s, qout);
 }
 
 cudaError_t enqueue_finalize(nep_handle *h, bool with_kinetic) {
@@ -423,46 +431,17 @@ const int LAUNCHES_PER_STEP = 16;
 }  // namespace
 
 // =====================================================================================================
-extern "C" {
+namespace {
 
-const char *nep_status_string(nep_status s) {
-  switch (s) {
-    case NEP_OK: return "NEP_OK";
-    case NEP_ERR_ARG: return "NEP_ERR_ARG";
-    case NEP_ERR_CUDA: return "NEP_ERR_CUDA";
-    case NEP_ERR_NEIGH_OVERFLOW: return "NEP_ERR_NEIGH_OVERFLOW";
-    case NEP_ERR_BOX_TOO_SMALL: return "NEP_ERR_BOX_TOO_SMALL";
-    case NEP_ERR_NAN: return "NEP_ERR_NAN";
-    case NEP_ERR_TIMEOUT: return "NEP_ERR_TIMEOUT";
-    case NEP_ERR_STATE: return "NEP_ERR_STATE";
-    case NEP_ERR_UNSUPPORTED: return "NEP_ERR_UNSUPPORTED";
-    case NEP_ERR_OOM: return "NEP_ERR_OOM";
-  }
-  return "NEP_ERR_UNKNOWN";
+template <class S>
+bool shape_matches(const nep_params *p) {
+  return p->n_max_R + 1 == S::NR && p->n_max_A + 1 == S::NA && p->basis_R == S::KR && p->basis_A == S::KA &&
+         p->l_max_3b == S::LMAX && p->l_max_4b == (S::FOURBODY ? 2 : 0) && p->n_neu == S::NNEU;
 }
 
-const char *nep_last_error(nep_handle *h) {
-  if (!h) return "null handle";
-  return h->err.c_str();
-}
-
-nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) {
-  if (!p || !out) return NEP_ERR_ARG;
-  *out = nullptr;
-  if (p->n_max_R + 1 != S::NR || p->n_max_A + 1 != S::NA || p->basis_R != S::KR || p->basis_A != S::KA ||
-      p->l_max_3b != S::LMAX || p->l_max_4b != (S::FOURBODY ? 2 : 0) || p->n_neu != S::NNEU)
-    return NEP_ERR_UNSUPPORTED;
-  if (p->precision != NEP_FP32 && p->precision != NEP_MIX_BF16 && p->precision != NEP_MIX_FP16)
-    return NEP_ERR_UNSUPPORTED;
-  if (!p->c_R || !p->c_A || !p->W0 || !p->b0 || !p->w1 || !p->q_scale) return NEP_ERR_ARG;
-  if (!(p->rc_R > 0.f) || !(p->rc_A > 0.f) || p->rc_A > p->rc_R || !(p->skin >= 0.f) || !(p->mass_amu > 0.0))
-    return NEP_ERR_ARG;
-  if (p->lj_eps != 0.f && (!(p->lj_rc > 0.f) || p->lj_rc > p->rc_R || !(p->lj_sigma > 0.f))) return NEP_ERR_ARG;
-  if (p->max_neighbors < 0 || p->max_neighbors > 128 || p->rebuild_every < 0) return NEP_ERR_ARG;
-
-  nep_handle *h = new (std::nothrow) nep_handle();
-  if (!h) return NEP_ERR_OOM;
-  Model<S> &M = h->model;
+// Model parameters in the kernels' layout (float32, LJ shifted-force constants precomputed in float64).
+template <class S>
+void fill_model(Model<S> &M, const nep_params *p) {
   for (int a = 0; a < S::NR; ++a)
     for (int b = 0; b < S::KR; ++b) M.cR[a][b] = p->c_R[a * S::KR + b];
   for (int a = 0; a < S::NA; ++a)
@@ -494,6 +473,53 @@ nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) 
   }
   const float rmax = std::max(p->rc_R, eps != 0.0 ? p->lj_rc : 0.f);
   M.rmax2 = rmax * rmax;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nep_status_string(nep_status s) {
+  switch (s) {
+    case NEP_OK: return "NEP_OK";
+    case NEP_ERR_ARG: return "NEP_ERR_ARG";
+    case NEP_ERR_CUDA: return "NEP_ERR_CUDA";
+    case NEP_ERR_NEIGH_OVERFLOW: return "NEP_ERR_NEIGH_OVERFLOW";
+    case NEP_ERR_BOX_TOO_SMALL: return "NEP_ERR_BOX_TOO_SMALL";
+    case NEP_ERR_NAN: return "NEP_ERR_NAN";
+    case NEP_ERR_TIMEOUT: return "NEP_ERR_TIMEOUT";
+    case NEP_ERR_STATE: return "NEP_ERR_STATE";
+    case NEP_ERR_UNSUPPORTED: return "NEP_ERR_UNSUPPORTED";
+    case NEP_ERR_OOM: return "NEP_ERR_OOM";
+  }
+  return "NEP_ERR_UNKNOWN";
+}
+
+const char *nep_last_error(nep_handle *h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) {
+  if (!p || !out) return NEP_ERR_ARG;
+  *out = nullptr;
+  int shape;
+  if (shape_matches<CuShape>(p)) shape = 0;
+  else if (shape_matches<StudentShape>(p)) shape = 1;
+  else return NEP_ERR_UNSUPPORTED;
+  if (p->precision != NEP_FP32 && p->precision != NEP_MIX_BF16 && p->precision != NEP_MIX_FP16)
+    return NEP_ERR_UNSUPPORTED;
+  if (!p->c_R || !p->c_A || !p->W0 || !p->b0 || !p->w1 || !p->q_scale) return NEP_ERR_ARG;
+  if (!(p->rc_R > 0.f) || !(p->rc_A > 0.f) || p->rc_A > p->rc_R || !(p->skin >= 0.f) || !(p->mass_amu > 0.0))
+    return NEP_ERR_ARG;
+  if (p->lj_eps != 0.f && (!(p->lj_rc > 0.f) || p->lj_rc > p->rc_R || !(p->lj_sigma > 0.f))) return NEP_ERR_ARG;
+  if (p->max_neighbors < 0 || p->max_neighbors > 128 || p->rebuild_every < 0) return NEP_ERR_ARG;
+
+  nep_handle *h = new (std::nothrow) nep_handle();
+  if (!h) return NEP_ERR_OOM;
+  h->shape = shape;
+  if (shape == 0) fill_model(h->model_t, p);
+  else fill_model(h->model_s, p);
   h->mass = p->mass_amu;
   h->skin = p->skin;
   h->rcR = p->rc_R;
@@ -584,7 +610,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->id, N)); A(dalloc(h->idb, N)); A(dalloc(h->cell_of, N)); A(dalloc(h->perm, N));
   A(dalloc(h->pos, N)); A(dalloc(h->pos_ref, N));
   A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N));
-  A(dalloc(reinterpret_cast<char *&>(h->G), N * GSTRIDE * (h->precision == NEP_FP32 ? 4 : 2)));
+  A(dalloc(reinterpret_cast<char *&>(h->G), N * (size_t)h->gs() * (h->precision == NEP_FP32 ? 4 : 2)));
   A(dalloc(h->nbr, N * (size_t)h->cap)); A(dalloc(h->nnum, N)); A(dalloc(h->nang, N)); A(dalloc(h->nown, N));
   A(dalloc(h->nband0, N));
   A(dalloc(h->count, (size_t)h->ncell)); A(dalloc(h->cursor, (size_t)h->ncell)); A(dalloc(h->start, (size_t)h->ncell + 1));
@@ -732,14 +758,15 @@ nep_status nep_get_descriptors(nep_handle *h, float *q) {
   if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
   if (h->n == 0) return NEP_OK;
   const size_t N = (size_t)h->n;
-  if (!h->qbuf) NEP_CUDA(h, dalloc(h->qbuf, 2 * N * S::NDES));
+  const size_t D = (size_t)h->ndes();
+  if (!h->qbuf) NEP_CUDA(h, dalloc(h->qbuf, 2 * N * D));
   nep_status s = compute_internal(h, h->qbuf);
   if (s != NEP_OK) return s;
   {
     Scope sc(h, KC_OTHER, 1);
-    NEP_CUDA(h, launch_store_rows(h->n, S::NDES, h->id, h->qbuf, h->qbuf + N * S::NDES, h->stream));
+    NEP_CUDA(h, launch_store_rows(h->n, (int)D, h->id, h->qbuf, h->qbuf + N * D, h->stream));
   }
-  NEP_CUDA(h, cudaMemcpyAsync(q, h->qbuf + N * S::NDES, N * S::NDES * sizeof(float), cudaMemcpyDefault, h->stream));
+  NEP_CUDA(h, cudaMemcpyAsync(q, h->qbuf + N * D, N * D * sizeof(float), cudaMemcpyDefault, h->stream));
   return check_device_status(h);
 }
 

@@ -9,8 +9,9 @@
 //            is the length of the owned part.
 //   Ffix     int64 [3][N]: forces in fixed point (2^-32 eV/Angstrom units), accumulated with
 //            integer atomics, so the sum does not depend on the order of the additions.
-//   G        float [N][128]: per-atom adjoint dU_i/ds_nlm (120 values, index n*24 + lm) followed by
-//            dU_i/dq_n of the radial descriptors (5 values) and padding.
+//   G        float or half [N][S::GS]: per-atom adjoint dU_i/ds_nlm (NA * NLM values, index n * NLM + lm)
+//            followed by dU_i/dq_n of the radial descriptors (NR <= 8 values) and padding
+//            (teacher shape: 5 x 24 + 8 = 128 per row; student shape: 4 x 8 + 8 = 40).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,8 +21,6 @@ namespace nep {
 
 constexpr int J_BITS = 27;
 constexpr uint32_t J_MASK = (1u << J_BITS) - 1u;
-constexpr int GSTRIDE = 128;     // floats per atom row of G
-constexpr int N_LM = 24;         // (l, m) components for l = 1..4
 constexpr float FIX_SCALE = 4294967296.0f;        // 2^32 fixed-point units per eV/Angstrom
 constexpr double FIX_INV = 1.0 / 4294967296.0;
 
@@ -57,18 +56,25 @@ struct RebuildArgs {
   Control *ctrl;
 };
 
-// Compile-time model shape: NR radial functions, NA angular, K basis functions, lmax = 4 3-body,
-// optional 4-body (l = 2), NNEU hidden neurons.
-template <int NR_, int NA_, int KR_, int KA_, bool FOURBODY_, int NNEU_>
+// Compile-time model shape: NR radial functions, NA angular channels, KR/KA basis functions, 3-body
+// harmonics l = 1..LMAX (NLM = LMAX (LMAX + 2) components), optional 4-body term (built from l = 2),
+// NNEU hidden neurons.  GS = elements per adjoint row (NA * NLM, then an 8-element tail).
+template <int NR_, int NA_, int KR_, int KA_, int LMAX_, bool FOURBODY_, int NNEU_>
 struct Shape {
-  static constexpr int NR = NR_, NA = NA_, KR = KR_, KA = KA_, NNEU = NNEU_;
+  static constexpr int NR = NR_, NA = NA_, KR = KR_, KA = KA_, LMAX = LMAX_, NNEU = NNEU_;
   static constexpr bool FOURBODY = FOURBODY_;
-  static constexpr int LMAX = 4;
+  static constexpr int NLM = LMAX * (LMAX + 2);
   static constexpr int NDES = NR + NA * LMAX + (FOURBODY ? NA : 0);
-  static_assert(NA * N_LM + NR <= GSTRIDE, "adjoint row too small");
+  static constexpr int GS = NA * NLM + 8;
+  static_assert(NLM % 8 == 0, "rows are read in 16-byte vectors of up to 8 values: LMAX must be 2 or 4");
+  static_assert(NR <= 8, "radial adjoint lives in the 8-element row tail");
+  static_assert(!FOURBODY || LMAX >= 2, "the 4-body term is built from the l = 2 sums");
 };
 
-using CuShape = Shape<5, 5, 8, 8, true, 30>;   // n_max 4/4, basis 8/8, l_max 4, 4-body, 30 neurons
+// The teacher NEP of the workload (n_max 4/4, basis 8/8, l_max 4, 4-body, 30 neurons) and the
+// distilled student (n_max 3/3, basis 8/8, l_max 2, no 4-body, 16 neurons).
+using CuShape = Shape<5, 5, 8, 8, 4, true, 30>;
+using StudentShape = Shape<4, 4, 8, 8, 2, false, 16>;
 
 // Model parameters, passed by value as a __grid_constant__ kernel argument so that every uniform
 // access compiles to a constant-bank operand.
@@ -153,7 +159,10 @@ __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K
 
 // Normalised real harmonics Yh_lm(u) = sqrt(4 pi / (2l+1)) Y_lm(u), l = 1..4 (24 values, m = -l..l),
 // so that sum_m Yh_lm(u) Yh_lm(v) = P_l(u . v).  Written as solid-harmonic polynomials of a unit vector.
-__device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[N_LM]) {
+// NLM = 8 computes l = 1, 2 only.
+template <int NLM>
+__device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[NLM]) {
+  static_assert(NLM == 8 || NLM == 24, "l_max 2 or 4");
   const float x2 = x * x, y2 = y * y, z2 = z * z;
   const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
   const float s10 = 3.1622776601683795f, s15 = 3.872983346207417f, s35 = 5.916079783099616f;
@@ -166,6 +175,7 @@ __device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[
   Y[5] = z2 - 0.5f * (x2 + y2);
   Y[6] = s3 * x * z;
   Y[7] = 0.5f * s3 * (x2 - y2);
+  if constexpr (NLM > 8) {
   // l = 3
   const float a3 = 4.f * z2 - x2 - y2;
   Y[8] = 0.25f * s10 * y * (3.f * x2 - y2);
@@ -187,6 +197,7 @@ __device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[
   Y[21] = 0.25f * s5 * (x2 - y2) * b4;
   Y[22] = 0.25f * s70 * x * z * (x2 - 3.f * y2);
   Y[23] = 0.125f * s35 * (x2 * x2 - 6.f * x2 * y2 + y2 * y2);
+  }
 }
 
 // Gradient of the solid-harmonic polynomial of component lm, evaluated at (x, y, z), accumulated

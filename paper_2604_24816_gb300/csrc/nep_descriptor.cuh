@@ -53,7 +53,7 @@ __device__ __forceinline__ void load_tail8(const GT *row, int off, float (&v)[8]
 template <class S>
 struct AtomSums {
   float qR[S::NR];
-  float s[S::NA][N_LM];
+  float s[S::NA][S::NLM];
   float elj;
   int nrad, nang, nact, cnt;
 };
@@ -69,7 +69,7 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
 #pragma unroll
   for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-    for (int c = 0; c < N_LM; ++c) A.s[a][c] = 0.f;
+    for (int c = 0; c < S::NLM; ++c) A.s[a][c] = 0.f;
   A.elj = 0.f;
   A.nrad = 0; A.nang = 0; A.nact = 0; A.cnt = cnt;
   NbrPipe<DE, DP, BLOCK> pipe;
@@ -110,12 +110,12 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
         for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
         g[a] = t;
       }
-      float Y[N_LM];
-      harmonics(dx * ir, dy * ir, dz * ir, Y);
+      float Y[S::NLM];
+      harmonics<S::NLM>(dx * ir, dy * ir, dz * ir, Y);
 #pragma unroll
       for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-        for (int c = 0; c < N_LM; ++c) A.s[a][c] = fmaf(g[a], Y[c], A.s[a][c]);
+        for (int c = 0; c < S::NLM; ++c) A.s[a][c] = fmaf(g[a], Y[c], A.s[a][c]);
       ++A.nang;
     }
   }
@@ -128,7 +128,7 @@ struct FourBody {
   float xx[S::NA], yy[S::NA], zz[S::NA], xy[S::NA], yz[S::NA], xz[S::NA];
 };
 
-// Descriptors [q_n | q_nl (n-major, l = 1..4) | q4_n = tr(T_n^3) = 3 det T_n].
+// Descriptors [q_n | q_nl (n-major, l = 1..LMAX) | q4_n = tr(T_n^3) = 3 det T_n (teacher shape only)].
 template <class S>
 __device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[S::NDES], FourBody<S> &T) {
 #pragma unroll
@@ -136,14 +136,14 @@ __device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[
 #pragma unroll
   for (int a = 0; a < S::NA; ++a) {
 #pragma unroll
-    for (int l = 1; l <= 4; ++l) {
+    for (int l = 1; l <= S::LMAX; ++l) {
       float t = 0.f;
 #pragma unroll
       for (int c = l * l - 1; c < (l + 1) * (l + 1) - 1; ++c) t = fmaf(A.s[a][c], A.s[a][c], t);
-      q[S::NR + a * 4 + (l - 1)] = t;
+      q[S::NR + a * S::LMAX + (l - 1)] = t;
     }
   }
-  if (S::FOURBODY) {
+  if constexpr (S::FOURBODY) {
     const float i3 = 0.57735026918962576f, third = 1.f / 3.f;
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
@@ -156,7 +156,7 @@ __device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[
       const float det = T.xx[a] * (T.yy[a] * T.zz[a] - T.yz[a] * T.yz[a]) -
                         T.xy[a] * (T.xy[a] * T.zz[a] - T.yz[a] * T.xz[a]) +
                         T.xz[a] * (T.xy[a] * T.yz[a] - T.yy[a] * T.xz[a]);
-      q[S::NR + S::NA * 4 + a] = 3.f * det;
+      q[S::NR + S::NA * S::LMAX + a] = 3.f * det;
     }
   }
 }
@@ -165,11 +165,11 @@ __device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[
 // d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m).
 template <class S>
 __device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, const FourBody<S> &T,
-                                                const float (&Fp)[S::NDES], float (&gl)[N_LM]) {
+                                                const float (&Fp)[S::NDES], float (&gl)[S::NLM]) {
 #pragma unroll
-  for (int c = 0; c < N_LM; ++c) gl[c] = 2.f * Fp[S::NR + a * 4 + lm_l(c) - 1] * A.s[a][c];
-  if (S::FOURBODY) {
-    const float f4 = Fp[S::NR + S::NA * 4 + a];
+  for (int c = 0; c < S::NLM; ++c) gl[c] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(c) - 1] * A.s[a][c];
+  if constexpr (S::FOURBODY) {
+    const float f4 = Fp[S::NR + S::NA * S::LMAX + a];
     const float Mxx = T.xx[a] * T.xx[a] + T.xy[a] * T.xy[a] + T.xz[a] * T.xz[a];
     const float Myy = T.xy[a] * T.xy[a] + T.yy[a] * T.yy[a] + T.yz[a] * T.yz[a];
     const float Mzz = T.xz[a] * T.xz[a] + T.yz[a] * T.yz[a] + T.zz[a] * T.zz[a];

@@ -93,21 +93,21 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
 
-    float *Gi = G + (size_t)i * GSTRIDE;
+    float *Gi = G + (size_t)i * S::GS;
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
-      float gl[N_LM];
+      float gl[S::NLM];
       adjoint_channel<S>(a, A, T, Fp, gl);
 #pragma unroll
-      for (int c = 0; c < N_LM; c += 4)
-        *reinterpret_cast<float4 *>(Gi + a * N_LM + c) = make_float4(gl[c], gl[c + 1], gl[c + 2], gl[c + 3]);
+      for (int c = 0; c < S::NLM; c += 4)
+        *reinterpret_cast<float4 *>(Gi + a * S::NLM + c) = make_float4(gl[c], gl[c + 1], gl[c + 2], gl[c + 3]);
     }
     {
       float tail[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int a = 0; a < S::NR; ++a) tail[a] = Fp[a];
-      *reinterpret_cast<float4 *>(Gi + S::NA * N_LM) = make_float4(tail[0], tail[1], tail[2], tail[3]);
-      *reinterpret_cast<float4 *>(Gi + S::NA * N_LM + 4) = make_float4(tail[4], tail[5], tail[6], tail[7]);
+      *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM) = make_float4(tail[0], tail[1], tail[2], tail[3]);
+      *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM + 4) = make_float4(tail[4], tail[5], tail[6], tail[7]);
     }
     const float ui = U + A.elj;
     usite[i] = ui;
@@ -137,20 +137,20 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   if (i < n) {
     const float4 pi = pos[i];
     constexpr int W = GTraits<GT>::W;
-    const GT *Gi = G + (size_t)i * GSTRIDE;
-    float gi[S::NA][N_LM];
+    const GT *Gi = G + (size_t)i * S::GS;
+    float gi[S::NA][S::NLM];
 #define GI(a, lm) gi[a][lm]
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-      for (int c = 0; c < N_LM; c += W) {
+      for (int c = 0; c < S::NLM; c += W) {
         float t[W];
-        load_vec(Gi + a * N_LM + c, t);
+        load_vec(Gi + a * S::NLM + c, t);
 #pragma unroll
         for (int k = 0; k < W; ++k) GI(a, c + k) = t[k];
       }
     float fpi[8];
-    load_tail8(Gi, S::NA * N_LM, fpi);
+    load_tail8(Gi, S::NA * S::NLM, fpi);
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
     const int cnt = nown[i];
@@ -165,9 +165,9 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       // pull the next angular neighbour's adjoint row into L1 while this pair is computed
       if (k + 1 < nb0 && k + 1 < cnt) {
         const uint32_t en = pipe.re[((k + 1) % FPIPE_DE) * FORCE_BLOCK];
-        const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * GSTRIDE);
+        const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * S::GS);
 #pragma unroll
-        for (int b = 0; b < (int)(GSTRIDE * sizeof(GT)); b += 128) prefetch_l1(gr + b);
+        for (int b = 0; b < (int)(S::GS * sizeof(GT)); b += 128) prefetch_l1(gr + b);
       }
       const int j = (int)(e & J_MASK);
       const float4 o = shift[e >> J_BITS];
@@ -177,14 +177,14 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       ++nact;
       const float ir = rsqrtf(r2);
       const float r = r2 * ir;
-      const GT *Gj = G + (size_t)j * GSTRIDE;
+      const GT *Gj = G + (size_t)j * S::GS;
       float coef = 0.f;                     // D = coef * d + (vx, vy, vz)
       float vx = 0.f, vy = 0.f, vz = 0.f;
       if (r2 < P.rcR2) {
         float f[S::KR], df[S::KR];
         cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
         float fpj[8];
-        load_tail8(Gj, S::NA * N_LM, fpj);
+        load_tail8(Gj, S::NA * S::NLM, fpj);
         float c = 0.f;
 #pragma unroll
         for (int a = 0; a < S::NR; ++a) {
@@ -214,15 +214,15 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
           g[a] = t; dg[a] = dt;
         }
         const float ux = dx * ir, uy = dy * ir, uz = dz * ir;
-        float Y[N_LM];
-        harmonics(ux, uy, uz, Y);
+        float Y[S::NLM];
+        harmonics<S::NLM>(ux, uy, uz, Y);
         float along = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
         // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u)
 #pragma unroll
-        for (int c = 0; c < N_LM; c += W) {
+        for (int c = 0; c < S::NLM; c += W) {
           float hj[S::NA][W];
 #pragma unroll
-          for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * N_LM + c, hj[a]);
+          for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * S::NLM + c, hj[a]);
 #pragma unroll
           for (int cc = 0; cc < W; ++cc) {
             const int lm = c + cc;
@@ -294,14 +294,18 @@ cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *
 int descriptor_blocks(int n) { return (n + DESC_BLOCK - 1) / DESC_BLOCK; }
 int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
 
-template cudaError_t launch_descriptor<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                const int32_t *, const int32_t *, float *, float *, float *,
+#define NEP_INSTANTIATE(SH)                                                                                    \
+  template cudaError_t launch_descriptor<SH>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *,   \
+                                             const int32_t *, float *, float *, float *, long long *, long long *,    \
+                                             int *, cudaStream_t);                                                    \
+  template cudaError_t launch_force<SH, float>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *, \
+                                               const int32_t *, const int32_t *, const float *, long long *,          \
+                                               long long *, int *, cudaStream_t);                                     \
+  template cudaError_t launch_force<SH, __half>(const Model<SH> &, const Geom &, int, const float4 *,                 \
+                                                const int32_t *, const int32_t *, const int32_t *, const __half *,    \
                                                 long long *, long long *, int *, cudaStream_t);
-template cudaError_t launch_force<CuShape, float>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                  const int32_t *, const int32_t *, const int32_t *, const float *,
-                                                  long long *, long long *, int *, cudaStream_t);
-template cudaError_t launch_force<CuShape, __half>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                   const int32_t *, const int32_t *, const int32_t *, const __half *,
-                                                   long long *, long long *, int *, cudaStream_t);
+NEP_INSTANTIATE(CuShape)
+NEP_INSTANTIATE(StudentShape)
+#undef NEP_INSTANTIATE
 
 }  // namespace nep

@@ -134,19 +134,19 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
     float Fp[S::NDES];
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
-    __half *Gi = G + (size_t)i * GSTRIDE;
+    __half *Gi = G + (size_t)i * S::GS;
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
-      float gl[N_LM];
+      float gl[S::NLM];
       adjoint_channel<S>(a, A, T, Fp, gl);
 #pragma unroll
-      for (int c = 0; c < N_LM; c += 8) *reinterpret_cast<uint4 *>(Gi + a * N_LM + c) = pack8_half(gl + c);
+      for (int c = 0; c < S::NLM; c += 8) *reinterpret_cast<uint4 *>(Gi + a * S::NLM + c) = pack8_half(gl + c);
     }
     {
       float tail[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int a = 0; a < S::NR; ++a) tail[a] = Fp[a];
-      *reinterpret_cast<uint4 *>(Gi + S::NA * N_LM) = pack8_half(tail);
+      *reinterpret_cast<uint4 *>(Gi + S::NA * S::NLM) = pack8_half(tail);
     }
     const float ui = U + A.elj;
     usite[i] = ui;
@@ -175,12 +175,14 @@ cudaError_t launch_descriptor_mixed(const Model<S> &P, const Geom &g, int n, con
 
 int mixed_descriptor_blocks(int n) { return (n + MIX_BLOCK - 1) / MIX_BLOCK; }
 
-template cudaError_t launch_descriptor_mixed<CuShape, __nv_bfloat16>(const Model<CuShape> &, const Geom &, int,
-                                                                     const float4 *, const int32_t *, const int32_t *,
-                                                                     __half *, float *, float *, long long *,
-                                                                     long long *, int *, cudaStream_t);
-template cudaError_t launch_descriptor_mixed<CuShape, __half>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                              const int32_t *, const int32_t *, __half *, float *,
-                                                              float *, long long *, long long *, int *, cudaStream_t);
+#define NEP_INSTANTIATE(SH, MT)                                                                                \
+  template cudaError_t launch_descriptor_mixed<SH, MT>(const Model<SH> &, const Geom &, int, const float4 *,          \
+                                                       const int32_t *, const int32_t *, __half *, float *, float *,  \
+                                                       long long *, long long *, int *, cudaStream_t);
+NEP_INSTANTIATE(CuShape, __nv_bfloat16)
+NEP_INSTANTIATE(CuShape, __half)
+NEP_INSTANTIATE(StudentShape, __nv_bfloat16)
+NEP_INSTANTIATE(StudentShape, __half)
+#undef NEP_INSTANTIATE
 
 }  // namespace nep

@@ -73,7 +73,7 @@ constexpr Layout make_layout() {
   L.vxb = take(N * 8); L.vyb = take(N * 8); L.vzb = take(N * 8);
   L.id = take(N * 4); L.idb = take(N * 4); L.cell_of = take(N * 4); L.perm = take(N * 4);
   L.pos = take(N * 16); L.pos_ref = take(N * 16);
-  L.F = take(N * 3 * 8); L.usite = take(N * 4); L.G = take(N * GSTRIDE * 4); L.nbr = take(N * CAP * 4);
+  L.F = take(N * 3 * 8); L.usite = take(N * 4); L.G = take(N * S::GS * 4); L.nbr = take(N * CAP * 4);
   L.nnum = take(N * 4); L.nang = take(N * 4); L.nown = take(N * 4); L.nband0 = take(N * 4);
   L.count = take((size_t)NC_MAX * 4); L.cursor = take((size_t)NC_MAX * 4); L.start = take(((size_t)NC_MAX + 1) * 4);
   L.tile_sums = take(((size_t)NC_MAX / 4096 + 2) * 4);

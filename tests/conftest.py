@@ -25,3 +25,20 @@ def model_params():
     import json
     with open(MODEL_PATH) as f:
         return json.load(f)
+
+
+STUDENT_SEED = 7331
+
+
+@pytest.fixture(scope="session")
+def student_params():
+    """A seeded, untrained model of the student shape (n_max 3/3, l_max 2, no 4-body, 16 neurons)."""
+    import nep_inputs as ni
+    from oracle.write_model import make_model
+    return make_model(ni.STUDENT_DIMS, STUDENT_SEED)
+
+
+@pytest.fixture(scope="session")
+def student_model(student_params):
+    import oracle
+    return oracle.Model(student_params)

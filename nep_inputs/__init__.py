@@ -120,6 +120,24 @@ def void_strain_workload(cells: int, void_radius: float = 50.0, strain_z: float 
                     box, temperature, 1.0, steps)
 
 
+def student_cell(seed: int, cells=(4, 4, 4), temperature_sigma: float = 0.05, strain=(0.0, 0.0, 0.0),
+                 vacancies: int = 0):
+    """One small periodic fcc Cu cell for student training and tests: nx*ny*nz conventional cells,
+    `vacancies` atoms removed at random, a diagonal strain (1 + e_x, 1 + e_y, 1 + e_z) applied to box and
+    positions, then Gaussian displacements of `temperature_sigma` Angstrom.  Returns (pos, box)."""
+    rng = np.random.default_rng(seed)
+    pos, box = fcc_lattice(*cells)
+    if vacancies > 0:
+        keep = np.ones(pos.shape[0], dtype=bool)
+        keep[rng.choice(pos.shape[0], size=vacancies, replace=False)] = False
+        pos = pos[keep]
+    scale = 1.0 + np.asarray(strain, dtype=np.float64)
+    pos = pos * scale
+    box = box * scale
+    pos = gaussian_displace(pos, box, temperature_sigma, rng)
+    return pos, box
+
+
 # Named workloads (sizes of the paper-shaped Cu runs).
 def workload(name: str) -> Workload:
     if name == "cu_4x4x4":        # 256 atoms, sigma 0.05 A, 300 K, 10 steps

@@ -9,6 +9,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "nep_gb300.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -19,8 +20,8 @@ def L():
     return nep.lib()
 
 
-def _declared_functions():
-    text = open(HEADER).read()
+def _declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
 
@@ -32,13 +33,18 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol(L):
-    for name in _declared_functions():
-        assert hasattr(L, name), name
+    assert len(HEADERS) >= 2
+    for h in HEADERS:
+        for name in _declared_functions(h):
+            assert hasattr(L, name), (h, name)
 
 
 def test_binding_covers_every_declared_symbol():
-    from paper_2604_24816_gb300 import nep
-    assert set(_declared_functions()) <= set(nep.EXPORTED)
+    from paper_2604_24816_gb300 import nep, student
+    declared = set()
+    for h in HEADERS:
+        declared |= set(_declared_functions(h))
+    assert declared <= set(nep.EXPORTED) | set(student.EXPORTED)
 
 
 def test_status_strings(L):

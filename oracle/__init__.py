@@ -64,6 +64,7 @@ def lib():
             L.oracle_neighbor_lists.argtypes = [C.c_int, _D, _D, C.c_double, C.c_int, _I64, _I32]
             L.oracle_descriptors.argtypes = [P, C.c_int, _D, _D, _D]
             L.oracle_energy_forces.argtypes = [P, C.c_int, _D, _D, _D, _D, _D, _D]
+            L.oracle_energy_forces_select.argtypes = [P, P, _I32, C.c_int, _D, _D, _D, _D, _D, _D]
             L.oracle_forces_sampled.argtypes = [P, C.c_int, _D, _D, C.c_int, _I64, _D, _D]
             L.oracle_q3b_ylm.argtypes = [P, C.c_int, _D, _D, _D]
             L.oracle_radial.argtypes = [P, C.c_int, C.c_double, _D, _D]
@@ -72,7 +73,8 @@ def lib():
             L.oracle_atom_site.restype = C.c_double
             L.oracle_md_nve.argtypes = [P, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, _D]
             for f in ("oracle_neighbor_counts", "oracle_neighbor_lists", "oracle_descriptors",
-                      "oracle_energy_forces", "oracle_forces_sampled", "oracle_q3b_ylm", "oracle_md_nve"):
+                      "oracle_energy_forces", "oracle_energy_forces_select", "oracle_forces_sampled",
+                      "oracle_q3b_ylm", "oracle_md_nve"):
                 getattr(L, f).restype = C.c_int
             _lib = L
     return _lib
@@ -163,6 +165,20 @@ def energy_forces(model: Model, x, box):
     E = np.zeros(1); U = np.zeros(n); F = np.zeros((n, 3)); W = np.zeros(9)
     if lib().oracle_energy_forces(model.ref(), n, _dp(x), _dp(box), _dp(E), _dp(U), _dp(F), _dp(W)) != 0:
         raise RuntimeError("oracle_energy_forces failed")
+    return float(E[0]), U, F, W.reshape(3, 3)
+
+
+def energy_forces_select(model_a: Model, model_b: Model, flags, x, box):
+    """Energy, site energies, forces and virial when atom i's site energy comes from model_b where
+    flags[i] != 0 and from model_a elsewhere (each atom's own model differentiated).
+    Returns (E, U[n], F[n,3], W[3,3])."""
+    x = _f64(x, (-1, 3)); box = _f64(box, (3,))
+    n = x.shape[0]
+    fl = np.ascontiguousarray(np.asarray(flags, dtype=np.int32).reshape(n))
+    E = np.zeros(1); U = np.zeros(n); F = np.zeros((n, 3)); W = np.zeros(9)
+    if lib().oracle_energy_forces_select(model_a.ref(), model_b.ref(), fl.ctypes.data_as(_I32), n, _dp(x), _dp(box),
+                                         _dp(E), _dp(U), _dp(F), _dp(W)) != 0:
+        raise RuntimeError("oracle_energy_forces_select failed")
     return float(E[0]), U, F, W.reshape(3, 3)
 
 

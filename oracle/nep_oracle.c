@@ -508,16 +508,22 @@ int oracle_descriptors(const onep *P, int n, const double *x, const double *box,
 
 /* Energy, site energies, forces and virial of the whole system.
  * W[a][b] = - sum_i sum_j r_ij[a] dU_i/dr_ij[b].  Any output pointer may be NULL. */
-int oracle_energy_forces(const onep *P, int n, const double *x, const double *box, double *E, double *U,
-                         double *F, double *W) {
+/* Energy, site energies, forces and virial.  Atom i's site energy comes from model Pb when flags[i] is
+ * nonzero and from Pa otherwise (flags == NULL: Pa everywhere): E = sum_i U_i^(model of i), and the
+ * forces are -dE/dr with each atom's own model differentiated (the per-atom teacher fallback). */
+static int energy_forces_select(const onep *Pa, const onep *Pb, const int *flags, int n, const double *x,
+                                const double *box, double *E, double *U, double *F, double *W) {
+    double rc = max_cut(Pa);
+    if (Pb && max_cut(Pb) > rc) rc = max_cut(Pb);
     nlist L;
-    if (nlist_build(&L, n, x, box, max_cut(P), 1) != 0) return -1;
+    if (nlist_build(&L, n, x, box, rc, 1) != 0) return -1;
     int64_t nnz = L.off[n];
     double *dU = (double *)malloc(sizeof(double) * 3 * (size_t)(nnz > 0 ? nnz : 1));
     double *Us = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
 #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < n; ++i) {
         int nn = (int)(L.off[i + 1] - L.off[i]);
+        const onep *P = (flags && flags[i]) ? Pb : Pa;
         Us[i] = atom_site(P, nn, L.d + 3 * L.off[i], dU + 3 * L.off[i], NULL);
     }
     /* serial, fixed-order accumulation */
@@ -540,6 +546,16 @@ int oracle_energy_forces(const onep *P, int n, const double *x, const double *bo
     free(dU); free(Us);
     nlist_free(&L);
     return 0;
+}
+
+int oracle_energy_forces(const onep *P, int n, const double *x, const double *box, double *E, double *U,
+                         double *F, double *W) {
+    return energy_forces_select(P, NULL, NULL, n, x, box, E, U, F, W);
+}
+
+int oracle_energy_forces_select(const onep *Pa, const onep *Pb, const int *flags, int n, const double *x,
+                                const double *box, double *E, double *U, double *F, double *W) {
+    return energy_forces_select(Pa, Pb, flags, n, x, box, E, U, F, W);
 }
 
 /* Forces and site energies on a sample of atoms only, for large systems:

@@ -42,3 +42,10 @@ def student_params():
 def student_model(student_params):
     import oracle
     return oracle.Model(student_params)
+
+
+@pytest.fixture(scope="session")
+def trained_student_params():
+    import json
+    with open(os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_student_trained.json")) as f:
+        return json.load(f)

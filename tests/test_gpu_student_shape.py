@@ -78,3 +78,34 @@ def test_student_mixed(api, student_params, student_model, mode):
     print(f"student {mode}: force RMSE {rmse:.2e}, max {np.abs(F - Fo).max():.2e} eV/A")
     assert rmse <= 5e-3
     assert abs(E - Eo) / abs(Eo) <= 2e-4
+
+
+def test_trained_student_against_oracle(api, trained_student_params):
+    """The distilled student model file through the MD kernels, against the oracle."""
+    m = oracle.Model(trained_student_params)
+    wl = ni.fcc_cu_workload(5, 600.0, 0.05, seed=47)
+    with api.NEP(trained_student_params) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        E, F, W = nep.compute()
+    Eo, Uo, Fo, Wo = oracle.energy_forces(m, wl.pos, wl.box)
+    assert np.abs(F - Fo).max() <= 1e-4
+    assert abs(E - Eo) / abs(Eo) <= 1e-6
+
+
+def test_trained_student_vs_teacher_on_fresh_md(api, model_params, trained_student_params):
+    """Teacher-MD snapshots from trajectories not used in training (another seed): student vs teacher
+    NEP-only forces, both on the GPU, against the workload's 30 meV/Angstrom bound."""
+    from paper_2604_24816_gb300 import distill
+    snaps = distill.generate(model_params, 4, 5, 25, 200, seed=9191, log=None)
+    d, ref = [], []
+    with api.NEP(trained_student_params, lj=False) as st:
+        for x, box, E, F, sp in snaps:
+            st.set_state(x, None, box)
+            Es, Fs, Ws = st.compute()
+            d.append(Fs - F)
+            ref.append(F)
+    d, ref = np.concatenate(d), np.concatenate(ref)
+    rmse = float(np.sqrt(np.mean(d ** 2)))
+    print(f"trained student vs teacher on fresh MD: force RMSE {rmse * 1e3:.1f} meV/A "
+          f"(teacher NEP-only force rms {np.sqrt(np.mean(ref ** 2)) * 1e3:.1f})")
+    assert rmse <= 0.030

@@ -103,3 +103,32 @@ def test_student_equals_embedded_teacher(student_params, cell):
     Et, Ut, Ft, Wt = oracle.energy_forces(oracle.Model(teacher), cell.pos, cell.box)
     np.testing.assert_allclose(Us, Ut, rtol=0, atol=1e-12)
     np.testing.assert_allclose(Fs, Ft, rtol=0, atol=1e-11)
+
+
+def test_select_reduces_to_single_models(student_model, model, cell):
+    n = cell.n
+    for flags, ref in ((np.zeros(n), student_model), (np.ones(n), model)):
+        E, U, F, W = oracle.energy_forces_select(student_model, model, flags, cell.pos, cell.box)
+        Er, Ur, Fr, Wr = oracle.energy_forces(ref, cell.pos, cell.box)
+        assert abs(E - Er) < 1e-12 * abs(Er)
+        np.testing.assert_allclose(F, Fr, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(W, Wr, rtol=0, atol=1e-10)
+
+
+def test_select_forces_are_minus_gradient_with_fixed_flags(student_model, model, cell):
+    """A mixed assignment (every third atom on the teacher): forces = -grad E at fixed flags."""
+    flags = (np.arange(cell.n) % 3 == 0).astype(np.int32)
+    E, U, F, W = oracle.energy_forces_select(student_model, model, flags, cell.pos, cell.box)
+    assert np.abs(F.sum(axis=0)).max() < 1e-10
+    Us = oracle.energy_forces(student_model, cell.pos, cell.box)[1]
+    Ut = oracle.energy_forces(model, cell.pos, cell.box)[1]
+    np.testing.assert_allclose(U, np.where(flags == 1, Ut, Us), rtol=0, atol=1e-12)
+    rng = np.random.default_rng(13)
+    h = 2e-5
+    for _ in range(6):
+        i, a = int(rng.integers(cell.n)), int(rng.integers(3))
+        xp = cell.pos.copy(); xp[i, a] += h
+        xm = cell.pos.copy(); xm[i, a] -= h
+        fd = -(oracle.energy_forces_select(student_model, model, flags, xp, cell.box)[0] -
+               oracle.energy_forces_select(student_model, model, flags, xm, cell.box)[0]) / (2 * h)
+        assert abs(fd - F[i, a]) <= 1e-7 * max(1.0, abs(F[i, a]))

@@ -50,7 +50,8 @@ typedef enum {
     NEP_ERR_TIMEOUT = 6,          /* a bounded wait (host on the stream, or a kernel on the tensor cores) expired */
     NEP_ERR_STATE = 7,            /* call out of order (e.g. nep_compute before nep_set_state) */
     NEP_ERR_UNSUPPORTED = 8,      /* model shape without a compiled kernel instance */
-    NEP_ERR_OOM = 9               /* device allocation failed */
+    NEP_ERR_OOM = 9,              /* device allocation failed */
+    NEP_ERR_FALLBACK_OVERFLOW = 10 /* more atoms flagged for the fallback model than its list holds */
 } nep_status;
 
 /* Arithmetic of the force evaluation.  NEP_FP32: everything in float32 (float64 integration and sums).
@@ -154,8 +155,28 @@ nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_
  * descriptor kernel, force evaluations, neighbour rebuilds, MD steps, kernel launches enqueued by the
  * library, list entries and pairs inside the largest cutoff seen by the descriptor kernel, then the
  * same four counts for the owned pairs seen by the force kernel: list entries, pairs inside the
- * largest cutoff, radial pairs, angular pairs}.  Pair counts sum over evaluations. */
-nep_status nep_get_counters(nep_handle *h, int64_t out[12]);
+ * largest cutoff, radial pairs, angular pairs, then the atom evaluations done by the fallback model
+ * (nep_set_fallback)}.  Pair and atom counts sum over evaluations. */
+nep_status nep_get_counters(nep_handle *h, int64_t out[13]);
+
+/* Per-atom fallback from a student-shaped model (n_max 3/3, l_max 2, no 4-body, 16 neurons) to a
+ * teacher-shaped model (the handle's model must be the student).  Every force evaluation flags each atom
+ * whose scaled descriptors q~_nu = q_scale_nu q_nu leave [q_lo_nu - margin w_nu, q_hi_nu + margin w_nu]
+ * (w = q_hi - q_lo; q_lo/q_hi: 12 floats, host memory, the student's training range) and takes that
+ * atom's site energy from the teacher: E = sum_i U_i^(model of i), F = -grad E with each atom's own model
+ * differentiated (the LJ term is shared and evaluated once).  The teacher runs in float32 on the
+ * flagged atoms only (compacted list).  max_fraction (0 < f <= 1; 0 = 1/16) sizes the flagged-atom list
+ * as a fraction of n; more flagged atoms in one evaluation returns NEP_ERR_FALLBACK_OVERFLOW.
+ * teacher == NULL switches the fallback off.  The teacher's rc_R must equal the student's.  Parameters
+ * are copied; the caller keeps ownership.  Because the flags can change from step to step, the energy is
+ * not conserved across a switch (reported, not corrected). */
+nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const float *q_lo, const float *q_hi,
+                            float margin, double max_fraction);
+
+/* After a force evaluation: flags [n] (host or device, may be NULL; original order; 1 = teacher) and the
+ * number of flagged atoms of the last evaluation.  NEP_ERR_STATE without a fallback or before the first
+ * evaluation of the current state. */
+nep_status nep_get_fallback(nep_handle *h, int *flags, int64_t *count);
 
 /* Upper limits of nep_compute_noalloc: the size of its fixed scratch array. */
 #define NEP_NOALLOC_MAX_ATOMS 8192

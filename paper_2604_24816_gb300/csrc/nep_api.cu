@@ -20,13 +20,15 @@
 
 #include "nep_gb300.h"
 #include "nep_common.cuh"
+#include "nep_descriptor.cuh"
 #include "nep_tc.cuh"
 
 namespace nep {
 // nep_force.cu
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                              float *, float *, float *, long long *, long long *, int *, cudaStream_t);
+                              float *, float *, float *, long long *, long long *, int *, const Fallback &,
+                              cudaStream_t);
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
                          const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
@@ -36,8 +38,17 @@ int force_blocks(int n);
 template <class S, class MT>
 cudaError_t launch_descriptor_mixed(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
                                     const int32_t *, __half *, float *, float *, long long *, long long *, int *,
-                                    cudaStream_t);
+                                    const Fallback &, cudaStream_t);
 int mixed_descriptor_blocks(int n);
+template <class S>
+cudaError_t launch_fallback_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
+                                       const int32_t *, const int *, const int *, int, float *, float *, long long *,
+                                       long long *, int *, cudaStream_t);
+template <class S>
+cudaError_t launch_fallback_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
+                                  const int32_t *, const int *, const int *, int, const float *, long long *,
+                                  long long *, int *, cudaStream_t);
+cudaError_t launch_fallback_flags(const int *, const int *, int, const int *, int *, cudaStream_t);
 // nep_neighbor.cu
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
 cudaError_t launch_neighbors(const RebuildArgs &, cudaStream_t);
@@ -136,6 +147,15 @@ struct nep_handle {
   long long launches[NEP_N_KERNEL_CLASSES] = {0};
   long long launch_total = 0;
 
+  // per-atom fallback to the teacher (student shape only)
+  bool fb_on = false;
+  Model<CuShape> fb_model{};
+  float fb_lo[16] = {0}, fb_hi[16] = {0};
+  double fb_frac = 1.0 / 16.0;
+  int fb_cap = 0;
+  int *fb_list = nullptr, *fb_count = nullptr;
+  float *fb_G = nullptr;
+
   int ndes() const { return shape == 0 ? CuShape::NDES : StudentShape::NDES; }
   int gs() const { return shape == 0 ? CuShape::GS : StudentShape::GS; }
 };
@@ -183,6 +203,8 @@ void free_system(nep_handle *h) {
   dfree(h->nbr); dfree(h->nnum); dfree(h->nang); dfree(h->nown); dfree(h->nband0);
   dfree(h->count); dfree(h->cursor); dfree(h->start); dfree(h->tile_sums);
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
+  dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
+  h->fb_cap = 0;
   h->io_i_elems = 0;
   h->n = 0;
   h->have_state = h->have_nlist = h->have_forces = false;
@@ -283,26 +305,42 @@ cudaError_t enqueue_rebuild(nep_handle *h) {
 template <class S>
 cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   const Geom g = geom_of(h);
+  Fallback fb{};
+  fb.on = h->fb_on ? 1 : 0;
+  if (fb.on) {
+    fb.cap = h->fb_cap; fb.list = h->fb_list; fb.count = h->fb_count;
+    for (int v = 0; v < 16; ++v) { fb.lo[v] = h->fb_lo[v]; fb.hi[v] = h->fb_hi[v]; }
+  }
   cudaError_t e;
   {
-    Scope sc(h, KC_DESC, 1);
+    Scope sc(h, KC_DESC, fb.on ? 2 : 1);
+    if (fb.on && (e = cudaMemsetAsync(h->fb_count, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
     if (h->precision == NEP_FP32)
       e = launch_descriptor<S>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<float *>(h->G), h->usite, qout, h->F,
-                               h->part_d, &h->ctrl->status, h->stream);
+                               h->part_d, &h->ctrl->status, fb, h->stream);
     else if (h->precision == NEP_MIX_BF16)
       e = launch_descriptor_mixed<S, __nv_bfloat16>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
-                                                     h->usite, qout, h->F, h->part_d, &h->ctrl->status, h->stream);
+                                                     h->usite, qout, h->F, h->part_d, &h->ctrl->status, fb, h->stream);
     else
       e = launch_descriptor_mixed<S, __half>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
-                                              h->usite, qout, h->F, h->part_d, &h->ctrl->status, h->stream);
+                                              h->usite, qout, h->F, h->part_d, &h->ctrl->status, fb, h->stream);
+    if (e == cudaSuccess && fb.on)
+      e = launch_fallback_descriptor<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list, h->fb_count,
+                                              h->fb_cap, h->fb_G, h->usite, h->part_d, h->counters, &h->ctrl->status,
+                                              h->stream);
   }
   if (e != cudaSuccess) return e;
-  Scope sc(h, KC_FORCE, 1);
+  Scope sc(h, KC_FORCE, fb.on ? 2 : 1);
   if (h->precision == NEP_FP32)
-    return launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G),
-                                  h->F, h->part_f, &h->ctrl->status, h->stream);
-  return launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const __half *>(h->G),
-                                 h->F, h->part_f, &h->ctrl->status, h->stream);
+    e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G), h->F,
+                               h->part_f, &h->ctrl->status, h->stream);
+  else
+    e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const __half *>(h->G),
+                                h->F, h->part_f, &h->ctrl->status, h->stream);
+  if (e == cudaSuccess && fb.on)
+    e = launch_fallback_force<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list, h->fb_count,
+                                       h->fb_cap, h->fb_G, h->F, h->part_f, &h->ctrl->status, h->stream);
+  return e;
 }
 
 cudaError_t enqueue_forces(nep_handle *h, float *qout) {
@@ -354,6 +392,8 @@ nep_status check_device_status(nep_handle *h) {
     return fail(h, NEP_ERR_NEIGH_OVERFLOW, "an atom has more neighbours within rc_R + skin than max_neighbors");
   if (st & ST_NAN) return fail(h, NEP_ERR_NAN, "non-finite position, energy or force");
   if (st & ST_TIMEOUT) return fail(h, NEP_ERR_TIMEOUT, "a bounded wait on the tensor cores ran out");
+  if (st & ST_FB_OVERFLOW)
+    return fail(h, NEP_ERR_FALLBACK_OVERFLOW, "more atoms left the student's range than the fallback list holds");
   return NEP_OK;
 }
 
@@ -426,6 +466,18 @@ nep_status upload_state(nep_handle *h, const double *x, const double *v) {
   return NEP_OK;
 }
 
+// Fallback buffers for the current system: flagged-atom list, its length, teacher adjoint rows.
+cudaError_t alloc_fallback(nep_handle *h) {
+  dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
+  const size_t N = (size_t)std::max(h->n, 1);
+  h->fb_cap = (int)std::min<double>((double)N, std::max(1.0, std::ceil((double)N * h->fb_frac)));
+  cudaError_t e = dalloc(h->fb_list, (size_t)h->fb_cap);
+  if (e == cudaSuccess) e = dalloc(h->fb_count, 1);
+  if (e == cudaSuccess) e = dalloc(h->fb_G, (size_t)h->fb_cap * CuShape::GS);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->fb_count, 0, sizeof(int), h->stream);
+  return e;
+}
+
 const int LAUNCHES_PER_STEP = 16;
 
 }  // namespace
@@ -491,6 +543,7 @@ const char *nep_status_string(nep_status s) {
     case NEP_ERR_STATE: return "NEP_ERR_STATE";
     case NEP_ERR_UNSUPPORTED: return "NEP_ERR_UNSUPPORTED";
     case NEP_ERR_OOM: return "NEP_ERR_OOM";
+    case NEP_ERR_FALLBACK_OVERFLOW: return "NEP_ERR_FALLBACK_OVERFLOW";
   }
   return "NEP_ERR_UNKNOWN";
 }
@@ -617,6 +670,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->tile_sums, (size_t)scan_tiles(h->ncell) + 1));
   A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 13 + 1));
   A(dalloc(h->part_k, (size_t)h->nb_k + 1)); A(dalloc(h->io, 6 * N));
+  if (h->fb_on) A(alloc_fallback(h));
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_system(h);
@@ -683,7 +737,7 @@ nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
       if (s != NEP_OK) return s;
     }
     for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
-    h->launch_total += (long long)LAUNCHES_PER_STEP * n_steps;
+    h->launch_total += (long long)(LAUNCHES_PER_STEP + (h->fb_on ? 2 : 0)) * n_steps;
   }
   return check_device_status(h);
 }
@@ -805,7 +859,7 @@ nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_
   return NEP_OK;
 }
 
-nep_status nep_get_counters(nep_handle *h, int64_t out[12]) {
+nep_status nep_get_counters(nep_handle *h, int64_t out[13]) {
   if (!h || !out) return NEP_ERR_ARG;
   nep_status s = check_device_status(h);
   if (s != NEP_OK && s != NEP_ERR_NEIGH_OVERFLOW && s != NEP_ERR_NAN) return s;
@@ -822,6 +876,73 @@ nep_status nep_get_counters(nep_handle *h, int64_t out[12]) {
   out[9] = c[5];                // force: owned active pairs
   out[10] = c[6];               // force: owned radial pairs
   out[11] = c[7];               // force: owned angular pairs
+  out[12] = c[9];               // atom evaluations by the fallback model
+  return NEP_OK;
+}
+
+nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const float *q_lo, const float *q_hi,
+                            float margin, double max_fraction) {
+  if (!h) return NEP_ERR_ARG;
+  if (teacher == nullptr) {
+    h->fb_on = false;
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    return NEP_OK;
+  }
+  if (h->shape != 1) return fail(h, NEP_ERR_UNSUPPORTED, "the fallback is for a student-shaped model");
+  if (!shape_matches<CuShape>(teacher)) return fail(h, NEP_ERR_UNSUPPORTED, "the fallback model must have the teacher shape");
+  if (!q_lo || !q_hi || !(margin >= 0.f) || !(max_fraction >= 0.0) || max_fraction > 1.0)
+    return fail(h, NEP_ERR_ARG, "invalid fallback range");
+  if (!teacher->c_R || !teacher->c_A || !teacher->W0 || !teacher->b0 || !teacher->w1 || !teacher->q_scale)
+    return fail(h, NEP_ERR_ARG, "fallback model arrays are NULL");
+  if (teacher->rc_R != h->rcR || teacher->rc_A > h->rcR)
+    return fail(h, NEP_ERR_ARG, "the fallback model must use the student's radial cutoff");
+  nep_params t = *teacher;
+  t.lj_eps = 0.f;                                  // the LJ term stays with the student's kernels
+  fill_model(h->fb_model, &t);
+  for (int v = 0; v < 16; ++v) { h->fb_lo[v] = -INFINITY; h->fb_hi[v] = INFINITY; }
+  for (int v = 0; v < StudentShape::NDES; ++v) {
+    const float w = q_hi[v] - q_lo[v];
+    h->fb_lo[v] = q_lo[v] - margin * w;
+    h->fb_hi[v] = q_hi[v] + margin * w;
+  }
+  h->fb_frac = max_fraction > 0.0 ? max_fraction : 1.0 / 16.0;
+  h->fb_on = true;
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  h->have_forces = false;
+  if (h->have_state) {
+    cudaError_t e = alloc_fallback(h);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->fb_on = false;
+      return fail(h, e == cudaErrorMemoryAllocation ? NEP_ERR_OOM : NEP_ERR_CUDA, "fallback allocation failed");
+    }
+  }
+  return NEP_OK;
+}
+
+nep_status nep_get_fallback(nep_handle *h, int *flags, int64_t *count) {
+  if (!h) return NEP_ERR_ARG;
+  if (!h->fb_on) return fail(h, NEP_ERR_STATE, "no fallback model is set");
+  if (!h->have_forces) return fail(h, NEP_ERR_STATE, "no force evaluation since the last state change");
+  int hc = 0;
+  NEP_CUDA(h, cudaMemcpyAsync(&hc, h->fb_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (flags && h->n > 0) {
+    const size_t N = (size_t)h->n;
+    if (h->io_i_elems < N) {
+      dfree(h->io_i);
+      NEP_CUDA(h, dalloc(h->io_i, N));
+      h->io_i_elems = N;
+    }
+    NEP_CUDA(h, cudaMemsetAsync(h->io_i, 0, N * sizeof(int32_t), h->stream));
+    {
+      Scope sc(h, KC_OTHER, 1);
+      NEP_CUDA(h, launch_fallback_flags(h->fb_list, h->fb_count, h->fb_cap, h->id, h->io_i, h->stream));
+    }
+    NEP_CUDA(h, cudaMemcpyAsync(flags, h->io_i, N * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+  }
+  nep_status s = check_device_status(h);
+  if (s != NEP_OK) return s;
+  if (count) *count = std::min(hc, h->fb_cap);
   return NEP_OK;
 }
 

@@ -28,6 +28,7 @@ constexpr double FIX_INV = 1.0 / 4294967296.0;
 enum : int {
   ST_OVERFLOW = 1,   // neighbour list capacity exceeded
   ST_NAN = 2,        // non-finite value seen
+  ST_FB_OVERFLOW = 8 // more atoms flagged for the fallback model than its list holds
 };
 
 // Device-side control block (one per handle).

@@ -50,6 +50,37 @@ __device__ __forceinline__ void load_tail8(const GT *row, int off, float (&v)[8]
   }
 }
 
+// Per-atom fallback to another model (the teacher) for atoms whose scaled descriptors leave a box:
+// an atom is flagged when some q~_nu = q_scale_nu q_nu lies outside [lo_nu, hi_nu].  Flagged atoms
+// get a zero adjoint row and no site energy from this model; their indices are appended to `list`
+// (order of arrival: the consumers only use integer atomics, so results do not depend on it).
+struct Fallback {
+  int on;
+  int cap;                 // capacity of list
+  int *list, *count;       // flagged atoms (cell-sorted indices), number flagged
+  float lo[16], hi[16];
+};
+
+template <class S>
+__device__ __forceinline__ bool out_of_range(const Fallback &fb, const Model<S> &P, const float (&q)[S::NDES]) {
+  bool out = false;
+  if constexpr (S::NDES <= 16) {       // the range box holds up to 16 descriptors (the student's 12)
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) {
+      const float t = q[v] * P.qs[v];
+      out |= (t < fb.lo[v]) | (t > fb.hi[v]);
+    }
+  }
+  return out;
+}
+
+// Append atom i to the fallback list (status bit ST_FB_OVERFLOW when the list is full).
+__device__ __forceinline__ void flag_atom(const Fallback &fb, int i, int *status) {
+  const int slot = atomicAdd(fb.count, 1);
+  if (slot < fb.cap) fb.list[slot] = i;
+  else atomicOr(status, ST_FB_OVERFLOW);
+}
+
 template <class S>
 struct AtomSums {
   float qR[S::NR];

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
 k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
              const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
              float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
-             long long *__restrict__ part, int *__restrict__ status) {
+             long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   __shared__ float4 shift[27];
   __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
   __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
@@ -72,6 +72,8 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
     }
+    const bool flagged = fb.on && out_of_range<S>(fb, P, q);
+    if (flagged) flag_atom(fb, i, status);
 
     // Network: U = sum_mu w1 tanh(sum_nu W0 q~_nu - b0) - b1; dU/dq~ accumulated in dq.
     float qt[S::NDES], dq[S::NDES];
@@ -91,7 +93,7 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     }
     float Fp[S::NDES];
 #pragma unroll
-    for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
+    for (int v = 0; v < S::NDES; ++v) Fp[v] = flagged ? 0.f : dq[v] * P.qs[v];   // flagged: no U_i here
 
     float *Gi = G + (size_t)i * S::GS;
 #pragma unroll
@@ -109,7 +111,7 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
       *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM) = make_float4(tail[0], tail[1], tail[2], tail[3]);
       *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM + 4) = make_float4(tail[4], tail[5], tail[6], tail[7]);
     }
-    const float ui = U + A.elj;
+    const float ui = flagged ? A.elj : U + A.elj;
     usite[i] = ui;
     if (!isfinite(ui)) atomicOr(status, ST_NAN);
     acc[0] = to_fix32(ui);
@@ -273,10 +275,10 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
                               const int32_t *nnum, float *G, float *usite, float *qout, long long *Ffix,
-                              long long *part, int *status, cudaStream_t st) {
+                              long long *part, int *status, const Fallback &fb, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
-  k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status);
+  k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status, fb);
   return cudaGetLastError();
 }
 
@@ -297,7 +299,7 @@ int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
 #define NEP_INSTANTIATE(SH)                                                                                    \
   template cudaError_t launch_descriptor<SH>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *,   \
                                              const int32_t *, float *, float *, float *, long long *, long long *,    \
-                                             int *, cudaStream_t);                                                    \
+                                             int *, const Fallback &, cudaStream_t);                                  \
   template cudaError_t launch_force<SH, float>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *, \
                                                const int32_t *, const int32_t *, const float *, long long *,          \
                                                long long *, int *, cudaStream_t);                                     \

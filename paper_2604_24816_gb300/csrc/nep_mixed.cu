@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(MIX_BLOCK, 2)
 k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
                    const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, __half *__restrict__ G,
                    float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
-                   long long *__restrict__ part, int *__restrict__ status) {
+                   long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   static_assert(S::NDES <= MIX_K && S::NNEU <= MIX_N, "network larger than one tensor-core tile");
   __shared__ float4 shift[27];
   __shared__ uint32_t ring_e[MIX_DE * MIX_BLOCK];
@@ -65,6 +65,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   FourBody<S> T;
   float q[S::NDES];
   long long acc[5] = {0, 0, 0, 0, 0};
+  bool flagged = false;
   if (live) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     accumulate_atom<S, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
@@ -73,6 +74,8 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
     }
+    flagged = fb.on && out_of_range<S>(fb, P, q);
+    if (flagged) flag_atom(fb, i, status);
   } else {
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) q[v] = 0.f;
@@ -133,7 +136,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   if (live) {
     float Fp[S::NDES];
 #pragma unroll
-    for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
+    for (int v = 0; v < S::NDES; ++v) Fp[v] = flagged ? 0.f : dq[v] * P.qs[v];   // flagged: no U_i here
     __half *Gi = G + (size_t)i * S::GS;
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
@@ -148,7 +151,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
       for (int a = 0; a < S::NR; ++a) tail[a] = Fp[a];
       *reinterpret_cast<uint4 *>(Gi + S::NA * S::NLM) = pack8_half(tail);
     }
-    const float ui = U + A.elj;
+    const float ui = flagged ? A.elj : U + A.elj;
     usite[i] = ui;
     if (!isfinite(ui)) atomicOr(status, ST_NAN);
     acc[0] = to_fix32(ui);
@@ -166,10 +169,11 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 template <class S, class MT>
 cudaError_t launch_descriptor_mixed(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
                                     const int32_t *nnum, __half *G, float *usite, float *qout, long long *Ffix,
-                                    long long *part, int *status, cudaStream_t st) {
+                                    long long *part, int *status, const Fallback &fb, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + MIX_BLOCK - 1) / MIX_BLOCK;
-  k_descriptor_mixed<S, MT><<<grid, MIX_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status);
+  k_descriptor_mixed<S, MT><<<grid, MIX_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status,
+                                                        fb);
   return cudaGetLastError();
 }
 
@@ -178,7 +182,8 @@ int mixed_descriptor_blocks(int n) { return (n + MIX_BLOCK - 1) / MIX_BLOCK; }
 #define NEP_INSTANTIATE(SH, MT)                                                                                \
   template cudaError_t launch_descriptor_mixed<SH, MT>(const Model<SH> &, const Geom &, int, const float4 *,          \
                                                        const int32_t *, const int32_t *, __half *, float *, float *,  \
-                                                       long long *, long long *, int *, cudaStream_t);
+                                                       long long *, long long *, int *, const Fallback &,             \
+                                                       cudaStream_t);
 NEP_INSTANTIATE(CuShape, __nv_bfloat16)
 NEP_INSTANTIATE(CuShape, __half)
 NEP_INSTANTIATE(StudentShape, __nv_bfloat16)

@@ -23,12 +23,14 @@
 #include <thread>
 
 #include "nep_common.cuh"
+#include "nep_descriptor.cuh"
 #include "nep_gb300.h"
 
 namespace nep {
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                              float *, float *, float *, long long *, long long *, int *, cudaStream_t);
+                              float *, float *, float *, long long *, long long *, int *, const Fallback &,
+                              cudaStream_t);
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
                          const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
@@ -244,7 +246,7 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   NA_CUDA(launch_cell_sort(a, st));
   NA_CUDA(launch_neighbors(a, st));
   NA_CUDA(launch_descriptor<S>(M, g, N, a.pos, a.nbr, a.nnum, (float *)at(LAYOUT.G), (float *)at(LAYOUT.usite),
-                               nullptr, Ffix, pd, &ctrl->status, st));
+                               nullptr, Ffix, pd, &ctrl->status, Fallback{}, st));
   NA_CUDA((launch_force<S, float>(M, g, N, a.pos, a.nbr, a.nown, a.nband0, (const float *)at(LAYOUT.G), Ffix, pf,
                           &ctrl->status, st)));
   NA_CUDA(launch_finalize(pd, descriptor_blocks(N), pf, force_blocks(N), nullptr, 0, sums, counters, st));

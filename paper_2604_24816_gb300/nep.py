@@ -52,7 +52,7 @@ class nep_params(C.Structure):
 EXPORTED = ("nep_create", "nep_destroy", "nep_set_state", "nep_build_neighbors", "nep_compute", "md_verlet_step",
             "nep_get_state", "nep_get_thermo", "nep_get_neighbors", "nep_get_descriptors", "nep_get_site_energies",
             "nep_set_timing", "nep_get_timing", "nep_get_counters", "nep_last_error", "nep_status_string",
-            "nep_compute_noalloc")
+            "nep_compute_noalloc", "nep_set_fallback", "nep_get_fallback")
 
 
 def lib():
@@ -84,6 +84,9 @@ def lib():
         L.nep_status_string.argtypes = [C.c_int]
         L.nep_status_string.restype = C.c_char_p
         L.nep_compute_noalloc.argtypes = [C.POINTER(nep_params), i64, vp, d, vp, vp, vp, vp]
+        L.nep_set_fallback.argtypes = [vp, C.POINTER(nep_params), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.c_float, C.c_double]
+        L.nep_get_fallback.argtypes = [vp, vp, C.POINTER(C.c_int64)]
         for f in EXPORTED:
             if f not in ("nep_last_error", "nep_status_string"):
                 getattr(L, f).restype = C.c_int
@@ -234,9 +237,40 @@ class NEP:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def counters(self) -> dict:
-        out = np.zeros(12, dtype=np.int64)
+        out = np.zeros(13, dtype=np.int64)
         self._check(self._L.nep_get_counters(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return dict(radial_pairs=int(out[0]), angular_pairs=int(out[1]), evaluations=int(out[2]),
                     rebuilds=int(out[3]), steps=int(out[4]), launches=int(out[5]), list_entries=int(out[6]),
                     active_pairs=int(out[7]), owned_list_entries=int(out[8]), owned_active_pairs=int(out[9]),
-                    owned_radial_pairs=int(out[10]), owned_angular_pairs=int(out[11]))
+                    owned_radial_pairs=int(out[10]), owned_angular_pairs=int(out[11]),
+                    fallback_atoms=int(out[12]))
+
+    def set_fallback(self, teacher: dict | None, q_lo=None, q_hi=None, margin: float = 0.05,
+                     max_fraction: float = 0.0):
+        """Per-atom fallback of this (student-shaped) model to `teacher` for atoms whose scaled
+        descriptors leave [q_lo - margin w, q_hi + margin w], w = q_hi - q_lo (nep_set_fallback)."""
+        if teacher is None:
+            self._check(self._L.nep_set_fallback(self._h, None, None, None, 0.0, 0.0))
+            return
+        f32 = lambda k: np.ascontiguousarray(np.asarray(teacher[k], dtype=np.float32).ravel())
+        self._fb_keep = {k: f32(k) for k in ("c_R", "c_A", "W0", "b0", "w1", "q_scale")}
+        fp = lambda k: self._fb_keep[k].ctypes.data_as(C.POINTER(C.c_float))
+        m = teacher
+        p = nep_params(int(m["n_max_R"]), int(m["n_max_A"]), int(m["basis_R"]), int(m["basis_A"]), int(m["l_max_3b"]),
+                       int(m["l_max_4b"]), int(m["n_neu"]), float(m["rc_R"]), float(m["rc_A"]),
+                       fp("c_R"), fp("c_A"), fp("W0"), fp("b0"), fp("w1"), float(m.get("b1", 0.0)), fp("q_scale"),
+                       0.0, float(m.get("lj_sigma", 1.0)), float(m.get("lj_rc", m["rc_R"])),
+                       float(m.get("mass_amu", 63.546)), float(m.get("skin", 1.0)), 0, 0, 0)
+        lo = np.ascontiguousarray(np.asarray(q_lo, dtype=np.float32))
+        hi = np.ascontiguousarray(np.asarray(q_hi, dtype=np.float32))
+        self._fb_keep["lo"], self._fb_keep["hi"] = lo, hi
+        self._check(self._L.nep_set_fallback(self._h, C.byref(p), lo.ctypes.data_as(C.POINTER(C.c_float)),
+                                             hi.ctypes.data_as(C.POINTER(C.c_float)), float(margin),
+                                             float(max_fraction)))
+
+    def fallback(self):
+        """(flags[n] int32, 1 = teacher; number of flagged atoms) of the last force evaluation."""
+        flags = np.zeros(max(self.n, 1), dtype=np.int32)
+        cnt = C.c_int64(0)
+        self._check(self._L.nep_get_fallback(self._h, flags.ctypes.data, C.byref(cnt)))
+        return flags[:self.n], int(cnt.value)

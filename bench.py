@@ -55,14 +55,20 @@ FLOPS = {
     "descriptor": dict(list_entry=11, active_pair=2, radial_pair=128, lj_pair=12, angular_pair=464, atom=4655),
     "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=220, lj_pair=13, angular_pair=1465, atom=3),
 }
+# The same static count for the student shape (4 radial + 4 angular channels, 8 basis functions,
+# l = 1, 2, no 4-body, 16 neurons), used for the student forms.
+FLOPS_STUDENT = {
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=112, lj_pair=12, angular_pair=193, atom=1016),
+    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=201, lj_pair=13, angular_pair=570, atom=3),
+}
 # Algorithmic bytes per atom per force evaluation (HBM, float32 path): positions 16 (x2 kernels), list
 # entries 4 each (descriptor: full row, force: owned half), adjoint row 512 written + read, fixed-point
 # force 24 zeroed + accumulated, site energy 4.
 BYTES = dict(per_atom=16 * 2 + 512 * 2 + 24 * 2 + 4, per_list_entry=4 * 1.5)
 
 
-def kernel_flops(kind: str, c: dict, n_atoms_evals: int) -> float:
-    f = FLOPS[kind]
+def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) -> float:
+    f = table[kind]
     if kind == "descriptor":
         lst, act, rad, ang = c["list_entries"], c["active_pairs"], c["radial_pairs"], c["angular_pairs"]
     else:
@@ -266,25 +272,58 @@ def run_reference(args, rank: int, ws: int):
     }), flush=True)
 
 
-# form name -> (library precision, arithmetic types, description)
+# form name -> library precision, model (teacher or distilled student), per-atom fallback to the
+# teacher, arithmetic types, description
+_MIX = ("network GEMMs on tcgen05 tensor cores with {} operands and f32 accumulation, float16 adjoint rows, "
+        "FP32 descriptors, float64 integration and sums")
 FORMS = {
-    "plain": ("fp32", "f32", "plain FP32 NEP (float64 integration and sums)"),
-    "mix_bf16": ("mix_bf16", "bf16/f32", "mixed precision: network GEMMs on tcgen05 tensor cores with bf16 operands and "
-                 "f32 accumulation, float16 adjoint rows, FP32 descriptors, float64 integration and sums"),
-    "mix_fp16": ("mix_fp16", "f16/f32", "mixed precision: network GEMMs on tcgen05 tensor cores with f16 operands and "
-                 "f32 accumulation, float16 adjoint rows, FP32 descriptors, float64 integration and sums"),
+    "plain": dict(precision="fp32", model="teacher", fallback=False, dtype="f32",
+                  desc="plain FP32 NEP (float64 integration and sums)"),
+    "mix_bf16": dict(precision="mix_bf16", model="teacher", fallback=False, dtype="bf16/f32",
+                     desc="mixed precision: " + _MIX.format("bf16")),
+    "mix_fp16": dict(precision="mix_fp16", model="teacher", fallback=False, dtype="f16/f32",
+                     desc="mixed precision: " + _MIX.format("f16")),
+    "student": dict(precision="fp32", model="student", fallback=False, dtype="f32",
+                    desc="distilled student NEP (n_max 3/3, l_max 2, no 4-body, 16 neurons), FP32"),
+    "student_bf16_fallback": dict(precision="mix_bf16", model="student", fallback=True, dtype="bf16/f32",
+                                  desc="distilled student NEP, " + _MIX.format("bf16") + "; per-atom fallback to the "
+                                       "FP32 teacher for atoms outside the student's training range (5 % margin)"),
 }
+FALLBACK_MARGIN = 0.05
+STUDENT_PATH = os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_student_trained.json")
 
 
-def time_form(form, model, wl, args, stream, dev, ws, atoms_total):
+def row_bytes(form: str) -> int:
+    """Bytes of one adjoint row G of the form's model (teacher 128 / student 40 values; float32 in the
+    plain forms, float16 in the mixed ones)."""
+    f = FORMS[form]
+    return (40 if f["model"] == "student" else 128) * (4 if f["precision"] == "fp32" else 2)
+
+
+def load_student() -> dict:
+    with open(STUDENT_PATH) as f:
+        return json.load(f)
+
+
+def make_nep(form, teacher, student, stream, args):
+    from paper_2604_24816_gb300 import NEP
+    f = FORMS[form]
+    h = NEP(student if f["model"] == "student" else teacher, stream=stream.cuda_stream,
+            rebuild_every=args.rebuild_every, precision=f["precision"], max_neighbors=args.max_neighbors)
+    if f["fallback"]:
+        h.set_fallback(teacher, student["q_lo"], student["q_hi"], margin=FALLBACK_MARGIN)
+    return h
+
+
+def time_form(form, teacher, student, wl, args, stream, dev, ws, atoms_total):
     """Throughput of another form on the same workload and start state (warm-up, then --form-steps
     CUDA-graph MD steps timed with events), plus its forces on the start state."""
     import torch
-    from paper_2604_24816_gb300 import NEP
-    with NEP(model, stream=stream.cuda_stream, rebuild_every=args.rebuild_every, precision=FORMS[form][0]) as h:
+    with make_nep(form, teacher, student, stream, args) as h:
         h.set_state(wl.pos, wl.vel, wl.box)
         _, F, _ = h.compute()
         h.step(wl.dt_fs, args.warmup)
+        c0 = h.counters()
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         dist_barrier(ws)
@@ -295,22 +334,28 @@ def time_form(form, model, wl, args, stream, dev, ws, atoms_total):
         torch.cuda.synchronize(dev)
         ms = dist_max(s.elapsed_time(e), ws, dev)
         th = h.thermo()
-    return {"value": atoms_total * args.form_steps / (ms * 1e-3), "ms_per_step": ms / args.form_steps,
-            "steps": args.form_steps, "dtype": FORMS[form][1], "pe_per_atom_end": th["pe"] / wl.n, "_F": F}
+        c1 = h.counters()
+    rec = {"value": atoms_total * args.form_steps / (ms * 1e-3), "ms_per_step": ms / args.form_steps,
+           "steps": args.form_steps, "dtype": FORMS[form]["dtype"], "pe_per_atom_end": th["pe"] / wl.n, "_F": F}
+    if FORMS[form]["fallback"]:
+        ev = max(1, c1["evaluations"] - c0["evaluations"])
+        rec["fallback_fraction"] = (c1["fallback_atoms"] - c0["fallback_atoms"]) / (ev * wl.n)
+    return rec
 
 
 def run_ours(args, rank: int, ws: int, local: int):
     import torch
-    from paper_2604_24816_gb300 import NEP, load_model, build
+    from paper_2604_24816_gb300 import load_model, build
 
     build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     model = load_model()
+    student = load_student()
     wl = ni.workload(args.workload) if rank == 0 else ni.fcc_cu_workload(
         64, 300.0, 0.05, seed=2 + rank, steps=200, name=args.workload)   # independent replica per rank
     stream = torch.cuda.Stream(device=dev)
-    nep = NEP(model, stream=stream.cuda_stream, rebuild_every=args.rebuild_every, precision=FORMS[args.form][0])
+    nep = make_nep(args.form, model, student, stream, args)
     nep.set_state(wl.pos, wl.vel, wl.box)
     nep.compute(forces=False)
 
@@ -345,8 +390,9 @@ def run_ours(args, rank: int, ws: int, local: int):
     th = nep.thermo()
     dc = {k: c1[k] - c0[k] for k in c1}
     evals = dc["evaluations"]
-    f_desc = kernel_flops("descriptor", dc, evals * wl.n)
-    f_force = kernel_flops("force", dc, evals * wl.n)
+    table = FLOPS_STUDENT if FORMS[args.form]["model"] == "student" else FLOPS
+    f_desc = kernel_flops("descriptor", dc, evals * wl.n, table)
+    f_force = kernel_flops("force", dc, evals * wl.n, table)
     peaks = load_peaks()
     clk = clocks.summary(t_host0, t_host1)
     peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -356,7 +402,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     dom_ms = tim[dominant][0]
     dom_launches = max(1, tim[dominant][1])
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = profiled_traffic(dominant)
+    traffic = profiled_traffic(dominant if args.form == "plain" else f"{dominant}:{args.form}")
     roofline = {
         "bound": "alu",
         "kernel": "k_descriptor_mixed" if dominant == "descriptor" and args.form != "plain" else f"k_{dominant}", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
@@ -398,7 +444,7 @@ def run_ours(args, rank: int, ws: int, local: int):
                "d2h_bytes_per_step": 48 * wl.n + 8 * 16, "steps": args.e2e_steps,
                "note": "per step: nep_set_state(x, v from pinned host) + md_verlet_step(1) (rebuild + 2 force "
                        "evaluations for the uploaded state) + nep_get_state(x, v to pinned host) + thermo"}
-    F_plain = None
+    F_plain = F_this = None
     others = [] if args.no_forms else [f for f in FORMS if f != args.form]
     if others:
         nep.set_state(wl.pos, wl.vel, wl.box)
@@ -406,12 +452,12 @@ def run_ours(args, rank: int, ws: int, local: int):
     nep.close()
     forms = {}
     for f in others:
-        forms[f] = time_form(f, model, wl, args, stream, dev, ws, atoms_total)
+        forms[f] = time_form(f, model, student, wl, args, stream, dev, ws, atoms_total)
         if f == "plain":
             F_plain = forms[f].pop("_F")
     if args.form == "plain":
         F_plain = F_this
-    if F_plain is not None:
+    if F_plain is not None and F_this is not None:
         idx = ni.sample_indices(wl.n, 8192, seed=11)
         for f, rec in forms.items():
             if "_F" in rec:
@@ -428,13 +474,15 @@ def run_ours(args, rank: int, ws: int, local: int):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": FORMS[args.form][1], "data": "synthetic",
-        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "form": FORMS[args.form][2],
+        "dtype": FORMS[args.form]["dtype"], "data": "synthetic",
+        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "form": FORMS[args.form]["desc"],
                    "dt_fs": wl.dt_fs, "temperature_K": wl.temperature,
                    "neighbor_rebuild": f"every {args.rebuild_every} steps + displacement check (skin/2)",
                    "rebuilds_in_timed_region": dc["rebuilds"],
+                   **({"fallback_fraction": dc["fallback_atoms"] / max(1, evals * wl.n),
+                       "fallback_margin": FALLBACK_MARGIN} if FORMS[args.form]["fallback"] else {}),
                    "l2": "inputs larger than L2: per-step working set ~"
-                         f"{(wl.n * (BYTES['per_atom'] + 48 * 2) + dc['list_entries'] / max(1, evals) * BYTES['per_list_entry']) / 1e9:.2f} GB"
+                         f"{(wl.n * (row_bytes(args.form) * 2 + BYTES['per_atom'] - 512 * 2 + 48 * 2) + dc['list_entries'] / max(1, evals) * BYTES['per_list_entry']) / 1e9:.2f} GB"
                          " (neighbour list, adjoint rows, state) vs 129 MB L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "model": "cu_nep4_synth (seeded)"},
         "roofline": roofline,
@@ -469,6 +517,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="plain", choices=tuple(FORMS))
     ap.add_argument("--form-steps", type=int, default=50)
+    ap.add_argument("--max-neighbors", type=int, default=0, help="neighbour-list capacity per atom (0 = 128)")
     ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -38,7 +38,7 @@ extern "C" {
 #endif
 
 #define NEP_MAX_ATOMS 134217727LL   /* 2^27 - 1 */
-#define NEP_N_KERNEL_CLASSES 8
+#define NEP_N_KERNEL_CLASSES 9
 
 typedef enum {
     NEP_OK = 0,
@@ -148,7 +148,8 @@ nep_status nep_set_timing(nep_handle *h, int enable);
 
 /* Accumulated milliseconds and launch counts per kernel class since timing was enabled:
  * classes 0 drift, 1 cell sort, 2 neighbour list, 3 descriptors+network, 4 forces, 5 kick,
- * 6 reductions, 7 un-permute/other. */
+ * 6 reductions, 7 un-permute/other, 8 fallback model (descriptors, network and forces of the flagged
+ * atoms, nep_set_fallback). */
 nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_t launches[NEP_N_KERNEL_CLASSES]);
 
 /* Counters since nep_set_state: out = {radial pairs (r < rc_R) and angular pairs (r < rc_A) seen by the

@@ -81,7 +81,9 @@ constexpr double KB_EV = 8.617333262e-5;
 constexpr double ACC_CONV = 9.64853321233100e-3;
 constexpr double WAIT_LIMIT_S = 900.0;
 
-enum KClass { KC_DRIFT = 0, KC_CELL = 1, KC_NEIGH = 2, KC_DESC = 3, KC_FORCE = 4, KC_KICK = 5, KC_RED = 6, KC_OTHER = 7 };
+enum KClass {
+  KC_DRIFT = 0, KC_CELL = 1, KC_NEIGH = 2, KC_DESC = 3, KC_FORCE = 4, KC_KICK = 5, KC_RED = 6, KC_OTHER = 7, KC_FB = 8
+};
 
 struct Timer {
   int cls;
@@ -312,9 +314,9 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
     for (int v = 0; v < 16; ++v) { fb.lo[v] = h->fb_lo[v]; fb.hi[v] = h->fb_hi[v]; }
   }
   cudaError_t e;
+  if (fb.on && (e = cudaMemsetAsync(h->fb_count, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
   {
-    Scope sc(h, KC_DESC, fb.on ? 2 : 1);
-    if (fb.on && (e = cudaMemsetAsync(h->fb_count, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
+    Scope sc(h, KC_DESC, 1);
     if (h->precision == NEP_FP32)
       e = launch_descriptor<S>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<float *>(h->G), h->usite, qout, h->F,
                                h->part_d, &h->ctrl->status, fb, h->stream);
@@ -324,22 +326,29 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
     else
       e = launch_descriptor_mixed<S, __half>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
                                               h->usite, qout, h->F, h->part_d, &h->ctrl->status, fb, h->stream);
-    if (e == cudaSuccess && fb.on)
-      e = launch_fallback_descriptor<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list, h->fb_count,
-                                              h->fb_cap, h->fb_G, h->usite, h->part_d, h->counters, &h->ctrl->status,
-                                              h->stream);
   }
   if (e != cudaSuccess) return e;
-  Scope sc(h, KC_FORCE, fb.on ? 2 : 1);
-  if (h->precision == NEP_FP32)
-    e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G), h->F,
-                               h->part_f, &h->ctrl->status, h->stream);
-  else
-    e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const __half *>(h->G),
-                                h->F, h->part_f, &h->ctrl->status, h->stream);
-  if (e == cudaSuccess && fb.on)
+  if (fb.on) {
+    Scope sc(h, KC_FB, 1);
+    e = launch_fallback_descriptor<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list, h->fb_count,
+                                            h->fb_cap, h->fb_G, h->usite, h->part_d, h->counters, &h->ctrl->status,
+                                            h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    Scope sc(h, KC_FORCE, 1);
+    if (h->precision == NEP_FP32)
+      e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G),
+                                 h->F, h->part_f, &h->ctrl->status, h->stream);
+    else
+      e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const __half *>(h->G),
+                                  h->F, h->part_f, &h->ctrl->status, h->stream);
+  }
+  if (e == cudaSuccess && fb.on) {
+    Scope sc(h, KC_FB, 1);
     e = launch_fallback_force<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list, h->fb_count,
                                        h->fb_cap, h->fb_G, h->F, h->part_f, &h->ctrl->status, h->stream);
+  }
   return e;
 }
 

@@ -20,9 +20,9 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libnep_gb300.so")
 DEFAULT_MODEL = os.path.join(_PKG, "params", "cu_nep4_synth.json")
-N_KERNEL_CLASSES = 8
+N_KERNEL_CLASSES = 9
 PRECISION = {"fp32": 0, "mix_bf16": 1, "mix_fp16": 2}
-KERNEL_CLASSES = ("drift", "cell_sort", "neighbors", "descriptor", "force", "kick", "reduce", "other")
+KERNEL_CLASSES = ("drift", "cell_sort", "neighbors", "descriptor", "force", "kick", "reduce", "other", "fallback")
 
 _lock = threading.Lock()
 _lib = None

@@ -52,14 +52,14 @@ FP32_LANES_PER_SM = 128
 # channels, 8 basis functions, l = 1..4, 4-body, 30 neurons).  The descriptor kernel visits every
 # list entry of every atom; the force kernel visits each unordered pair once (its owner's half list).
 FLOPS = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=128, lj_pair=12, angular_pair=464, atom=4655),
-    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=220, lj_pair=13, angular_pair=1465, atom=3),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=56, lj_pair=12, angular_pair=464, atom=4815),
+    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=149, lj_pair=13, angular_pair=1465, atom=3),
 }
 # The same static count for the student shape (4 radial + 4 angular channels, 8 basis functions,
 # l = 1, 2, no 4-body, 16 neurons), used for the student forms.
 FLOPS_STUDENT = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=112, lj_pair=12, angular_pair=193, atom=1016),
-    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=201, lj_pair=13, angular_pair=570, atom=3),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=56, lj_pair=12, angular_pair=193, atom=1144),
+    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=149, lj_pair=13, angular_pair=570, atom=3),
 }
 # Algorithmic bytes per atom per force evaluation (HBM, float32 path): positions 16 (x2 kernels), list
 # entries 4 each (descriptor: full row, force: owned half), adjoint row 512 written + read, fixed-point

@@ -10,7 +10,8 @@
 //   Ffix     int64 [3][N]: forces in fixed point (2^-32 eV/Angstrom units), accumulated with
 //            integer atomics, so the sum does not depend on the order of the additions.
 //   G        float or half [N][S::GS]: per-atom adjoint dU_i/ds_nlm (NA * NLM values, index n * NLM + lm)
-//            followed by dU_i/dq_n of the radial descriptors (NR <= 8 values) and padding
+//            followed by the radial adjoint in basis space dU_i/dQ_k = sum_n dU_i/dq_n cR_nk (KR <= 8
+//            values, Q_k = sum_j f_k(r_ij) the radial basis sums) and padding
 //            (teacher shape: 5 x 24 + 8 = 128 per row; student shape: 4 x 8 + 8 = 40).
 #pragma once
 

@@ -83,7 +83,8 @@ __device__ __forceinline__ void flag_atom(const Fallback &fb, int i, int *status
 
 template <class S>
 struct AtomSums {
-  float qR[S::NR];
+  float QR[S::KR];        // radial basis sums sum_j f_k(r_ij); q_n = sum_k cR_nk QR_k
+  static_assert(S::KR <= 8, "the radial adjoint in basis space lives in the 8-element row tail");
   float s[S::NA][S::NLM];
   float elj;
   int nrad, nang, nact, cnt;
@@ -96,7 +97,7 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
                                                 int cnt, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A) {
   const float4 pi = pos[i];
 #pragma unroll
-  for (int a = 0; a < S::NR; ++a) A.qR[a] = 0.f;
+  for (int k = 0; k < S::KR; ++k) A.QR[k] = 0.f;
 #pragma unroll
   for (int a = 0; a < S::NA; ++a)
 #pragma unroll
@@ -120,9 +121,7 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
       float f[S::KR];
       cheb_basis<S::KR>(r, P.inv_rcR, f);
 #pragma unroll
-      for (int a = 0; a < S::NR; ++a)
-#pragma unroll
-        for (int b = 0; b < S::KR; ++b) A.qR[a] = fmaf(P.cR[a][b], f[b], A.qR[a]);
+      for (int k = 0; k < S::KR; ++k) A.QR[k] += f[k];
       ++A.nrad;
     }
     if (P.lj_on != 0.f && r2 < P.lj_rc2) {
@@ -161,9 +160,15 @@ struct FourBody {
 
 // Descriptors [q_n | q_nl (n-major, l = 1..LMAX) | q4_n = tr(T_n^3) = 3 det T_n (teacher shape only)].
 template <class S>
-__device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[S::NDES], FourBody<S> &T) {
+__device__ __forceinline__ void descriptors_of(const Model<S> &P, const AtomSums<S> &A, float (&q)[S::NDES],
+                                               FourBody<S> &T) {
 #pragma unroll
-  for (int a = 0; a < S::NR; ++a) q[a] = A.qR[a];
+  for (int a = 0; a < S::NR; ++a) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < S::KR; ++k) t = fmaf(P.cR[a][k], A.QR[k], t);
+    q[a] = t;
+  }
 #pragma unroll
   for (int a = 0; a < S::NA; ++a) {
 #pragma unroll
@@ -189,6 +194,21 @@ __device__ __forceinline__ void descriptors_of(const AtomSums<S> &A, float (&q)[
                         T.xz[a] * (T.xy[a] * T.yz[a] - T.yy[a] * T.xz[a]);
       q[S::NR + S::NA * S::LMAX + a] = 3.f * det;
     }
+  }
+}
+
+// Radial adjoint in basis space, stored in the row tail: tail_k = dU/dQR_k = sum_n Fp_n cR_nk, so the
+// force kernel contracts it directly with the basis derivatives f_k'(r) of each pair.
+template <class S>
+__device__ __forceinline__ void radial_tail(const Model<S> &P, const float (&Fp)[S::NDES], float (&tail)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float t = 0.f;
+    if (k < S::KR) {
+#pragma unroll
+      for (int a = 0; a < S::NR; ++a) t = fmaf(Fp[a], P.cR[a][k], t);
+    }
+    tail[k] = t;
   }
 }
 

@@ -66,7 +66,7 @@ k_fb_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n
     accumulate_atom<S, FB_DE, FB_DP, FB_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
     float q[S::NDES];
     FourBody<S> T;
-    descriptors_of<S>(A, q, T);
+    descriptors_of<S>(P, A, q, T);
     float qt[S::NDES], dq[S::NDES];
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) { qt[v] = q[v] * P.qs[v]; dq[v] = 0.f; }
@@ -94,8 +94,10 @@ k_fb_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n
       for (int c = 0; c < S::NLM; c += 4)
         *reinterpret_cast<float4 *>(Gi + a * S::NLM + c) = make_float4(gl[c], gl[c + 1], gl[c + 2], gl[c + 3]);
     }
+    float tail[8];
+    radial_tail<S>(P, Fp, tail);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) Gi[S::NA * S::NLM + t] = t < S::NR ? Fp[t] : 0.f;
+    for (int t = 0; t < 8; ++t) Gi[S::NA * S::NLM + t] = tail[t];
     usite[i] += U;                       // the student kernel left the LJ energy there
     if (!isfinite(U)) atomicOr(status, ST_NAN);
     acc[0] += to_fix32(U);
@@ -128,9 +130,9 @@ k_fb_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, con
         const float4 t = *reinterpret_cast<const float4 *>(Gi + a * S::NLM + c);
         gi[a][c] = t.x; gi[a][c + 1] = t.y; gi[a][c + 2] = t.z; gi[a][c + 3] = t.w;
       }
-    float fpi[S::NR];
+    float fpi[S::KR];
 #pragma unroll
-    for (int a = 0; a < S::NR; ++a) fpi[a] = Gi[S::NA * S::NLM + a];
+    for (int k = 0; k < S::KR; ++k) fpi[k] = Gi[S::NA * S::NLM + k];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
     const int cnt = nnum[i];
@@ -153,12 +155,7 @@ k_fb_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, con
         cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
         float c = 0.f;
 #pragma unroll
-        for (int a = 0; a < S::NR; ++a) {
-          float dg = 0.f;
-#pragma unroll
-          for (int b = 0; b < S::KR; ++b) dg = fmaf(P.cR[a][b], df[b], dg);
-          c = fmaf(fpi[a], dg, c);
-        }
+        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k], df[k], c);
         coef = c * ir;
       }
       if (r2 < P.rcA2) {

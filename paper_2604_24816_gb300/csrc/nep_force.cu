@@ -67,7 +67,7 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
     float q[S::NDES];
     FourBody<S> T;
-    descriptors_of<S>(A, q, T);
+    descriptors_of<S>(P, A, q, T);
     if (qout != nullptr) {
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
@@ -105,9 +105,8 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
         *reinterpret_cast<float4 *>(Gi + a * S::NLM + c) = make_float4(gl[c], gl[c + 1], gl[c + 2], gl[c + 3]);
     }
     {
-      float tail[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int a = 0; a < S::NR; ++a) tail[a] = Fp[a];
+      float tail[8];
+      radial_tail<S>(P, Fp, tail);
       *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM) = make_float4(tail[0], tail[1], tail[2], tail[3]);
       *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM + 4) = make_float4(tail[4], tail[5], tail[6], tail[7]);
     }
@@ -189,12 +188,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
         load_tail8(Gj, S::NA * S::NLM, fpj);
         float c = 0.f;
 #pragma unroll
-        for (int a = 0; a < S::NR; ++a) {
-          float dg = 0.f;
-#pragma unroll
-          for (int b = 0; b < S::KR; ++b) dg = fmaf(P.cR[a][b], df[b], dg);
-          c = fmaf(fpi[a] + fpj[a], dg, c);
-        }
+        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k] + fpj[k], df[k], c);
         coef = c * ir;
         ++nrad;
       }

@@ -69,7 +69,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   if (live) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     accumulate_atom<S, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
-    descriptors_of<S>(A, q, T);
+    descriptors_of<S>(P, A, q, T);
     if (qout != nullptr) {
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
@@ -146,9 +146,8 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
       for (int c = 0; c < S::NLM; c += 8) *reinterpret_cast<uint4 *>(Gi + a * S::NLM + c) = pack8_half(gl + c);
     }
     {
-      float tail[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int a = 0; a < S::NR; ++a) tail[a] = Fp[a];
+      float tail[8];
+      radial_tail<S>(P, Fp, tail);
       *reinterpret_cast<uint4 *>(Gi + S::NA * S::NLM) = pack8_half(tail);
     }
     const float ui = flagged ? A.elj : U + A.elj;

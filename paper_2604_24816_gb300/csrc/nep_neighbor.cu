@@ -182,8 +182,8 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
   id[t] = idb[t];
 }
 
-// One thread per atom, two passes over the candidates of the 27 neighbouring cell images.  Pass 1
-// counts the accepted j per segment; pass 2 writes each entry at its segment's running offset.
+// One thread per atom, one pass over the candidates of the 27 neighbouring cell images and one over
+// the accepted entries (below).
 //
 // Segments: the pair (i, j) is "owned" by i when r_ij lies in the upper half-space (see owns_pair;
 // exactly one of r_ij and r_ji = -r_ij is owned, so every unordered pair has one owner), and the row
@@ -192,7 +192,10 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
 // The force kernel walks only the owned part (each pair once, Newton's third law); the descriptor
 // kernel walks the whole row.  Because every atom of a lattice owns exactly half of each shell and the
 // bands follow the shells, the per-pair branches stay warp-uniform without a full sort.
-// Rows are staged in shared memory ([k][thread]) and flushed row-coalesced.
+// Pass 1 walks the 27 neighbouring cells once, counts the accepted j per segment and keeps the
+// accepted entries in shared memory ([k][thread], candidate order); pass 2 re-classifies only those
+// (about 78 of ~510 candidates) and stores each at its segment's running offset.  Its 4-byte stores
+// into the neighbour-major list are scattered across rows; L2 merges them into full sectors.
 constexpr int NB_THREADS = 64;
 constexpr int NB_STAGE = 128;          // staged entries per atom (lists longer than this are an overflow)
 constexpr float OWN_EPS = 0.5f;        // Angstrom; lattice-vector components are either ~0 or >= a/2
@@ -214,73 +217,74 @@ __device__ __forceinline__ bool owns_pair(float dx, float dy, float dz) {
   return dz > 0.f;
 }
 
+// Squared distance with an explicit operation order, so that both passes classify a pair identically.
+__device__ __forceinline__ float nb_r2(float a, float b, float c) { return fmaf(a, a, fmaf(b, b, c * c)); }
+
 __global__ void __launch_bounds__(NB_THREADS)
 k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_start, const Geom geom, int cap,
             Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
             int32_t *__restrict__ nown, int32_t *__restrict__ nband0, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
   __shared__ float4 shift[27];
-  extern __shared__ uint32_t stage[];            // [NB_STAGE][NB_THREADS]
+  extern __shared__ uint32_t stage[];            // [NB_STAGE][NB_THREADS] accepted entries (candidate order)
   fill_shift_table(shift, geom);
   __syncthreads();
-  const int i = blockIdx.x * NB_THREADS + threadIdx.x;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * NB_THREADS + t;
   const bool live = i < n;
   const int limit = min(cap, NB_STAGE);
-  // four 16-bit counters per 64-bit word: own = owned segments by band, oth = not-owned segments
   unsigned long long own = 0ull, oth = 0ull, own_off = 0ull, oth_off = 0ull;
+  int acc = 0;
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-  int cx = 0, cy = 0, cz = 0;
   if (live) {
     pi = pos[i];
-    cx = cell_x(pi.w); cy = cell_y(pi.w); cz = cell_z(pi.w);
-  }
-  for (int pass = 0; pass < 2; ++pass) {
-    if (live) {
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int zz = (cz + dz + geom.ncz) % geom.ncz;
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int yy = (cy + dy + geom.ncy) % geom.ncy;
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int xx = (cx + dx + geom.ncx) % geom.ncx;
-            const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-            const float4 o = shift[sh];
-            const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
-            const int b = cell_start[c], e = cell_start[c + 1];
-            for (int j = b; j < e; ++j) {
-              if (j == i && sh == 13) continue;
-              const float4 pj = pos[j];
-              const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
-              const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-              if (r2 < B.b3) {
-                const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
-                const unsigned long long one = 1ull << (16 * bd);
-                const bool ow = owns_pair(ddx, ddy, ddz);
-                if (pass == 0) {
-                  if (ow) own += one; else oth += one;
-                } else {
-                  int k;
-                  if (ow) { k = (int)((own_off >> (16 * bd)) & 0xffffull); own_off += one; }
-                  else { k = (int)((oth_off >> (16 * bd)) & 0xffffull); oth_off += one; }
-                  if (k < limit) stage[k * NB_THREADS + threadIdx.x] = (uint32_t)j | ((uint32_t)sh << J_BITS);
-                }
-              }
+    const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (cz + dz + geom.ncz) % geom.ncz;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = (cy + dy + geom.ncy) % geom.ncy;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = (cx + dx + geom.ncx) % geom.ncx;
+          const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+          const float4 o = shift[sh];
+          const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
+          const int b = cell_start[c], e = cell_start[c + 1];
+          for (int j = b; j < e; ++j) {
+            if (j == i && sh == 13) continue;
+            const float4 pj = pos[j];
+            const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
+            const float r2 = nb_r2(ddx, ddy, ddz);
+            if (r2 < B.b3) {
+              const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
+              const unsigned long long one = 1ull << (16 * bd);
+              if (owns_pair(ddx, ddy, ddz)) own += one; else oth += one;
+              if (acc < NB_STAGE) stage[acc * NB_THREADS + t] = (uint32_t)j | ((uint32_t)sh << J_BITS);
+              ++acc;
             }
           }
         }
       }
     }
-    if (pass == 0) {
-      // exclusive offsets: owned bands 0..3, then not-owned bands 0..3
-      unsigned long long run = 0ull;
-      for (int bd = 0; bd < 4; ++bd) {
-        own_off |= run << (16 * bd);
-        run += (own >> (16 * bd)) & 0xffffull;
-      }
-      for (int bd = 0; bd < 4; ++bd) {
-        oth_off |= run << (16 * bd);
-        run += (oth >> (16 * bd)) & 0xffffull;
-      }
-    }
+  }
+  {
+    unsigned long long run = 0ull;
+    for (int bd = 0; bd < 4; ++bd) { own_off |= run << (16 * bd); run += (own >> (16 * bd)) & 0xffffull; }
+    for (int bd = 0; bd < 4; ++bd) { oth_off |= run << (16 * bd); run += (oth >> (16 * bd)) & 0xffffull; }
+  }
+  // place the accepted entries (same arithmetic as above, so the same band and owner)
+  const int m = min(acc, NB_STAGE);
+  for (int s = 0; s < m; ++s) {
+    const uint32_t e = stage[s * NB_THREADS + t];
+    const float4 o = shift[e >> J_BITS];
+    const float4 pj = pos[e & J_MASK];
+    const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
+    const float r2 = nb_r2(ddx, ddy, ddz);
+    const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
+    const unsigned long long one = 1ull << (16 * bd);
+    int k;
+    if (owns_pair(ddx, ddy, ddz)) { k = (int)((own_off >> (16 * bd)) & 0xffffull); own_off += one; }
+    else { k = (int)((oth_off >> (16 * bd)) & 0xffffull); oth_off += one; }
+    if (k < limit) nbr[(size_t)k * n + i] = (int32_t)e;
   }
   int n_own = 0, n_oth = 0, n_ang = 0;
   for (int bd = 0; bd < 4; ++bd) {
@@ -291,18 +295,12 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
   const int total = n_own + n_oth;
   const int kept = min(total, limit);
   if (live) {
-    if (total > kept) atomicOr(&ctrl->status, ST_OVERFLOW);
+    if (total > kept || acc > NB_STAGE) atomicOr(&ctrl->status, ST_OVERFLOW);
     nnum[i] = kept;
     nown[i] = min(n_own, kept);
     nang[i] = n_ang;
     nband0[i] = min((int)(own & 0xffffull), kept);
   }
-  __syncthreads();
-  // row-coalesced flush of the staged rows
-  int kmax = live ? kept : 0;
-  for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-  for (int k = 0; k < kmax; ++k)
-    if (k < kept && live) nbr[(size_t)k * n + i] = (int32_t)stage[k * NB_THREADS + threadIdx.x];
 }
 
 // ---------------------------------------------------------------------------------------------------

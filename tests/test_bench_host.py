@@ -48,13 +48,22 @@ def test_single_rank_helpers_are_identity():
 
 
 def test_flop_model_counts_units():
+    """The FLOP model is the table's per-unit counts times the pair counters of the right kernel
+    (descriptor: full rows; force: owned half rows), for both model shapes."""
     c = dict(list_entries=78, active_pairs=42, radial_pairs=42, angular_pairs=18, owned_list_entries=39,
              owned_active_pairs=21, owned_radial_pairs=21, owned_angular_pairs=9)
-    f_desc = bench.kernel_flops("descriptor", c, 1)
-    f_force = bench.kernel_flops("force", c, 1)
-    assert f_desc == 11 * 78 + 2 * 42 + 128 * 42 + 12 * 42 + 464 * 18 + 4655
-    assert f_force == 11 * 39 + 32 * 21 + 220 * 21 + 13 * 21 + 1465 * 9 + 3
-    assert 15e3 < f_desc < 25e3 and 15e3 < f_force < 25e3
+    for table in (bench.FLOPS, bench.FLOPS_STUDENT):
+        d, f = table["descriptor"], table["force"]
+        f_desc = bench.kernel_flops("descriptor", c, 1, table)
+        f_force = bench.kernel_flops("force", c, 1, table)
+        assert f_desc == (d["list_entry"] * 78 + d["active_pair"] * 42 + (d["radial_pair"] + d["lj_pair"]) * 42 +
+                          d["angular_pair"] * 18 + d["atom"])
+        assert f_force == (f["list_entry"] * 39 + f["active_pair"] * 21 + (f["radial_pair"] + f["lj_pair"]) * 21 +
+                           f["angular_pair"] * 9 + f["atom"])
+    teacher = bench.kernel_flops("force", c, 1) + bench.kernel_flops("descriptor", c, 1)
+    student = (bench.kernel_flops("force", c, 1, bench.FLOPS_STUDENT) +
+               bench.kernel_flops("descriptor", c, 1, bench.FLOPS_STUDENT))
+    assert 25e3 < teacher < 45e3 and 8e3 < student < 0.5 * teacher
 
 
 def test_traffic_lookup_requires_matching_source(tmp_path, monkeypatch):

@@ -481,7 +481,7 @@ def run_ours(args, rank: int, ws: int, local: int):
                    "rebuilds_in_timed_region": dc["rebuilds"],
                    **({"fallback_fraction": dc["fallback_atoms"] / max(1, evals * wl.n),
                        "fallback_margin": FALLBACK_MARGIN} if FORMS[args.form]["fallback"] else {}),
-                   "l2": "inputs larger than L2: per-step working set ~"
+                   "l2": "inputs larger than L2: per-step algorithmic traffic ~"
                          f"{(wl.n * (row_bytes(args.form) * 2 + BYTES['per_atom'] - 512 * 2 + 48 * 2) + dc['list_entries'] / max(1, evals) * BYTES['per_list_entry']) / 1e9:.2f} GB"
                          " (neighbour list, adjoint rows, state) vs 129 MB L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "model": "cu_nep4_synth (seeded)"},

@@ -79,7 +79,8 @@ def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) ->
 
 
 # sources of the descriptor and force kernels: a committed traffic figure is used only while they are unchanged
-SOURCE_FILES = ("nep_force.cu", "nep_common.cuh", "nep_descriptor.cuh", "nep_mixed.cu", "nep_tc.cuh")
+SOURCE_FILES = ("nep_force.cu", "nep_common.cuh", "nep_descriptor.cuh", "nep_mixed.cu", "nep_tc.cuh", "nep_neighbor.cu",
+                "nep_fallback.cu")
 
 
 def source_hash() -> str:

@@ -366,6 +366,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     torch.cuda.synchronize(dev)
     nep.set_timing(True)
     c0 = nep.counters()
+    th0 = nep.thermo()
     clocks = ClockSampler(local)
     time.sleep(0.3)
 
@@ -445,6 +446,22 @@ def run_ours(args, rank: int, ws: int, local: int):
                "d2h_bytes_per_step": 48 * wl.n + 8 * 16, "steps": args.e2e_steps,
                "note": "per step: nep_set_state(x, v from pinned host) + md_verlet_step(1) (rebuild + 2 force "
                        "evaluations for the uploaded state) + nep_get_state(x, v to pinned host) + thermo"}
+    ablations = None
+    if args.form == "plain" and not args.no_ablations:
+        # kernel variants of the paper's design on the same state, against the production kernels
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.set_timing(True)
+        nep.compute(forces=False)
+        t_ref = nep.timing()
+        nep.set_timing(False)
+        ablations = {"force_fixed_point_ms": round(t_ref["force"][0], 4),
+                     "descriptor_ms": round(t_ref["descriptor"][0], 4)}
+        for v in ("float_scatter", "tile1", "tile3"):
+            ablations[v + "_ms"] = round(min(nep.run_variant(v)[0] for _ in range(3)), 4)
+        ablations["note"] = ("float_scatter: force kernel with float atomicAdd (order-dependent sums) vs the "
+                             "fixed-point integer atomics; tile1/tile3: descriptor kernel with 1 or 3 angular "
+                             "channels per neighbour pass and s_nlm through global memory vs all 5 channels in "
+                             "registers; single launches, CUDA events")
     F_plain = F_this = None
     others = [] if args.no_forms else [f for f in FORMS if f != args.form]
     if others:
@@ -495,9 +512,12 @@ def run_ours(args, rank: int, ws: int, local: int):
                            "radial": dc["radial_pairs"] / max(1, evals * wl.n),
                            "angular": dc["angular_pairs"] / max(1, evals * wl.n),
                            "owned_angular": dc["owned_angular_pairs"] / max(1, evals * wl.n)},
-        "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"]},
+        "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"],
+                       "energy_change_per_atom": ((th["pe"] + th["ke"]) - (th0["pe"] + th0["ke"])) / wl.n,
+                       "over_fs": args.steps * wl.dt_fs},
         "e2e": e2e,
         "forms": forms or None,
+        "ablations": ablations,
         "source_hash": source_hash(),
     }
     if ws == 1 and not args.no_cpu_baseline:
@@ -520,6 +540,7 @@ def main(argv=None):
     ap.add_argument("--form-steps", type=int, default=50)
     ap.add_argument("--max-neighbors", type=int, default=0, help="neighbour-list capacity per atom (0 = 128)")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-ablations", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -179,6 +179,19 @@ nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const floa
  * evaluation of the current state. */
 nep_status nep_get_fallback(nep_handle *h, int *flags, int64_t *count);
 
+/* Kernel variants of the paper's own design, kept for ablation (plain float32 teacher path only):
+ *   NEP_VARIANT_FLOAT_SCATTER  the force kernel with float atomicAdd scatter (Section V.B, Optimization 1)
+ *                              instead of 64-bit fixed-point integer atomics: the result depends on the
+ *                              order in which additions arrive, so repeated runs may differ in the last bits;
+ *   NEP_VARIANT_TILE1 / TILE3  the descriptor kernel with channel tiling (Algorithm 1): the angular
+ *                              neighbours are walked once per tile of 1 or 3 channels, with s_nlm passed
+ *                              through a global array (the paper's sum_fxyz) instead of registers.
+ * One force evaluation on the current state with the variant; *ms = the variant kernel's time (CUDA
+ * events), F (may be NULL; host or device; [n][3], caller's order) = the forces it produced.  The
+ * handle's own results are recomputed on the next request. */
+enum { NEP_VARIANT_FLOAT_SCATTER = 1, NEP_VARIANT_TILE1 = 2, NEP_VARIANT_TILE3 = 3 };
+nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F);
+
 /* Upper limits of nep_compute_noalloc: the size of its fixed scratch array. */
 #define NEP_NOALLOC_MAX_ATOMS 8192
 #define NEP_NOALLOC_MAX_CELLS 32768

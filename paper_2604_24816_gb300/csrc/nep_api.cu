@@ -49,6 +49,16 @@ cudaError_t launch_fallback_force(const Model<S> &, const Geom &, int, const flo
                                   const int32_t *, const int *, const int *, int, const float *, long long *,
                                   long long *, int *, cudaStream_t);
 cudaError_t launch_fallback_flags(const int *, const int *, int, const int *, int *, cudaStream_t);
+// nep_force.cu / nep_ablation.cu: kernel variants for ablation
+template <class S>
+cudaError_t launch_force_float_scatter(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
+                                       const int32_t *, const int32_t *, const float *, float *, long long *, int *,
+                                       cudaStream_t);
+template <class S, int NT>
+cudaError_t launch_descriptor_tiled(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
+                                    const int32_t *, float *, float *, long long *, long long *, int *, float *,
+                                    cudaStream_t);
+cudaError_t launch_store_float3(int, const int *, const float *, double *, cudaStream_t);
 // nep_neighbor.cu
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
 cudaError_t launch_neighbors(const RebuildArgs &, cudaStream_t);
@@ -158,6 +168,9 @@ struct nep_handle {
   int *fb_list = nullptr, *fb_count = nullptr;
   float *fb_G = nullptr;
 
+  // buffers of the ablation variants (allocated on first use)
+  float *abl_f = nullptr, *abl_s = nullptr;
+
   int ndes() const { return shape == 0 ? CuShape::NDES : StudentShape::NDES; }
   int gs() const { return shape == 0 ? CuShape::GS : StudentShape::GS; }
 };
@@ -206,6 +219,7 @@ void free_system(nep_handle *h) {
   dfree(h->count); dfree(h->cursor); dfree(h->start); dfree(h->tile_sums);
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
   dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
+  dfree(h->abl_f); dfree(h->abl_s);
   h->fb_cap = 0;
   h->io_i_elems = 0;
   h->n = 0;
@@ -927,6 +941,68 @@ nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const floa
     }
   }
   return NEP_OK;
+}
+
+nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
+  if (!h || !ms) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_TILE3) return fail(h, NEP_ERR_ARG, "unknown variant");
+  if (h->shape != 0 || h->precision != NEP_FP32 || h->fb_on)
+    return fail(h, NEP_ERR_UNSUPPORTED, "the variants exist for the plain float32 teacher path");
+  if (h->n == 0) { *ms = 0.0; return NEP_OK; }
+  nep_status s = ensure_nlist(h);
+  if (s != NEP_OK) return s;
+  const Geom g = geom_of(h);
+  const size_t N = (size_t)h->n;
+  float *G = static_cast<float *>(h->G);
+  cudaEvent_t a = nullptr, b = nullptr;
+  NEP_CUDA(h, cudaEventCreate(&a));
+  NEP_CUDA(h, cudaEventCreate(&b));
+  cudaError_t e = cudaSuccess;
+  {
+    Scope sc(h, KC_OTHER, 3);
+    if (variant == NEP_VARIANT_FLOAT_SCATTER) {
+      if (!h->abl_f) e = dalloc(h->abl_f, 3 * N);
+      if (e == cudaSuccess)
+        e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
+                                       h->part_d, &h->ctrl->status, Fallback{}, h->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->abl_f, 0, 3 * N * sizeof(float), h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+      if (e == cudaSuccess)
+        e = launch_force_float_scatter<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->abl_f,
+                                                h->part_f, &h->ctrl->status, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = launch_store_float3(h->n, h->id, h->abl_f, h->io, h->stream);
+    } else {
+      if (!h->abl_s) e = dalloc(h->abl_s, (size_t)CuShape::NA * CuShape::NLM * N);
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+      if (e == cudaSuccess) {
+        if (variant == NEP_VARIANT_TILE1)
+          e = launch_descriptor_tiled<CuShape, 1>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, h->F,
+                                                  h->part_d, &h->ctrl->status, h->abl_s, h->stream);
+        else
+          e = launch_descriptor_tiled<CuShape, 3>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, h->F,
+                                                  h->part_d, &h->ctrl->status, h->abl_s, h->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess)
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->F, h->part_f,
+                                         &h->ctrl->status, h->stream);
+      if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
+    }
+  }
+  if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, h->io, 3 * N * sizeof(double), cudaMemcpyDefault, h->stream);
+  h->have_forces = false;              // the handle's own results are recomputed on the next request
+  if (e != cudaSuccess) {
+    cudaEventDestroy(a); cudaEventDestroy(b);
+    return cuda_fail(h, e, "variant");
+  }
+  s = check_device_status(h);
+  float m = 0.f;
+  if (s == NEP_OK && cudaEventElapsedTime(&m, a, b) != cudaSuccess) s = cuda_fail(h, cudaGetLastError(), "timing");
+  cudaEventDestroy(a); cudaEventDestroy(b);
+  *ms = m;
+  return s;
 }
 
 nep_status nep_get_fallback(nep_handle *h, int *flags, int64_t *count) {

@@ -122,12 +122,14 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
   block_sum_store<5>(acc, part);
 }
 
-template <class S, class GT>
+// FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float atomicAdd
+// into Ff, whose result depends on the order in which the additions arrive.
+template <class S, class GT, bool FS = false>
 __global__ void __launch_bounds__(FORCE_BLOCK, NEP_FORCE_MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
         const int32_t *__restrict__ nbr, const int32_t *__restrict__ nown, const int32_t *__restrict__ nband0,
         const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
-        int *__restrict__ status) {
+        int *__restrict__ status, float *__restrict__ Ff = nullptr) {
   __shared__ float4 shift[27];
   __shared__ uint32_t ring_e[FPIPE_DE * FORCE_BLOCK];
   __shared__ float4 ring_p[FPIPE_DP * FORCE_BLOCK];
@@ -241,17 +243,25 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
       fx += Dx; fy += Dy; fz += Dz;
       // Newton's third law: F_j -= D_ij, accumulated in fixed point (order-independent sum)
-      atomicAdd(Ffix + j, (unsigned long long)(-to_fix32(Dx)));
-      atomicAdd(Ffix + (size_t)n + j, (unsigned long long)(-to_fix32(Dy)));
-      atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)(-to_fix32(Dz)));
+      if constexpr (FS) {
+        atomicAdd(Ff + j, -Dx); atomicAdd(Ff + (size_t)n + j, -Dy); atomicAdd(Ff + 2 * (size_t)n + j, -Dz);
+      } else {
+        atomicAdd(Ffix + j, (unsigned long long)(-to_fix32(Dx)));
+        atomicAdd(Ffix + (size_t)n + j, (unsigned long long)(-to_fix32(Dy)));
+        atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)(-to_fix32(Dz)));
+      }
       wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
       wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
       wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
     }
     pipe.finish();
-    atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
-    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
-    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
+    if constexpr (FS) {
+      atomicAdd(Ff + i, fx); atomicAdd(Ff + (size_t)n + i, fy); atomicAdd(Ff + 2 * (size_t)n + i, fz);
+    } else {
+      atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
+      atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
+      atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
+    }
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
     // each unordered pair once: W = -sum_pairs r_ij (x) D_ij
     acc[0] = -to_fix32(wxx); acc[1] = -to_fix32(wxy); acc[2] = -to_fix32(wxz);
@@ -286,6 +296,20 @@ cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *
                                                reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }
+
+// Ablation: the same force kernel with float atomicAdd scatter into Ff [3][n] (zeroed by the caller).
+template <class S>
+cudaError_t launch_force_float_scatter(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
+                                       const int32_t *nown, const int32_t *nband0, const float *G, float *Ff,
+                                       long long *part, int *status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
+  k_force<S, float, true><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G, nullptr, part, status, Ff);
+  return cudaGetLastError();
+}
+template cudaError_t launch_force_float_scatter<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
+                                                         const int32_t *, const int32_t *, const int32_t *,
+                                                         const float *, float *, long long *, int *, cudaStream_t);
 
 int descriptor_blocks(int n) { return (n + DESC_BLOCK - 1) / DESC_BLOCK; }
 int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }

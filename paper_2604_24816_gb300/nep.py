@@ -52,7 +52,7 @@ class nep_params(C.Structure):
 EXPORTED = ("nep_create", "nep_destroy", "nep_set_state", "nep_build_neighbors", "nep_compute", "md_verlet_step",
             "nep_get_state", "nep_get_thermo", "nep_get_neighbors", "nep_get_descriptors", "nep_get_site_energies",
             "nep_set_timing", "nep_get_timing", "nep_get_counters", "nep_last_error", "nep_status_string",
-            "nep_compute_noalloc", "nep_set_fallback", "nep_get_fallback")
+            "nep_compute_noalloc", "nep_set_fallback", "nep_get_fallback", "nep_run_variant")
 
 
 def lib():
@@ -87,6 +87,7 @@ def lib():
         L.nep_set_fallback.argtypes = [vp, C.POINTER(nep_params), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.c_float, C.c_double]
         L.nep_get_fallback.argtypes = [vp, vp, C.POINTER(C.c_int64)]
+        L.nep_run_variant.argtypes = [vp, C.c_int, d, vp]
         for f in EXPORTED:
             if f not in ("nep_last_error", "nep_status_string"):
                 getattr(L, f).restype = C.c_int
@@ -267,6 +268,17 @@ class NEP:
         self._check(self._L.nep_set_fallback(self._h, C.byref(p), lo.ctypes.data_as(C.POINTER(C.c_float)),
                                              hi.ctypes.data_as(C.POINTER(C.c_float)), float(margin),
                                              float(max_fraction)))
+
+    VARIANTS = {"float_scatter": 1, "tile1": 2, "tile3": 3}
+
+    def run_variant(self, name: str):
+        """One force evaluation with a kernel variant of the paper's design (nep_run_variant):
+        returns (variant kernel milliseconds, forces [n][3])."""
+        ms = np.zeros(1)
+        F = np.zeros((max(self.n, 1), 3))
+        self._check(self._L.nep_run_variant(self._h, self.VARIANTS[name], ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                            F.ctypes.data))
+        return float(ms[0]), F[:self.n]
 
     def fallback(self):
         """(flags[n] int32, 1 = teacher; number of flagged atoms) of the last force evaluation."""

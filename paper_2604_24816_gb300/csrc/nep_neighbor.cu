@@ -182,8 +182,7 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
   id[t] = idb[t];
 }
 
-// One thread per atom, one pass over the candidates of the 27 neighbouring cell images and one over
-// the accepted entries (below).
+// One warp per atom over the candidates of the 27 neighbouring cell images (below).
 //
 // Segments: the pair (i, j) is "owned" by i when r_ij lies in the upper half-space (see owns_pair;
 // exactly one of r_ij and r_ji = -r_ij is owned, so every unordered pair has one owner), and the row
@@ -192,11 +191,9 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
 // The force kernel walks only the owned part (each pair once, Newton's third law); the descriptor
 // kernel walks the whole row.  Because every atom of a lattice owns exactly half of each shell and the
 // bands follow the shells, the per-pair branches stay warp-uniform without a full sort.
-// Pass 1 walks the 27 neighbouring cells once, counts the accepted j per segment and keeps the
-// accepted entries in shared memory ([k][thread], candidate order); pass 2 re-classifies only those
-// (about 78 of ~510 candidates) and stores each at its segment's running offset.  Its 4-byte stores
-// into the neighbour-major list are scattered across rows; L2 merges them into full sectors.
-constexpr int NB_THREADS = 64;
+// The placement's 4-byte stores into the neighbour-major list are scattered across rows; L2 merges
+// them into full sectors before they reach DRAM.
+constexpr int NB_WARPS = 8;            // atoms (one warp each) per block
 constexpr int NB_STAGE = 128;          // staged entries per atom (lists longer than this are an overflow)
 constexpr float OWN_EPS = 0.5f;        // Angstrom; lattice-vector components are either ~0 or >= a/2
 
@@ -220,87 +217,132 @@ __device__ __forceinline__ bool owns_pair(float dx, float dy, float dz) {
 // Squared distance with an explicit operation order, so that both passes classify a pair identically.
 __device__ __forceinline__ float nb_r2(float a, float b, float c) { return fmaf(a, a, fmaf(b, b, c * c)); }
 
-__global__ void __launch_bounds__(NB_THREADS)
+// Segment of an accepted pair: owned by i (0..3) or not (4..7), by build-time distance band.
+__device__ __forceinline__ int segment_of(float dx, float dy, float dz, float r2, const Bands &B) {
+  const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
+  return owns_pair(dx, dy, dz) ? bd : 4 + bd;
+}
+
+// The candidate scan and segment placement of atom i by one warp (see k_neighbors).
+__device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__restrict__ pos,
+                                                  const int *__restrict__ cell_start, const Geom &geom,
+                                                  const Bands &B, int limit, const float4 *shift, uint32_t *stage,
+                                                  uint8_t *skey, int lane, int32_t *__restrict__ nbr,
+                                                  int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
+                                                  int32_t *__restrict__ nown, int32_t *__restrict__ nband0,
+                                                  Control *ctrl) {
+  const unsigned lower = (1u << lane) - 1u;
+  const float4 pi = pos[i];
+  const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
+  const bool xwrap = cx == 0 || cx == geom.ncx - 1;
+  int acc = 0;                                         // accepted so far (warp-uniform)
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int zz = (cz + dz + geom.ncz) % geom.ncz;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = (cy + dy + geom.ncy) % geom.ncy;
+      const int row = (zz * geom.ncy + yy) * geom.ncx;
+      const int shb = 3 * (dy + 1) + 9 * (dz + 1);
+      const int parts = xwrap ? 3 : 1;
+      for (int part = 0; part < parts; ++part) {
+        int b, e;
+        if (!xwrap) {
+          b = cell_start[row + cx - 1];
+          e = cell_start[row + cx + 2];
+        } else {
+          const int xx = (cx + part - 1 + geom.ncx) % geom.ncx;
+          b = cell_start[row + xx];
+          e = cell_start[row + xx + 1];
+        }
+        for (int j0 = b; j0 < e; j0 += 32) {
+          const int j = j0 + lane;
+          bool ok = false;
+          int key = 0;
+          uint32_t ent = 0;
+          if (j < e && j != i) {
+            const float4 pj = pos[j];
+            const int dx = xwrap ? part - 1 : cell_x(pj.w) - cx;
+            const int sh = (dx + 1) + shb;
+            const float4 o = shift[sh];
+            const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
+            const float r2 = nb_r2(ddx, ddy, ddz);
+            if (r2 < B.b3) {
+              ok = true;
+              key = segment_of(ddx, ddy, ddz, r2, B);
+              ent = (uint32_t)j | ((uint32_t)sh << J_BITS);
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, ok);
+          if (ok) {
+            const int slot = acc + __popc(m & lower);
+            if (slot < NB_STAGE) { stage[slot] = ent; skey[slot] = (uint8_t)key; }
+          }
+          acc += __popc(m);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // segment sizes and offsets (warp-uniform), then placement in candidate order within each segment
+  const int ms = min(acc, NB_STAGE);
+  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int s0 = 0; s0 < ms; s0 += 32) {
+    const int key = s0 + lane < ms ? (int)skey[s0 + lane] : 8;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) cnt[g] += __popc(__ballot_sync(0xffffffffu, key == g));
+  }
+  int run[8];
+  {
+    int o = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) { run[g] = o; o += cnt[g]; }
+  }
+  for (int s0 = 0; s0 < ms; s0 += 32) {
+    const bool valid = s0 + lane < ms;
+    const int key = valid ? (int)skey[s0 + lane] : 8;
+    const uint32_t ent = valid ? stage[s0 + lane] : 0u;
+    int k = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const unsigned bal = __ballot_sync(0xffffffffu, key == g);
+      if (key == g) k = run[g] + __popc(bal & lower);
+      run[g] += __popc(bal);
+    }
+    if (valid && k < limit) nbr[(size_t)k * n + i] = (int32_t)ent;
+  }
+  if (lane == 0) {
+    const int n_own = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    const int kept = min(acc, limit);
+    if (acc > kept || acc > NB_STAGE) atomicOr(&ctrl->status, ST_OVERFLOW);
+    nnum[i] = kept;
+    nown[i] = min(n_own, kept);
+    nang[i] = cnt[0] + cnt[1] + cnt[4] + cnt[5];
+    nband0[i] = min(cnt[0], kept);
+  }
+}
+
+// One warp per atom i.  The lanes test 32 candidates at a time (coalesced position loads, the atom's
+// own position broadcast): for each of the 9 (dy, dz) rows of the 27-cell stencil the three cells
+// x-1, x, x+1 are consecutive in the cell-sorted arrays, so the row is one contiguous range and a
+// candidate's x offset comes from its packed cell coordinate (rows that wrap around the periodic x
+// boundary are walked cell by cell).  Accepted entries go to a per-warp shared-memory stage in
+// candidate order (ballot + popc), then are placed by segment: [owned | not owned] x band, candidate
+// order inside a segment -- the same row as the thread-per-atom formulation, with 32-wide work
+// instead of divergent per-thread cell loops.
+__global__ void __launch_bounds__(NB_WARPS * 32)
 k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_start, const Geom geom, int cap,
             Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
             int32_t *__restrict__ nown, int32_t *__restrict__ nband0, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
   __shared__ float4 shift[27];
-  extern __shared__ uint32_t stage[];            // [NB_STAGE][NB_THREADS] accepted entries (candidate order)
+  __shared__ uint32_t stage[NB_WARPS][NB_STAGE];
+  __shared__ uint8_t skey[NB_WARPS][NB_STAGE];
   fill_shift_table(shift, geom);
   __syncthreads();
-  const int t = threadIdx.x;
-  const int i = blockIdx.x * NB_THREADS + t;
-  const bool live = i < n;
-  const int limit = min(cap, NB_STAGE);
-  unsigned long long own = 0ull, oth = 0ull, own_off = 0ull, oth_off = 0ull;
-  int acc = 0;
-  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (live) {
-    pi = pos[i];
-    const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (cz + dz + geom.ncz) % geom.ncz;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = (cy + dy + geom.ncy) % geom.ncy;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = (cx + dx + geom.ncx) % geom.ncx;
-          const int sh = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-          const float4 o = shift[sh];
-          const int c = (zz * geom.ncy + yy) * geom.ncx + xx;
-          const int b = cell_start[c], e = cell_start[c + 1];
-          for (int j = b; j < e; ++j) {
-            if (j == i && sh == 13) continue;
-            const float4 pj = pos[j];
-            const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
-            const float r2 = nb_r2(ddx, ddy, ddz);
-            if (r2 < B.b3) {
-              const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
-              const unsigned long long one = 1ull << (16 * bd);
-              if (owns_pair(ddx, ddy, ddz)) own += one; else oth += one;
-              if (acc < NB_STAGE) stage[acc * NB_THREADS + t] = (uint32_t)j | ((uint32_t)sh << J_BITS);
-              ++acc;
-            }
-          }
-        }
-      }
-    }
-  }
-  {
-    unsigned long long run = 0ull;
-    for (int bd = 0; bd < 4; ++bd) { own_off |= run << (16 * bd); run += (own >> (16 * bd)) & 0xffffull; }
-    for (int bd = 0; bd < 4; ++bd) { oth_off |= run << (16 * bd); run += (oth >> (16 * bd)) & 0xffffull; }
-  }
-  // place the accepted entries (same arithmetic as above, so the same band and owner)
-  const int m = min(acc, NB_STAGE);
-  for (int s = 0; s < m; ++s) {
-    const uint32_t e = stage[s * NB_THREADS + t];
-    const float4 o = shift[e >> J_BITS];
-    const float4 pj = pos[e & J_MASK];
-    const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
-    const float r2 = nb_r2(ddx, ddy, ddz);
-    const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
-    const unsigned long long one = 1ull << (16 * bd);
-    int k;
-    if (owns_pair(ddx, ddy, ddz)) { k = (int)((own_off >> (16 * bd)) & 0xffffull); own_off += one; }
-    else { k = (int)((oth_off >> (16 * bd)) & 0xffffull); oth_off += one; }
-    if (k < limit) nbr[(size_t)k * n + i] = (int32_t)e;
-  }
-  int n_own = 0, n_oth = 0, n_ang = 0;
-  for (int bd = 0; bd < 4; ++bd) {
-    const int a = (int)((own >> (16 * bd)) & 0xffffull), b = (int)((oth >> (16 * bd)) & 0xffffull);
-    n_own += a; n_oth += b;
-    if (bd < 2) n_ang += a + b;
-  }
-  const int total = n_own + n_oth;
-  const int kept = min(total, limit);
-  if (live) {
-    if (total > kept || acc > NB_STAGE) atomicOr(&ctrl->status, ST_OVERFLOW);
-    nnum[i] = kept;
-    nown[i] = min(n_own, kept);
-    nang[i] = n_ang;
-    nband0[i] = min((int)(own & 0xffffull), kept);
-  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * NB_WARPS + w;
+  if (i >= n) return;                                  // whole warp (i is warp-uniform); no barrier below
+  neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), shift, stage[w], skey[w], lane, nbr, nnum,
+                    nang, nown, nband0, ctrl);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -335,9 +377,8 @@ cudaError_t launch_neighbors(const RebuildArgs &a, cudaStream_t st) {
   g.ncx = a.nc[0]; g.ncy = a.nc[1]; g.ncz = a.nc[2];
   Bands B;
   B.b0 = a.ba2; B.b1 = a.ra2; B.b2 = a.br2; B.b3 = a.rl2;
-  const size_t smem = (size_t)NB_STAGE * NB_THREADS * sizeof(uint32_t);
-  k_neighbors<<<blocks_for(a.n, NB_THREADS), NB_THREADS, smem, st>>>(a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum,
-                                                                      a.nang, a.nown, a.nband0, a.ctrl);
+  k_neighbors<<<blocks_for(a.n, NB_WARPS), NB_WARPS * 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum,
+                                                                   a.nang, a.nown, a.nband0, a.ctrl);
   return cudaGetLastError();
 }
 

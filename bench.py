@@ -78,14 +78,26 @@ def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) ->
             f["angular_pair"] * ang + f["atom"] * n_atoms_evals)
 
 
-# sources of the descriptor and force kernels: a committed traffic figure is used only while they are unchanged
-SOURCE_FILES = ("nep_force.cu", "nep_common.cuh", "nep_descriptor.cuh", "nep_mixed.cu", "nep_tc.cuh", "nep_neighbor.cu",
-                "nep_fallback.cu")
+# The sources each profiled kernel is built from: a committed traffic figure is used only while they
+# are unchanged (kernel names as in profiles/traffic_per_launch.txt; ":form" for the non-plain forms).
+_CORE = ("nep_common.cuh", "nep_descriptor.cuh")
+KERNEL_SOURCES = {
+    "neighbors": ("nep_neighbor.cu", "nep_common.cuh"),
+    "descriptor": ("nep_force.cu",) + _CORE,
+    "force": ("nep_force.cu",) + _CORE,
+    "descriptor:mix_bf16": ("nep_mixed.cu", "nep_tc.cuh") + _CORE,
+    "force:mix_bf16": ("nep_force.cu",) + _CORE,
+    "descriptor:student_bf16_fallback": ("nep_mixed.cu", "nep_tc.cuh", "nep_fallback.cu") + _CORE,
+    "force:student_bf16_fallback": ("nep_force.cu", "nep_fallback.cu") + _CORE,
+}
+SOURCE_FILES = tuple(sorted({f for v in KERNEL_SOURCES.values() for f in v}))
 
 
-def source_hash() -> str:
+def source_hash(kernel: str | None = None) -> str:
+    """Hash of the sources of `kernel` (all kernel sources when None)."""
+    files = SOURCE_FILES if kernel is None else KERNEL_SOURCES.get(kernel, SOURCE_FILES)
     h = hashlib.sha256()
-    for f in SOURCE_FILES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2604_24816_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -97,7 +109,7 @@ def profiled_traffic(kernel: str):
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(path):
         return None
-    cur = source_hash()
+    cur = source_hash(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == cur:

@@ -226,7 +226,7 @@ __device__ __forceinline__ int segment_of(float dx, float dy, float dz, float r2
 // The candidate scan and segment placement of atom i by one warp (see k_neighbors).
 __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__restrict__ pos,
                                                   const int *__restrict__ cell_start, const Geom &geom,
-                                                  const Bands &B, int limit, const float4 *shift, uint32_t *stage,
+                                                  const Bands &B, int limit, uint32_t *stage,
                                                   uint8_t *skey, int lane, int32_t *__restrict__ nbr,
                                                   int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
                                                   int32_t *__restrict__ nown, int32_t *__restrict__ nband0,
@@ -237,9 +237,13 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
   const bool xwrap = cx == 0 || cx == geom.ncx - 1;
   int acc = 0;                                         // accepted so far (warp-uniform)
   for (int dz = -1; dz <= 1; ++dz) {
-    const int zz = (cz + dz + geom.ncz) % geom.ncz;
+    int zz = cz + dz;
+    zz += zz < 0 ? geom.ncz : (zz >= geom.ncz ? -geom.ncz : 0);
+    const float oz = dz < 0 ? -geom.lz : (dz > 0 ? geom.lz : 0.f);   // = the image offset table entry
     for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = (cy + dy + geom.ncy) % geom.ncy;
+      int yy = cy + dy;
+      yy += yy < 0 ? geom.ncy : (yy >= geom.ncy ? -geom.ncy : 0);
+      const float oy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
       const int row = (zz * geom.ncy + yy) * geom.ncx;
       const int shb = 3 * (dy + 1) + 9 * (dz + 1);
       const int parts = xwrap ? 3 : 1;
@@ -249,7 +253,8 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
           b = cell_start[row + cx - 1];
           e = cell_start[row + cx + 2];
         } else {
-          const int xx = (cx + part - 1 + geom.ncx) % geom.ncx;
+          int xx = cx + part - 1;
+          xx += xx < 0 ? geom.ncx : (xx >= geom.ncx ? -geom.ncx : 0);
           b = cell_start[row + xx];
           e = cell_start[row + xx + 1];
         }
@@ -261,14 +266,13 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
           if (j < e && j != i) {
             const float4 pj = pos[j];
             const int dx = xwrap ? part - 1 : cell_x(pj.w) - cx;
-            const int sh = (dx + 1) + shb;
-            const float4 o = shift[sh];
-            const float ddx = pj.x - pi.x + o.x, ddy = pj.y - pi.y + o.y, ddz = pj.z - pi.z + o.z;
+            const float ox = dx < 0 ? -geom.lx : (dx > 0 ? geom.lx : 0.f);
+            const float ddx = pj.x - pi.x + ox, ddy = pj.y - pi.y + oy, ddz = pj.z - pi.z + oz;
             const float r2 = nb_r2(ddx, ddy, ddz);
             if (r2 < B.b3) {
               ok = true;
               key = segment_of(ddx, ddy, ddz, r2, B);
-              ent = (uint32_t)j | ((uint32_t)sh << J_BITS);
+              ent = (uint32_t)j | ((uint32_t)((dx + 1) + shb) << J_BITS);
             }
           }
           const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -333,15 +337,12 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
             Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
             int32_t *__restrict__ nown, int32_t *__restrict__ nband0, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  __shared__ float4 shift[27];
   __shared__ uint32_t stage[NB_WARPS][NB_STAGE];
   __shared__ uint8_t skey[NB_WARPS][NB_STAGE];
-  fill_shift_table(shift, geom);
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * NB_WARPS + w;
-  if (i >= n) return;                                  // whole warp (i is warp-uniform); no barrier below
-  neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), shift, stage[w], skey[w], lane, nbr, nnum,
+  if (i >= n) return;                                  // whole warp (i is warp-uniform); no barrier in the kernel
+  neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], skey[w], lane, nbr, nnum,
                     nang, nown, nband0, ctrl);
 }
 

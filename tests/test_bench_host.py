@@ -72,9 +72,15 @@ def test_traffic_lookup_requires_matching_source(tmp_path, monkeypatch):
     (tmp_path / "paper_2604_24816_gb300" / "csrc").mkdir(parents=True)
     for f in bench.SOURCE_FILES:
         (tmp_path / "paper_2604_24816_gb300" / "csrc" / f).write_text("x")
-    h = bench.source_hash()
-    (tmp_path / "profiles" / "traffic_per_launch.txt").write_text(f"# header\nforce {h} 1000 10\nforce deadbeef 5 1\n")
+    h = bench.source_hash("force")
+    hn = bench.source_hash("neighbors")
+    (tmp_path / "profiles" / "traffic_per_launch.txt").write_text(
+        f"# header\nforce {h} 1000 10\nforce deadbeef 5 1\nneighbors {hn} 300 10\n")
     assert bench.profiled_traffic("force") == dict(bytes=1000.0, atoms=10)
+    # a change to another kernel's source leaves the force figure valid, a change to its own does not
+    (tmp_path / "paper_2604_24816_gb300" / "csrc" / "nep_neighbor.cu").write_text("changed")
+    assert bench.profiled_traffic("force") == dict(bytes=1000.0, atoms=10)
+    assert bench.profiled_traffic("neighbors") is None
     (tmp_path / "paper_2604_24816_gb300" / "csrc" / "nep_force.cu").write_text("changed")
     assert bench.profiled_traffic("force") is None
 

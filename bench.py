@@ -365,8 +365,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     torch.cuda.set_device(dev)
     model = load_model()
     student = load_student()
-    wl = ni.workload(args.workload) if rank == 0 else ni.fcc_cu_workload(
-        64, 300.0, 0.05, seed=2 + rank, steps=200, name=args.workload)   # independent replica per rank
+    wl = ni.workload(args.workload)       # every rank runs an independent replica of the same workload
     stream = torch.cuda.Stream(device=dev)
     nep = make_nep(args.form, model, student, stream, args)
     nep.set_state(wl.pos, wl.vel, wl.box)

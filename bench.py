@@ -241,9 +241,17 @@ def cpu_baseline(seconds_hint: float = 15.0) -> dict:
     t0 = time.perf_counter()
     oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, 1.0, steps)
     dt = time.perf_counter() - t0
-    return {"value": wl.n * steps / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+    used = oracle.get_threads()
+    # the same oracle on one thread, 2 steps (a few seconds)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, 1.0, 2)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    return {"value": wl.n * steps / dt, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"fcc Cu 16x16x16 cells ({wl.n} atoms), {steps} velocity-Verlet steps "
-                      f"({steps + 1} force evaluations, fresh neighbour search each), FP64, {dt:.1f} s"}
+                      f"({steps + 1} force evaluations, fresh neighbour search each), FP64, {dt:.1f} s",
+            "value_1_thread": wl.n * 2 / dt1, "sample_1_thread": f"same cell, 2 steps on 1 thread, {dt1:.1f} s"}
 
 
 # ---------------------------------------------------------------------------------------------------

@@ -279,3 +279,24 @@ def test_unwrapped_input_positions(api, model_params, model, c1):
         E, F, W = nep.compute()
     Eo, Uo, Fo, Wo = oracle.energy_forces(model, c1.pos, c1.box)
     assert np.abs(F - Fo).max() <= 1e-4 and abs(E - Eo) / abs(Eo) <= 1e-6
+
+
+def test_checkpoint_resume_is_bit_identical(api, model_params):
+    """Checkpoint/resume through nep_get_state/nep_set_state: 20 steps in one run equal 10 steps, a
+    checkpoint to host memory, a fresh handle and 10 more steps, bit for bit (the checkpoint falls on a
+    scheduled rebuild, and every kernel is deterministic)."""
+    wl = ni.fcc_cu_workload(6, 300.0, 0.05, seed=97)
+    with api.NEP(model_params, rebuild_every=10) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.step(1.0, 20)
+        xa, va = nep.get_state()
+        assert nep.counters()["rebuilds"] == 3
+    with api.NEP(model_params, rebuild_every=10) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.step(1.0, 10)
+        x10, v10 = nep.get_state()
+    with api.NEP(model_params, rebuild_every=10) as nep:
+        nep.set_state(x10, v10, wl.box)
+        nep.step(1.0, 10)
+        xb, vb = nep.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)

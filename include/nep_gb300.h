@@ -218,6 +218,12 @@ nep_status nep_compute_noalloc(const nep_params *params, int64_t n, const double
 /* Last error message of the handle (never NULL). */
 const char *nep_last_error(nep_handle *h);
 
+/* Self-test of the failure path of the tensor-core kernels' bounded waits: one block waits on an
+ * mbarrier that nothing arrives on, with the same helper and at most `polls` polls (1 .. 2^24), and
+ * *timed_out = 1 when the wait ran out and the kernel ended normally (0 would mean the barrier
+ * completed).  Synchronous; uses the current device; no handle. */
+nep_status nep_selftest_bounded_wait(int64_t polls, int *timed_out);
+
 /* Name of a status code (never NULL). */
 const char *nep_status_string(nep_status s);
 

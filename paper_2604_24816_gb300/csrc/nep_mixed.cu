@@ -10,6 +10,7 @@
 // the descriptor adjoint are float32; the adjoint rows G are stored as float16 (the paper's half-precision
 // storage of the per-atom gradient and angular accumulators), read by k_force<S, __half>.
 #include "nep_descriptor.cuh"
+#include "nep_gb300.h"
 #include "nep_tc.cuh"
 
 namespace nep {
@@ -191,3 +192,36 @@ NEP_INSTANTIATE(StudentShape, __half)
 #undef NEP_INSTANTIATE
 
 }  // namespace nep
+
+// ---------------------------------------------------------------------------------------------------
+// Self-test of the bounded mbarrier wait used above: one block initialises an mbarrier that nothing
+// ever arrives on, waits with the same helper and a small poll limit, and reports the outcome in the
+// same status word the kernels use -- a wait that runs out ends the kernel normally.
+namespace nep {
+namespace {
+__global__ void k_wait_selftest(long polls, int *status) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait(&mbar, 0, polls);
+  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+}  // namespace
+}  // namespace nep
+
+extern "C" nep_status nep_selftest_bounded_wait(int64_t polls, int *timed_out) {
+  if (!timed_out || polls < 1 || polls > (1LL << 24)) return NEP_ERR_ARG;
+  int *d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return NEP_ERR_OOM; }
+  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    nep::k_wait_selftest<<<1, 32>>>((long)polls, d);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return NEP_ERR_CUDA;
+  *timed_out = (h & nep::ST_TIMEOUT) ? 1 : 0;
+  return NEP_OK;
+}

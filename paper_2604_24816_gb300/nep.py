@@ -52,7 +52,8 @@ class nep_params(C.Structure):
 EXPORTED = ("nep_create", "nep_destroy", "nep_set_state", "nep_build_neighbors", "nep_compute", "md_verlet_step",
             "nep_get_state", "nep_get_thermo", "nep_get_neighbors", "nep_get_descriptors", "nep_get_site_energies",
             "nep_set_timing", "nep_get_timing", "nep_get_counters", "nep_last_error", "nep_status_string",
-            "nep_compute_noalloc", "nep_set_fallback", "nep_get_fallback", "nep_run_variant")
+            "nep_compute_noalloc", "nep_set_fallback", "nep_get_fallback", "nep_run_variant",
+            "nep_selftest_bounded_wait")
 
 
 def lib():
@@ -88,6 +89,7 @@ def lib():
                                        C.c_float, C.c_double]
         L.nep_get_fallback.argtypes = [vp, vp, C.POINTER(C.c_int64)]
         L.nep_run_variant.argtypes = [vp, C.c_int, d, vp]
+        L.nep_selftest_bounded_wait.argtypes = [i64, C.POINTER(C.c_int)]
         for f in EXPORTED:
             if f not in ("nep_last_error", "nep_status_string"):
                 getattr(L, f).restype = C.c_int

@@ -300,3 +300,19 @@ def test_checkpoint_resume_is_bit_identical(api, model_params):
         nep.step(1.0, 10)
         xb, vb = nep.get_state()
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_bounded_wait_runs_out_and_reports(api):
+    """The tensor-core kernels wait on mbarriers with a poll limit; a wait on a barrier that nothing
+    arrives on ends the kernel with the timeout bit set, and the context stays usable."""
+    import ctypes as C
+    L = api.lib()
+    flag = C.c_int(-1)
+    assert L.nep_selftest_bounded_wait(1 << 12, C.byref(flag)) == 0
+    assert flag.value == 1
+    # the context still works afterwards
+    wl = ni.workload("cu_4x4x4")
+    with api.NEP(precision="mix_bf16") as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        E, F, W = nep.compute()
+    assert np.isfinite(E) and np.all(np.isfinite(F))

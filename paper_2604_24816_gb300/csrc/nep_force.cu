@@ -24,6 +24,7 @@
 //
 // Everything is float32 except the per-block energy/virial partial sums (float64).
 #include "nep_descriptor.cuh"
+#include "nep_tc.cuh"
 
 namespace nep {
 
@@ -122,124 +123,196 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
   block_sum_store<5>(acc, part);
 }
 
+// Adjoint row G_i of the force kernel: in registers for small shapes; for the teacher shape (120
+// angular values) it is parked in tensor memory (TMEM) and read back one chunk of lm components at a
+// time.  TMEM is per-SM storage outside L1, so this halves the register footprint (2 -> 4 resident
+// blocks) without taking L1 capacity from the gathered neighbour rows G_j.
+#ifndef NEP_FORCE_MINB_TM
+#define NEP_FORCE_MINB_TM 3
+#endif
+template <class S>
+struct ForceCfg {
+  static constexpr bool TM = S::NLM > 8 && S::NA == 5;
+  static constexpr int MINB = TM ? NEP_FORCE_MINB_TM : NEP_FORCE_MINB;
+  static constexpr uint32_t TCOLS = 128;   // TMEM columns per block: >= NA * NLM, a power of two
+  // neighbour pipeline depth; with 3 resident blocks the shallower ring and no L1 prefetch of the
+  // next neighbour row measured best
+  static constexpr int DE = TM ? 4 : FPIPE_DE, DP = TM ? 2 : FPIPE_DP;
+  static constexpr bool PREFETCH = !TM;
+  static_assert(!TM || S::NA * S::NLM <= (int)TCOLS, "adjoint row does not fit the TMEM allocation");
+  static_assert(!TM || FORCE_BLOCK == 128, "one TMEM lane per thread: 4 warps cover the 128 lanes");
+};
+
 // FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float atomicAdd
 // into Ff, whose result depends on the order in which the additions arrive.
+//
+// With the row in TMEM the pair loop runs to the warp's largest owned count (threads past their own
+// count, or past the last atom, idle with a predicate) so that the angular block, which holds the
+// warp-collective TMEM loads, is entered by whole warps: lanes without an angular pair in that
+// iteration compute on a harmless stand-in pair and discard the result.
 template <class S, class GT, bool FS = false>
-__global__ void __launch_bounds__(FORCE_BLOCK, NEP_FORCE_MINB)
+__global__ void __launch_bounds__(FORCE_BLOCK, ForceCfg<S>::MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
         const int32_t *__restrict__ nbr, const int32_t *__restrict__ nown, const int32_t *__restrict__ nband0,
         const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status, float *__restrict__ Ff = nullptr) {
+  constexpr bool TM = ForceCfg<S>::TM;
+  constexpr int W = GTraits<GT>::W;
   __shared__ float4 shift[27];
-  __shared__ uint32_t ring_e[FPIPE_DE * FORCE_BLOCK];
-  __shared__ float4 ring_p[FPIPE_DP * FORCE_BLOCK];
+  constexpr int DE = ForceCfg<S>::DE, DP = ForceCfg<S>::DP;
+  __shared__ uint32_t ring_e[DE * FORCE_BLOCK];
+  __shared__ float4 ring_p[DP * FORCE_BLOCK];
+  __shared__ uint32_t tmem_base;
+  if constexpr (TM) {
+    if (threadIdx.x < 32) tmem_alloc(&tmem_base, ForceCfg<S>::TCOLS);
+    tc_fence_before();
+  }
   fill_shift_table(shift, geom);
   __syncthreads();
+  uint32_t trow = 0;   // this thread's TMEM lane, column 0
+  if constexpr (TM) {
+    tc_fence_after();
+    trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  const int ii = live ? i : 0;            // the row read (and ignored) by threads past the last atom
   long long acc[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  if (i < n) {
-    const float4 pi = pos[i];
-    constexpr int W = GTraits<GT>::W;
-    const GT *Gi = G + (size_t)i * S::GS;
-    float gi[S::NA][S::NLM];
-#define GI(a, lm) gi[a][lm]
+  const float4 pi = pos[ii];
+  const GT *Gi = G + (size_t)ii * S::GS;
+  // G_i[a][lm] lives at TMEM column (lm - lm mod W) NA + a W + lm mod W: chunk c of W components
+  // holds all channels in NA consecutive groups of W columns.
+  float gi[TM ? 1 : S::NA][TM ? 1 : S::NLM];
 #pragma unroll
-    for (int a = 0; a < S::NA; ++a)
+  for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-      for (int c = 0; c < S::NLM; c += W) {
-        float t[W];
-        load_vec(Gi + a * S::NLM + c, t);
+    for (int c = 0; c < S::NLM; c += W) {
+      float t[W];
+      load_vec(Gi + a * S::NLM + c, t);
+      if constexpr (TM) {
+        tmem_st(trow + (uint32_t)(c * S::NA + a * W), t);
+      } else {
 #pragma unroll
-        for (int k = 0; k < W; ++k) GI(a, c + k) = t[k];
+        for (int k = 0; k < W; ++k) gi[a][c + k] = t[k];
       }
-    float fpi[8];
-    load_tail8(Gi, S::NA * S::NLM, fpi);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
-    const int cnt = nown[i];
-    const int nb0 = nband0[i];
-    int nrad = 0, nang = 0, nact = 0;
-    NbrPipe<FPIPE_DE, FPIPE_DP, FORCE_BLOCK> pipe;
-    pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
-    for (int k = 0; k < cnt; ++k) {
-      uint32_t e;
-      float4 pj;
+    }
+  if constexpr (TM) tmem_wait_st();
+  float fpi[8];
+  load_tail8(Gi, S::NA * S::NLM, fpi);
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
+  const int cnt = live ? nown[i] : 0;
+  const int nb0 = live ? nband0[i] : 0;
+  int nrad = 0, nang = 0, nact = 0;
+  NbrPipe<DE, DP, FORCE_BLOCK> pipe;
+  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, cnt);
+  const int trip = TM ? __reduce_max_sync(0xffffffffu, cnt) : cnt;
+  for (int k = 0; k < trip; ++k) {
+    const bool valid = k < cnt;
+    uint32_t e = 0u;
+    float4 pj = pi;
+    if (valid) {
       pipe.get(k, e, pj);
       // pull the next angular neighbour's adjoint row into L1 while this pair is computed
-      if (k + 1 < nb0 && k + 1 < cnt) {
-        const uint32_t en = pipe.re[((k + 1) % FPIPE_DE) * FORCE_BLOCK];
+      if (ForceCfg<S>::PREFETCH && k + 1 < nb0 && k + 1 < cnt) {
+        const uint32_t en = pipe.re[((k + 1) % DE) * FORCE_BLOCK];
         const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * S::GS);
 #pragma unroll
         for (int b = 0; b < (int)(S::GS * sizeof(GT)); b += 128) prefetch_l1(gr + b);
       }
-      const int j = (int)(e & J_MASK);
-      const float4 o = shift[e >> J_BITS];
-      const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 >= P.rmax2) continue;
-      ++nact;
-      const float ir = rsqrtf(r2);
-      const float r = r2 * ir;
-      const GT *Gj = G + (size_t)j * S::GS;
-      float coef = 0.f;                     // D = coef * d + (vx, vy, vz)
-      float vx = 0.f, vy = 0.f, vz = 0.f;
-      if (r2 < P.rcR2) {
-        float f[S::KR], df[S::KR];
-        cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
-        float fpj[8];
-        load_tail8(Gj, S::NA * S::NLM, fpj);
-        float c = 0.f;
+    }
+    const int j = (int)(e & J_MASK);
+    const float4 o = shift[e >> J_BITS];
+    const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const bool act = valid && r2 < P.rmax2;
+    if constexpr (!TM) {
+      if (!act) continue;
+    }
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    float coef = 0.f;                     // D = coef * d + (vx, vy, vz)
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    if (act && r2 < P.rcR2) {
+      float f[S::KR], df[S::KR];
+      cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
+      float fpj[8];
+      load_tail8(G + (size_t)j * S::GS, S::NA * S::NLM, fpj);
+      float c = 0.f;
 #pragma unroll
-        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k] + fpj[k], df[k], c);
-        coef = c * ir;
-        ++nrad;
+      for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k] + fpj[k], df[k], c);
+      coef = c * ir;
+      ++nrad;
+    }
+    if (act && P.lj_on != 0.f && r2 < P.lj_rc2) {
+      float el, dl;
+      lj_pair<S>(P, r2, r, el, dl);
+      coef = fmaf(dl, ir, coef);
+    }
+    const bool ang = act && r2 < P.rcA2;
+    bool enter = ang;
+    if constexpr (TM) enter = __any_sync(0xffffffffu, ang);
+    if (enter) {
+      if constexpr (TM) __syncwarp();
+      // stand-in pair for lanes that only take part in the warp-collective loads: r = 1 along x,
+      // the row of atom ii
+      const bool si = TM && !ang;
+      const float ar = si ? 1.f : r, air = si ? 1.f : ir;
+      const float ux = si ? 1.f : dx * ir, uy = si ? 0.f : dy * ir, uz = si ? 0.f : dz * ir;
+      const GT *Gj = G + (size_t)(si ? ii : j) * S::GS;
+      float f[S::KA], df[S::KA];
+      cheb_basis_d<S::KA>(ar, P.inv_rcA, f, df);
+      float g[S::NA], dg[S::NA];
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) {
+        float t = 0.f, dt = 0.f;
+#pragma unroll
+        for (int b = 0; b < S::KA; ++b) { t = fmaf(P.cA[a][b], f[b], t); dt = fmaf(P.cA[a][b], df[b], dt); }
+        g[a] = t; dg[a] = dt;
       }
-      if (P.lj_on != 0.f && r2 < P.lj_rc2) {
-        float el, dl;
-        lj_pair<S>(P, r2, r, el, dl);
-        coef = fmaf(dl, ir, coef);
-      }
-      if (r2 < P.rcA2) {
-        ++nang;
-        float f[S::KA], df[S::KA];
-        cheb_basis_d<S::KA>(r, P.inv_rcA, f, df);
-        float g[S::NA], dg[S::NA];
+      float Y[S::NLM];
+      harmonics<S::NLM>(ux, uy, uz, Y);
+      float along = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+      // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u)
 #pragma unroll
-        for (int a = 0; a < S::NA; ++a) {
-          float t = 0.f, dt = 0.f;
+      for (int c = 0; c < S::NLM; c += W) {
+        float hj[S::NA][W], hi[S::NA][W];
 #pragma unroll
-          for (int b = 0; b < S::KA; ++b) { t = fmaf(P.cA[a][b], f[b], t); dt = fmaf(P.cA[a][b], df[b], dt); }
-          g[a] = t; dg[a] = dt;
+        for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * S::NLM + c, hj[a]);
+        if constexpr (TM) {
+          uint32_t cols[S::NA];
+#pragma unroll
+          for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
+          tmem_ld5(cols, hi);
+        } else {
+#pragma unroll
+          for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+            for (int cc = 0; cc < W; ++cc) hi[a][cc] = gi[a][c + cc];
         }
-        const float ux = dx * ir, uy = dy * ir, uz = dz * ir;
-        float Y[S::NLM];
-        harmonics<S::NLM>(ux, uy, uz, Y);
-        float along = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-        // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u)
 #pragma unroll
-        for (int c = 0; c < S::NLM; c += W) {
-          float hj[S::NA][W];
+        for (int cc = 0; cc < W; ++cc) {
+          const int lm = c + cc;
+          const float sgn = (lm_l(lm) & 1) ? -1.f : 1.f;
+          float av = 0.f, bv = 0.f;
 #pragma unroll
-          for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * S::NLM + c, hj[a]);
-#pragma unroll
-          for (int cc = 0; cc < W; ++cc) {
-            const int lm = c + cc;
-            const float sgn = (lm_l(lm) & 1) ? -1.f : 1.f;
-            float av = 0.f, bv = 0.f;
-#pragma unroll
-            for (int a = 0; a < S::NA; ++a) {
-              const float gjv = hj[a][cc];
-              const float H = fmaf(sgn, gjv, GI(a, lm));
-              av = fmaf(H, dg[a], av);
-              bv = fmaf(H, g[a], bv);
-            }
-            along = fmaf(av - (float)lm_l(lm) * ir * bv, Y[lm], along);
-            harmonic_grad_acc(lm, ux, uy, uz, bv, bx, by, bz);
+          for (int a = 0; a < S::NA; ++a) {
+            const float H = fmaf(sgn, hj[a][cc], hi[a][cc]);
+            av = fmaf(H, dg[a], av);
+            bv = fmaf(H, g[a], bv);
           }
+          along = fmaf(av - (float)lm_l(lm) * air * bv, Y[lm], along);
+          harmonic_grad_acc(lm, ux, uy, uz, bv, bx, by, bz);
         }
+      }
+      if (ang) {
+        ++nang;
         coef = fmaf(along, ir, coef);
         vx = bx * ir; vy = by * ir; vz = bz * ir;
       }
+    }
+    if (act) {
+      ++nact;
       const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
       fx += Dx; fy += Dy; fz += Dz;
       // Newton's third law: F_j -= D_ij, accumulated in fixed point (order-independent sum)
@@ -254,7 +327,9 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
       wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
     }
-    pipe.finish();
+  }
+  pipe.finish();
+  if (live) {
     if constexpr (FS) {
       atomicAdd(Ff + i, fx); atomicAdd(Ff + (size_t)n + i, fy); atomicAdd(Ff + 2 * (size_t)n + i, fz);
     } else {
@@ -269,8 +344,15 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     acc[6] = -to_fix32(wzx); acc[7] = -to_fix32(wzy); acc[8] = -to_fix32(wzz);
     acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang;
   }
+  if constexpr (TM) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc_fence_after();
+      tmem_dealloc(tmem_base, ForceCfg<S>::TCOLS);
+    }
+  }
   block_sum_store<13>(acc, part);
-#undef GI
 }
 
 // ---------------------------------------------------------------------------------------------------

@@ -21,15 +21,18 @@ __global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool moved = false;
   if (i < n) {
-    double ux = vx[i] + kick * fix_to_double(F[i]);
-    double uy = vy[i] + kick * fix_to_double(F[(size_t)n + i]);
-    double uz = vz[i] + kick * fix_to_double(F[2 * (size_t)n + i]);
+    // kick_fix = kick * 2^-32: one conversion and one FMA per component on the narrow FP64 pipe
+    const double kick_fix = kick * FIX_INV;
+    double ux = fma(kick_fix, (double)F[i], vx[i]);
+    double uy = fma(kick_fix, (double)F[(size_t)n + i], vy[i]);
+    double uz = fma(kick_fix, (double)F[2 * (size_t)n + i], vz[i]);
     vx[i] = ux; vy[i] = uy; vz[i] = uz;
     const double px = x[i] + dt * ux, py = y[i] + dt * uy, pz = z[i] + dt * uz;
     x[i] = px; y[i] = py; z[i] = pz;
     const float4 p = pos[i];
     const int cx = cell_x(p.w), cy = cell_y(p.w), cz = cell_z(p.w);
-    const float4 q = make_float4((float)(px - cx * lx), (float)(py - cy * ly), (float)(pz - cz * lz), p.w);
+    const float4 q = make_float4((float)fma(-(double)cx, lx, px), (float)fma(-(double)cy, ly, py),
+                                 (float)fma(-(double)cz, lz, pz), p.w);
     pos[i] = q;
     const float4 r = pos_ref[i];
     const float ddx = q.x - r.x, ddy = q.y - r.y, ddz = q.z - r.z;
@@ -70,9 +73,10 @@ __global__ void k_kick(int n, double *__restrict__ vx, double *__restrict__ vy, 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   long long acc[1] = {0};
   if (i < n) {
-    const double ux = vx[i] + kick * fix_to_double(F[i]);
-    const double uy = vy[i] + kick * fix_to_double(F[(size_t)n + i]);
-    const double uz = vz[i] + kick * fix_to_double(F[2 * (size_t)n + i]);
+    const double kick_fix = kick * FIX_INV;
+    const double ux = fma(kick_fix, (double)F[i], vx[i]);
+    const double uy = fma(kick_fix, (double)F[(size_t)n + i], vy[i]);
+    const double uz = fma(kick_fix, (double)F[2 * (size_t)n + i], vz[i]);
     vx[i] = ux; vy[i] = uy; vz[i] = uz;
     acc[0] = __double2ll_rn(0.5 * mass * KE_CONV * (ux * ux + uy * uy + uz * uz) * 4294967296.0);
   }

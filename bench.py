@@ -50,10 +50,15 @@ FP32_LANES_PER_SM = 128
 # Algorithmic FP32 FLOPs of the method per unit (static count of the arithmetic each unit needs,
 # FMA = 2, add/mul = 1, each transcendental = 1), for the compiled shape (5 radial + 5 angular
 # channels, 8 basis functions, l = 1..4, 4-body, 30 neurons).  The descriptor kernel visits every
-# list entry of every atom; the force kernel visits each unordered pair once (its owner's half list).
+# list entry of every atom.  The force kernel of the float32 teacher ("force_full") visits every
+# ordered pair with the own adjoint row only; the half-list form ("force": float16 rows, and the
+# half-list ablation) visits each unordered pair once and forms H = G^i + (-1)^l G^j (120 more FMAs
+# per angular pair, and fp_i + fp_j per radial pair).
 FLOPS = {
     "descriptor": dict(list_entry=11, active_pair=2, radial_pair=56, lj_pair=12, angular_pair=464, atom=4815),
     "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=149, lj_pair=13, angular_pair=1465, atom=3),
+    "force_full": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=141, lj_pair=14, angular_pair=1225,
+                       atom=3),
 }
 # The same static count for the student shape (4 radial + 4 angular channels, 8 basis functions,
 # l = 1, 2, no 4-body, 16 neurons), used for the student forms.
@@ -67,13 +72,18 @@ FLOPS_STUDENT = {
 BYTES = dict(per_atom=16 * 2 + 512 * 2 + 24 * 2 + 4, per_list_entry=4 * 1.5)
 
 
+def force_kind(form: str) -> str:
+    """FLOP table of the force kernel a form runs: the full-row form for the float32 teacher."""
+    return "force_full" if form == "plain" else "force"
+
+
 def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) -> float:
     f = table[kind]
     if kind == "descriptor":
         lst, act, rad, ang = c["list_entries"], c["active_pairs"], c["radial_pairs"], c["angular_pairs"]
     else:
-        lst, act, rad, ang = (c["owned_list_entries"], c["owned_active_pairs"], c["owned_radial_pairs"],
-                              c["owned_angular_pairs"])
+        lst, act, rad, ang = (c["force_list_entries"], c["force_active_pairs"], c["force_radial_pairs"],
+                              c["force_angular_pairs"])
     return (f["list_entry"] * lst + f["active_pair"] * act + f["radial_pair"] * rad + f["lj_pair"] * rad +
             f["angular_pair"] * ang + f["atom"] * n_atoms_evals)
 
@@ -413,7 +423,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     evals = dc["evaluations"]
     table = FLOPS_STUDENT if FORMS[args.form]["model"] == "student" else FLOPS
     f_desc = kernel_flops("descriptor", dc, evals * wl.n, table)
-    f_force = kernel_flops("force", dc, evals * wl.n, table)
+    f_force = kernel_flops(force_kind(args.form), dc, evals * wl.n, table)
     peaks = load_peaks()
     clk = clocks.summary(t_host0, t_host1)
     peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -475,10 +485,12 @@ def run_ours(args, rank: int, ws: int, local: int):
         nep.set_timing(False)
         ablations = {"force_fixed_point_ms": round(t_ref["force"][0], 4),
                      "descriptor_ms": round(t_ref["descriptor"][0], 4)}
-        for v in ("float_scatter", "tile1", "tile3"):
+        for v in ("float_scatter", "half_list", "tile1", "tile3"):
             ablations[v + "_ms"] = round(min(nep.run_variant(v)[0] for _ in range(3)), 4)
-        ablations["note"] = ("float_scatter: force kernel with float atomicAdd (order-dependent sums) vs the "
-                             "fixed-point integer atomics; tile1/tile3: descriptor kernel with 1 or 3 angular "
+        ablations["note"] = ("float_scatter: the full-row force kernel with float atomicAdd (order-dependent "
+                             "sums) vs the fixed-point integer atomics; half_list: force kernel over each "
+                             "unordered pair once, gathering the neighbour's adjoint row, vs every ordered "
+                             "pair with the own row only; tile1/tile3: descriptor kernel with 1 or 3 angular "
                              "channels per neighbour pass and s_nlm through global memory vs all 5 channels in "
                              "registers; single launches, CUDA events")
     F_plain = F_this = None
@@ -530,7 +542,7 @@ def run_ours(args, rank: int, ws: int, local: int):
         "pairs_per_atom": {"list": dc["list_entries"] / max(1, evals * wl.n),
                            "radial": dc["radial_pairs"] / max(1, evals * wl.n),
                            "angular": dc["angular_pairs"] / max(1, evals * wl.n),
-                           "owned_angular": dc["owned_angular_pairs"] / max(1, evals * wl.n)},
+                           "force_kernel_angular": dc["force_angular_pairs"] / max(1, evals * wl.n)},
         "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"],
                        "energy_change_per_atom": ((th["pe"] + th["ke"]) - (th0["pe"] + th0["ke"])) / wl.n,
                        "over_fs": args.steps * wl.dt_fs},

@@ -155,9 +155,10 @@ nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_
 /* Counters since nep_set_state: out = {radial pairs (r < rc_R) and angular pairs (r < rc_A) seen by the
  * descriptor kernel, force evaluations, neighbour rebuilds, MD steps, kernel launches enqueued by the
  * library, list entries and pairs inside the largest cutoff seen by the descriptor kernel, then the
- * same four counts for the owned pairs seen by the force kernel: list entries, pairs inside the
- * largest cutoff, radial pairs, angular pairs, then the atom evaluations done by the fallback model
- * (nep_set_fallback)}.  Pair and atom counts sum over evaluations. */
+ * same four counts for the rows walked by the force kernel (whole rows for the float32 teacher, the
+ * owned half of each row otherwise): list entries, pairs inside the largest cutoff, radial pairs,
+ * angular pairs, then the atom evaluations done by the fallback model (nep_set_fallback)}.  Pair and
+ * atom counts sum over evaluations. */
 nep_status nep_get_counters(nep_handle *h, int64_t out[13]);
 
 /* Per-atom fallback from a student-shaped model (n_max 3/3, l_max 2, no 4-body, 16 neurons) to a
@@ -179,17 +180,20 @@ nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const floa
  * evaluation of the current state. */
 nep_status nep_get_fallback(nep_handle *h, int *flags, int64_t *count);
 
-/* Kernel variants of the paper's own design, kept for ablation (plain float32 teacher path only):
+/* Kernel variants kept for ablation (plain float32 teacher path only):
  *   NEP_VARIANT_FLOAT_SCATTER  the force kernel with float atomicAdd scatter (Section V.B, Optimization 1)
  *                              instead of 64-bit fixed-point integer atomics: the result depends on the
  *                              order in which additions arrive, so repeated runs may differ in the last bits;
  *   NEP_VARIANT_TILE1 / TILE3  the descriptor kernel with channel tiling (Algorithm 1): the angular
  *                              neighbours are walked once per tile of 1 or 3 channels, with s_nlm passed
- *                              through a global array (the paper's sum_fxyz) instead of registers.
+ *                              through a global array (the paper's sum_fxyz) instead of registers;
+ *   NEP_VARIANT_HALF_LIST      the force kernel over the owned half of each row: every unordered pair once,
+ *                              with the adjoint rows of both atoms (the neighbour's gathered), instead of
+ *                              every ordered pair with the own row only.
  * One force evaluation on the current state with the variant; *ms = the variant kernel's time (CUDA
  * events), F (may be NULL; host or device; [n][3], caller's order) = the forces it produced.  The
  * handle's own results are recomputed on the next request. */
-enum { NEP_VARIANT_FLOAT_SCATTER = 1, NEP_VARIANT_TILE1 = 2, NEP_VARIANT_TILE3 = 3 };
+enum { NEP_VARIANT_FLOAT_SCATTER = 1, NEP_VARIANT_TILE1 = 2, NEP_VARIANT_TILE3 = 3, NEP_VARIANT_HALF_LIST = 4 };
 nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F);
 
 /* Upper limits of nep_compute_noalloc: the size of its fixed scratch array. */

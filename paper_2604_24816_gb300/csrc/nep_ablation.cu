@@ -51,7 +51,8 @@ k_descriptor_tiled(const __grid_constant__ Model<S> P, const Geom geom, const in
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= P.rmax2) continue;
         ++nact;
-        const float r = r2 * rsqrtf(r2);
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
         if (r2 < P.rcR2) {
           float f[S::KR];
           cheb_basis<S::KR>(r, P.inv_rcR, f);
@@ -61,7 +62,7 @@ k_descriptor_tiled(const __grid_constant__ Model<S> P, const Geom geom, const in
         }
         if (P.lj_on != 0.f && r2 < P.lj_rc2) {
           float el, dl;
-          lj_pair<S>(P, r2, r, el, dl);
+          lj_pair<S>(P, r2, r, ir, el, dl);
           elj = fmaf(0.5f, el, elj);
         }
         if (r2 < P.rcA2) ++nang;

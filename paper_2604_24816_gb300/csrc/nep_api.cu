@@ -31,7 +31,7 @@ cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 
                               cudaStream_t);
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
+                         const int32_t *, const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
 // nep_mixed.cu
@@ -54,6 +54,10 @@ template <class S>
 cudaError_t launch_force_float_scatter(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
                                        const int32_t *, const int32_t *, const float *, float *, long long *, int *,
                                        cudaStream_t);
+template <class S>
+cudaError_t launch_force_half_list(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
+                                   const int32_t *, const int32_t *, const float *, long long *, long long *, int *,
+                                   cudaStream_t);
 template <class S, int NT>
 cudaError_t launch_descriptor_tiled(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
                                     const int32_t *, float *, float *, long long *, long long *, int *, float *,
@@ -352,10 +356,10 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   {
     Scope sc(h, KC_FORCE, 1);
     if (h->precision == NEP_FP32)
-      e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const float *>(h->G),
+      e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, static_cast<const float *>(h->G),
                                  h->F, h->part_f, &h->ctrl->status, h->stream);
     else
-      e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nown, h->nband0, static_cast<const __half *>(h->G),
+      e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, static_cast<const __half *>(h->G),
                                   h->F, h->part_f, &h->ctrl->status, h->stream);
   }
   if (e == cudaSuccess && fb.on) {
@@ -946,7 +950,8 @@ nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const floa
 nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
   if (!h || !ms) return NEP_ERR_ARG;
   if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
-  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_TILE3) return fail(h, NEP_ERR_ARG, "unknown variant");
+  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_HALF_LIST)
+    return fail(h, NEP_ERR_ARG, "unknown variant");
   if (h->shape != 0 || h->precision != NEP_FP32 || h->fb_on)
     return fail(h, NEP_ERR_UNSUPPORTED, "the variants exist for the plain float32 teacher path");
   if (h->n == 0) { *ms = 0.0; return NEP_OK; }
@@ -969,10 +974,19 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
       if (e == cudaSuccess) e = cudaMemsetAsync(h->abl_f, 0, 3 * N * sizeof(float), h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
       if (e == cudaSuccess)
-        e = launch_force_float_scatter<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->abl_f,
+        e = launch_force_float_scatter<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nband0, G, h->abl_f,
                                                 h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess) e = launch_store_float3(h->n, h->id, h->abl_f, h->io, h->stream);
+    } else if (variant == NEP_VARIANT_HALF_LIST) {
+      e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
+                                     h->part_d, &h->ctrl->status, Fallback{}, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+      if (e == cudaSuccess)
+        e = launch_force_half_list<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->F,
+                                            h->part_f, &h->ctrl->status, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     } else {
       if (!h->abl_s) e = dalloc(h->abl_s, (size_t)CuShape::NA * CuShape::NLM * N);
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
@@ -986,7 +1000,7 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
       }
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess)
-        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->F, h->part_f,
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, G, h->F, h->part_f,
                                          &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     }

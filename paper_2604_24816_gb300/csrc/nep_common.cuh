@@ -113,11 +113,13 @@ __device__ __forceinline__ void fill_shift_table(float4 *tab, const Geom &g) {
 }
 
 // Chebyshev basis f_k(r) = (T_k(x) + 1)/2 * fc(r), x = 2 (r/rc - 1)^2 - 1, fc = (1 + cos(pi r/rc))/2.
+// The cutoff uses the hardware sine/cosine (absolute error below 2^-21.4 for arguments in [-pi, pi];
+// here pi r / rc lies in [0, pi]), a few instructions instead of the range-reduced library call.
 template <int K>
 __device__ __forceinline__ void cheb_basis(float r, float inv_rc, float (&f)[K]) {
   float s, c;
   const float t = r * inv_rc;
-  sincospif(t, &s, &c);
+  __sincosf(3.14159265358979f * t, &s, &c);
   const float fc = 0.5f + 0.5f * c;
   const float u = t - 1.f;
   const float x = 2.f * u * u - 1.f;
@@ -137,7 +139,7 @@ template <int K>
 __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K], float (&df)[K]) {
   float s, c;
   const float t = r * inv_rc;
-  sincospif(t, &s, &c);
+  __sincosf(3.14159265358979f * t, &s, &c);
   const float fc = 0.5f + 0.5f * c;
   const float dfc = -0.5f * 3.14159265358979f * inv_rc * s;
   const float u = t - 1.f;
@@ -249,14 +251,17 @@ __device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, floa
 
 __host__ __device__ constexpr int lm_l(int lm) { return lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4)); }
 
-// Shifted-force LJ pair energy E(r) and dE/dr, from r^2 (r also passed).
+// Shifted-force LJ pair energy E(r) and dE/dr, from r^2, r and ir = 1/r (reciprocal square root).
+// No division: 1/r^2 = ir^2 refined by one Newton step (error about 1 ulp, which the twelfth power
+// would otherwise amplify from the reciprocal square root's 2 ulp), 1/r = ir.
 template <class S>
-__device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, float &e, float &de) {
-  const float ir2 = 1.f / r2;
+__device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, float ir, float &e, float &de) {
+  float ir2 = ir * ir;
+  ir2 = fmaf(ir2, fmaf(-r2, ir2, 1.f), ir2);
   const float ir6 = ir2 * ir2 * ir2;
   const float a12 = P.lj_c12 * ir6 * ir6, a6 = P.lj_c6 * ir6;
   e = a12 - a6 - P.lj_e_rc - (r - P.lj_rc) * P.lj_de_rc;
-  de = (-12.f * a12 + 6.f * a6) / r - P.lj_de_rc;
+  de = fmaf(-12.f, a12, 6.f * a6) * ir - P.lj_de_rc;
 }
 
 // Exact conversion of a float to 64-bit fixed point with 32 fractional bits, without a 64-bit
@@ -290,10 +295,12 @@ __device__ __forceinline__ long long to_fix32(float v) {
 }
 
 // Block-wide sum of NV int64 values into out[blockIdx.x * NV + v].  Integer addition is associative,
-// so the result does not depend on the reduction order.
-template <int NV>
+// so the result does not depend on the reduction order.  NW bounds the warps per block (the size of
+// the shared scratch).
+template <int NV, int NW = 32>
 __device__ __forceinline__ void block_sum_store(long long (&v)[NV], long long *out) {
-  __shared__ long long red[32][NV];
+  static_assert(NW >= 1 && NW <= 32, "1..32 warps");
+  __shared__ long long red[NW][NV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -309,7 +316,7 @@ __device__ __forceinline__ void block_sum_store(long long (&v)[NV], long long *o
     const int nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      long long t = lane < nw ? red[lane][k] : 0ll;
+      long long t = lane < nw && lane < NW ? red[lane][k] : 0ll;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
       if (lane == 0) out[(size_t)blockIdx.x * NV + k] = t;

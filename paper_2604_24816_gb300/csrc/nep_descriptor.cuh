@@ -126,7 +126,7 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
     }
     if (P.lj_on != 0.f && r2 < P.lj_rc2) {
       float el, dl;
-      lj_pair<S>(P, r2, r, el, dl);
+      lj_pair<S>(P, r2, r, ir, el, dl);
       A.elj = fmaf(0.5f, el, A.elj);
     }
     if (r2 < P.rcA2) {

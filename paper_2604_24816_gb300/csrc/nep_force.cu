@@ -12,19 +12,25 @@
 //                T_n rebuilt from the l = 2 sums, then the one-hidden-layer tanh network (Section III.B
 //                equation) with its gradient.  It stores the per-atom adjoint G_nlm = dU_i/ds_nlm and
 //                dU_i/dq_n (radial), and the site energy.
-//  k_force       F_i = sum_j D_ij with D_ij = dU_i/dr_ij - dU_j/dr_ji.  The radial part uses both atoms'
-//                dU/dq_n; the angular part uses H_nlm = G^i_nlm + (-1)^l G^j_nlm because the pair
-//                geometry g_n(r) Yh_lm(u) is shared by both directions (Yh_lm(-u) = (-1)^l Yh_lm(u)).
-//                Since D_ji = -D_ij exactly, each unordered pair is evaluated once, by its owner (the
-//                owned part of the list), which adds D_ij to F_i and -D_ij to F_j.  The scatter uses
-//                64-bit fixed-point integer atomics (2^-32 eV/Angstrom units): integer addition is
-//                associative, so the forces are bitwise reproducible whatever the order of the
-//                atomics -- the atomic scatter of the paper's consolidated backward kernel (Section V.B,
-//                Optimization 1) made deterministic.  Virial W = -sum_pairs r_ij (x) D_ij.
+//  k_force       forces and virial from the adjoint rows, in one of two forms (both deterministic):
+//                full row (the float32 teacher): every ordered pair (i, j) of i's row gives
+//                d_ij = dU_i/dr_ij from atom i's own row only -- radial sum_k dU/dQ_k f_k'(r) r^, angular
+//                sum_nlm G_nlm d[g_n(r) Yh_lm(u)]/dr_ij, half of the LJ pair force -- which is added to F_i
+//                and subtracted from F_j; no neighbour row is read.  Half list (float16 rows, the
+//                student): D_ij = dU_i/dr_ij - dU_j/dr_ji for each unordered pair once, by its owner (the
+//                owned part of the list), with H_nlm = G^i_nlm + (-1)^l G^j_nlm because the pair geometry
+//                g_n(r) Yh_lm(u) is shared by both directions (Yh_lm(-u) = (-1)^l Yh_lm(u)) and D_ji = -D_ij
+//                exactly; the owner adds D_ij to F_i and -D_ij to F_j.  The scatter uses 64-bit fixed-point
+//                integer atomics (2^-32 eV/Angstrom units): integer addition is associative, so the forces
+//                are bitwise reproducible whatever the order of the atomics -- the atomic scatter of the
+//                paper's consolidated backward kernel (Section V.B, Optimization 1) made deterministic.
+//                Virial W = -sum over the evaluated pairs of r_ij (x) (d_ij or D_ij).
 //
 // Everything is float32 except the per-block energy/virial partial sums (float64).
 #include "nep_descriptor.cuh"
 #include "nep_tc.cuh"
+
+#include <type_traits>
 
 namespace nep {
 
@@ -120,7 +126,7 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     acc[3] = A.cnt;
     acc[4] = A.nact;
   }
-  block_sum_store<5>(acc, part);
+  block_sum_store<5, DESC_BLOCK / 32>(acc, part);
 }
 
 // Adjoint row G_i of the force kernel: in registers for small shapes; for the teacher shape (120
@@ -143,17 +149,19 @@ struct ForceCfg {
   static_assert(!TM || FORCE_BLOCK == 128, "one TMEM lane per thread: 4 warps cover the 128 lanes");
 };
 
-// FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float atomicAdd
-// into Ff, whose result depends on the order in which the additions arrive.
+// FULL = true walks the whole row (nrow = full row lengths) with atom i's own adjoint only; FULL =
+// false walks the owned half (nrow = owned counts) and gathers the neighbour's row (see the file
+// header).  FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float
+// atomicAdd into Ff, whose result depends on the order in which the additions arrive.
 //
 // With the row in TMEM the pair loop runs to the warp's largest owned count (threads past their own
 // count, or past the last atom, idle with a predicate) so that the angular block, which holds the
 // warp-collective TMEM loads, is entered by whole warps: lanes without an angular pair in that
 // iteration compute on a harmless stand-in pair and discard the result.
-template <class S, class GT, bool FS = false>
+template <class S, class GT, bool FS = false, bool FULL = false>
 __global__ void __launch_bounds__(FORCE_BLOCK, ForceCfg<S>::MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nown, const int32_t *__restrict__ nband0,
+        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
         const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status, float *__restrict__ Ff = nullptr) {
   constexpr bool TM = ForceCfg<S>::TM;
@@ -201,7 +209,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   load_tail8(Gi, S::NA * S::NLM, fpi);
   float fx = 0.f, fy = 0.f, fz = 0.f;
   float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
-  const int cnt = live ? nown[i] : 0;
+  const int cnt = live ? nrow[i] : 0;
   const int nb0 = live ? nband0[i] : 0;
   int nrad = 0, nang = 0, nact = 0;
   NbrPipe<DE, DP, FORCE_BLOCK> pipe;
@@ -214,7 +222,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     if (valid) {
       pipe.get(k, e, pj);
       // pull the next angular neighbour's adjoint row into L1 while this pair is computed
-      if (ForceCfg<S>::PREFETCH && k + 1 < nb0 && k + 1 < cnt) {
+      if (ForceCfg<S>::PREFETCH && !FULL && k + 1 < nb0 && k + 1 < cnt) {
         const uint32_t en = pipe.re[((k + 1) % DE) * FORCE_BLOCK];
         const char *gr = reinterpret_cast<const char *>(G + (size_t)(en & J_MASK) * S::GS);
 #pragma unroll
@@ -236,18 +244,23 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     if (act && r2 < P.rcR2) {
       float f[S::KR], df[S::KR];
       cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
-      float fpj[8];
-      load_tail8(G + (size_t)j * S::GS, S::NA * S::NLM, fpj);
       float c = 0.f;
+      if constexpr (FULL) {
 #pragma unroll
-      for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k] + fpj[k], df[k], c);
+        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k], df[k], c);
+      } else {
+        float fpj[8];
+        load_tail8(G + (size_t)j * S::GS, S::NA * S::NLM, fpj);
+#pragma unroll
+        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k] + fpj[k], df[k], c);
+      }
       coef = c * ir;
       ++nrad;
     }
     if (act && P.lj_on != 0.f && r2 < P.lj_rc2) {
       float el, dl;
-      lj_pair<S>(P, r2, r, el, dl);
-      coef = fmaf(dl, ir, coef);
+      lj_pair<S>(P, r2, r, ir, el, dl);
+      coef = fmaf(FULL ? 0.5f * dl : dl, ir, coef);   // FULL: each atom of the pair takes half
     }
     const bool ang = act && r2 < P.rcA2;
     bool enter = ang;
@@ -277,8 +290,10 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 #pragma unroll
       for (int c = 0; c < S::NLM; c += W) {
         float hj[S::NA][W], hi[S::NA][W];
+        if constexpr (!FULL) {
 #pragma unroll
-        for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * S::NLM + c, hj[a]);
+          for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * S::NLM + c, hj[a]);
+        }
         if constexpr (TM) {
           uint32_t cols[S::NA];
 #pragma unroll
@@ -297,7 +312,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
           float av = 0.f, bv = 0.f;
 #pragma unroll
           for (int a = 0; a < S::NA; ++a) {
-            const float H = fmaf(sgn, hj[a][cc], hi[a][cc]);
+            const float H = FULL ? hi[a][cc] : fmaf(sgn, hj[a][cc], hi[a][cc]);
             av = fmaf(H, dg[a], av);
             bv = fmaf(H, g[a], bv);
           }
@@ -352,7 +367,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
       tmem_dealloc(tmem_base, ForceCfg<S>::TCOLS);
     }
   }
-  block_sum_store<13>(acc, part);
+  block_sum_store<13, FORCE_BLOCK / 32>(acc, part);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -368,25 +383,54 @@ cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const flo
   return cudaGetLastError();
 }
 
+// Which form of the force kernel runs: the full-row gather-free form for the teacher shape with
+// float32 rows (its half-list gathers of 512-byte rows are the slowest part), the half list with
+// gathers otherwise (float16 rows and the student's 160-byte rows are cheap to gather, and the half
+// list does 0.6x the arithmetic).
+template <class S, class GT>
+constexpr bool force_full_row() {
+  return ForceCfg<S>::TM && std::is_same<GT, float>::value;
+}
+
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                         const int32_t *nown, const int32_t *nband0, const GT *G, long long *Ffix, long long *part,
-                         int *status, cudaStream_t st) {
+                         const int32_t *nnum, const int32_t *nown, const int32_t *nband0, const GT *G,
+                         long long *Ffix, long long *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S, GT><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
-                                               reinterpret_cast<unsigned long long *>(Ffix), part, status);
+  constexpr bool full = force_full_row<S, GT>();
+  k_force<S, GT, false, full><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, full ? nnum : nown, nband0, G,
+                                                           reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }
 
-// Ablation: the same force kernel with float atomicAdd scatter into Ff [3][n] (zeroed by the caller).
+// Ablation: the teacher's half-list force kernel with float32 rows (each unordered pair once by its
+// owner, gathering the neighbour's adjoint row), instead of the full-row form.
+template <class S>
+cudaError_t launch_force_half_list(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
+                                   const int32_t *nown, const int32_t *nband0, const float *G, long long *Ffix,
+                                   long long *part, int *status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
+  k_force<S, float, false, false><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
+                                                               reinterpret_cast<unsigned long long *>(Ffix), part,
+                                                               status);
+  return cudaGetLastError();
+}
+template cudaError_t launch_force_half_list<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
+                                                     const int32_t *, const int32_t *, const int32_t *, const float *,
+                                                     long long *, long long *, int *, cudaStream_t);
+
+// Ablation: the production (full-row) force kernel with float atomicAdd scatter into Ff [3][n] (zeroed
+// by the caller) instead of fixed-point integer atomics.
 template <class S>
 cudaError_t launch_force_float_scatter(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                                       const int32_t *nown, const int32_t *nband0, const float *G, float *Ff,
+                                       const int32_t *nnum, const int32_t *nband0, const float *G, float *Ff,
                                        long long *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S, float, true><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G, nullptr, part, status, Ff);
+  k_force<S, float, true, true><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, nband0, G, nullptr, part,
+                                                             status, Ff);
   return cudaGetLastError();
 }
 template cudaError_t launch_force_float_scatter<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
@@ -401,11 +445,11 @@ int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
                                              const int32_t *, float *, float *, float *, long long *, long long *,    \
                                              int *, const Fallback &, cudaStream_t);                                  \
   template cudaError_t launch_force<SH, float>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *, \
-                                               const int32_t *, const int32_t *, const float *, long long *,          \
-                                               long long *, int *, cudaStream_t);                                     \
+                                               const int32_t *, const int32_t *, const int32_t *, const float *,      \
+                                               long long *, long long *, int *, cudaStream_t);                        \
   template cudaError_t launch_force<SH, __half>(const Model<SH> &, const Geom &, int, const float4 *,                 \
-                                                const int32_t *, const int32_t *, const int32_t *, const __half *,    \
-                                                long long *, long long *, int *, cudaStream_t);
+                                                const int32_t *, const int32_t *, const int32_t *, const int32_t *,   \
+                                                const __half *, long long *, long long *, int *, cudaStream_t);
 NEP_INSTANTIATE(CuShape)
 NEP_INSTANTIATE(StudentShape)
 #undef NEP_INSTANTIATE

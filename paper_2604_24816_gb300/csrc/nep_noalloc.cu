@@ -33,7 +33,7 @@ cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 
                               cudaStream_t);
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
+                         const int32_t *, const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
@@ -247,7 +247,7 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   NA_CUDA(launch_neighbors(a, st));
   NA_CUDA(launch_descriptor<S>(M, g, N, a.pos, a.nbr, a.nnum, (float *)at(LAYOUT.G), (float *)at(LAYOUT.usite),
                                nullptr, Ffix, pd, &ctrl->status, Fallback{}, st));
-  NA_CUDA((launch_force<S, float>(M, g, N, a.pos, a.nbr, a.nown, a.nband0, (const float *)at(LAYOUT.G), Ffix, pf,
+  NA_CUDA((launch_force<S, float>(M, g, N, a.pos, a.nbr, a.nnum, a.nown, a.nband0, (const float *)at(LAYOUT.G), Ffix, pf,
                           &ctrl->status, st)));
   NA_CUDA(launch_finalize(pd, descriptor_blocks(N), pf, force_blocks(N), nullptr, 0, sums, counters, st));
   const bool f_dev = F && device_pointer(F);

@@ -244,8 +244,8 @@ class NEP:
         self._check(self._L.nep_get_counters(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         return dict(radial_pairs=int(out[0]), angular_pairs=int(out[1]), evaluations=int(out[2]),
                     rebuilds=int(out[3]), steps=int(out[4]), launches=int(out[5]), list_entries=int(out[6]),
-                    active_pairs=int(out[7]), owned_list_entries=int(out[8]), owned_active_pairs=int(out[9]),
-                    owned_radial_pairs=int(out[10]), owned_angular_pairs=int(out[11]),
+                    active_pairs=int(out[7]), force_list_entries=int(out[8]), force_active_pairs=int(out[9]),
+                    force_radial_pairs=int(out[10]), force_angular_pairs=int(out[11]),
                     fallback_atoms=int(out[12]))
 
     def set_fallback(self, teacher: dict | None, q_lo=None, q_hi=None, margin: float = 0.05,
@@ -271,11 +271,11 @@ class NEP:
                                              hi.ctypes.data_as(C.POINTER(C.c_float)), float(margin),
                                              float(max_fraction)))
 
-    VARIANTS = {"float_scatter": 1, "tile1": 2, "tile3": 3}
+    VARIANTS = {"float_scatter": 1, "tile1": 2, "tile3": 3, "half_list": 4}
 
     def run_variant(self, name: str):
-        """One force evaluation with a kernel variant of the paper's design (nep_run_variant):
-        returns (variant kernel milliseconds, forces [n][3])."""
+        """One force evaluation with a kernel variant kept for ablation (nep_run_variant): returns
+        (variant kernel milliseconds, forces [n][3])."""
         ms = np.zeros(1)
         F = np.zeros((max(self.n, 1), 3))
         self._check(self._L.nep_run_variant(self._h, self.VARIANTS[name], ms.ctypes.data_as(C.POINTER(C.c_double)),

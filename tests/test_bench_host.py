@@ -49,21 +49,30 @@ def test_single_rank_helpers_are_identity():
 
 def test_flop_model_counts_units():
     """The FLOP model is the table's per-unit counts times the pair counters of the right kernel
-    (descriptor: full rows; force: owned half rows), for both model shapes."""
-    c = dict(list_entries=78, active_pairs=42, radial_pairs=42, angular_pairs=18, owned_list_entries=39,
-             owned_active_pairs=21, owned_radial_pairs=21, owned_angular_pairs=9)
+    (descriptor: full rows; force: the rows the force kernel walked), for both model shapes."""
+    half = dict(list_entries=78, active_pairs=42, radial_pairs=42, angular_pairs=18, force_list_entries=39,
+                force_active_pairs=21, force_radial_pairs=21, force_angular_pairs=9)
     for table in (bench.FLOPS, bench.FLOPS_STUDENT):
         d, f = table["descriptor"], table["force"]
-        f_desc = bench.kernel_flops("descriptor", c, 1, table)
-        f_force = bench.kernel_flops("force", c, 1, table)
+        f_desc = bench.kernel_flops("descriptor", half, 1, table)
+        f_force = bench.kernel_flops("force", half, 1, table)
         assert f_desc == (d["list_entry"] * 78 + d["active_pair"] * 42 + (d["radial_pair"] + d["lj_pair"]) * 42 +
                           d["angular_pair"] * 18 + d["atom"])
         assert f_force == (f["list_entry"] * 39 + f["active_pair"] * 21 + (f["radial_pair"] + f["lj_pair"]) * 21 +
                            f["angular_pair"] * 9 + f["atom"])
-    teacher = bench.kernel_flops("force", c, 1) + bench.kernel_flops("descriptor", c, 1)
-    student = (bench.kernel_flops("force", c, 1, bench.FLOPS_STUDENT) +
-               bench.kernel_flops("descriptor", c, 1, bench.FLOPS_STUDENT))
+    teacher = bench.kernel_flops("force", half, 1) + bench.kernel_flops("descriptor", half, 1)
+    student = (bench.kernel_flops("force", half, 1, bench.FLOPS_STUDENT) +
+               bench.kernel_flops("descriptor", half, 1, bench.FLOPS_STUDENT))
     assert 25e3 < teacher < 45e3 and 8e3 < student < 0.6 * teacher
+    # the full-row form: every ordered pair, without the H_nlm and fp_i + fp_j terms of the half list
+    full = dict(half, force_list_entries=78, force_active_pairs=42, force_radial_pairs=42, force_angular_pairs=18)
+    h, g = bench.FLOPS["force"], bench.FLOPS["force_full"]
+    assert g["angular_pair"] == h["angular_pair"] - 2 * 120 and g["radial_pair"] == h["radial_pair"] - 8
+    assert g["lj_pair"] == h["lj_pair"] + 1
+    ratio = bench.kernel_flops("force_full", full, 1) / bench.kernel_flops("force", half, 1)
+    assert 1.4 < ratio < 2.0
+    assert bench.force_kind("plain") == "force_full"
+    assert all(bench.force_kind(f) == "force" for f in bench.FORMS if f != "plain")
 
 
 def test_traffic_lookup_requires_matching_source(tmp_path, monkeypatch):

@@ -1,6 +1,7 @@
-"""Kernel variants of the paper's own design (nep_run_variant) against the production kernels and the
-oracle: the float-atomic force scatter (order-dependent float sums; forces equal to the fixed-point
-path within float rounding) and the channel-tiled descriptor kernel (same descriptors, same forces)."""
+"""Kernel variants kept for ablation (nep_run_variant) against the production kernels and the oracle:
+the float-atomic force scatter (order-dependent float sums; forces equal to the fixed-point path within
+float rounding), the half-list force kernel (each unordered pair once, gathering the neighbour's row)
+and the channel-tiled descriptor kernel (same descriptors, same forces)."""
 import numpy as np
 import pytest
 
@@ -21,7 +22,7 @@ def api():
     return pkg
 
 
-@pytest.mark.parametrize("variant", ["float_scatter", "tile1", "tile3"])
+@pytest.mark.parametrize("variant", ["float_scatter", "tile1", "tile3", "half_list"])
 def test_variant_forces(api, model_params, model, variant):
     wl = ni.fcc_cu_workload(6, 300.0, 0.05, seed=91)
     with api.NEP(model_params) as nep:

@@ -158,6 +158,26 @@ struct FourBody {
   float xx[S::NA], yy[S::NA], zz[S::NA], xy[S::NA], yz[S::NA], xz[S::NA];
 };
 
+// Traceless T_n from the l = 2 sums s2[n][m] (components 3..7 of s_nl m, m = -2..2) and the 4-body
+// descriptors q4_n = tr(T_n^3) = 3 det T_n, written to q[NR + NA LMAX + n].
+template <class S>
+__device__ __forceinline__ void fourbody_tensors(const float (&s2)[S::NA][5], FourBody<S> &T, float (&q)[S::NDES]) {
+  const float i3 = 0.57735026918962576f, third = 1.f / 3.f;
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) {
+    T.xy[a] = s2[a][0] * i3;
+    T.yz[a] = s2[a][1] * i3;
+    T.xz[a] = s2[a][3] * i3;
+    T.xx[a] = s2[a][4] * i3 - s2[a][2] * third;
+    T.yy[a] = -s2[a][4] * i3 - s2[a][2] * third;
+    T.zz[a] = 2.f * s2[a][2] * third;
+    const float det = T.xx[a] * (T.yy[a] * T.zz[a] - T.yz[a] * T.yz[a]) -
+                      T.xy[a] * (T.xy[a] * T.zz[a] - T.yz[a] * T.xz[a]) +
+                      T.xz[a] * (T.xy[a] * T.yz[a] - T.yy[a] * T.xz[a]);
+    q[S::NR + S::NA * S::LMAX + a] = 3.f * det;
+  }
+}
+
 // Descriptors [q_n | q_nl (n-major, l = 1..LMAX) | q4_n = tr(T_n^3) = 3 det T_n (teacher shape only)].
 template <class S>
 __device__ __forceinline__ void descriptors_of(const Model<S> &P, const AtomSums<S> &A, float (&q)[S::NDES],
@@ -180,21 +200,39 @@ __device__ __forceinline__ void descriptors_of(const Model<S> &P, const AtomSums
     }
   }
   if constexpr (S::FOURBODY) {
-    const float i3 = 0.57735026918962576f, third = 1.f / 3.f;
+    float s2[S::NA][5];
 #pragma unroll
-    for (int a = 0; a < S::NA; ++a) {
-      T.xy[a] = A.s[a][3] * i3;
-      T.yz[a] = A.s[a][4] * i3;
-      T.xz[a] = A.s[a][6] * i3;
-      T.xx[a] = A.s[a][7] * i3 - A.s[a][5] * third;
-      T.yy[a] = -A.s[a][7] * i3 - A.s[a][5] * third;
-      T.zz[a] = 2.f * A.s[a][5] * third;
-      const float det = T.xx[a] * (T.yy[a] * T.zz[a] - T.yz[a] * T.yz[a]) -
-                        T.xy[a] * (T.xy[a] * T.zz[a] - T.yz[a] * T.xz[a]) +
-                        T.xz[a] * (T.xy[a] * T.yz[a] - T.yy[a] * T.xz[a]);
-      q[S::NR + S::NA * S::LMAX + a] = 3.f * det;
-    }
+    for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+      for (int m = 0; m < 5; ++m) s2[a][m] = A.s[a][3 + m];
+    fourbody_tensors<S>(s2, T, q);
   }
+}
+
+// The one-hidden-layer network (Section III.B equation): U = sum_mu w1_mu tanh(sum_nu W0_mu,nu q~_nu -
+// b0_mu) - b1 with q~ = q_scale q; returns U and Fp_nu = dU/dq_nu (zero for an atom flagged for the
+// fallback model, whose site energy comes from the other model).
+template <class S>
+__device__ __forceinline__ float network(const Model<S> &P, const float (&q)[S::NDES], bool flagged,
+                                         float (&Fp)[S::NDES]) {
+  float qt[S::NDES], dq[S::NDES];
+#pragma unroll
+  for (int v = 0; v < S::NDES; ++v) { qt[v] = q[v] * P.qs[v]; dq[v] = 0.f; }
+  float U = -P.b1;
+#pragma unroll
+  for (int mu = 0; mu < S::NNEU; ++mu) {
+    float z = -P.b0[mu];
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) z = fmaf(P.W0[mu][v], qt[v], z);
+    const float h = tanhf(z);
+    U = fmaf(P.w1[mu], h, U);
+    const float t = P.w1[mu] * (1.f - h * h);
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) dq[v] = fmaf(t, P.W0[mu][v], dq[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < S::NDES; ++v) Fp[v] = flagged ? 0.f : dq[v] * P.qs[v];
+  return U;
 }
 
 // Radial adjoint in basis space, stored in the row tail: tail_k = dU/dQR_k = sum_n Fp_n cR_nk, so the
@@ -212,6 +250,24 @@ __device__ __forceinline__ void radial_tail(const Model<S> &P, const float (&Fp)
   }
 }
 
+// 4-body part of the adjoint of channel a for the l = 2 components 3..7, per unit dU/dq4_a:
+// d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m.
+template <class S>
+__device__ __forceinline__ void fourbody_adjoint(int a, const FourBody<S> &T, float (&g4)[5]) {
+  const float Mxx = T.xx[a] * T.xx[a] + T.xy[a] * T.xy[a] + T.xz[a] * T.xz[a];
+  const float Myy = T.xy[a] * T.xy[a] + T.yy[a] * T.yy[a] + T.yz[a] * T.yz[a];
+  const float Mzz = T.xz[a] * T.xz[a] + T.yz[a] * T.yz[a] + T.zz[a] * T.zz[a];
+  const float Mxy = T.xx[a] * T.xy[a] + T.xy[a] * T.yy[a] + T.xz[a] * T.yz[a];
+  const float Myz = T.xy[a] * T.xz[a] + T.yy[a] * T.yz[a] + T.yz[a] * T.zz[a];
+  const float Mxz = T.xx[a] * T.xz[a] + T.xy[a] * T.yz[a] + T.xz[a] * T.zz[a];
+  const float s3 = 1.7320508075688772f;
+  g4[0] = 2.f * s3 * Mxy;
+  g4[1] = 2.f * s3 * Myz;
+  g4[2] = 2.f * Mzz - Mxx - Myy;
+  g4[3] = 2.f * s3 * Mxz;
+  g4[4] = s3 * (Mxx - Myy);
+}
+
 // Adjoint of channel a: gl[c] = dU/ds_{a,c} = 2 Fp_{a,l(c)} s_{a,c} (+ 4-body gradient for l = 2:
 // d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m).
 template <class S>
@@ -221,18 +277,10 @@ __device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, con
   for (int c = 0; c < S::NLM; ++c) gl[c] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(c) - 1] * A.s[a][c];
   if constexpr (S::FOURBODY) {
     const float f4 = Fp[S::NR + S::NA * S::LMAX + a];
-    const float Mxx = T.xx[a] * T.xx[a] + T.xy[a] * T.xy[a] + T.xz[a] * T.xz[a];
-    const float Myy = T.xy[a] * T.xy[a] + T.yy[a] * T.yy[a] + T.yz[a] * T.yz[a];
-    const float Mzz = T.xz[a] * T.xz[a] + T.yz[a] * T.yz[a] + T.zz[a] * T.zz[a];
-    const float Mxy = T.xx[a] * T.xy[a] + T.xy[a] * T.yy[a] + T.xz[a] * T.yz[a];
-    const float Myz = T.xy[a] * T.xz[a] + T.yy[a] * T.yz[a] + T.yz[a] * T.zz[a];
-    const float Mxz = T.xx[a] * T.xz[a] + T.xy[a] * T.yz[a] + T.xz[a] * T.zz[a];
-    const float s3 = 1.7320508075688772f;
-    gl[3] = fmaf(f4, 2.f * s3 * Mxy, gl[3]);
-    gl[4] = fmaf(f4, 2.f * s3 * Myz, gl[4]);
-    gl[5] = fmaf(f4, 2.f * Mzz - Mxx - Myy, gl[5]);
-    gl[6] = fmaf(f4, 2.f * s3 * Mxz, gl[6]);
-    gl[7] = fmaf(f4, s3 * (Mxx - Myy), gl[7]);
+    float g4[5];
+    fourbody_adjoint<S>(a, T, g4);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) gl[3 + m] = fmaf(f4, g4[m], gl[3 + m]);
   }
 }
 

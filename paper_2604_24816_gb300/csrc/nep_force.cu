@@ -1,7 +1,9 @@
 // nep_force.cu -- NEP descriptors, network and chain-rule forces on sm_103a.
 //
 // Two kernels per force evaluation, one thread per atom (cell-sorted order), both reading the
-// distance-sorted neighbour list of nep_neighbor.cu:
+// distance-sorted neighbour list of nep_neighbor.cu.  For the teacher shape both keep their 120-value
+// per-atom arrays (the sums s_nlm, the adjoint row G_i) in tensor memory (TMEM) rather than registers,
+// which doubles (descriptor) or 1.5x (force) the resident warps:
 //
 //  k_descriptor  radial descriptors q_n (Section III.B), shifted-force LJ energy, angular sums
 //                s_nlm = sum_j g_n(r_ij) Yh_lm(u_ij) for l = 1..4 (24 (l,m) components per channel,
@@ -82,25 +84,8 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     const bool flagged = fb.on && out_of_range<S>(fb, P, q);
     if (flagged) flag_atom(fb, i, status);
 
-    // Network: U = sum_mu w1 tanh(sum_nu W0 q~_nu - b0) - b1; dU/dq~ accumulated in dq.
-    float qt[S::NDES], dq[S::NDES];
-#pragma unroll
-    for (int v = 0; v < S::NDES; ++v) { qt[v] = q[v] * P.qs[v]; dq[v] = 0.f; }
-    float U = -P.b1;
-#pragma unroll
-    for (int mu = 0; mu < S::NNEU; ++mu) {
-      float z = -P.b0[mu];
-#pragma unroll
-      for (int v = 0; v < S::NDES; ++v) z = fmaf(P.W0[mu][v], qt[v], z);
-      const float h = tanhf(z);
-      U = fmaf(P.w1[mu], h, U);
-      const float t = P.w1[mu] * (1.f - h * h);
-#pragma unroll
-      for (int v = 0; v < S::NDES; ++v) dq[v] = fmaf(t, P.W0[mu][v], dq[v]);
-    }
     float Fp[S::NDES];
-#pragma unroll
-    for (int v = 0; v < S::NDES; ++v) Fp[v] = flagged ? 0.f : dq[v] * P.qs[v];   // flagged: no U_i here
+    const float U = network<S>(P, q, flagged, Fp);   // flagged: no U_i from this model
 
     float *Gi = G + (size_t)i * S::GS;
 #pragma unroll
@@ -125,6 +110,207 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
     acc[2] = A.nang;
     acc[3] = A.cnt;
     acc[4] = A.nact;
+  }
+  block_sum_store<5, DESC_BLOCK / 32>(acc, part);
+}
+
+// Teacher-shape descriptor kernel with the 120 angular sums s_nlm accumulated in tensor memory (TMEM)
+// instead of registers, so that 4 blocks fit per SM instead of 2 (128 registers, 4 x 128 TMEM columns).  Layout as for the force kernel's
+// adjoint row: s[a][lm] at TMEM column (lm - lm mod 4) NA + 4 a + lm mod 4 of the thread's lane; each
+// angular pair reads, updates and writes back one chunk of 4 components x NA channels at a time.
+// The pair loop runs to the warp's longest row (see k_force) so that the warp-collective TMEM
+// accesses are made by whole warps; lanes without an angular pair add g = 0.
+#ifndef NEP_DESC_MINB_TM
+#define NEP_DESC_MINB_TM 4
+#endif
+template <class S>
+__global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB_TM)
+k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
+                const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
+                float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
+                long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
+  static_assert(S::NA == 5 && S::NLM == 24 && S::FOURBODY && DESC_BLOCK == 128, "teacher shape, 4 warps");
+  constexpr int W = 4;
+  constexpr uint32_t TCOLS = 128;
+  __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
+  __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
+  __shared__ uint32_t tmem_base;
+  if (threadIdx.x < 32) tmem_alloc(&tmem_base, TCOLS);
+  tc_fence_before();
+  fill_shift_table(shift, geom);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  const int ii = live ? i : 0;
+  long long acc[5] = {0, 0, 0, 0, 0};
+  if (live) { Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0; }
+  {
+    const float z[W] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < S::NLM; c += W)
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) tmem_st(trow + (uint32_t)(c * S::NA + a * W), z);
+    tmem_wait_st();
+  }
+  float QR[S::KR];
+#pragma unroll
+  for (int k = 0; k < S::KR; ++k) QR[k] = 0.f;
+  float elj = 0.f;
+  int nrad = 0, nang = 0, nact = 0;
+  const int cnt = live ? nnum[i] : 0;
+  const float4 pi = pos[ii];
+  NbrPipe<PIPE_DE, PIPE_DP, DESC_BLOCK> pipe;
+  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, cnt);
+  const int trip = __reduce_max_sync(0xffffffffu, cnt);
+  for (int k = 0; k < trip; ++k) {
+    const bool valid = k < cnt;
+    uint32_t e = 0u;
+    float4 pj = pi;
+    if (valid) pipe.get(k, e, pj);
+    const float4 o = shift[e >> J_BITS];
+    const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const bool act = valid && r2 < P.rmax2;
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    if (act) {
+      ++nact;
+      if (r2 < P.rcR2) {
+        float f[S::KR];
+        cheb_basis<S::KR>(r, P.inv_rcR, f);
+#pragma unroll
+        for (int b = 0; b < S::KR; ++b) QR[b] += f[b];
+        ++nrad;
+      }
+      if (P.lj_on != 0.f && r2 < P.lj_rc2) {
+        float el, dl;
+        lj_pair<S>(P, r2, r, ir, el, dl);
+        elj = fmaf(0.5f, el, elj);
+      }
+    }
+    const bool ang = act && r2 < P.rcA2;
+    if (__any_sync(0xffffffffu, ang)) {
+      __syncwarp();
+      const float ar = ang ? r : 1.f;
+      const float ux = ang ? dx * ir : 1.f, uy = ang ? dy * ir : 0.f, uz = ang ? dz * ir : 0.f;
+      float f[S::KA];
+      cheb_basis<S::KA>(ar, P.inv_rcA, f);
+      float g[S::NA];
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) {
+        float t = 0.f;
+#pragma unroll
+        for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
+        g[a] = ang ? t : 0.f;
+      }
+      float Y[S::NLM];
+      harmonics<S::NLM>(ux, uy, uz, Y);
+#pragma unroll
+      for (int c = 0; c < S::NLM; c += W) {
+        uint32_t cols[S::NA];
+#pragma unroll
+        for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
+        float sv[S::NA][W];
+        tmem_ld5(cols, sv);
+#pragma unroll
+        for (int a = 0; a < S::NA; ++a) {
+#pragma unroll
+          for (int cc = 0; cc < W; ++cc) sv[a][cc] = fmaf(g[a], Y[c + cc], sv[a][cc]);
+          tmem_st(cols[a], sv[a]);
+        }
+      }
+      tmem_wait_st();
+      if (ang) ++nang;
+    }
+  }
+  pipe.finish();
+
+  // descriptors: radial from the basis sums, angular q_nl = sum_m s_nlm^2, 4-body from the l = 2 sums
+  float q[S::NDES];
+#pragma unroll
+  for (int a = 0; a < S::NR; ++a) {
+    float t = 0.f;
+#pragma unroll
+    for (int b = 0; b < S::KR; ++b) t = fmaf(P.cR[a][b], QR[b], t);
+    q[a] = t;
+  }
+#pragma unroll
+  for (int v = S::NR; v < S::NR + S::NA * S::LMAX; ++v) q[v] = 0.f;
+  float s2[S::NA][5];
+#pragma unroll
+  for (int c = 0; c < S::NLM; c += W) {
+    uint32_t cols[S::NA];
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
+    float sv[S::NA][W];
+    tmem_ld5(cols, sv);
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+      for (int cc = 0; cc < W; ++cc) {
+        const int lm = c + cc;
+        float &ql = q[S::NR + a * S::LMAX + lm_l(lm) - 1];
+        ql = fmaf(sv[a][cc], sv[a][cc], ql);
+        if (lm >= 3 && lm < 8) s2[a][lm - 3] = sv[a][cc];
+      }
+  }
+  FourBody<S> T;
+  fourbody_tensors<S>(s2, T, q);
+  if (live && qout != nullptr) {
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
+  }
+  const bool flagged = live && fb.on && out_of_range<S>(fb, P, q);
+  if (flagged) flag_atom(fb, i, status);
+  float Fp[S::NDES];
+  const float U = network<S>(P, q, flagged, Fp);
+
+  // adjoint row: G[a][lm] = 2 Fp_{a,l} s_{a,lm} (+ 4-body terms for l = 2), then the radial tail
+  float *Gi = G + (size_t)ii * S::GS;
+  float g4[S::NA][5];
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
+#pragma unroll
+  for (int c = 0; c < S::NLM; c += W) {
+    uint32_t cols[S::NA];
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
+    float sv[S::NA][W];
+    tmem_ld5(cols, sv);
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) {
+      float gl[W];
+#pragma unroll
+      for (int cc = 0; cc < W; ++cc) {
+        const int lm = c + cc;
+        gl[cc] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(lm) - 1] * sv[a][cc];
+        if (lm >= 3 && lm < 8) gl[cc] = fmaf(Fp[S::NR + S::NA * S::LMAX + a], g4[a][lm - 3], gl[cc]);
+      }
+      if (live) *reinterpret_cast<float4 *>(Gi + a * S::NLM + c) = make_float4(gl[0], gl[1], gl[2], gl[3]);
+    }
+  }
+  if (live) {
+    float tail[8];
+    radial_tail<S>(P, Fp, tail);
+    *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM) = make_float4(tail[0], tail[1], tail[2], tail[3]);
+    *reinterpret_cast<float4 *>(Gi + S::NA * S::NLM + 4) = make_float4(tail[4], tail[5], tail[6], tail[7]);
+    const float ui = flagged ? elj : U + elj;
+    usite[i] = ui;
+    if (!isfinite(ui)) atomicOr(status, ST_NAN);
+    acc[0] = to_fix32(ui);
+    acc[1] = nrad;
+    acc[2] = nang;
+    acc[3] = cnt;
+    acc[4] = nact;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TCOLS);
   }
   block_sum_store<5, DESC_BLOCK / 32>(acc, part);
 }
@@ -373,13 +559,19 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 // ---------------------------------------------------------------------------------------------------
 // Host launchers (called from nep_api.cu).
 
+#ifndef NEP_DESC_TM
+#define NEP_DESC_TM 1
+#endif
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
                               const int32_t *nnum, float *G, float *usite, float *qout, long long *Ffix,
                               long long *part, int *status, const Fallback &fb, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
-  k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status, fb);
+  if constexpr (ForceCfg<S>::TM && NEP_DESC_TM)
+    k_descriptor_tm<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status, fb);
+  else
+    k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status, fb);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 
 #include "nep_common.cuh"
+#include "nep_tc.cuh"
 
 namespace nep {
 
@@ -281,6 +282,158 @@ __device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, con
     fourbody_adjoint<S>(a, T, g4);
 #pragma unroll
     for (int m = 0; m < 5; ++m) gl[3 + m] = fmaf(f4, g4[m], gl[3 + m]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Teacher shape with the 120 angular sums s_nlm in tensor memory (TMEM) instead of registers: s[a][lm]
+// at column (lm - lm mod 4) NA + 4 a + lm mod 4 of the thread's lane (TMEM_W = 4 components x NA
+// channels per chunk, the same layout as the force kernel's adjoint row).  All TMEM accesses are
+// warp-collective, so the neighbour walk runs to the warp's longest row (threads past their own row,
+// or past the last atom, idle with a predicate) and the angular update is made by whole warps, lanes
+// without an angular pair adding g = 0.
+constexpr int TMEM_W = 4;
+
+template <class S>
+__device__ __forceinline__ void tmem_chunk_cols(uint32_t trow, int c, uint32_t (&cols)[S::NA]) {
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * TMEM_W);
+}
+
+// Zero the sums, then walk atom ii's row (cnt entries; cnt = 0 for threads past the last atom):
+// radial basis sums QR and the LJ energy in registers, s_nlm in TMEM.
+template <class S, int DE, int DP, int BLOCK>
+__device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const float4 *shift, uint32_t trow, int ii,
+                                                   int n, const float4 *__restrict__ pos,
+                                                   const int32_t *__restrict__ nbr, int cnt, uint32_t *ring_e,
+                                                   float4 *ring_p, float (&QR)[S::KR], float &elj, int &nrad,
+                                                   int &nang, int &nact) {
+  static_assert(S::NA == 5 && S::NLM == 24, "teacher shape");
+  constexpr int W = TMEM_W;
+  {
+    const float z[W] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < S::NLM; c += W)
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) tmem_st(trow + (uint32_t)(c * S::NA + a * W), z);
+    tmem_wait_st();
+  }
+#pragma unroll
+  for (int k = 0; k < S::KR; ++k) QR[k] = 0.f;
+  elj = 0.f;
+  nrad = 0; nang = 0; nact = 0;
+  const float4 pi = pos[ii];
+  NbrPipe<DE, DP, BLOCK> pipe;
+  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, cnt);
+  const int trip = __reduce_max_sync(0xffffffffu, cnt);
+  for (int k = 0; k < trip; ++k) {
+    const bool valid = k < cnt;
+    uint32_t e = 0u;
+    float4 pj = pi;
+    if (valid) pipe.get(k, e, pj);
+    const float4 o = shift[e >> J_BITS];
+    const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const bool act = valid && r2 < P.rmax2;
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    if (act) {
+      ++nact;
+      if (r2 < P.rcR2) {
+        float f[S::KR];
+        cheb_basis<S::KR>(r, P.inv_rcR, f);
+#pragma unroll
+        for (int b = 0; b < S::KR; ++b) QR[b] += f[b];
+        ++nrad;
+      }
+      if (P.lj_on != 0.f && r2 < P.lj_rc2) {
+        float el, dl;
+        lj_pair<S>(P, r2, r, ir, el, dl);
+        elj = fmaf(0.5f, el, elj);
+      }
+    }
+    const bool ang = act && r2 < P.rcA2;
+    if (__any_sync(0xffffffffu, ang)) {
+      __syncwarp();
+      const float ar = ang ? r : 1.f;
+      const float ux = ang ? dx * ir : 1.f, uy = ang ? dy * ir : 0.f, uz = ang ? dz * ir : 0.f;
+      float f[S::KA];
+      cheb_basis<S::KA>(ar, P.inv_rcA, f);
+      float g[S::NA];
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) {
+        float t = 0.f;
+#pragma unroll
+        for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
+        g[a] = ang ? t : 0.f;
+      }
+      float Y[S::NLM];
+      harmonics<S::NLM>(ux, uy, uz, Y);
+#pragma unroll
+      for (int c = 0; c < S::NLM; c += W) {
+        uint32_t cols[S::NA];
+        tmem_chunk_cols<S>(trow, c, cols);
+        float sv[S::NA][W];
+        tmem_ld5(cols, sv);
+#pragma unroll
+        for (int a = 0; a < S::NA; ++a) {
+#pragma unroll
+          for (int cc = 0; cc < W; ++cc) sv[a][cc] = fmaf(g[a], Y[c + cc], sv[a][cc]);
+          tmem_st(cols[a], sv[a]);
+        }
+      }
+      tmem_wait_st();
+      if (ang) ++nang;
+    }
+  }
+  pipe.finish();
+}
+
+// Descriptors from the radial basis sums and the TMEM sums (q_nl = sum_m s_nlm^2, 4-body from the
+// l = 2 sums), as descriptors_of.
+template <class S>
+__device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow, const float (&QR)[S::KR],
+                                               float (&q)[S::NDES], FourBody<S> &T) {
+  constexpr int W = TMEM_W;
+#pragma unroll
+  for (int a = 0; a < S::NR; ++a) {
+    float t = 0.f;
+#pragma unroll
+    for (int b = 0; b < S::KR; ++b) t = fmaf(P.cR[a][b], QR[b], t);
+    q[a] = t;
+  }
+#pragma unroll
+  for (int v = S::NR; v < S::NR + S::NA * S::LMAX; ++v) q[v] = 0.f;
+  float s2[S::NA][5];
+#pragma unroll
+  for (int c = 0; c < S::NLM; c += W) {
+    uint32_t cols[S::NA];
+    tmem_chunk_cols<S>(trow, c, cols);
+    float sv[S::NA][W];
+    tmem_ld5(cols, sv);
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+      for (int cc = 0; cc < W; ++cc) {
+        const int lm = c + cc;
+        float &ql = q[S::NR + a * S::LMAX + lm_l(lm) - 1];
+        ql = fmaf(sv[a][cc], sv[a][cc], ql);
+        if (lm >= 3 && lm < 8) s2[a][lm - 3] = sv[a][cc];
+      }
+  }
+  fourbody_tensors<S>(s2, T, q);
+}
+
+// The adjoint of components c..c+3 of channel a, gl = 2 Fp_{a,l} s + (4-body terms for l = 2), as
+// adjoint_channel; g4 = fourbody_adjoint of channel a.
+template <class S>
+__device__ __forceinline__ void adjoint_chunk(int a, int c, const float (&sv)[TMEM_W], const float (&g4)[5],
+                                              const float (&Fp)[S::NDES], float (&gl)[TMEM_W]) {
+#pragma unroll
+  for (int cc = 0; cc < TMEM_W; ++cc) {
+    const int lm = c + cc;
+    gl[cc] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(lm) - 1] * sv[cc];
+    if (S::FOURBODY && lm >= 3 && lm < 8) gl[cc] = fmaf(Fp[S::NR + S::NA * S::LMAX + a], g4[lm - 3], gl[cc]);
   }
 }
 

@@ -115,11 +115,8 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 }
 
 // Teacher-shape descriptor kernel with the 120 angular sums s_nlm accumulated in tensor memory (TMEM)
-// instead of registers, so that 4 blocks fit per SM instead of 2 (128 registers, 4 x 128 TMEM columns).  Layout as for the force kernel's
-// adjoint row: s[a][lm] at TMEM column (lm - lm mod 4) NA + 4 a + lm mod 4 of the thread's lane; each
-// angular pair reads, updates and writes back one chunk of 4 components x NA channels at a time.
-// The pair loop runs to the warp's longest row (see k_force) so that the warp-collective TMEM
-// accesses are made by whole warps; lanes without an angular pair add g = 0.
+// instead of registers (accumulate_atom_tm), so that 4 blocks fit per SM instead of 2 (128 registers,
+// 4 x 128 TMEM columns).
 #ifndef NEP_DESC_MINB_TM
 #define NEP_DESC_MINB_TM 4
 #endif
@@ -130,7 +127,7 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
                 float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
                 long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   static_assert(S::NA == 5 && S::NLM == 24 && S::FOURBODY && DESC_BLOCK == 128, "teacher shape, 4 warps");
-  constexpr int W = 4;
+  constexpr int W = TMEM_W;
   constexpr uint32_t TCOLS = 128;
   __shared__ float4 shift[27];
   __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
@@ -147,118 +144,14 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   const int ii = live ? i : 0;
   long long acc[5] = {0, 0, 0, 0, 0};
   if (live) { Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0; }
-  {
-    const float z[W] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int c = 0; c < S::NLM; c += W)
-#pragma unroll
-      for (int a = 0; a < S::NA; ++a) tmem_st(trow + (uint32_t)(c * S::NA + a * W), z);
-    tmem_wait_st();
-  }
-  float QR[S::KR];
-#pragma unroll
-  for (int k = 0; k < S::KR; ++k) QR[k] = 0.f;
-  float elj = 0.f;
-  int nrad = 0, nang = 0, nact = 0;
   const int cnt = live ? nnum[i] : 0;
-  const float4 pi = pos[ii];
-  NbrPipe<PIPE_DE, PIPE_DP, DESC_BLOCK> pipe;
-  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, cnt);
-  const int trip = __reduce_max_sync(0xffffffffu, cnt);
-  for (int k = 0; k < trip; ++k) {
-    const bool valid = k < cnt;
-    uint32_t e = 0u;
-    float4 pj = pi;
-    if (valid) pipe.get(k, e, pj);
-    const float4 o = shift[e >> J_BITS];
-    const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const bool act = valid && r2 < P.rmax2;
-    const float ir = rsqrtf(r2);
-    const float r = r2 * ir;
-    if (act) {
-      ++nact;
-      if (r2 < P.rcR2) {
-        float f[S::KR];
-        cheb_basis<S::KR>(r, P.inv_rcR, f);
-#pragma unroll
-        for (int b = 0; b < S::KR; ++b) QR[b] += f[b];
-        ++nrad;
-      }
-      if (P.lj_on != 0.f && r2 < P.lj_rc2) {
-        float el, dl;
-        lj_pair<S>(P, r2, r, ir, el, dl);
-        elj = fmaf(0.5f, el, elj);
-      }
-    }
-    const bool ang = act && r2 < P.rcA2;
-    if (__any_sync(0xffffffffu, ang)) {
-      __syncwarp();
-      const float ar = ang ? r : 1.f;
-      const float ux = ang ? dx * ir : 1.f, uy = ang ? dy * ir : 0.f, uz = ang ? dz * ir : 0.f;
-      float f[S::KA];
-      cheb_basis<S::KA>(ar, P.inv_rcA, f);
-      float g[S::NA];
-#pragma unroll
-      for (int a = 0; a < S::NA; ++a) {
-        float t = 0.f;
-#pragma unroll
-        for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
-        g[a] = ang ? t : 0.f;
-      }
-      float Y[S::NLM];
-      harmonics<S::NLM>(ux, uy, uz, Y);
-#pragma unroll
-      for (int c = 0; c < S::NLM; c += W) {
-        uint32_t cols[S::NA];
-#pragma unroll
-        for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
-        float sv[S::NA][W];
-        tmem_ld5(cols, sv);
-#pragma unroll
-        for (int a = 0; a < S::NA; ++a) {
-#pragma unroll
-          for (int cc = 0; cc < W; ++cc) sv[a][cc] = fmaf(g[a], Y[c + cc], sv[a][cc]);
-          tmem_st(cols[a], sv[a]);
-        }
-      }
-      tmem_wait_st();
-      if (ang) ++nang;
-    }
-  }
-  pipe.finish();
-
-  // descriptors: radial from the basis sums, angular q_nl = sum_m s_nlm^2, 4-body from the l = 2 sums
+  float QR[S::KR], elj;
+  int nrad, nang, nact;
+  accumulate_atom_tm<S, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, cnt, ring_e, ring_p, QR, elj,
+                                                      nrad, nang, nact);
   float q[S::NDES];
-#pragma unroll
-  for (int a = 0; a < S::NR; ++a) {
-    float t = 0.f;
-#pragma unroll
-    for (int b = 0; b < S::KR; ++b) t = fmaf(P.cR[a][b], QR[b], t);
-    q[a] = t;
-  }
-#pragma unroll
-  for (int v = S::NR; v < S::NR + S::NA * S::LMAX; ++v) q[v] = 0.f;
-  float s2[S::NA][5];
-#pragma unroll
-  for (int c = 0; c < S::NLM; c += W) {
-    uint32_t cols[S::NA];
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
-    float sv[S::NA][W];
-    tmem_ld5(cols, sv);
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a)
-#pragma unroll
-      for (int cc = 0; cc < W; ++cc) {
-        const int lm = c + cc;
-        float &ql = q[S::NR + a * S::LMAX + lm_l(lm) - 1];
-        ql = fmaf(sv[a][cc], sv[a][cc], ql);
-        if (lm >= 3 && lm < 8) s2[a][lm - 3] = sv[a][cc];
-      }
-  }
   FourBody<S> T;
-  fourbody_tensors<S>(s2, T, q);
+  descriptors_tm<S>(P, trow, QR, q, T);
   if (live && qout != nullptr) {
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
@@ -268,7 +161,7 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   float Fp[S::NDES];
   const float U = network<S>(P, q, flagged, Fp);
 
-  // adjoint row: G[a][lm] = 2 Fp_{a,l} s_{a,lm} (+ 4-body terms for l = 2), then the radial tail
+  // adjoint row from the TMEM sums, then the radial tail
   float *Gi = G + (size_t)ii * S::GS;
   float g4[S::NA][5];
 #pragma unroll
@@ -276,19 +169,13 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
 #pragma unroll
   for (int c = 0; c < S::NLM; c += W) {
     uint32_t cols[S::NA];
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
+    tmem_chunk_cols<S>(trow, c, cols);
     float sv[S::NA][W];
     tmem_ld5(cols, sv);
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
       float gl[W];
-#pragma unroll
-      for (int cc = 0; cc < W; ++cc) {
-        const int lm = c + cc;
-        gl[cc] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(lm) - 1] * sv[a][cc];
-        if (lm >= 3 && lm < 8) gl[cc] = fmaf(Fp[S::NR + S::NA * S::LMAX + a], g4[a][lm - 3], gl[cc]);
-      }
+      adjoint_chunk<S>(a, c, sv[a], g4[a], Fp, gl);
       if (live) *reinterpret_cast<float4 *>(Gi + a * S::NLM + c) = make_float4(gl[0], gl[1], gl[2], gl[3]);
     }
   }

@@ -41,9 +41,15 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
                    long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   static_assert(S::NDES <= MIX_K && S::NNEU <= MIX_N, "network larger than one tensor-core tile");
   __shared__ float4 shift[27];
-  __shared__ uint32_t ring_e[MIX_DE * MIX_BLOCK];
-  __shared__ float4 ring_p[MIX_DP * MIX_BLOCK];
-  __shared__ __align__(1024) MT sA[MIX_BLOCK * MIX_K];     // A tile: q~ rows, then T rows
+  // The neighbour-pipeline ring is dead once every thread has walked its row, so the GEMMs' A tile
+  // (q~ rows, then T rows) overlays it: less shared memory per block leaves more of the unified
+  // L1/shared storage to L1, which caches the gathered neighbour positions.
+  constexpr int RING_BYTES = MIX_DP * MIX_BLOCK * 16 + MIX_DE * MIX_BLOCK * 4;
+  constexpr int A_BYTES = MIX_BLOCK * MIX_K * (int)sizeof(MT);
+  __shared__ __align__(1024) unsigned char smem_ring[RING_BYTES > A_BYTES ? RING_BYTES : A_BYTES];
+  float4 *ring_p = reinterpret_cast<float4 *>(smem_ring);
+  uint32_t *ring_e = reinterpret_cast<uint32_t *>(smem_ring + MIX_DP * MIX_BLOCK * 16);
+  MT *sA = reinterpret_cast<MT *>(smem_ring);
   __shared__ __align__(1024) MT sW[MIX_N * MIX_K];         // B of the forward GEMM: W0[neuron][descriptor]
   __shared__ __align__(1024) MT sWt[MIX_K * MIX_N];        // B of the backward GEMM: W0[descriptor][neuron]
   __shared__ __align__(8) uint64_t mbar;
@@ -82,6 +88,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) q[v] = 0.f;
   }
+  __syncthreads();     // every thread's row walk (and its ring copies) is done before the A tile overlays the ring
 #pragma unroll
   for (int k = 0; k < MIX_K; ++k) sA[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>(k < S::NDES ? q[k] * P.qs[k] : 0.f);
   fence_async_smem();
@@ -164,7 +171,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   tc_fence_before();
   __syncthreads();
   if (t < 32) tmem_dealloc(tmem, 64);
-  block_sum_store<5>(acc, part);
+  block_sum_store<5, MIX_BLOCK / 32>(acc, part);
 }
 
 template <class S, class MT>

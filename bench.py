@@ -90,14 +90,14 @@ def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) ->
 
 # The sources each profiled kernel is built from: a committed traffic figure is used only while they
 # are unchanged (kernel names as in profiles/traffic_per_launch.txt; ":form" for the non-plain forms).
-_CORE = ("nep_common.cuh", "nep_descriptor.cuh")
+_CORE = ("nep_common.cuh", "nep_descriptor.cuh", "nep_tc.cuh")
 KERNEL_SOURCES = {
     "neighbors": ("nep_neighbor.cu", "nep_common.cuh"),
     "descriptor": ("nep_force.cu",) + _CORE,
     "force": ("nep_force.cu",) + _CORE,
-    "descriptor:mix_bf16": ("nep_mixed.cu", "nep_tc.cuh") + _CORE,
+    "descriptor:mix_bf16": ("nep_mixed.cu",) + _CORE,
     "force:mix_bf16": ("nep_force.cu",) + _CORE,
-    "descriptor:student_bf16_fallback": ("nep_mixed.cu", "nep_tc.cuh", "nep_fallback.cu") + _CORE,
+    "descriptor:student_bf16_fallback": ("nep_mixed.cu", "nep_fallback.cu") + _CORE,
     "force:student_bf16_fallback": ("nep_force.cu", "nep_fallback.cu") + _CORE,
 }
 SOURCE_FILES = tuple(sorted({f for v in KERNEL_SOURCES.values() for f in v}))

@@ -204,8 +204,9 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
 
 // Adjoint row G_i of the force kernel: in registers for small shapes; for the teacher shape (120
 // angular values) it is parked in tensor memory (TMEM) and read back one chunk of lm components at a
-// time.  TMEM is per-SM storage outside L1, so this halves the register footprint (2 -> 4 resident
-// blocks) without taking L1 capacity from the gathered neighbour rows G_j.
+// time.  TMEM is per-SM storage outside L1, so this cuts the register footprint (255 -> 128-168
+// registers: 4 resident blocks for the full-row form, 3 for the half list) without taking L1 capacity
+// from the gathered neighbour data.
 #ifndef NEP_FORCE_MINB_TM
 #define NEP_FORCE_MINB_TM 3
 #endif
@@ -231,8 +232,11 @@ struct ForceCfg {
 // count, or past the last atom, idle with a predicate) so that the angular block, which holds the
 // warp-collective TMEM loads, is entered by whole warps: lanes without an angular pair in that
 // iteration compute on a harmless stand-in pair and discard the result.
+#ifndef NEP_FORCE_MINB_FULL
+#define NEP_FORCE_MINB_FULL 4
+#endif
 template <class S, class GT, bool FS = false, bool FULL = false>
-__global__ void __launch_bounds__(FORCE_BLOCK, ForceCfg<S>::MINB)
+__global__ void __launch_bounds__(FORCE_BLOCK, FULL && ForceCfg<S>::TM ? NEP_FORCE_MINB_FULL : ForceCfg<S>::MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
         const int32_t *__restrict__ nbr, const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
         const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,

@@ -102,8 +102,12 @@ nep_status nep_destroy(nep_handle *h);
 
 /* Load a configuration.  x: [n][3] positions (need not be wrapped), v: [n][3] velocities in
  * Angstrom/fs or NULL for zero, box: host [3] edge lengths.  Allocates device buffers for n atoms
- * (kept when n and the box are unchanged since the last call) and invalidates the neighbour list and
- * forces.  n = 0 is accepted (every later call is a no-op). */
+ * (kept when n and the box are unchanged since the last call) and invalidates the forces.  When n and
+ * the box are unchanged and a neighbour list exists, the list and the internal cell order are kept:
+ * the next evaluation rebuilds the list only if an atom moved more than skin/2 from the positions it
+ * was built for (the same test as between MD steps; positions are taken at their periodic image
+ * nearest the previous ones).  Otherwise the neighbour list is invalidated.  n = 0 is accepted (every
+ * later call is a no-op). */
 nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double *v, const double *box);
 
 /* Build the cell list and the neighbour list (cutoff rc_R + skin) for the current positions:

@@ -72,6 +72,10 @@ int md_blocks(int n);
 cudaError_t launch_kick_drift(int, double *, double *, double *, double *, double *, double *, const long long *, float4 *,
                               const float4 *, double, double, const double *, float, Control *, cudaStream_t);
 cudaError_t launch_control(Control *, bool, cudaStream_t);
+cudaError_t launch_control_check(Control *, cudaStream_t);
+cudaError_t launch_load_state_sorted(int, const double *, const double *, const int *, double *, double *, double *,
+                                     double *, double *, double *, float4 *, const float4 *, const double *,
+                                     const double *, float, Control *, cudaStream_t);
 cudaError_t launch_kick(int, double *, double *, double *, const long long *, double, double, long long *, cudaStream_t);
 cudaError_t launch_kinetic(int, const double *, const double *, const double *, double, long long *, cudaStream_t);
 cudaError_t launch_finalize(const long long *, int, const long long *, int, const long long *, int, double *,
@@ -125,6 +129,7 @@ struct nep_handle {
   int nc[3] = {0, 0, 0};
   int ncell = 0;
   bool have_state = false, have_nlist = false, have_forces = false;
+  bool recheck = false;   // an upload kept the list: check the displacements before the next evaluation
 
   // device buffers
   double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
@@ -425,7 +430,18 @@ nep_status check_device_status(nep_handle *h) {
 }
 
 nep_status ensure_nlist(nep_handle *h) {
+  if (h->have_nlist && h->recheck) {
+    // an upload kept the list: rebuild (on the device) only if an atom moved more than skin/2
+    {
+      Scope sc(h, KC_CELL, 1);
+      NEP_CUDA(h, launch_control_check(h->ctrl, h->stream));
+    }
+    NEP_CUDA(h, enqueue_rebuild(h));
+    h->recheck = false;
+    return NEP_OK;
+  }
   if (h->have_nlist) return NEP_OK;
+  h->recheck = false;
   {
     Scope sc(h, KC_CELL, 1);
     NEP_CUDA(h, launch_control(h->ctrl, true, h->stream));
@@ -491,6 +507,29 @@ nep_status upload_state(nep_handle *h, const double *x, const double *v) {
   }
   h->have_state = true;
   return NEP_OK;
+}
+
+// Upload into the current cell-sorted order (the list is kept; see k_load_state_sorted).
+nep_status upload_state_sorted(nep_handle *h, const double *x, const double *v) {
+  const size_t N = (size_t)h->n;
+  NEP_CUDA(h, cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int), h->stream));
+  const double *xs = x, *vs = v;
+  if (!is_device_ptr(x)) {
+    NEP_CUDA(h, cudaMemcpyAsync(h->io, x, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    xs = h->io;
+  }
+  if (v && !is_device_ptr(v)) {
+    NEP_CUDA(h, cudaMemcpyAsync(h->io + 3 * N, v, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    vs = h->io + 3 * N;
+  }
+  const float hs = 0.5f * h->skin;
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_load_state_sorted(h->n, xs, vs, h->id, h->x, h->y, h->z, h->vx, h->vy, h->vz, h->pos,
+                                         h->pos_ref, h->l, h->L, hs * hs, h->ctrl, h->stream));
+  }
+  h->recheck = true;
+  return check_device_status(h);
 }
 
 // Fallback buffers for the current system: flagged-atom list, its length, teacher adjoint rows.
@@ -661,6 +700,12 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   }
   cudaStreamSynchronize(h->stream);
   const bool same = h->have_state && h->n == (int)n && h->L[0] == box[0] && h->L[1] == box[1] && h->L[2] == box[2];
+  if (same && h->have_nlist) {
+    // Same size and box with a neighbour list: keep the list and the cell order; the next
+    // evaluation rebuilds only if an atom moved more than skin/2 from where the list was built.
+    h->have_forces = false;
+    return upload_state_sorted(h, x, v);
+  }
   if (same) {
     // Same size and box: keep every buffer (and the captured step graph); upload and invalidate.
     h->have_nlist = h->have_forces = false;

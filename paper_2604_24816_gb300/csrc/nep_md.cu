@@ -58,6 +58,20 @@ __global__ void k_control(Control *ctrl) {
   }
 }
 
+// Outside MD steps, after an upload that kept the list: rebuild only if an atom moved more than
+// skin/2 (or a rebuild was requested); the step counters are not touched.
+__global__ void k_control_check(Control *ctrl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int rb = ctrl->moved | ctrl->force_rebuild;
+  ctrl->do_rebuild = rb;
+  if (rb) {
+    ctrl->moved = 0;
+    ctrl->force_rebuild = 0;
+    ctrl->steps_since = 0;
+    ctrl->rebuilds += 1;
+  }
+}
+
 // Rebuild unconditionally (outside MD steps).
 __global__ void k_control_force(Control *ctrl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -146,6 +160,48 @@ __global__ void k_load_state(int n, const double *__restrict__ xin, const double
     vx[s] = 0.0; vy[s] = 0.0; vz[s] = 0.0;
   }
   id[s] = s;
+}
+
+// Upload into the current cell-sorted order, keeping the neighbour list: slot s takes the input atom
+// id[s] (original order).  Each position is moved to its periodic image nearest the slot's current
+// position (so the cell-relative coordinate stays continuous, as between rebuilds), the cell-relative
+// float32 coordinate is refreshed in the slot's cell, and an atom that moved more than skin/2 from
+// the positions the list was built for sets ctrl->moved (the next evaluation then rebuilds).
+__global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const double *__restrict__ vin,
+                                    const int *__restrict__ id, double *__restrict__ x, double *__restrict__ y,
+                                    double *__restrict__ z, double *__restrict__ vx, double *__restrict__ vy,
+                                    double *__restrict__ vz, float4 *__restrict__ pos,
+                                    const float4 *__restrict__ pos_ref, double lx, double ly, double lz, double Lx,
+                                    double Ly, double Lz, float half_skin2, Control *ctrl) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  bool moved = false;
+  if (s < n) {
+    const size_t o = 3 * (size_t)id[s];
+    double a = xin[o], b = xin[o + 1], c = xin[o + 2];
+    if (!(isfinite(a) && isfinite(b) && isfinite(c))) {
+      atomicOr(&ctrl->status, ST_NAN);
+      moved = true;
+    } else {
+      a -= Lx * rint((a - x[s]) / Lx);
+      b -= Ly * rint((b - y[s]) / Ly);
+      c -= Lz * rint((c - z[s]) / Lz);
+    }
+    x[s] = a; y[s] = b; z[s] = c;
+    if (vin != nullptr) {
+      vx[s] = vin[o]; vy[s] = vin[o + 1]; vz[s] = vin[o + 2];
+    } else {
+      vx[s] = 0.0; vy[s] = 0.0; vz[s] = 0.0;
+    }
+    const float4 p = pos[s];
+    const int cx = cell_x(p.w), cy = cell_y(p.w), cz = cell_z(p.w);
+    const float4 q = make_float4((float)fma(-(double)cx, lx, a), (float)fma(-(double)cy, ly, b),
+                                 (float)fma(-(double)cz, lz, c), p.w);
+    pos[s] = q;
+    const float4 r = pos_ref[s];
+    const float ddx = q.x - r.x, ddy = q.y - r.y, ddz = q.z - r.z;
+    moved = moved || !(ddx * ddx + ddy * ddy + ddz * ddz <= half_skin2);
+  }
+  if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->moved, 1);
 }
 
 // Sorted SoA -> original-order [n][3] float64 (positions wrapped into the box when L != nullptr).
@@ -245,6 +301,21 @@ cudaError_t launch_finalize(const long long *pd, int nbd, const long long *pf, i
 cudaError_t launch_load_state(int n, const double *xin, const double *vin, double *x, double *y, double *z, double *vx,
                               double *vy, double *vz, int *id, int *status, cudaStream_t st) {
   if (n > 0) k_load_state<<<bl(n, 256), 256, 0, st>>>(n, xin, vin, x, y, z, vx, vy, vz, id, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_control_check(Control *ctrl, cudaStream_t st) {
+  k_control_check<<<1, 32, 0, st>>>(ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_state_sorted(int n, const double *xin, const double *vin, const int *id, double *x, double *y,
+                                     double *z, double *vx, double *vy, double *vz, float4 *pos, const float4 *pos_ref,
+                                     const double l[3], const double L[3], float half_skin2, Control *ctrl,
+                                     cudaStream_t st) {
+  if (n > 0)
+    k_load_state_sorted<<<bl(n, 256), 256, 0, st>>>(n, xin, vin, id, x, y, z, vx, vy, vz, pos, pos_ref, l[0], l[1],
+                                                    l[2], L[0], L[1], L[2], half_skin2, ctrl);
   return cudaGetLastError();
 }
 

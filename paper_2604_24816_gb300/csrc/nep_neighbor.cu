@@ -246,6 +246,14 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
       const float oy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
       const int row = (zz * geom.ncy + yy) * geom.ncx;
       const int shb = 3 * (dy + 1) + 9 * (dz + 1);
+      {
+        // skip a row of three cells whose (y, z) slab lies beyond the list radius from atom i (its
+        // cell-relative position gives the gaps); the 1e-4 margin keeps every candidate a float32
+        // distance test could accept, so the lists are unchanged
+        const float gy = dy < 0 ? pi.y : (dy > 0 ? geom.ly - pi.y : 0.f);
+        const float gz = dz < 0 ? pi.z : (dz > 0 ? geom.lz - pi.z : 0.f);
+        if (gy * gy + gz * gz > B.b3 * 1.0001f) continue;
+      }
       const int parts = xwrap ? 3 : 1;
       for (int part = 0; part < parts; ++part) {
         int b, e;

@@ -316,3 +316,41 @@ def test_bounded_wait_runs_out_and_reports(api):
         nep.set_state(wl.pos, wl.vel, wl.box)
         E, F, W = nep.compute()
     assert np.isfinite(E) and np.all(np.isfinite(F))
+
+
+def test_reupload_keeps_the_list_within_the_skin(api, model_params, model):
+    """nep_set_state on the same system keeps the neighbour list while every atom stays within
+    skin/2 of where the list was built (positions may come back as another periodic image), and the
+    forces are the oracle's for the uploaded positions."""
+    wl = ni.fcc_cu_workload(4, 300.0, 0.05, seed=71)
+    rng = np.random.default_rng(72)
+    with api.NEP(model_params, rebuild_every=0) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.step(1.0, 5)
+        x, v = nep.get_state()
+        r0 = nep.counters()["rebuilds"]
+        x2 = x + 0.03 * rng.standard_normal(x.shape)
+        x2[0] += wl.box                                   # another periodic image of atom 0
+        x2[1, 2] -= wl.box[2]
+        nep.set_state(x2, v, wl.box)
+        E, F, W = nep.compute()
+        assert nep.counters()["rebuilds"] == r0
+        nep.step(1.0, 2)                                  # and MD continues from the uploaded state
+    Eo, Uo, Fo, Wo = oracle.energy_forces(model, x2, wl.box)
+    assert np.abs(F - Fo).max() <= 1e-4
+    assert abs(E - Eo) / abs(Eo) <= 1e-6
+
+
+def test_reupload_rebuilds_when_atoms_moved_beyond_the_skin(api, model_params):
+    """A rigid translation by 0.7 A (> skin/2) forces a rebuild; the forces are translation invariant."""
+    wl = ni.fcc_cu_workload(4, 300.0, 0.05, seed=73)
+    with api.NEP(model_params, rebuild_every=0) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        E0, F0, _ = nep.compute()
+        r0 = nep.counters()["rebuilds"]
+        nep.set_state(wl.pos + np.array([0.7, -0.4, 0.3]), wl.vel, wl.box)
+        E1, F1, _ = nep.compute()
+        assert nep.counters()["rebuilds"] == r0 + 1
+    # float32 rounding of the shifted cell-relative coordinates: the float32 path's bound
+    assert np.abs(F1 - F0).max() <= 1e-4
+    assert abs(E1 - E0) <= 1e-6 * abs(E0)

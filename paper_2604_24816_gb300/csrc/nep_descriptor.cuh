@@ -286,38 +286,49 @@ __device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, con
 }
 
 // ---------------------------------------------------------------------------------------------------
-// Teacher shape with the 120 angular sums s_nlm in tensor memory (TMEM) instead of registers: s[a][lm]
-// at column (lm - lm mod 4) NA + 4 a + lm mod 4 of the thread's lane (TMEM_W = 4 components x NA
-// channels per chunk, the same layout as the force kernel's adjoint row).  All TMEM accesses are
+// Teacher shape with the angular sums s_nlm of the first NT channels in tensor memory (TMEM) instead
+// of registers (NT = 5: all 120; NT = 4: 96, the fifth channel's 24 in registers): s[a][lm] at column
+// (lm - lm mod 4) NT + 4 a + lm mod 4 of the thread's lane (TMEM_W = 4 components x NT channels per
+// chunk, the same layout as the force kernel's adjoint row for NT = 5).  All TMEM accesses are
 // warp-collective, so the neighbour walk runs to the warp's longest row (threads past their own row,
 // or past the last atom, idle with a predicate) and the angular update is made by whole warps, lanes
 // without an angular pair adding g = 0.
 constexpr int TMEM_W = 4;
 
-template <class S>
-__device__ __forceinline__ void tmem_chunk_cols(uint32_t trow, int c, uint32_t (&cols)[S::NA]) {
+template <int NT>
+__device__ __forceinline__ void tmem_chunk_cols(uint32_t trow, int c, uint32_t (&cols)[NT]) {
 #pragma unroll
-  for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * TMEM_W);
+  for (int a = 0; a < NT; ++a) cols[a] = trow + (uint32_t)(c * NT + a * TMEM_W);
 }
 
+// The sums of the channels kept in registers (NA - NT of them; one unused row when NT = NA).
+template <class S, int NT>
+struct RegSums {
+  float s[S::NA > NT ? S::NA - NT : 1][S::NLM];
+};
+
 // Zero the sums, then walk atom ii's row (cnt entries; cnt = 0 for threads past the last atom):
-// radial basis sums QR and the LJ energy in registers, s_nlm in TMEM.
-template <class S, int DE, int DP, int BLOCK>
+// radial basis sums QR and the LJ energy in registers, s_nlm in TMEM (channels < NT) and R.
+template <class S, int NT, int DE, int DP, int BLOCK>
 __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const float4 *shift, uint32_t trow, int ii,
                                                    int n, const float4 *__restrict__ pos,
                                                    const int32_t *__restrict__ nbr, int cnt, uint32_t *ring_e,
-                                                   float4 *ring_p, float (&QR)[S::KR], float &elj, int &nrad,
-                                                   int &nang, int &nact) {
-  static_assert(S::NA == 5 && S::NLM == 24, "teacher shape");
+                                                   float4 *ring_p, float (&QR)[S::KR], RegSums<S, NT> &R,
+                                                   float &elj, int &nrad, int &nang, int &nact) {
+  static_assert(S::NA == 5 && S::NLM == 24 && (NT == 4 || NT == 5), "teacher shape");
   constexpr int W = TMEM_W;
   {
     const float z[W] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int c = 0; c < S::NLM; c += W)
 #pragma unroll
-      for (int a = 0; a < S::NA; ++a) tmem_st(trow + (uint32_t)(c * S::NA + a * W), z);
+      for (int a = 0; a < NT; ++a) tmem_st(trow + (uint32_t)(c * NT + a * W), z);
     tmem_wait_st();
   }
+#pragma unroll
+  for (int a = NT; a < S::NA; ++a)
+#pragma unroll
+    for (int c = 0; c < S::NLM; ++c) R.s[a - NT][c] = 0.f;
 #pragma unroll
   for (int k = 0; k < S::KR; ++k) QR[k] = 0.f;
   elj = 0.f;
@@ -371,17 +382,21 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
       harmonics<S::NLM>(ux, uy, uz, Y);
 #pragma unroll
       for (int c = 0; c < S::NLM; c += W) {
-        uint32_t cols[S::NA];
-        tmem_chunk_cols<S>(trow, c, cols);
-        float sv[S::NA][W];
+        uint32_t cols[NT];
+        tmem_chunk_cols<NT>(trow, c, cols);
+        float sv[NT][W];
         tmem_ld5(cols, sv);
 #pragma unroll
-        for (int a = 0; a < S::NA; ++a) {
+        for (int a = 0; a < NT; ++a) {
 #pragma unroll
           for (int cc = 0; cc < W; ++cc) sv[a][cc] = fmaf(g[a], Y[c + cc], sv[a][cc]);
           tmem_st(cols[a], sv[a]);
         }
       }
+#pragma unroll
+      for (int a = NT; a < S::NA; ++a)
+#pragma unroll
+        for (int c = 0; c < S::NLM; ++c) R.s[a - NT][c] = fmaf(g[a], Y[c], R.s[a - NT][c]);
       tmem_wait_st();
       if (ang) ++nang;
     }
@@ -389,11 +404,24 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
   pipe.finish();
 }
 
-// Descriptors from the radial basis sums and the TMEM sums (q_nl = sum_m s_nlm^2, 4-body from the
+// The sums of chunk c (components c..c+3) of every channel: TMEM for a < NT, registers after.
+template <class S, int NT>
+__device__ __forceinline__ void sums_chunk(uint32_t trow, int c, const RegSums<S, NT> &R, float (&sv)[S::NA][TMEM_W]) {
+  uint32_t cols[NT];
+  tmem_chunk_cols<NT>(trow, c, cols);
+  float tv[NT][TMEM_W];
+  tmem_ld5(cols, tv);
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+    for (int cc = 0; cc < TMEM_W; ++cc) sv[a][cc] = a < NT ? tv[a < NT ? a : 0][cc] : R.s[a < NT ? 0 : a - NT][c + cc];
+}
+
+// Descriptors from the radial basis sums and the sums s_nlm (q_nl = sum_m s_nlm^2, 4-body from the
 // l = 2 sums), as descriptors_of.
-template <class S>
+template <class S, int NT>
 __device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow, const float (&QR)[S::KR],
-                                               float (&q)[S::NDES], FourBody<S> &T) {
+                                               const RegSums<S, NT> &R, float (&q)[S::NDES], FourBody<S> &T) {
   constexpr int W = TMEM_W;
 #pragma unroll
   for (int a = 0; a < S::NR; ++a) {
@@ -407,10 +435,8 @@ __device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow,
   float s2[S::NA][5];
 #pragma unroll
   for (int c = 0; c < S::NLM; c += W) {
-    uint32_t cols[S::NA];
-    tmem_chunk_cols<S>(trow, c, cols);
     float sv[S::NA][W];
-    tmem_ld5(cols, sv);
+    sums_chunk<S, NT>(trow, c, R, sv);
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll

@@ -147,11 +147,12 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   const int cnt = live ? nnum[i] : 0;
   float QR[S::KR], elj;
   int nrad, nang, nact;
-  accumulate_atom_tm<S, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, cnt, ring_e, ring_p, QR, elj,
-                                                      nrad, nang, nact);
+  RegSums<S, S::NA> R;                      // empty: every channel in TMEM
+  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, cnt, ring_e, ring_p,
+                                                             QR, R, elj, nrad, nang, nact);
   float q[S::NDES];
   FourBody<S> T;
-  descriptors_tm<S>(P, trow, QR, q, T);
+  descriptors_tm<S, S::NA>(P, trow, QR, R, q, T);
   if (live && qout != nullptr) {
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
@@ -168,10 +169,8 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
 #pragma unroll
   for (int c = 0; c < S::NLM; c += W) {
-    uint32_t cols[S::NA];
-    tmem_chunk_cols<S>(trow, c, cols);
     float sv[S::NA][W];
-    tmem_ld5(cols, sv);
+    sums_chunk<S, S::NA>(trow, c, R, sv);
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
       float gl[W];

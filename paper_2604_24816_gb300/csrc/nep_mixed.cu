@@ -32,14 +32,27 @@ __device__ __forceinline__ uint4 pack8_half(const float *v) {
   return w;
 }
 
-// The student shape needs far fewer registers: ask for 6 resident blocks (measured best) instead of 2.
+// Teacher shape: the angular sums of 4 of the 5 channels are accumulated in TMEM (96 columns,
+// accumulate_atom_tm), the fifth channel's 24 in registers, and the two network GEMMs take turns in the
+// remaining 32 columns (the forward result is read out before the backward GEMM overwrites it): 128
+// columns per block and 4 resident blocks (124 registers) instead of 245 registers and 2.  The student shape keeps its
+// sums in registers and asks for 6 resident blocks (measured best).
+#ifndef NEP_MIX_MINB_TM
+#define NEP_MIX_MINB_TM 4
+#endif
 template <class S, class MT>
-__global__ void __launch_bounds__(MIX_BLOCK, S::NLM > 8 ? 2 : 6)
+__global__ void __launch_bounds__(MIX_BLOCK, S::NLM > 8 ? NEP_MIX_MINB_TM : 6)
 k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
                    const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, __half *__restrict__ G,
                    float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
                    long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   static_assert(S::NDES <= MIX_K && S::NNEU <= MIX_N, "network larger than one tensor-core tile");
+  constexpr bool TM = S::NLM > 8;
+  constexpr int NT = 4;                                   // TM: channels whose sums live in TMEM
+  constexpr uint32_t TCOLS = TM ? 128 : 64;
+  constexpr uint32_t ZCOL = TM ? NT * S::NLM : 0;         // forward GEMM result
+  constexpr uint32_t DCOL = TM ? NT * S::NLM : 32;        // backward GEMM result (TM: the same columns)
+  static_assert(!TM || (NT * S::NLM + MIX_N <= (int)TCOLS && MIX_BLOCK == 128), "TMEM budget");
   __shared__ float4 shift[27];
   // The neighbour-pipeline ring is dead once every thread has walked its row, so the GEMMs' A tile
   // (q~ rows, then T rows) overlays it: less shared memory per block leaves more of the unified
@@ -61,7 +74,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
       sW[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>((t < S::NNEU && k < S::NDES) ? P.W0[t][k] : 0.f);
       sWt[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>((t < S::NDES && k < S::NNEU) ? P.W0[k][t] : 0.f);
     }
-    tmem_alloc(&tmem_base, 64);
+    tmem_alloc(&tmem_base, TCOLS);
     tc_fence_before();
   }
   if (t == 0) mbar_init(&mbar, 1);
@@ -74,7 +87,25 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   float q[S::NDES];
   long long acc[5] = {0, 0, 0, 0, 0};
   bool flagged = false;
-  if (live) {
+  RegSums<S, NT> R;
+  uint32_t trow = 0;
+  if constexpr (TM) {
+    tc_fence_after();
+    trow = tmem_base + ((uint32_t)(t & ~31) << 16);
+    A.cnt = live ? nnum[i] : 0;
+    if (live) { Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0; }
+    accumulate_atom_tm<S, NT, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, trow, live ? i : 0, n, pos, nbr, A.cnt, ring_e,
+                                                         ring_p, A.QR, R, A.elj, A.nrad, A.nang, A.nact);
+    descriptors_tm<S, NT>(P, trow, A.QR, R, q, T);        // zero for threads past the last atom (empty row)
+    if (live) {
+      if (qout != nullptr) {
+#pragma unroll
+        for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
+      }
+      flagged = fb.on && out_of_range<S>(fb, P, q);
+      if (flagged) flag_atom(fb, i, status);
+    }
+  } else if (live) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     accumulate_atom<S, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
     descriptors_of<S>(P, A, q, T);
@@ -92,6 +123,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 #pragma unroll
   for (int k = 0; k < MIX_K; ++k) sA[tile_off(t, k, MIX_K / 8)] = to_mma_type<MT>(k < S::NDES ? q[k] * P.qs[k] : 0.f);
   fence_async_smem();
+  tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
@@ -100,15 +132,15 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   if (t == 0) {
 #pragma unroll
     for (int ks = 0; ks < MIX_K / 16; ++ks)
-      umma_f16(tmem, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo), umma_smem_desc(smem_addr(sW) + ks * 256, lbo, sbo),
-               idesc, ks);
+      umma_f16(tmem + ZCOL, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo),
+               umma_smem_desc(smem_addr(sW) + ks * 256, lbo, sbo), idesc, ks);
     umma_commit(&mbar);
   }
   bool ok = mbar_wait(&mbar, 0, MIX_WAIT);
   tc_fence_after();
   const uint32_t lane_base = (uint32_t)(t & ~31) << 16;
   float z[32];
-  tmem_ld32(tmem + lane_base, z);
+  tmem_ld32(tmem + lane_base + ZCOL, z);
 
   // activation, site energy and the backward GEMM operand, in float32
   float U = -P.b1;
@@ -127,32 +159,55 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 #pragma unroll
   for (int k = 0; k < MIX_N; ++k) sA[tile_off(t, k, MIX_N / 8)] = to_mma_type<MT>(tr[k]);
   fence_async_smem();
+  tc_fence_before();   // every thread has read the forward result before the backward GEMM may overwrite it
   __syncthreads();
   tc_fence_after();
   if (t == 0) {
 #pragma unroll
     for (int ks = 0; ks < MIX_N / 16; ++ks)
-      umma_f16(tmem + 32, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo),
+      umma_f16(tmem + DCOL, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo),
                umma_smem_desc(smem_addr(sWt) + ks * 256, lbo, sbo), idesc, ks);
     umma_commit(&mbar);
   }
   ok = mbar_wait(&mbar, 1, MIX_WAIT) && ok;
   tc_fence_after();
   float dq[32];
-  tmem_ld32(tmem + lane_base + 32, dq);
+  tmem_ld32(tmem + lane_base + DCOL, dq);
   if (!ok && t == 0) atomicOr(status, ST_TIMEOUT);
 
+  float Fp[S::NDES];
+#pragma unroll
+  for (int v = 0; v < S::NDES; ++v) Fp[v] = flagged ? 0.f : dq[v] * P.qs[v];   // flagged: no U_i here
+  __half *Gi = G + (size_t)(live ? i : 0) * S::GS;
+  if constexpr (TM) {
+    // adjoint from the sums (TMEM chunks read by whole warps; rows stored for live atoms only)
+    float g4[S::NA][5];
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
+#pragma unroll
+    for (int c = 0; c < S::NLM; c += TMEM_W) {
+      float sv[S::NA][TMEM_W];
+      sums_chunk<S, NT>(trow, c, R, sv);
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) {
+        float gl[TMEM_W];
+        adjoint_chunk<S>(a, c, sv[a], g4[a], Fp, gl);
+        const __half2 h0 = __floats2half2_rn(gl[0], gl[1]), h1 = __floats2half2_rn(gl[2], gl[3]);
+        if (live)
+          *reinterpret_cast<uint2 *>(Gi + a * S::NLM + c) =
+              make_uint2(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1));
+      }
+    }
+  }
   if (live) {
-    float Fp[S::NDES];
+    if constexpr (!TM) {
 #pragma unroll
-    for (int v = 0; v < S::NDES; ++v) Fp[v] = flagged ? 0.f : dq[v] * P.qs[v];   // flagged: no U_i here
-    __half *Gi = G + (size_t)i * S::GS;
+      for (int a = 0; a < S::NA; ++a) {
+        float gl[S::NLM];
+        adjoint_channel<S>(a, A, T, Fp, gl);
 #pragma unroll
-    for (int a = 0; a < S::NA; ++a) {
-      float gl[S::NLM];
-      adjoint_channel<S>(a, A, T, Fp, gl);
-#pragma unroll
-      for (int c = 0; c < S::NLM; c += 8) *reinterpret_cast<uint4 *>(Gi + a * S::NLM + c) = pack8_half(gl + c);
+        for (int c = 0; c < S::NLM; c += 8) *reinterpret_cast<uint4 *>(Gi + a * S::NLM + c) = pack8_half(gl + c);
+      }
     }
     {
       float tail[8];
@@ -170,7 +225,7 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   }
   tc_fence_before();
   __syncthreads();
-  if (t < 32) tmem_dealloc(tmem, 64);
+  if (t < 32) tmem_dealloc(tmem, TCOLS);
   block_sum_store<5, MIX_BLOCK / 32>(acc, part);
 }
 

@@ -137,8 +137,8 @@ __device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[8]) {
 // Wait until this thread's TMEM stores have completed.
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Five groups of W columns (W = 4 or 8) at c[0..4] of this thread's lane, loaded and waited for in one
-// statement, so that no use of the values can be scheduled before the wait.
+// Five (or four) groups of W columns (W = 4 or 8) at c[0..] of this thread's lane, loaded and waited
+// for in one statement, so that no use of the values can be scheduled before the wait.
 __device__ __forceinline__ void tmem_ld5(const uint32_t (&c)[5], float (&v)[5][4]) {
   uint32_t r[20];
   asm volatile(
@@ -154,6 +154,22 @@ __device__ __forceinline__ void tmem_ld5(const uint32_t (&c)[5], float (&v)[5][4
       : "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]));
 #pragma unroll
   for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[a][k] = __uint_as_float(r[4 * a + k]);
+}
+__device__ __forceinline__ void tmem_ld5(const uint32_t (&c)[4], float (&v)[4][4]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%17];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%18];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%19];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]));
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[a][k] = __uint_as_float(r[4 * a + k]);
 }

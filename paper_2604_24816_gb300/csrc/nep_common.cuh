@@ -42,6 +42,7 @@ struct Control {
   int rebuild_every;    // 0 = displacement-triggered only
   long long rebuilds;   // neighbour builds done
   long long steps;      // MD steps done
+  int nb_next;          // next group of atoms for the neighbour scan (reset by each rebuild)
 };
 
 // Arguments of the rebuild chain (cell sort + neighbour list).

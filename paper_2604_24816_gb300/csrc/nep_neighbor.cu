@@ -18,14 +18,17 @@
 // their error does not grow with the box size (float64 appears only in the wrap and cell assignment).
 #include "nep_common.cuh"
 
+#include <algorithm>
+
 namespace nep {
 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-__global__ void k_cell_zero(int ncell, int *__restrict__ count, int *__restrict__ cursor, const Control *ctrl) {
+__global__ void k_cell_zero(int ncell, int *__restrict__ count, int *__restrict__ cursor, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->nb_next = 0;   // the neighbour scan's work counter
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
     count[c] = 0;
     cursor[c] = 0;
@@ -43,19 +46,19 @@ __global__ void k_cell_assign(int n, double *__restrict__ x, double *__restrict_
                               double Ly, double Lz, double lx, double ly, double lz, int ncx, int ncy, int ncz,
                               int *__restrict__ cell_of, int *__restrict__ count, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  double px = x[s], py = y[s], pz = z[s];
-  if (!(isfinite(px) && isfinite(py) && isfinite(pz))) {
-    atomicOr(&ctrl->status, ST_NAN);
-    px = py = pz = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double px = x[s], py = y[s], pz = z[s];
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) {
+      atomicOr(&ctrl->status, ST_NAN);
+      px = py = pz = 0.0;
+    }
+    px = wrap_coord(px, Lx); py = wrap_coord(py, Ly); pz = wrap_coord(pz, Lz);
+    x[s] = px; y[s] = py; z[s] = pz;
+    const int cx = min((int)(px / lx), ncx - 1), cy = min((int)(py / ly), ncy - 1), cz = min((int)(pz / lz), ncz - 1);
+    const int c = (cz * ncy + cy) * ncx + cx;
+    cell_of[s] = c;
+    atomicAdd(count + c, 1);
   }
-  px = wrap_coord(px, Lx); py = wrap_coord(py, Ly); pz = wrap_coord(pz, Lz);
-  x[s] = px; y[s] = py; z[s] = pz;
-  const int cx = min((int)(px / lx), ncx - 1), cy = min((int)(py / ly), ncy - 1), cz = min((int)(pz / lz), ncz - 1);
-  const int c = (cz * ncy + cy) * ncx + cx;
-  cell_of[s] = c;
-  atomicAdd(count + c, 1);
 }
 
 // Exclusive scan of count[0..m) into start[0..m], start[m] = total.  Tile scan + carry pass + add.
@@ -113,35 +116,35 @@ __global__ void k_scan_carry(int ntiles, int *__restrict__ tile_sums, int m, int
 
 __global__ void k_scan_add(int m, int *__restrict__ out, const int *__restrict__ tile_sums, const Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < m) out[idx] += tile_sums[idx / SCAN_TILE];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m; idx += gridDim.x * blockDim.x)
+    out[idx] += tile_sums[idx / SCAN_TILE];
 }
 
 __global__ void k_scatter(int n, const int *__restrict__ cell_of, const int *__restrict__ start, int *__restrict__ cursor,
                           int *__restrict__ perm, const Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int c = cell_of[s];
-  perm[start[c] + atomicAdd(cursor + c, 1)] = s;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int c = cell_of[s];
+    perm[start[c] + atomicAdd(cursor + c, 1)] = s;
+  }
 }
 
 // One thread per cell: insertion sort of the cell's slots by original id (ids are unique).
 __global__ void k_cell_sort(int ncell, const int *__restrict__ start, int *__restrict__ perm, const int *__restrict__ id,
                             const Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int b = start[c], e = start[c + 1];
-  for (int p = b + 1; p < e; ++p) {
-    const int s = perm[p];
-    const int key = id[s];
-    int q = p;
-    while (q > b && id[perm[q - 1]] > key) {
-      perm[q] = perm[q - 1];
-      --q;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const int b = start[c], e = start[c + 1];
+    for (int p = b + 1; p < e; ++p) {
+      const int s = perm[p];
+      const int key = id[s];
+      int q = p;
+      while (q > b && id[perm[q - 1]] > key) {
+        perm[q] = perm[q - 1];
+        --q;
+      }
+      perm[q] = s;
     }
-    perm[q] = s;
   }
 }
 
@@ -153,19 +156,19 @@ __global__ void k_permute(int n, const int *__restrict__ perm, const double *__r
                           int *__restrict__ idb, float4 *__restrict__ pos, float4 *__restrict__ pos_ref, double lx,
                           double ly, double lz, int ncx, int ncy, const Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int s = perm[t];
-  const double px = x[s], py = y[s], pz = z[s];
-  xb[t] = px; yb[t] = py; zb[t] = pz;
-  vxb[t] = vx[s]; vyb[t] = vy[s]; vzb[t] = vz[s];
-  idb[t] = id[s];
-  const int c = cell_of[s];
-  const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
-  const float4 p = make_float4((float)(px - cx * lx), (float)(py - cy * ly), (float)(pz - cz * lz),
-                               __int_as_float(cx | (cy << 10) | (cz << 20)));
-  pos[t] = p;
-  pos_ref[t] = p;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int s = perm[t];
+    const double px = x[s], py = y[s], pz = z[s];
+    xb[t] = px; yb[t] = py; zb[t] = pz;
+    vxb[t] = vx[s]; vyb[t] = vy[s]; vzb[t] = vz[s];
+    idb[t] = id[s];
+    const int c = cell_of[s];
+    const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+    const float4 p = make_float4((float)(px - cx * lx), (float)(py - cy * ly), (float)(pz - cz * lz),
+                                 __int_as_float(cx | (cy << 10) | (cz << 20)));
+    pos[t] = p;
+    pos_ref[t] = p;
+  }
 }
 
 __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
@@ -175,11 +178,11 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
                             const double *__restrict__ vyb, const double *__restrict__ vzb,
                             const int *__restrict__ idb, const Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  x[t] = xb[t]; y[t] = yb[t]; z[t] = zb[t];
-  vx[t] = vxb[t]; vy[t] = vyb[t]; vz[t] = vzb[t];
-  id[t] = idb[t];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    x[t] = xb[t]; y[t] = yb[t]; z[t] = zb[t];
+    vx[t] = vxb[t]; vy[t] = vyb[t]; vz[t] = vzb[t];
+    id[t] = idb[t];
+  }
 }
 
 // One warp per atom over the candidates of the 27 neighbouring cell images (below).
@@ -348,10 +351,23 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
   __shared__ uint32_t stage[NB_WARPS][NB_STAGE];
   __shared__ uint8_t skey[NB_WARPS][NB_STAGE];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * NB_WARPS + w;
-  if (i >= n) return;                                  // whole warp (i is warp-uniform); no barrier in the kernel
-  neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], skey[w], lane, nbr, nnum,
-                    nang, nown, nband0, ctrl);
+  // The grid is capped at the resident blocks (a launch on a step without a rebuild then costs a few
+  // microseconds whatever the atom count); each block takes the next group of NB_WARPS consecutive
+  // atoms from a counter, which keeps the order of the hardware's own block scheduling (a static
+  // stride over the atoms measured 25 % slower).
+  __shared__ int group;
+  for (;;) {
+    if (threadIdx.x == 0) group = atomicAdd(&ctrl->nb_next, 1);
+    __syncthreads();
+    const int g = group;
+    __syncthreads();                                   // read by every warp before the next take
+    if ((long long)g * NB_WARPS >= n) break;           // block-uniform
+    const int i = g * NB_WARPS + w;                    // warp-uniform
+    if (i < n)
+      neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], skey[w], lane, nbr, nnum,
+                        nang, nown, nband0, ctrl);
+    __syncwarp();                                      // the stage is reused by the warp's next atom
+  }
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -360,21 +376,43 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
 
 static int blocks_for(long long m, int b) { return (int)((m + b - 1) / b); }
 
+// Grid of the rebuild-chain kernels: enough blocks for m items, at most what is resident at once (the
+// occupancy calculator's blocks per SM x the SM count); the kernels loop over the rest.  Every step
+// launches the chain and the kernels return at once when it does not rebuild, so the grid size is
+// what such a step pays for.
+static int sm_count() {
+  static int sms = 0;
+  if (sms <= 0) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess ||
+        sms <= 0)
+      sms = 152;
+  }
+  return sms;
+}
+template <class K>
+static int resident_grid(K kernel, long long m, int per_block, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0)
+    per_sm = 1;
+  return (int)std::min<long long>(blocks_for(m, per_block), (long long)sm_count() * per_sm);
+}
+
 cudaError_t launch_cell_sort(const RebuildArgs &a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   k_cell_zero<<<min(blocks_for(a.ncell, 256), 4096), 256, 0, st>>>(a.ncell, a.count, a.cursor, a.ctrl);
-  k_cell_assign<<<blocks_for(a.n, 256), 256, 0, st>>>(a.n, a.x, a.y, a.z, a.L[0], a.L[1], a.L[2], a.l[0], a.l[1],
+  k_cell_assign<<<resident_grid(k_cell_assign, a.n, 256, 256), 256, 0, st>>>(a.n, a.x, a.y, a.z, a.L[0], a.L[1], a.L[2], a.l[0], a.l[1],
                                                       a.l[2], a.nc[0], a.nc[1], a.nc[2], a.cell_of, a.count, a.ctrl);
   const int ntiles = blocks_for(a.ncell, SCAN_TILE);
   k_scan_tiles<<<ntiles, SCAN_THREADS, 0, st>>>(a.ncell, a.count, a.start, a.tile_sums, a.ctrl);
   k_scan_carry<<<1, 32, 0, st>>>(ntiles, a.tile_sums, a.ncell, a.start, a.ctrl);
-  k_scan_add<<<blocks_for(a.ncell, 256), 256, 0, st>>>(a.ncell, a.start, a.tile_sums, a.ctrl);
-  k_scatter<<<blocks_for(a.n, 256), 256, 0, st>>>(a.n, a.cell_of, a.start, a.cursor, a.perm, a.ctrl);
-  k_cell_sort<<<blocks_for(a.ncell, 128), 128, 0, st>>>(a.ncell, a.start, a.perm, a.id, a.ctrl);
-  k_permute<<<blocks_for(a.n, 256), 256, 0, st>>>(a.n, a.perm, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.id, a.cell_of, a.xb,
+  k_scan_add<<<resident_grid(k_scan_add, a.ncell, 256, 256), 256, 0, st>>>(a.ncell, a.start, a.tile_sums, a.ctrl);
+  k_scatter<<<resident_grid(k_scatter, a.n, 256, 256), 256, 0, st>>>(a.n, a.cell_of, a.start, a.cursor, a.perm, a.ctrl);
+  k_cell_sort<<<resident_grid(k_cell_sort, a.ncell, 128, 128), 128, 0, st>>>(a.ncell, a.start, a.perm, a.id, a.ctrl);
+  k_permute<<<resident_grid(k_permute, a.n, 256, 256), 256, 0, st>>>(a.n, a.perm, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.id, a.cell_of, a.xb,
                                                   a.yb, a.zb, a.vxb, a.vyb, a.vzb, a.idb, a.pos, a.pos_ref, a.l[0],
                                                   a.l[1], a.l[2], a.nc[0], a.nc[1], a.ctrl);
-  k_copy_back<<<blocks_for(a.n, 256), 256, 0, st>>>(a.n, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.id, a.xb, a.yb, a.zb,
+  k_copy_back<<<resident_grid(k_copy_back, a.n, 256, 256), 256, 0, st>>>(a.n, a.x, a.y, a.z, a.vx, a.vy, a.vz, a.id, a.xb, a.yb, a.zb,
                                                     a.vxb, a.vyb, a.vzb, a.idb, a.ctrl);
   return cudaGetLastError();
 }
@@ -386,7 +424,7 @@ cudaError_t launch_neighbors(const RebuildArgs &a, cudaStream_t st) {
   g.ncx = a.nc[0]; g.ncy = a.nc[1]; g.ncz = a.nc[2];
   Bands B;
   B.b0 = a.ba2; B.b1 = a.ra2; B.b2 = a.br2; B.b3 = a.rl2;
-  k_neighbors<<<blocks_for(a.n, NB_WARPS), NB_WARPS * 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum,
+  k_neighbors<<<resident_grid(k_neighbors, a.n, NB_WARPS, NB_WARPS * 32), NB_WARPS * 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum,
                                                                    a.nang, a.nown, a.nband0, a.ctrl);
   return cudaGetLastError();
 }

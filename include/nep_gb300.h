@@ -193,11 +193,23 @@ nep_status nep_get_fallback(nep_handle *h, int *flags, int64_t *count);
  *                              through a global array (the paper's sum_fxyz) instead of registers;
  *   NEP_VARIANT_HALF_LIST      the force kernel over the owned half of each row: every unordered pair once,
  *                              with the adjoint rows of both atoms (the neighbour's gathered), instead of
- *                              every ordered pair with the own row only.
+ *                              every ordered pair with the own row only;
+ *   NEP_VARIANT_SEPARATE_DESCRIPTOR / _FORCE  the descriptor kernel and the full-row force kernel as two
+ *                              launches with the adjoint rows through device memory, instead of the fused
+ *                              kernel (*ms = the named kernel's time; the other variants' force and
+ *                              descriptor kernels are these, with one part changed).
+ * The float-scatter and half-list variants run after the separate descriptor kernel.
  * One force evaluation on the current state with the variant; *ms = the variant kernel's time (CUDA
  * events), F (may be NULL; host or device; [n][3], caller's order) = the forces it produced.  The
  * handle's own results are recomputed on the next request. */
-enum { NEP_VARIANT_FLOAT_SCATTER = 1, NEP_VARIANT_TILE1 = 2, NEP_VARIANT_TILE3 = 3, NEP_VARIANT_HALF_LIST = 4 };
+enum {
+  NEP_VARIANT_FLOAT_SCATTER = 1,
+  NEP_VARIANT_TILE1 = 2,
+  NEP_VARIANT_TILE3 = 3,
+  NEP_VARIANT_HALF_LIST = 4,
+  NEP_VARIANT_SEPARATE_DESCRIPTOR = 5,
+  NEP_VARIANT_SEPARATE_FORCE = 6
+};
 nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F);
 
 /* Upper limits of nep_compute_noalloc: the size of its fixed scratch array. */

@@ -16,6 +16,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "nep_gb300.h"
@@ -32,6 +33,12 @@ cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
                          const int32_t *, const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
+template <class S>
+cudaError_t launch_fused(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *, float *,
+                         float *, long long *, long long *, long long *, int *, cudaStream_t);
+#ifndef NEP_FUSED
+#define NEP_FUSED 1
+#endif
 int descriptor_blocks(int n);
 int force_blocks(int n);
 // nep_mixed.cu
@@ -159,6 +166,7 @@ struct nep_handle {
   // graph of one MD step
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
+  long long graph_launches = 0;   // our kernel launches in one captured step
 
   // timing
   bool timing = false;
@@ -330,6 +338,16 @@ cudaError_t enqueue_rebuild(nep_handle *h) {
 template <class S>
 cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   const Geom g = geom_of(h);
+  if constexpr (std::is_same<S, CuShape>::value && NEP_FUSED) {
+    if (h->precision == NEP_FP32 && !h->fb_on) {
+      // the float32 teacher: descriptors, network and forces in one kernel (forces zeroed first)
+      Scope sc(h, KC_FORCE, 1);
+      cudaError_t e = cudaMemsetAsync(h->F, 0, 3 * (size_t)h->n * sizeof(long long), h->stream);
+      if (e != cudaSuccess) return e;
+      return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, h->nnum, h->usite, qout, h->F, h->part_d, h->part_f,
+                                   &h->ctrl->status, h->stream);
+    }
+  }
   Fallback fb{};
   fb.on = h->fb_on ? 1 : 0;
   if (fb.on) {
@@ -472,6 +490,7 @@ nep_status build_graph(nep_handle *h, double dt) {
   NEP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = enqueue_step(h, dt);
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+  h->graph_launches = h->launch_total - before;   // kernels of one captured step
   h->launch_total = before;
   if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capture step"); }
   if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
@@ -544,7 +563,6 @@ cudaError_t alloc_fallback(nep_handle *h) {
   return e;
 }
 
-const int LAUNCHES_PER_STEP = 16;
 
 }  // namespace
 
@@ -809,7 +827,7 @@ nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
       if (s != NEP_OK) return s;
     }
     for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
-    h->launch_total += (long long)(LAUNCHES_PER_STEP + (h->fb_on ? 2 : 0)) * n_steps;
+    h->launch_total += h->graph_launches * n_steps;
   }
   return check_device_status(h);
 }
@@ -995,7 +1013,7 @@ nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const floa
 nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
   if (!h || !ms) return NEP_ERR_ARG;
   if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
-  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_HALF_LIST)
+  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_SEPARATE_FORCE)
     return fail(h, NEP_ERR_ARG, "unknown variant");
   if (h->shape != 0 || h->precision != NEP_FP32 || h->fb_on)
     return fail(h, NEP_ERR_UNSUPPORTED, "the variants exist for the plain float32 teacher path");
@@ -1023,14 +1041,27 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
                                                 h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess) e = launch_store_float3(h->n, h->id, h->abl_f, h->io, h->stream);
-    } else if (variant == NEP_VARIANT_HALF_LIST) {
+    } else if (variant == NEP_VARIANT_HALF_LIST || variant == NEP_VARIANT_SEPARATE_FORCE) {
       e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
                                      h->part_d, &h->ctrl->status, Fallback{}, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && variant == NEP_VARIANT_HALF_LIST)
         e = launch_force_half_list<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->F,
                                             h->part_f, &h->ctrl->status, h->stream);
+      if (e == cudaSuccess && variant == NEP_VARIANT_SEPARATE_FORCE)
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, G, h->F,
+                                         h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
+    } else if (variant == NEP_VARIANT_SEPARATE_DESCRIPTOR) {
+      e = cudaEventRecord(a, h->stream);
+      if (e == cudaSuccess)
+        e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
+                                       h->part_d, &h->ctrl->status, Fallback{}, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess)
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, G, h->F,
+                                         h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     } else {
       if (!h->abl_s) e = dalloc(h->abl_s, (size_t)CuShape::NA * CuShape::NLM * N);

@@ -222,67 +222,22 @@ struct ForceCfg {
   static_assert(!TM || FORCE_BLOCK == 128, "one TMEM lane per thread: 4 warps cover the 128 lanes");
 };
 
-// FULL = true walks the whole row (nrow = full row lengths) with atom i's own adjoint only; FULL =
-// false walks the owned half (nrow = owned counts) and gathers the neighbour's row (see the file
-// header).  FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float
-// atomicAdd into Ff, whose result depends on the order in which the additions arrive.
-//
-// With the row in TMEM the pair loop runs to the warp's largest owned count (threads past their own
-// count, or past the last atom, idle with a predicate) so that the angular block, which holds the
-// warp-collective TMEM loads, is entered by whole warps: lanes without an angular pair in that
-// iteration compute on a harmless stand-in pair and discard the result.
-#ifndef NEP_FORCE_MINB_FULL
-#define NEP_FORCE_MINB_FULL 4
-#endif
-template <class S, class GT, bool FS = false, bool FULL = false>
-__global__ void __launch_bounds__(FORCE_BLOCK, FULL && ForceCfg<S>::TM ? NEP_FORCE_MINB_FULL : ForceCfg<S>::MINB)
-k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
-        const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
-        int *__restrict__ status, float *__restrict__ Ff = nullptr) {
+// The pair loop of the force kernel (see k_force), for atom i whose adjoint row is already in place:
+// in TMEM at trow (teacher shape) or in gi (registers), radial tail in fpi.  Adds d_ij (FULL) or D_ij
+// to F_i and subtracts it from F_j, and leaves the virial and pair counters in acc.
+template <class S, class GT, bool FS, bool FULL>
+__device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shift, uint32_t trow,
+                                            const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
+                                            const float (&fpi)[8], int i, bool live, int ii, int n,
+                                            const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
+                                            const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
+                                            const GT *__restrict__ G, uint32_t *ring_e, float4 *ring_p,
+                                            unsigned long long *__restrict__ Ffix, int *__restrict__ status,
+                                            float *__restrict__ Ff, long long (&acc)[13]) {
   constexpr bool TM = ForceCfg<S>::TM;
   constexpr int W = GTraits<GT>::W;
-  __shared__ float4 shift[27];
   constexpr int DE = ForceCfg<S>::DE, DP = ForceCfg<S>::DP;
-  __shared__ uint32_t ring_e[DE * FORCE_BLOCK];
-  __shared__ float4 ring_p[DP * FORCE_BLOCK];
-  __shared__ uint32_t tmem_base;
-  if constexpr (TM) {
-    if (threadIdx.x < 32) tmem_alloc(&tmem_base, ForceCfg<S>::TCOLS);
-    tc_fence_before();
-  }
-  fill_shift_table(shift, geom);
-  __syncthreads();
-  uint32_t trow = 0;   // this thread's TMEM lane, column 0
-  if constexpr (TM) {
-    tc_fence_after();
-    trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
-  }
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = i < n;
-  const int ii = live ? i : 0;            // the row read (and ignored) by threads past the last atom
-  long long acc[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const float4 pi = pos[ii];
-  const GT *Gi = G + (size_t)ii * S::GS;
-  // G_i[a][lm] lives at TMEM column (lm - lm mod W) NA + a W + lm mod W: chunk c of W components
-  // holds all channels in NA consecutive groups of W columns.
-  float gi[TM ? 1 : S::NA][TM ? 1 : S::NLM];
-#pragma unroll
-  for (int a = 0; a < S::NA; ++a)
-#pragma unroll
-    for (int c = 0; c < S::NLM; c += W) {
-      float t[W];
-      load_vec(Gi + a * S::NLM + c, t);
-      if constexpr (TM) {
-        tmem_st(trow + (uint32_t)(c * S::NA + a * W), t);
-      } else {
-#pragma unroll
-        for (int k = 0; k < W; ++k) gi[a][c + k] = t[k];
-      }
-    }
-  if constexpr (TM) tmem_wait_st();
-  float fpi[8];
-  load_tail8(Gi, S::NA * S::NLM, fpi);
   float fx = 0.f, fy = 0.f, fz = 0.f;
   float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
   const int cnt = live ? nrow[i] : 0;
@@ -435,6 +390,70 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     acc[6] = -to_fix32(wzx); acc[7] = -to_fix32(wzy); acc[8] = -to_fix32(wzz);
     acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang;
   }
+}
+
+// FULL = true walks the whole row (nrow = full row lengths) with atom i's own adjoint only; FULL =
+// false walks the owned half (nrow = owned counts) and gathers the neighbour's row (see the file
+// header).  FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float
+// atomicAdd into Ff, whose result depends on the order in which the additions arrive.
+//
+// With the row in TMEM the pair loop runs to the warp's largest owned count (threads past their own
+// count, or past the last atom, idle with a predicate) so that the angular block, which holds the
+// warp-collective TMEM loads, is entered by whole warps: lanes without an angular pair in that
+// iteration compute on a harmless stand-in pair and discard the result.
+#ifndef NEP_FORCE_MINB_FULL
+#define NEP_FORCE_MINB_FULL 4
+#endif
+template <class S, class GT, bool FS = false, bool FULL = false>
+__global__ void __launch_bounds__(FORCE_BLOCK, FULL && ForceCfg<S>::TM ? NEP_FORCE_MINB_FULL : ForceCfg<S>::MINB)
+k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
+        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
+        const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
+        int *__restrict__ status, float *__restrict__ Ff = nullptr) {
+  constexpr bool TM = ForceCfg<S>::TM;
+  constexpr int W = GTraits<GT>::W;
+  __shared__ float4 shift[27];
+  constexpr int DE = ForceCfg<S>::DE, DP = ForceCfg<S>::DP;
+  __shared__ uint32_t ring_e[DE * FORCE_BLOCK];
+  __shared__ float4 ring_p[DP * FORCE_BLOCK];
+  __shared__ uint32_t tmem_base;
+  if constexpr (TM) {
+    if (threadIdx.x < 32) tmem_alloc(&tmem_base, ForceCfg<S>::TCOLS);
+    tc_fence_before();
+  }
+  fill_shift_table(shift, geom);
+  __syncthreads();
+  uint32_t trow = 0;   // this thread's TMEM lane, column 0
+  if constexpr (TM) {
+    tc_fence_after();
+    trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  const int ii = live ? i : 0;            // the row read (and ignored) by threads past the last atom
+  long long acc[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const GT *Gi = G + (size_t)ii * S::GS;
+  // G_i[a][lm] lives at TMEM column (lm - lm mod W) NA + a W + lm mod W: chunk c of W components
+  // holds all channels in NA consecutive groups of W columns.
+  float gi[TM ? 1 : S::NA][TM ? 1 : S::NLM];
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+    for (int c = 0; c < S::NLM; c += W) {
+      float t[W];
+      load_vec(Gi + a * S::NLM + c, t);
+      if constexpr (TM) {
+        tmem_st(trow + (uint32_t)(c * S::NA + a * W), t);
+      } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) gi[a][c + k] = t[k];
+      }
+    }
+  if constexpr (TM) tmem_wait_st();
+  float fpi[8];
+  load_tail8(Gi, S::NA * S::NLM, fpi);
+  force_pairs<S, GT, FS, FULL>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, nrow, nband0, G, ring_e, ring_p, Ffix,
+                               status, Ff, acc);
   if constexpr (TM) {
     tc_fence_before();
     __syncthreads();
@@ -444,6 +463,103 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
     }
   }
   block_sum_store<13, FORCE_BLOCK / 32>(acc, part);
+}
+
+// Descriptors, network and forces of the float32 teacher in one kernel.  The full-row force form reads
+// no neighbour row, so no atom waits for another's adjoint row: the angular sums s_nlm are accumulated
+// in TMEM, turned into the adjoint row in place, and the force pass walks the row again with it, so no
+// adjoint row goes through HBM and one launch (and its tail wave) is saved.  The forces are scattered
+// with atomics into Ffix, which the caller zeroes before the launch (a block may add to F_j before
+// atom j's own block has started).
+#ifndef NEP_FUSED_MINB
+#define NEP_FUSED_MINB 4
+#endif
+template <class S>
+__global__ void __launch_bounds__(DESC_BLOCK, NEP_FUSED_MINB)
+k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
+            const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ usite,
+            float *__restrict__ qout, unsigned long long *__restrict__ Ffix, long long *__restrict__ part_d,
+            long long *__restrict__ part_f, int *__restrict__ status) {
+  static_assert(ForceCfg<S>::TM && DESC_BLOCK == 128 && FORCE_BLOCK == 128, "teacher shape, 4 warps");
+  static_assert(ForceCfg<S>::DE <= PIPE_DE && ForceCfg<S>::DP <= PIPE_DP, "one ring serves both passes");
+  constexpr int W = TMEM_W;
+  constexpr uint32_t TCOLS = 128;
+  __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
+  __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
+  __shared__ uint32_t tmem_base;
+  if (threadIdx.x < 32) tmem_alloc(&tmem_base, TCOLS);
+  tc_fence_before();
+  fill_shift_table(shift, geom);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  const int ii = live ? i : 0;
+  const int cnt = live ? nnum[i] : 0;
+
+  // descriptors and network (as k_descriptor_tm)
+  float QR[S::KR], elj;
+  int nrad, nang, nact;
+  RegSums<S, S::NA> R;
+  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, cnt, ring_e, ring_p,
+                                                             QR, R, elj, nrad, nang, nact);
+  float q[S::NDES];
+  FourBody<S> T;
+  descriptors_tm<S, S::NA>(P, trow, QR, R, q, T);
+  if (live && qout != nullptr) {
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
+  }
+  float Fp[S::NDES];
+  const float U = network<S>(P, q, false, Fp);
+
+  // the adjoint row replaces the sums in TMEM (same columns, chunk by chunk); radial tail in registers
+  float g4[S::NA][5];
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
+#pragma unroll
+  for (int c = 0; c < S::NLM; c += W) {
+    float sv[S::NA][W];
+    sums_chunk<S, S::NA>(trow, c, R, sv);
+    uint32_t cols[S::NA];
+    tmem_chunk_cols<S::NA>(trow, c, cols);
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) {
+      float gl[W];
+      adjoint_chunk<S>(a, c, sv[a], g4[a], Fp, gl);
+      tmem_st(cols[a], gl);
+    }
+  }
+  tmem_wait_st();
+  float fpi[8];
+  radial_tail<S>(P, Fp, fpi);
+  long long acc_d[5] = {0, 0, 0, 0, 0};
+  if (live) {
+    const float ui = U + elj;
+    usite[i] = ui;
+    if (!isfinite(ui)) atomicOr(status, ST_NAN);
+    acc_d[0] = to_fix32(ui);
+    acc_d[1] = nrad;
+    acc_d[2] = nang;
+    acc_d[3] = cnt;
+    acc_d[4] = nact;
+  }
+  block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);   // before the force pass: fewer live registers
+
+  // forces: every ordered pair of the row with the own adjoint row (as k_force, FULL)
+  const float gi[1][1] = {{0.f}};
+  long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  force_pairs<S, float, false, true>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, nnum, nnum, nullptr, ring_e,
+                                     ring_p, Ffix, status, nullptr, acc_f);
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TCOLS);
+  }
+  block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -518,6 +634,21 @@ cudaError_t launch_force_float_scatter(const Model<S> &P, const Geom &g, int n, 
 template cudaError_t launch_force_float_scatter<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
                                                          const int32_t *, const int32_t *, const int32_t *,
                                                          const float *, float *, long long *, int *, cudaStream_t);
+
+// Fused descriptor + force evaluation of the float32 teacher (k_nep_fused); Ffix must be zero.
+template <class S>
+cudaError_t launch_fused(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
+                         const int32_t *nnum, float *usite, float *qout, long long *Ffix, long long *part_d,
+                         long long *part_f, int *status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
+  k_nep_fused<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, usite, qout,
+                                              reinterpret_cast<unsigned long long *>(Ffix), part_d, part_f, status);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fused<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *, const int32_t *,
+                                           const int32_t *, float *, float *, long long *, long long *, long long *,
+                                           int *, cudaStream_t);
 
 int descriptor_blocks(int n) { return (n + DESC_BLOCK - 1) / DESC_BLOCK; }
 int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }

@@ -271,7 +271,8 @@ class NEP:
                                              hi.ctypes.data_as(C.POINTER(C.c_float)), float(margin),
                                              float(max_fraction)))
 
-    VARIANTS = {"float_scatter": 1, "tile1": 2, "tile3": 3, "half_list": 4}
+    VARIANTS = {"float_scatter": 1, "tile1": 2, "tile3": 3, "half_list": 4, "separate_descriptor": 5,
+                "separate_force": 6}
 
     def run_variant(self, name: str):
         """One force evaluation with a kernel variant kept for ablation (nep_run_variant): returns

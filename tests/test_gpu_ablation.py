@@ -1,4 +1,5 @@
-"""Kernel variants kept for ablation (nep_run_variant) against the production kernels and the oracle:
+"""Kernel variants kept for ablation (nep_run_variant) against the production kernel and the oracle:
+the separate descriptor and full-row force kernels (the production fused kernel's work as two launches),
 the float-atomic force scatter (order-dependent float sums; forces equal to the fixed-point path within
 float rounding), the half-list force kernel (each unordered pair once, gathering the neighbour's row)
 and the channel-tiled descriptor kernel (same descriptors, same forces)."""
@@ -22,7 +23,8 @@ def api():
     return pkg
 
 
-@pytest.mark.parametrize("variant", ["float_scatter", "tile1", "tile3", "half_list"])
+@pytest.mark.parametrize("variant", ["float_scatter", "tile1", "tile3", "half_list", "separate_descriptor",
+                                     "separate_force"])
 def test_variant_forces(api, model_params, model, variant):
     wl = ni.fcc_cu_workload(6, 300.0, 0.05, seed=91)
     with api.NEP(model_params) as nep:

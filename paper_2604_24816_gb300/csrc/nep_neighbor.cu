@@ -343,7 +343,7 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
 // candidate order (ballot + popc), then are placed by segment: [owned | not owned] x band, candidate
 // order inside a segment -- the same row as the thread-per-atom formulation, with 32-wide work
 // instead of divergent per-thread cell loops.
-__global__ void __launch_bounds__(NB_WARPS * 32)
+__global__ void __launch_bounds__(NB_WARPS * 32, 6)   // 40 registers: 6 resident blocks
 k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_start, const Geom geom, int cap,
             Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
             int32_t *__restrict__ nown, int32_t *__restrict__ nband0, Control *ctrl) {

@@ -1,8 +1,8 @@
 """Irregular inputs for the kernels whose neighbour walk runs warp-uniformly (the teacher's descriptor
 and force kernels keep their per-atom arrays in tensor memory, whose accesses are warp-collective):
-a strained, strongly displaced cell with vacancies and a small cell with a spherical void, so that the
-rows of the atoms in one warp differ in length and in their angular entries, and the atom counts leave
-the last block partly empty.  Float32 path, float16-row path and the half-list force variant, each
+a strained, displaced cell with vacancies, a small cell with a spherical void and a sparse gas (a single
+partial block; some atoms without any angular neighbour), so that the rows of the atoms in one warp
+differ in length and in their angular entries, and the atom counts leave the last block partly empty.  Float32 path, float16-row path and the half-list force variant, each
 against the oracle."""
 import numpy as np
 import pytest
@@ -24,12 +24,27 @@ def api():
     return pkg
 
 
+def _gas(n=37, box=(13.0, 13.5, 14.0), rmin=2.3, seed=404):
+    """A sparse gas: n atoms placed at random with no pair closer than rmin -- one partial block,
+    rows of 0 to 6 angular and 9 to 15 list entries."""
+    rng = np.random.default_rng(seed)
+    box = np.asarray(box)
+    pts = []
+    while len(pts) < n:
+        p = rng.uniform(0.0, 1.0, 3) * box
+        d = np.asarray(pts).reshape(-1, 3) - p
+        d -= box * np.round(d / box)
+        if not len(pts) or np.sqrt((d ** 2).sum(1)).min() >= rmin:
+            pts.append(p)
+    return np.asarray(pts), box
+
+
 def _cells():
     # 0.07 A displacements: closest pair 2.24 A, |F| up to 10 eV/A (stronger disorder brings atoms
     # within 1.5 A, where float32 rounding of the LJ core alone exceeds the 1e-4 eV/A bound)
     pos, box = ni.student_cell(306, (5, 5, 5), 0.07, (0.01, -0.02, 0.0), 10)
     void = ni.void_strain_workload(6, void_radius=5.0, strain_z=0.02, seed=9)
-    return {"disordered": (pos, box), "void": (void.pos, void.box)}
+    return {"disordered": (pos, box), "void": (void.pos, void.box), "gas": _gas()}
 
 
 CELLS = _cells()
@@ -42,6 +57,8 @@ def cell(request, model):
     row = np.diff(oracle.neighbor_lists(pos, box, 6.0)[0])
     assert pos.shape[0] % 128 != 0                  # ragged last block
     assert ang.max() - ang.min() >= 3 and row.max() - row.min() >= 5   # rows of unequal length
+    if request.param == "gas":
+        assert ang.min() == 0                       # atoms without an angular neighbour
     return request.param, pos, box, oracle.energy_forces(model, pos, box)
 
 

@@ -162,7 +162,9 @@ nep_status nep_get_timing(nep_handle *h, double ms[NEP_N_KERNEL_CLASSES], int64_
  * same four counts for the rows walked by the force kernel (whole rows for the float32 teacher, the
  * owned half of each row otherwise): list entries, pairs inside the largest cutoff, radial pairs,
  * angular pairs, then the atom evaluations done by the fallback model (nep_set_fallback)}.  Pair and
- * atom counts sum over evaluations. */
+ * atom counts sum over evaluations.  List entries count the entries walked: the far band of each row
+ * part (entries built beyond rc_R + 0.4 skin) is left out while no atom has moved more than
+ * (0.4 skin - 0.02 A)/2 since the last rebuild, since none of its pairs can then be inside rc_R. */
 nep_status nep_get_counters(nep_handle *h, int64_t out[13]);
 
 /* Per-atom fallback from a student-shaped model (n_max 3/3, l_max 2, no 4-body, 16 neurons) to a

@@ -19,7 +19,7 @@ constexpr int T_DE = 8, T_DP = 4;
 template <class S, int NT>
 __global__ void __launch_bounds__(TB, 2)
 k_descriptor_tiled(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-                   const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
+                   const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ G,
                    float *__restrict__ usite, long long *__restrict__ Ffix, long long *__restrict__ part,
                    int *__restrict__ status, float *__restrict__ sbuf) {
   __shared__ float4 shift[27];
@@ -32,7 +32,8 @@ k_descriptor_tiled(const __grid_constant__ Model<S> P, const Geom geom, const in
   if (i < n) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     const float4 pi = pos[i];
-    const int cnt = nnum[i];
+    const RowSpan sp = full_row(X, i, skip_far(X));
+    const int cnt = sp.c;
     // radial basis sums and LJ energy over the full row
     float QR[S::KR];
 #pragma unroll
@@ -41,7 +42,7 @@ k_descriptor_tiled(const __grid_constant__ Model<S> P, const Geom geom, const in
     int nrad = 0, nang = 0, nact = 0;
     {
       NbrPipe<T_DE, T_DP, TB> pipe;
-      pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
+      pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, sp);
       for (int k = 0; k < cnt; ++k) {
         uint32_t e;
         float4 pj;
@@ -86,7 +87,7 @@ k_descriptor_tiled(const __grid_constant__ Model<S> P, const Geom geom, const in
 #pragma unroll
         for (int c = 0; c < S::NLM; ++c) s[a][c] = 0.f;
       NbrPipe<T_DE, T_DP, TB> pipe;
-      pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
+      pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, sp);
       for (int k = 0; k < cnt; ++k) {
         uint32_t e;
         float4 pj;
@@ -211,10 +212,10 @@ __global__ void k_store_float3(int n, const int *__restrict__ id, const float *_
 
 template <class S, int NT>
 cudaError_t launch_descriptor_tiled(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                                    const int32_t *nnum, float *G, float *usite, long long *Ffix, long long *part,
+                                    const RowExt &X, float *G, float *usite, long long *Ffix, long long *part,
                                     int *status, float *sbuf, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_descriptor_tiled<S, NT><<<(n + TB - 1) / TB, TB, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, Ffix, part, status,
+  k_descriptor_tiled<S, NT><<<(n + TB - 1) / TB, TB, 0, st>>>(P, g, n, pos, nbr, X, G, usite, Ffix, part, status,
                                                                sbuf);
   return cudaGetLastError();
 }
@@ -227,10 +228,10 @@ cudaError_t launch_store_float3(int n, const int *id, const float *Ff, double *o
 int tiled_descriptor_blocks(int n) { return (n + TB - 1) / TB; }
 
 template cudaError_t launch_descriptor_tiled<CuShape, 1>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                         const int32_t *, const int32_t *, float *, float *,
+                                                         const int32_t *, const RowExt &, float *, float *,
                                                          long long *, long long *, int *, float *, cudaStream_t);
 template cudaError_t launch_descriptor_tiled<CuShape, 3>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                         const int32_t *, const int32_t *, float *, float *,
+                                                         const int32_t *, const RowExt &, float *, float *,
                                                          long long *, long long *, int *, float *, cudaStream_t);
 
 }  // namespace nep

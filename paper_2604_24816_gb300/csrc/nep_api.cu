@@ -27,14 +27,14 @@
 namespace nep {
 // nep_force.cu
 template <class S>
-cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
+cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
                               float *, float *, float *, long long *, long long *, int *, const Fallback &,
                               cudaStream_t);
 template <class S, class GT>
-cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
+cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
+                         const GT *, long long *, long long *, int *, cudaStream_t);
 template <class S>
-cudaError_t launch_fused(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *, float *,
+cudaError_t launch_fused(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &, float *,
                          float *, long long *, long long *, long long *, int *, cudaStream_t);
 #ifndef NEP_FUSED
 #define NEP_FUSED 1
@@ -44,7 +44,7 @@ int force_blocks(int n);
 // nep_mixed.cu
 template <class S, class MT>
 cudaError_t launch_descriptor_mixed(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
-                                    const int32_t *, __half *, float *, float *, long long *, long long *, int *,
+                                    const RowExt &, __half *, float *, float *, long long *, long long *, int *,
                                     const Fallback &, cudaStream_t);
 int mixed_descriptor_blocks(int n);
 template <class S>
@@ -59,15 +59,13 @@ cudaError_t launch_fallback_flags(const int *, const int *, int, const int *, in
 // nep_force.cu / nep_ablation.cu: kernel variants for ablation
 template <class S>
 cudaError_t launch_force_float_scatter(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
-                                       const int32_t *, const int32_t *, const float *, float *, long long *, int *,
-                                       cudaStream_t);
+                                       const RowExt &, const float *, float *, long long *, int *, cudaStream_t);
 template <class S>
 cudaError_t launch_force_half_list(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
-                                   const int32_t *, const int32_t *, const float *, long long *, long long *, int *,
-                                   cudaStream_t);
+                                   const RowExt &, const float *, long long *, long long *, int *, cudaStream_t);
 template <class S, int NT>
 cudaError_t launch_descriptor_tiled(const Model<S> &, const Geom &, int, const float4 *, const int32_t *,
-                                    const int32_t *, float *, float *, long long *, long long *, int *, float *,
+                                    const RowExt &, float *, float *, long long *, long long *, int *, float *,
                                     cudaStream_t);
 cudaError_t launch_store_float3(int, const int *, const float *, double *, cudaStream_t);
 // nep_neighbor.cu
@@ -146,7 +144,7 @@ struct nep_handle {
   long long *F = nullptr;          // fixed-point forces [3][n]
   float *usite = nullptr, *qbuf = nullptr;
   void *G = nullptr;               // adjoint rows: float32 (plain) or float16 (mixed) [n][GS]
-  int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr, *nown = nullptr, *nband0 = nullptr;
+  int32_t *nbr = nullptr, *nnum = nullptr, *nang = nullptr, *nown = nullptr, *nband0 = nullptr, *nfar = nullptr;
   int *count = nullptr, *cursor = nullptr, *start = nullptr, *tile_sums = nullptr;
   long long *part_d = nullptr, *part_f = nullptr, *part_k = nullptr;   // per-block int64 partial sums
   double *sums = nullptr;
@@ -232,7 +230,7 @@ void free_system(nep_handle *h) {
   dfree(h->xb); dfree(h->yb); dfree(h->zb); dfree(h->vxb); dfree(h->vyb); dfree(h->vzb);
   dfree(h->id); dfree(h->idb); dfree(h->cell_of); dfree(h->perm);
   dfree(h->pos); dfree(h->pos_ref); dfree(h->F); dfree(h->usite); dfree(h->G); dfree(h->qbuf);
-  dfree(h->nbr); dfree(h->nnum); dfree(h->nang); dfree(h->nown); dfree(h->nband0);
+  dfree(h->nbr); dfree(h->nnum); dfree(h->nang); dfree(h->nown); dfree(h->nband0); dfree(h->nfar);
   dfree(h->count); dfree(h->cursor); dfree(h->start); dfree(h->tile_sums);
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
   dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
@@ -297,6 +295,14 @@ void collect_timers(nep_handle *h) {
   h->timers_used = 0;
 }
 
+// Largest squared displacement since the build (Angstrom^2) below which the far band (list entries
+// built at r >= rc_R + FAR_EDGE skin) cannot hold a pair inside rc_R: two atoms close by at most twice
+// the largest displacement, with a 0.02 Angstrom margin for float32 coordinates.  -1: never skip.
+float far_dmax2(float skin) {
+  const float d = 0.5f * (FAR_EDGE * skin - 0.02f);
+  return d > 0.f ? d * d : -1.f;
+}
+
 RebuildArgs rebuild_args(nep_handle *h) {
   RebuildArgs a;
   a.n = h->n; a.ncell = h->ncell;
@@ -306,13 +312,17 @@ RebuildArgs rebuild_args(nep_handle *h) {
   a.id = h->id; a.idb = h->idb; a.cell_of = h->cell_of; a.count = h->count; a.cursor = h->cursor;
   a.start = h->start; a.tile_sums = h->tile_sums; a.perm = h->perm;
   a.pos = h->pos; a.pos_ref = h->pos_ref; a.nbr = h->nbr; a.nnum = h->nnum; a.nang = h->nang; a.nown = h->nown; a.nband0 = h->nband0;
+  a.nfar = h->nfar;
   a.cap = h->cap;
-  const float rl = h->rcR + h->skin, ra = h->rcA + h->skin;
-  a.rl2 = rl * rl; a.ra2 = ra * ra;
+  const float rl = h->rcR + h->skin, ra = h->rcA + h->skin, fs = h->rcR + FAR_EDGE * h->skin;
+  a.rl2 = rl * rl; a.ra2 = ra * ra; a.fs2 = fs * fs;
   a.ba2 = h->rcA * h->rcA; a.br2 = h->rcR * h->rcR;
   a.ctrl = h->ctrl;
   return a;
 }
+
+// The list extents the row walks read; the far bands are left out while ctrl->skip_far is set.
+RowExt rows_of(nep_handle *h) { return RowExt{h->nnum, h->nown, h->nband0, h->nfar, h->ctrl}; }
 
 Geom geom_of(nep_handle *h) {
   Geom g;
@@ -344,7 +354,7 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
       Scope sc(h, KC_FORCE, 1);
       cudaError_t e = cudaMemsetAsync(h->F, 0, 3 * (size_t)h->n * sizeof(long long), h->stream);
       if (e != cudaSuccess) return e;
-      return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, h->nnum, h->usite, qout, h->F, h->part_d, h->part_f,
+      return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F, h->part_d, h->part_f,
                                    &h->ctrl->status, h->stream);
     }
   }
@@ -359,13 +369,13 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   {
     Scope sc(h, KC_DESC, 1);
     if (h->precision == NEP_FP32)
-      e = launch_descriptor<S>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<float *>(h->G), h->usite, qout, h->F,
+      e = launch_descriptor<S>(M, g, h->n, h->pos, h->nbr, rows_of(h), static_cast<float *>(h->G), h->usite, qout, h->F,
                                h->part_d, &h->ctrl->status, fb, h->stream);
     else if (h->precision == NEP_MIX_BF16)
-      e = launch_descriptor_mixed<S, __nv_bfloat16>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
+      e = launch_descriptor_mixed<S, __nv_bfloat16>(M, g, h->n, h->pos, h->nbr, rows_of(h), static_cast<__half *>(h->G),
                                                      h->usite, qout, h->F, h->part_d, &h->ctrl->status, fb, h->stream);
     else
-      e = launch_descriptor_mixed<S, __half>(M, g, h->n, h->pos, h->nbr, h->nnum, static_cast<__half *>(h->G),
+      e = launch_descriptor_mixed<S, __half>(M, g, h->n, h->pos, h->nbr, rows_of(h), static_cast<__half *>(h->G),
                                               h->usite, qout, h->F, h->part_d, &h->ctrl->status, fb, h->stream);
   }
   if (e != cudaSuccess) return e;
@@ -379,10 +389,10 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   {
     Scope sc(h, KC_FORCE, 1);
     if (h->precision == NEP_FP32)
-      e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, static_cast<const float *>(h->G),
+      e = launch_force<S, float>(M, g, h->n, h->pos, h->nbr, rows_of(h), static_cast<const float *>(h->G),
                                  h->F, h->part_f, &h->ctrl->status, h->stream);
     else
-      e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, static_cast<const __half *>(h->G),
+      e = launch_force<S, __half>(M, g, h->n, h->pos, h->nbr, rows_of(h), static_cast<const __half *>(h->G),
                                   h->F, h->part_f, &h->ctrl->status, h->stream);
   }
   if (e == cudaSuccess && fb.on) {
@@ -685,6 +695,7 @@ nep_status nep_create(const nep_params *p, void *cuda_stream, nep_handle **out) 
   cudaMemsetAsync(h->counters, 0, 16 * sizeof(long long), h->stream);
   Control c0{};
   c0.rebuild_every = h->rebuild_every;
+  c0.far_dmax2 = far_dmax2(h->skin);
   cudaMemcpyAsync(h->ctrl, &c0, sizeof(Control), cudaMemcpyHostToDevice, h->stream);
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { nep_destroy(h); return NEP_ERR_CUDA; }
   *out = h;
@@ -755,7 +766,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N));
   A(dalloc(reinterpret_cast<char *&>(h->G), N * (size_t)h->gs() * (h->precision == NEP_FP32 ? 4 : 2)));
   A(dalloc(h->nbr, N * (size_t)h->cap)); A(dalloc(h->nnum, N)); A(dalloc(h->nang, N)); A(dalloc(h->nown, N));
-  A(dalloc(h->nband0, N));
+  A(dalloc(h->nband0, N)); A(dalloc(h->nfar, N));
   A(dalloc(h->count, (size_t)h->ncell)); A(dalloc(h->cursor, (size_t)h->ncell)); A(dalloc(h->start, (size_t)h->ncell + 1));
   A(dalloc(h->tile_sums, (size_t)scan_tiles(h->ncell) + 1));
   A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 13 + 1));
@@ -772,6 +783,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   NEP_CUDA(h, cudaMemsetAsync(h->counters, 0, 16 * sizeof(long long), h->stream));
   Control c0{};
   c0.rebuild_every = h->rebuild_every;
+  c0.far_dmax2 = far_dmax2(h->skin);
   NEP_CUDA(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Control), cudaMemcpyHostToDevice, h->stream));
   return upload_state(h, x, v);
 }
@@ -1032,35 +1044,35 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
     if (variant == NEP_VARIANT_FLOAT_SCATTER) {
       if (!h->abl_f) e = dalloc(h->abl_f, 3 * N);
       if (e == cudaSuccess)
-        e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
+        e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->usite, nullptr, h->F,
                                        h->part_d, &h->ctrl->status, Fallback{}, h->stream);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->abl_f, 0, 3 * N * sizeof(float), h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
       if (e == cudaSuccess)
-        e = launch_force_float_scatter<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nband0, G, h->abl_f,
+        e = launch_force_float_scatter<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->abl_f,
                                                 h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess) e = launch_store_float3(h->n, h->id, h->abl_f, h->io, h->stream);
     } else if (variant == NEP_VARIANT_HALF_LIST || variant == NEP_VARIANT_SEPARATE_FORCE) {
-      e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
+      e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->usite, nullptr, h->F,
                                      h->part_d, &h->ctrl->status, Fallback{}, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
       if (e == cudaSuccess && variant == NEP_VARIANT_HALF_LIST)
-        e = launch_force_half_list<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nown, h->nband0, G, h->F,
+        e = launch_force_half_list<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->F,
                                             h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess && variant == NEP_VARIANT_SEPARATE_FORCE)
-        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, G, h->F,
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->F,
                                          h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     } else if (variant == NEP_VARIANT_SEPARATE_DESCRIPTOR) {
       e = cudaEventRecord(a, h->stream);
       if (e == cudaSuccess)
-        e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, nullptr, h->F,
+        e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->usite, nullptr, h->F,
                                        h->part_d, &h->ctrl->status, Fallback{}, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess)
-        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, G, h->F,
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->F,
                                          h->part_f, &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     } else {
@@ -1068,15 +1080,15 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
       if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
       if (e == cudaSuccess) {
         if (variant == NEP_VARIANT_TILE1)
-          e = launch_descriptor_tiled<CuShape, 1>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, h->F,
+          e = launch_descriptor_tiled<CuShape, 1>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->usite, h->F,
                                                   h->part_d, &h->ctrl->status, h->abl_s, h->stream);
         else
-          e = launch_descriptor_tiled<CuShape, 3>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, G, h->usite, h->F,
+          e = launch_descriptor_tiled<CuShape, 3>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->usite, h->F,
                                                   h->part_d, &h->ctrl->status, h->abl_s, h->stream);
       }
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess)
-        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, h->nnum, h->nown, h->nband0, G, h->F, h->part_f,
+        e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->F, h->part_f,
                                          &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     }

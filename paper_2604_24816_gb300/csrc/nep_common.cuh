@@ -32,6 +32,13 @@ enum : int {
   ST_FB_OVERFLOW = 8 // more atoms flagged for the fallback model than its list holds
 };
 
+// The far band of a neighbour-list row starts at rc_R + FAR_EDGE * skin.  For fcc Cu at rc_R = 5 A and
+// a 1 A skin this edge (5.4 A) lies between the 5.11 A and 5.72 A shells, so every atom's far band is
+// the same shell and the walked rows stay aligned across the lanes of a warp; an edge inside a shell's
+// thermal spread gives neighbouring atoms walked counts that differ by one or two, which misaligns the
+// lanes' bands and costs more than the skipped entries save.
+constexpr float FAR_EDGE = 0.4f;
+
 // Device-side control block (one per handle).
 struct Control {
   int status;           // OR of ST_* bits
@@ -43,6 +50,9 @@ struct Control {
   long long rebuilds;   // neighbour builds done
   long long steps;      // MD steps done
   int nb_next;          // next group of atoms for the neighbour scan (reset by each rebuild)
+  float dmax2;          // largest squared displacement of an atom since the last rebuild (Angstrom^2)
+  float far_dmax2;      // below this, no list entry of the far band can be inside the largest cutoff
+  int skip_far;         // decision for the current evaluation: row walks may skip the far band
 };
 
 // Arguments of the rebuild chain (cell sort + neighbour list).
@@ -53,9 +63,10 @@ struct RebuildArgs {
   double *x, *y, *z, *vx, *vy, *vz, *xb, *yb, *zb, *vxb, *vyb, *vzb;
   int *id, *idb, *cell_of, *count, *cursor, *start, *tile_sums, *perm;
   float4 *pos, *pos_ref;
-  int32_t *nbr, *nnum, *nang, *nown, *nband0;
+  int32_t *nbr, *nnum, *nang, *nown, *nband0, *nfar;
   int cap;
   float rl2, ra2, ba2, br2;   // (rc_R+skin)^2, (rc_A+skin)^2, rc_A^2, rc_R^2
+  float fs2;                  // (rc_R + FAR_EDGE skin)^2: where the far band starts
   Control *ctrl;
 };
 
@@ -344,6 +355,38 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// The entries of a row that a walk visits: c entries, the first c1 at list slots 0..c1-1, the rest
+// after a gap of `gap` slots (the owned part's far band, skipped together with the other part's).
+struct RowSpan {
+  int c, c1, gap;
+};
+// Whole row [owned | not owned], each part ending with its far band (counts packed in nfar: owned in
+// the low 16 bits).  skip: leave both far bands out.
+__device__ __forceinline__ RowSpan full_row(int nnum, int nown, int nfar, bool skip) {
+  if (!skip) return RowSpan{nnum, nnum, 0};
+  const int of = nfar & 0xffff, nf = nfar >> 16;
+  return RowSpan{nnum - of - nf, nown - of, of};
+}
+// The owned part only (each unordered pair once).
+__device__ __forceinline__ RowSpan owned_row(int nown, int nfar, bool skip) {
+  const int c = skip ? nown - (nfar & 0xffff) : nown;
+  return RowSpan{c, c, 0};
+}
+
+// The per-atom extents of the neighbour list that the row walks read, and the control block whose
+// skip_far says whether this evaluation leaves the far bands out (nullptr: never).
+struct RowExt {
+  const int32_t *nnum, *nown, *nband0, *nfar;
+  const Control *ctrl;
+};
+__device__ __forceinline__ bool skip_far(const RowExt &X) { return X.ctrl != nullptr && X.ctrl->skip_far != 0; }
+__device__ __forceinline__ RowSpan full_row(const RowExt &X, int i, bool skip) {
+  return skip ? full_row(X.nnum[i], X.nown[i], X.nfar[i], true) : RowSpan{X.nnum[i], X.nnum[i], 0};
+}
+__device__ __forceinline__ RowSpan owned_row(const RowExt &X, int i, bool skip) {
+  return skip ? owned_row(X.nown[i], X.nfar[i], true) : RowSpan{X.nown[i], X.nown[i], 0};
+}
+
 template <int DE, int DP, int BLOCK>
 struct NbrPipe {
   static_assert(DE >= 2 * DP && DP >= 1, "entries must run at least twice as far ahead as positions");
@@ -352,14 +395,18 @@ struct NbrPipe {
   const int32_t *row;      // &nbr[0 * n + i]
   size_t n;
   const float4 *pos;
-  int cnt;
+  int cnt, c1, gap;        // the walked entries (RowSpan)
+
+  // list slot of the k-th walked entry
+  __device__ __forceinline__ size_t slot(int k) const { return (size_t)(k < c1 ? k : k + gap); }
 
   __device__ __forceinline__ void start(uint32_t *ring_e, float4 *ring_p, const int32_t *row_, size_t n_,
-                                        const float4 *pos_, int cnt_) {
-    re = ring_e + threadIdx.x; rp = ring_p + threadIdx.x; row = row_; n = n_; pos = pos_; cnt = cnt_;
+                                        const float4 *pos_, RowSpan sp) {
+    re = ring_e + threadIdx.x; rp = ring_p + threadIdx.x; row = row_; n = n_; pos = pos_;
+    cnt = sp.c; c1 = sp.c1; gap = sp.gap;
 #pragma unroll
     for (int k = 0; k < DE; ++k)
-      if (k < cnt) cp_async4(re + k * BLOCK, row + (size_t)k * n);
+      if (k < cnt) cp_async4(re + k * BLOCK, row + slot(k) * n);
     cp_async_commit();
     cp_async_wait<0>();
 #pragma unroll
@@ -368,6 +415,10 @@ struct NbrPipe {
       cp_async_commit();
     }
   }
+  __device__ __forceinline__ void start(uint32_t *ring_e, float4 *ring_p, const int32_t *row_, size_t n_,
+                                        const float4 *pos_, int cnt_) {
+    start(ring_e, ring_p, row_, n_, pos_, RowSpan{cnt_, cnt_, 0});
+  }
 
   // Entry k (0 <= k < cnt, called for k = 0, 1, 2, ... in order): its packed list entry and the
   // neighbour's position; issues the copies for entries k + DE and k + DP.
@@ -375,7 +426,7 @@ struct NbrPipe {
     cp_async_wait<DP - 1>();
     e = re[(k % DE) * BLOCK];
     p = rp[(k % DP) * BLOCK];
-    if (k + DE < cnt) cp_async4(re + ((k + DE) % DE) * BLOCK, row + (size_t)(k + DE) * n);
+    if (k + DE < cnt) cp_async4(re + ((k + DE) % DE) * BLOCK, row + slot(k + DE) * n);
     if (k + DP < cnt) cp_async16(rp + ((k + DP) % DP) * BLOCK, pos + (re[((k + DP) % DE) * BLOCK] & J_MASK));
     cp_async_commit();
   }

@@ -95,7 +95,8 @@ struct AtomSums {
 template <class S, int DE, int DP, int BLOCK>
 __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 *shift, int i, int n,
                                                 const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
-                                                int cnt, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A) {
+                                                RowSpan sp, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A) {
+  const int cnt = sp.c;
   const float4 pi = pos[i];
 #pragma unroll
   for (int k = 0; k < S::KR; ++k) A.QR[k] = 0.f;
@@ -106,7 +107,7 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
   A.elj = 0.f;
   A.nrad = 0; A.nang = 0; A.nact = 0; A.cnt = cnt;
   NbrPipe<DE, DP, BLOCK> pipe;
-  pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, cnt);
+  pipe.start(ring_e, ring_p, nbr + i, (size_t)n, pos, sp);
   for (int k = 0; k < cnt; ++k) {
     uint32_t e;
     float4 pj;
@@ -151,6 +152,12 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
     }
   }
   pipe.finish();
+}
+template <class S, int DE, int DP, int BLOCK>
+__device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 *shift, int i, int n,
+                                                const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
+                                                int cnt, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A) {
+  accumulate_atom<S, DE, DP, BLOCK>(P, shift, i, n, pos, nbr, RowSpan{cnt, cnt, 0}, ring_e, ring_p, A);
 }
 
 // Traceless 4-body tensors T_n rebuilt from the l = 2 sums (components 3..7 = m -2..2).
@@ -312,7 +319,7 @@ struct RegSums {
 template <class S, int NT, int DE, int DP, int BLOCK>
 __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const float4 *shift, uint32_t trow, int ii,
                                                    int n, const float4 *__restrict__ pos,
-                                                   const int32_t *__restrict__ nbr, int cnt, uint32_t *ring_e,
+                                                   const int32_t *__restrict__ nbr, RowSpan sp, uint32_t *ring_e,
                                                    float4 *ring_p, float (&QR)[S::KR], RegSums<S, NT> &R,
                                                    float &elj, int &nrad, int &nang, int &nact) {
   static_assert(S::NA == 5 && S::NLM == 24 && (NT == 4 || NT == 5), "teacher shape");
@@ -334,8 +341,9 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
   elj = 0.f;
   nrad = 0; nang = 0; nact = 0;
   const float4 pi = pos[ii];
+  const int cnt = sp.c;
   NbrPipe<DE, DP, BLOCK> pipe;
-  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, cnt);
+  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, sp);
   const int trip = __reduce_max_sync(0xffffffffu, cnt);
   for (int k = 0; k < trip; ++k) {
     const bool valid = k < cnt;

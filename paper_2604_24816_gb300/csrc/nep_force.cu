@@ -60,7 +60,7 @@ constexpr int FPIPE_DP = 3;
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB)
 k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-             const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
+             const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ G,
              float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
              long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   __shared__ float4 shift[27];
@@ -70,10 +70,12 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   long long acc[5] = {0, 0, 0, 0, 0};
+  const bool skip = skip_far(X);
   if (i < n) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
     AtomSums<S> A;
-    accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
+    accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, i, n, pos, nbr, full_row(X, i, skip), ring_e, ring_p,
+                                                     A);
     float q[S::NDES];
     FourBody<S> T;
     descriptors_of<S>(P, A, q, T);
@@ -123,7 +125,7 @@ k_descriptor(const __grid_constant__ Model<S> P, const Geom geom, const int n, c
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_DESC_MINB_TM)
 k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-                const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ G,
+                const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ G,
                 float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
                 long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   static_assert(S::NA == 5 && S::NLM == 24 && S::FOURBODY && DESC_BLOCK == 128, "teacher shape, 4 warps");
@@ -144,11 +146,12 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   const int ii = live ? i : 0;
   long long acc[5] = {0, 0, 0, 0, 0};
   if (live) { Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0; }
-  const int cnt = live ? nnum[i] : 0;
+  const RowSpan sp = live ? full_row(X, i, skip_far(X)) : RowSpan{0, 0, 0};
+  const int cnt = sp.c;
   float QR[S::KR], elj;
   int nrad, nang, nact;
   RegSums<S, S::NA> R;                      // empty: every channel in TMEM
-  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, cnt, ring_e, ring_p,
+  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
                                                              QR, R, elj, nrad, nang, nact);
   float q[S::NDES];
   FourBody<S> T;
@@ -230,8 +233,7 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
                                             const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
                                             const float (&fpi)[8], int i, bool live, int ii, int n,
                                             const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
-                                            const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
-                                            const GT *__restrict__ G, uint32_t *ring_e, float4 *ring_p,
+                                            RowSpan sp, int nb0, const GT *__restrict__ G, uint32_t *ring_e, float4 *ring_p,
                                             unsigned long long *__restrict__ Ffix, int *__restrict__ status,
                                             float *__restrict__ Ff, long long (&acc)[13]) {
   constexpr bool TM = ForceCfg<S>::TM;
@@ -240,11 +242,10 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
   const float4 pi = pos[ii];
   float fx = 0.f, fy = 0.f, fz = 0.f;
   float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
-  const int cnt = live ? nrow[i] : 0;
-  const int nb0 = live ? nband0[i] : 0;
+  const int cnt = sp.c;
   int nrad = 0, nang = 0, nact = 0;
   NbrPipe<DE, DP, FORCE_BLOCK> pipe;
-  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, cnt);
+  pipe.start(ring_e, ring_p, nbr + ii, (size_t)n, pos, sp);
   const int trip = TM ? __reduce_max_sync(0xffffffffu, cnt) : cnt;
   for (int k = 0; k < trip; ++k) {
     const bool valid = k < cnt;
@@ -392,9 +393,9 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
   }
 }
 
-// FULL = true walks the whole row (nrow = full row lengths) with atom i's own adjoint only; FULL =
-// false walks the owned half (nrow = owned counts) and gathers the neighbour's row (see the file
-// header).  FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float
+// FULL = true walks the whole row with atom i's own adjoint only; FULL = false walks the owned half
+// and gathers the neighbour's row (see the file header).  Either leaves the far bands out when the
+// control block allows it (RowExt, skip_far).  FS = true is the paper's scatter (Section V.B, Optimization 1) kept as an ablation: float
 // atomicAdd into Ff, whose result depends on the order in which the additions arrive.
 //
 // With the row in TMEM the pair loop runs to the warp's largest owned count (threads past their own
@@ -407,8 +408,8 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
 template <class S, class GT, bool FS = false, bool FULL = false>
 __global__ void __launch_bounds__(FORCE_BLOCK, FULL && ForceCfg<S>::TM ? NEP_FORCE_MINB_FULL : ForceCfg<S>::MINB)
 k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-        const int32_t *__restrict__ nbr, const int32_t *__restrict__ nrow, const int32_t *__restrict__ nband0,
-        const GT *__restrict__ G, unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
+        const int32_t *__restrict__ nbr, const RowExt X, const GT *__restrict__ G,
+        unsigned long long *__restrict__ Ffix, long long *__restrict__ part,
         int *__restrict__ status, float *__restrict__ Ff = nullptr) {
   constexpr bool TM = ForceCfg<S>::TM;
   constexpr int W = GTraits<GT>::W;
@@ -452,8 +453,10 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   if constexpr (TM) tmem_wait_st();
   float fpi[8];
   load_tail8(Gi, S::NA * S::NLM, fpi);
-  force_pairs<S, GT, FS, FULL>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, nrow, nband0, G, ring_e, ring_p, Ffix,
-                               status, Ff, acc);
+  const bool skip = skip_far(X);
+  const RowSpan sp = !live ? RowSpan{0, 0, 0} : (FULL ? full_row(X, i, skip) : owned_row(X, i, skip));
+  force_pairs<S, GT, FS, FULL>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, sp, live ? X.nband0[i] : 0, G,
+                               ring_e, ring_p, Ffix, status, Ff, acc);
   if constexpr (TM) {
     tc_fence_before();
     __syncthreads();
@@ -477,7 +480,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_FUSED_MINB)
 k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-            const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, float *__restrict__ usite,
+            const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ usite,
             float *__restrict__ qout, unsigned long long *__restrict__ Ffix, long long *__restrict__ part_d,
             long long *__restrict__ part_f, int *__restrict__ status) {
   static_assert(ForceCfg<S>::TM && DESC_BLOCK == 128 && FORCE_BLOCK == 128, "teacher shape, 4 warps");
@@ -497,13 +500,14 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = i < n;
   const int ii = live ? i : 0;
-  const int cnt = live ? nnum[i] : 0;
+  const RowSpan sp = live ? full_row(X, i, skip_far(X)) : RowSpan{0, 0, 0};
+  const int cnt = sp.c;
 
   // descriptors and network (as k_descriptor_tm)
   float QR[S::KR], elj;
   int nrad, nang, nact;
   RegSums<S, S::NA> R;
-  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, cnt, ring_e, ring_p,
+  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
                                                              QR, R, elj, nrad, nang, nact);
   float q[S::NDES];
   FourBody<S> T;
@@ -551,7 +555,7 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   // forces: every ordered pair of the row with the own adjoint row (as k_force, FULL)
   const float gi[1][1] = {{0.f}};
   long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  force_pairs<S, float, false, true>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, nnum, nnum, nullptr, ring_e,
+  force_pairs<S, float, false, true>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, sp, 0, nullptr, ring_e,
                                      ring_p, Ffix, status, nullptr, acc_f);
   tc_fence_before();
   __syncthreads();
@@ -570,14 +574,14 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
 #endif
 template <class S>
 cudaError_t launch_descriptor(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                              const int32_t *nnum, float *G, float *usite, float *qout, long long *Ffix,
+                              const RowExt &X, float *G, float *usite, float *qout, long long *Ffix,
                               long long *part, int *status, const Fallback &fb, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
   if constexpr (ForceCfg<S>::TM && NEP_DESC_TM)
-    k_descriptor_tm<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status, fb);
+    k_descriptor_tm<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, G, usite, qout, Ffix, part, status, fb);
   else
-    k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status, fb);
+    k_descriptor<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, G, usite, qout, Ffix, part, status, fb);
   return cudaGetLastError();
 }
 
@@ -592,12 +596,12 @@ constexpr bool force_full_row() {
 
 template <class S, class GT>
 cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                         const int32_t *nnum, const int32_t *nown, const int32_t *nband0, const GT *G,
+                         const RowExt &X, const GT *G,
                          long long *Ffix, long long *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
   constexpr bool full = force_full_row<S, GT>();
-  k_force<S, GT, false, full><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, full ? nnum : nown, nband0, G,
+  k_force<S, GT, false, full><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, G,
                                                            reinterpret_cast<unsigned long long *>(Ffix), part, status);
   return cudaGetLastError();
 }
@@ -606,48 +610,48 @@ cudaError_t launch_force(const Model<S> &P, const Geom &g, int n, const float4 *
 // owner, gathering the neighbour's adjoint row), instead of the full-row form.
 template <class S>
 cudaError_t launch_force_half_list(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                                   const int32_t *nown, const int32_t *nband0, const float *G, long long *Ffix,
+                                   const RowExt &X, const float *G, long long *Ffix,
                                    long long *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S, float, false, false><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nown, nband0, G,
+  k_force<S, float, false, false><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, G,
                                                                reinterpret_cast<unsigned long long *>(Ffix), part,
                                                                status);
   return cudaGetLastError();
 }
 template cudaError_t launch_force_half_list<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                     const int32_t *, const int32_t *, const int32_t *, const float *,
-                                                     long long *, long long *, int *, cudaStream_t);
+                                                     const int32_t *, const RowExt &, const float *, long long *,
+                                                     long long *, int *, cudaStream_t);
 
 // Ablation: the production (full-row) force kernel with float atomicAdd scatter into Ff [3][n] (zeroed
 // by the caller) instead of fixed-point integer atomics.
 template <class S>
 cudaError_t launch_force_float_scatter(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                                       const int32_t *nnum, const int32_t *nband0, const float *G, float *Ff,
+                                       const RowExt &X, const float *G, float *Ff,
                                        long long *part, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + FORCE_BLOCK - 1) / FORCE_BLOCK;
-  k_force<S, float, true, true><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, nband0, G, nullptr, part,
+  k_force<S, float, true, true><<<grid, FORCE_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, G, nullptr, part,
                                                              status, Ff);
   return cudaGetLastError();
 }
 template cudaError_t launch_force_float_scatter<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *,
-                                                         const int32_t *, const int32_t *, const int32_t *,
-                                                         const float *, float *, long long *, int *, cudaStream_t);
+                                                         const int32_t *, const RowExt &, const float *, float *,
+                                                         long long *, int *, cudaStream_t);
 
 // Fused descriptor + force evaluation of the float32 teacher (k_nep_fused); Ffix must be zero.
 template <class S>
 cudaError_t launch_fused(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                         const int32_t *nnum, float *usite, float *qout, long long *Ffix, long long *part_d,
+                         const RowExt &X, float *usite, float *qout, long long *Ffix, long long *part_d,
                          long long *part_f, int *status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
-  k_nep_fused<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, usite, qout,
+  k_nep_fused<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, usite, qout,
                                               reinterpret_cast<unsigned long long *>(Ffix), part_d, part_f, status);
   return cudaGetLastError();
 }
 template cudaError_t launch_fused<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *, const int32_t *,
-                                           const int32_t *, float *, float *, long long *, long long *, long long *,
+                                           const RowExt &, float *, float *, long long *, long long *, long long *,
                                            int *, cudaStream_t);
 
 int descriptor_blocks(int n) { return (n + DESC_BLOCK - 1) / DESC_BLOCK; }
@@ -655,14 +659,14 @@ int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }
 
 #define NEP_INSTANTIATE(SH)                                                                                    \
   template cudaError_t launch_descriptor<SH>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *,   \
-                                             const int32_t *, float *, float *, float *, long long *, long long *,    \
+                                             const RowExt &, float *, float *, float *, long long *, long long *,    \
                                              int *, const Fallback &, cudaStream_t);                                  \
   template cudaError_t launch_force<SH, float>(const Model<SH> &, const Geom &, int, const float4 *, const int32_t *, \
-                                               const int32_t *, const int32_t *, const int32_t *, const float *,      \
-                                               long long *, long long *, int *, cudaStream_t);                        \
+                                               const RowExt &, const float *, long long *, long long *, int *,         \
+                                               cudaStream_t);                                                         \
   template cudaError_t launch_force<SH, __half>(const Model<SH> &, const Geom &, int, const float4 *,                 \
-                                                const int32_t *, const int32_t *, const int32_t *, const int32_t *,   \
-                                                const __half *, long long *, long long *, int *, cudaStream_t);
+                                                const int32_t *, const RowExt &, const __half *, long long *,         \
+                                                long long *, int *, cudaStream_t);
 NEP_INSTANTIATE(CuShape)
 NEP_INSTANTIATE(StudentShape)
 #undef NEP_INSTANTIATE

@@ -13,6 +13,17 @@ constexpr double KE_CONV = 103.642696562;          // 1 amu Angstrom^2/fs^2 in e
 
 __device__ __forceinline__ double fix_to_double(long long f) { return (double)f * FIX_INV; }
 
+// The warp's displacement news: any atom past skin/2 (-> rebuild), and the largest squared
+// displacement since the rebuild (non-negative floats order like their bit patterns).
+__device__ __forceinline__ void note_displacement(bool moved, float dd, Control *ctrl) {
+  const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(dd));
+  const bool any = __any_sync(0xffffffffu, moved);
+  if ((threadIdx.x & 31) == 0) {
+    if (any) atomicOr(&ctrl->moved, 1);
+    if (m > 0u) atomicMax(reinterpret_cast<unsigned *>(&ctrl->dmax2), m);
+  }
+}
+
 __global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                              const long long *__restrict__ F, float4 *__restrict__ pos,
@@ -20,6 +31,7 @@ __global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__
                              double lz, float half_skin2, Control *ctrl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool moved = false;
+  float dd = 0.f;                      // squared displacement since the rebuild (capped; NaN -> cap)
   if (i < n) {
     // kick_fix = kick * 2^-32: one conversion and one FMA per component on the narrow FP64 pipe
     const double kick_fix = kick * FIX_INV;
@@ -38,11 +50,19 @@ __global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__
     const float ddx = q.x - r.x, ddy = q.y - r.y, ddz = q.z - r.z;
     const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
     moved = !(d2 <= half_skin2);       // also true for NaN
+    dd = d2 <= 1.0e30f ? d2 : 1.0e30f;
   }
-  if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->moved, 1);
+  note_displacement(moved, dd, ctrl);
 }
 
 // Decide whether this step rebuilds the neighbour list.
+// After the rebuild decision: may the row walks of this evaluation leave the far bands out (no atom
+// moved far enough since the build to bring a far-band pair inside rc_R)?
+__device__ __forceinline__ void decide_far(Control *ctrl) {
+  if (ctrl->do_rebuild) ctrl->dmax2 = 0.f;
+  ctrl->skip_far = ctrl->dmax2 < ctrl->far_dmax2 ? 1 : 0;
+}
+
 __global__ void k_control(Control *ctrl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   ctrl->steps += 1;
@@ -56,6 +76,7 @@ __global__ void k_control(Control *ctrl) {
     ctrl->steps_since = 0;
     ctrl->rebuilds += 1;
   }
+  decide_far(ctrl);
 }
 
 // Outside MD steps, after an upload that kept the list: rebuild only if an atom moved more than
@@ -70,6 +91,7 @@ __global__ void k_control_check(Control *ctrl) {
     ctrl->steps_since = 0;
     ctrl->rebuilds += 1;
   }
+  decide_far(ctrl);
 }
 
 // Rebuild unconditionally (outside MD steps).
@@ -80,6 +102,7 @@ __global__ void k_control_force(Control *ctrl) {
   ctrl->force_rebuild = 0;
   ctrl->steps_since = 0;
   ctrl->rebuilds += 1;
+  decide_far(ctrl);
 }
 
 __global__ void k_kick(int n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
@@ -175,6 +198,7 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
                                     double Ly, double Lz, float half_skin2, Control *ctrl) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   bool moved = false;
+  float dd = 0.f;
   if (s < n) {
     const size_t o = 3 * (size_t)id[s];
     double a = xin[o], b = xin[o + 1], c = xin[o + 2];
@@ -199,9 +223,11 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
     pos[s] = q;
     const float4 r = pos_ref[s];
     const float ddx = q.x - r.x, ddy = q.y - r.y, ddz = q.z - r.z;
-    moved = moved || !(ddx * ddx + ddy * ddy + ddz * ddz <= half_skin2);
+    const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+    moved = moved || !(d2 <= half_skin2);
+    dd = moved ? 1.0e30f : d2;
   }
-  if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->moved, 1);
+  note_displacement(moved, dd, ctrl);
 }
 
 // Sorted SoA -> original-order [n][3] float64 (positions wrapped into the box when L != nullptr).

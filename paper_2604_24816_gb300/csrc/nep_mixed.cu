@@ -43,7 +43,7 @@ __device__ __forceinline__ uint4 pack8_half(const float *v) {
 template <class S, class MT>
 __global__ void __launch_bounds__(MIX_BLOCK, S::NLM > 8 ? NEP_MIX_MINB_TM : 6)
 k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
-                   const int32_t *__restrict__ nbr, const int32_t *__restrict__ nnum, __half *__restrict__ G,
+                   const int32_t *__restrict__ nbr, const RowExt X, __half *__restrict__ G,
                    float *__restrict__ usite, float *__restrict__ qout, long long *__restrict__ Ffix,
                    long long *__restrict__ part, int *__restrict__ status, const __grid_constant__ Fallback fb) {
   static_assert(S::NDES <= MIX_K && S::NNEU <= MIX_N, "network larger than one tensor-core tile");
@@ -92,9 +92,10 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
   if constexpr (TM) {
     tc_fence_after();
     trow = tmem_base + ((uint32_t)(t & ~31) << 16);
-    A.cnt = live ? nnum[i] : 0;
+    const RowSpan sp = live ? full_row(X, i, skip_far(X)) : RowSpan{0, 0, 0};
+    A.cnt = sp.c;
     if (live) { Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0; }
-    accumulate_atom_tm<S, NT, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, trow, live ? i : 0, n, pos, nbr, A.cnt, ring_e,
+    accumulate_atom_tm<S, NT, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, trow, live ? i : 0, n, pos, nbr, sp, ring_e,
                                                          ring_p, A.QR, R, A.elj, A.nrad, A.nang, A.nact);
     descriptors_tm<S, NT>(P, trow, A.QR, R, q, T);        // zero for threads past the last atom (empty row)
     if (live) {
@@ -107,7 +108,8 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
     }
   } else if (live) {
     Ffix[i] = 0; Ffix[(size_t)n + i] = 0; Ffix[2 * (size_t)n + i] = 0;
-    accumulate_atom<S, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, i, n, pos, nbr, nnum[i], ring_e, ring_p, A);
+    accumulate_atom<S, MIX_DE, MIX_DP, MIX_BLOCK>(P, shift, i, n, pos, nbr, full_row(X, i, skip_far(X)), ring_e,
+                                                  ring_p, A);
     descriptors_of<S>(P, A, q, T);
     if (qout != nullptr) {
 #pragma unroll
@@ -231,11 +233,11 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 
 template <class S, class MT>
 cudaError_t launch_descriptor_mixed(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
-                                    const int32_t *nnum, __half *G, float *usite, float *qout, long long *Ffix,
+                                    const RowExt &X, __half *G, float *usite, float *qout, long long *Ffix,
                                     long long *part, int *status, const Fallback &fb, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + MIX_BLOCK - 1) / MIX_BLOCK;
-  k_descriptor_mixed<S, MT><<<grid, MIX_BLOCK, 0, st>>>(P, g, n, pos, nbr, nnum, G, usite, qout, Ffix, part, status,
+  k_descriptor_mixed<S, MT><<<grid, MIX_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, G, usite, qout, Ffix, part, status,
                                                         fb);
   return cudaGetLastError();
 }
@@ -244,7 +246,7 @@ int mixed_descriptor_blocks(int n) { return (n + MIX_BLOCK - 1) / MIX_BLOCK; }
 
 #define NEP_INSTANTIATE(SH, MT)                                                                                \
   template cudaError_t launch_descriptor_mixed<SH, MT>(const Model<SH> &, const Geom &, int, const float4 *,          \
-                                                       const int32_t *, const int32_t *, __half *, float *, float *,  \
+                                                       const int32_t *, const RowExt &, __half *, float *, float *,   \
                                                        long long *, long long *, int *, const Fallback &,             \
                                                        cudaStream_t);
 NEP_INSTANTIATE(CuShape, __nv_bfloat16)

@@ -190,10 +190,13 @@ __global__ void k_copy_back(int n, double *__restrict__ x, double *__restrict__ 
 // Segments: the pair (i, j) is "owned" by i when r_ij lies in the upper half-space (see owns_pair;
 // exactly one of r_ij and r_ji = -r_ij is owned, so every unordered pair has one owner), and the row
 // is laid out as [owned | not owned], each part grouped by build-time distance band:
-// [0, rc_A), [rc_A, rc_A + skin), [rc_A + skin, rc_R), [rc_R, rc_R + skin), stencil order inside a band.
-// The force kernel walks only the owned part (each pair once, Newton's third law); the descriptor
-// kernel walks the whole row.  Because every atom of a lattice owns exactly half of each shell and the
-// bands follow the shells, the per-pair branches stay warp-uniform without a full sort.
+// [0, rc_A), [rc_A, rc_A + skin), [rc_A + skin, rc_R), [rc_R, rc_R + e), [rc_R + e, rc_R + skin) with
+// e = FAR_EDGE skin, in stencil order inside a band.  The half-list force kernels walk only the owned part (each pair once,
+// Newton's third law); the other walks take the whole row.  The last ("far") band of each part can
+// only hold a pair inside rc_R after some atom moved more than e/2 since the build, so while the
+// largest displacement stays below that the walks leave both far bands out (their counts go to
+// nfar).  Because every atom of a lattice owns exactly half of each shell and the bands follow the
+// shells, the per-pair branches stay warp-uniform without a full sort.
 // The placement's 4-byte stores into the neighbour-major list are scattered across rows; L2 merges
 // them into full sectors before they reach DRAM.
 constexpr int NB_WARPS = 8;            // atoms (one warp each) per block
@@ -201,8 +204,9 @@ constexpr int NB_STAGE = 128;          // staged entries per atom (lists longer 
 constexpr float OWN_EPS = 0.5f;        // Angstrom; lattice-vector components are either ~0 or >= a/2
 
 struct Bands {
-  float b0, b1, b2, b3;                // squared band edges: rc_A^2, (rc_A+skin)^2, rc_R^2, (rc_R+skin)^2
+  float b0, b1, b2, b3, b4;  // squared band edges: rc_A^2, (rc_A+skin)^2, rc_R^2, (rc_R+e)^2, (rc_R+skin)^2
 };
+constexpr int NB_SEG = 10;             // segments of a row: [owned | not owned] x 5 distance bands
 
 // Upper half-space test, exactly antisymmetric: owns_pair(d) != owns_pair(-d) for d != 0.  The
 // tolerance makes near-zero components of lattice vectors (thermal noise) defer to the next axis, so
@@ -220,20 +224,29 @@ __device__ __forceinline__ bool owns_pair(float dx, float dy, float dz) {
 // Squared distance with an explicit operation order, so that both passes classify a pair identically.
 __device__ __forceinline__ float nb_r2(float a, float b, float c) { return fmaf(a, a, fmaf(b, b, c * c)); }
 
-// Segment of an accepted pair: owned by i (0..3) or not (4..7), by build-time distance band.
+// Segment of an accepted pair: owned by i (0..4) or not (5..9), by build-time distance band.
 __device__ __forceinline__ int segment_of(float dx, float dy, float dz, float r2, const Bands &B) {
-  const int bd = r2 < B.b0 ? 0 : (r2 < B.b1 ? 1 : (r2 < B.b2 ? 2 : 3));
-  return owns_pair(dx, dy, dz) ? bd : 4 + bd;
+  const int bd = (int)(r2 >= B.b0) + (int)(r2 >= B.b1) + (int)(r2 >= B.b2) + (int)(r2 >= B.b3);   // edges below r2
+  return owns_pair(dx, dy, dz) ? bd : 5 + bd;
+}
+
+// This chunk's entries of segment `lane % 5` (lanes 0..4) or `5 + lane % 5` (lanes 5..9); key NB_SEG
+// marks an empty slot.  fsh = 6 (lane % 5).
+__device__ __forceinline__ int segment_counts(int key, int lane, unsigned fsh) {
+  const unsigned lo = key < 5 ? 1u << (6 * key) : 0u;
+  const unsigned hi = key >= 5 && key < NB_SEG ? 1u << (6 * (key - 5)) : 0u;
+  const unsigned slo = __reduce_add_sync(0xffffffffu, lo), shi = __reduce_add_sync(0xffffffffu, hi);
+  return (int)(((lane < 5 ? slo : shi) >> fsh) & 63u);
 }
 
 // The candidate scan and segment placement of atom i by one warp (see k_neighbors).
 __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__restrict__ pos,
                                                   const int *__restrict__ cell_start, const Geom &geom,
-                                                  const Bands &B, int limit, uint32_t *stage,
+                                                  const Bands &B, int limit, uint32_t *stage, float *sdd,
                                                   uint8_t *skey, int lane, int32_t *__restrict__ nbr,
                                                   int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
                                                   int32_t *__restrict__ nown, int32_t *__restrict__ nband0,
-                                                  Control *ctrl) {
+                                                  int32_t *__restrict__ nfar, Control *ctrl) {
   const unsigned lower = (1u << lane) - 1u;
   const float4 pi = pos[i];
   const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
@@ -255,7 +268,7 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
         // distance test could accept, so the lists are unchanged
         const float gy = dy < 0 ? pi.y : (dy > 0 ? geom.ly - pi.y : 0.f);
         const float gz = dz < 0 ? pi.z : (dz > 0 ? geom.lz - pi.z : 0.f);
-        if (gy * gy + gz * gz > B.b3 * 1.0001f) continue;
+        if (gy * gy + gz * gz > B.b4 * 1.0001f) continue;
       }
       const int parts = xwrap ? 3 : 1;
       for (int part = 0; part < parts; ++part) {
@@ -272,24 +285,25 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
         for (int j0 = b; j0 < e; j0 += 32) {
           const int j = j0 + lane;
           bool ok = false;
-          int key = 0;
           uint32_t ent = 0;
+          float ddx = 0.f, ddy = 0.f, ddz = 0.f;
           if (j < e && j != i) {
             const float4 pj = pos[j];
             const int dx = xwrap ? part - 1 : cell_x(pj.w) - cx;
             const float ox = dx < 0 ? -geom.lx : (dx > 0 ? geom.lx : 0.f);
-            const float ddx = pj.x - pi.x + ox, ddy = pj.y - pi.y + oy, ddz = pj.z - pi.z + oz;
-            const float r2 = nb_r2(ddx, ddy, ddz);
-            if (r2 < B.b3) {
+            ddx = pj.x - pi.x + ox; ddy = pj.y - pi.y + oy; ddz = pj.z - pi.z + oz;
+            if (nb_r2(ddx, ddy, ddz) < B.b4) {
               ok = true;
-              key = segment_of(ddx, ddy, ddz, r2, B);
               ent = (uint32_t)j | ((uint32_t)((dx + 1) + shb) << J_BITS);
             }
           }
           const unsigned m = __ballot_sync(0xffffffffu, ok);
           if (ok) {
             const int slot = acc + __popc(m & lower);
-            if (slot < NB_STAGE) { stage[slot] = ent; skey[slot] = (uint8_t)key; }
+            if (slot < NB_STAGE) {
+              stage[slot] = ent;
+              sdd[slot] = ddx; sdd[NB_STAGE + slot] = ddy; sdd[2 * NB_STAGE + slot] = ddz;
+            }
           }
           acc += __popc(m);
         }
@@ -297,41 +311,55 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
     }
   }
   __syncwarp();
-  // segment sizes and offsets (warp-uniform), then placement in candidate order within each segment
+  // Segments of the staged entries (classified here, 32 accepted pairs at a time, rather than in the
+  // sparse candidate loop; the same float32 arithmetic as the acceptance test), their sizes and offsets,
+  // then placement in candidate order within each segment.  Lane g < NB_SEG keeps segment g's count
+  // and running offset; a chunk of 32 staged entries is counted with two warp reductions of one-hot
+  // 6-bit fields (segments 0..4 and 5..9: at most 32 per field, no carries).
   const int ms = min(acc, NB_STAGE);
-  int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const unsigned fsh = 6u * (unsigned)(lane % 5);
+  int mycnt = 0;
   for (int s0 = 0; s0 < ms; s0 += 32) {
-    const int key = s0 + lane < ms ? (int)skey[s0 + lane] : 8;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) cnt[g] += __popc(__ballot_sync(0xffffffffu, key == g));
+    int key = NB_SEG;
+    if (s0 + lane < ms) {
+      const float ddx = sdd[s0 + lane], ddy = sdd[NB_STAGE + s0 + lane], ddz = sdd[2 * NB_STAGE + s0 + lane];
+      key = segment_of(ddx, ddy, ddz, nb_r2(ddx, ddy, ddz), B);
+      skey[s0 + lane] = (uint8_t)key;
+    }
+    mycnt += segment_counts(key, lane, fsh);
   }
-  int run[8];
-  {
-    int o = 0;
+  __syncwarp();
+  if (lane >= NB_SEG) mycnt = 0;
+  int incl = mycnt;                                    // inclusive prefix over lanes 0..NB_SEG-1
 #pragma unroll
-    for (int g = 0; g < 8; ++g) { run[g] = o; o += cnt[g]; }
+  for (int d = 1; d < 16; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
   }
+  int myrun = incl - mycnt;                            // next slot of segment `lane`
   for (int s0 = 0; s0 < ms; s0 += 32) {
     const bool valid = s0 + lane < ms;
-    const int key = valid ? (int)skey[s0 + lane] : 8;
+    const int key = valid ? (int)skey[s0 + lane] : NB_SEG;
     const uint32_t ent = valid ? stage[s0 + lane] : 0u;
-    int k = 0;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const unsigned bal = __ballot_sync(0xffffffffu, key == g);
-      if (key == g) k = run[g] + __popc(bal & lower);
-      run[g] += __popc(bal);
-    }
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int k = __shfl_sync(0xffffffffu, myrun, key) + __popc(grp & lower);
     if (valid && k < limit) nbr[(size_t)k * n + i] = (int32_t)ent;
+    myrun += segment_counts(key, lane, fsh);
   }
+  const int c0 = __shfl_sync(0xffffffffu, mycnt, 0), c1 = __shfl_sync(0xffffffffu, mycnt, 1);
+  const int c4 = __shfl_sync(0xffffffffu, mycnt, 4), c5 = __shfl_sync(0xffffffffu, mycnt, 5);
+  const int c6 = __shfl_sync(0xffffffffu, mycnt, 6), c9 = __shfl_sync(0xffffffffu, mycnt, 9);
+  const int n_own = __shfl_sync(0xffffffffu, incl, 4);
   if (lane == 0) {
-    const int n_own = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     const int kept = min(acc, limit);
     if (acc > kept || acc > NB_STAGE) atomicOr(&ctrl->status, ST_OVERFLOW);
     nnum[i] = kept;
     nown[i] = min(n_own, kept);
-    nang[i] = cnt[0] + cnt[1] + cnt[4] + cnt[5];
-    nband0[i] = min(cnt[0], kept);
+    nang[i] = c0 + c1 + c5 + c6;
+    nband0[i] = min(c0, kept);
+    // far bands (each part's last): skippable while no atom moved far enough to bring them in range;
+    // zero when the row overflowed (the evaluation then reports the overflow)
+    nfar[i] = acc > kept ? 0 : (c4 | (c9 << 16));
   }
 }
 
@@ -343,13 +371,14 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
 // candidate order (ballot + popc), then are placed by segment: [owned | not owned] x band, candidate
 // order inside a segment -- the same row as the thread-per-atom formulation, with 32-wide work
 // instead of divergent per-thread cell loops.
-__global__ void __launch_bounds__(NB_WARPS * 32, 6)   // 40 registers: 6 resident blocks
+__global__ void __launch_bounds__(NB_WARPS * 32, 6)   // 40 registers at most: 6 resident blocks
 k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_start, const Geom geom, int cap,
             Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
-            int32_t *__restrict__ nown, int32_t *__restrict__ nband0, Control *ctrl) {
+            int32_t *__restrict__ nown, int32_t *__restrict__ nband0, int32_t *__restrict__ nfar, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
   __shared__ uint32_t stage[NB_WARPS][NB_STAGE];
   __shared__ uint8_t skey[NB_WARPS][NB_STAGE];
+  __shared__ float sdd[NB_WARPS][3 * NB_STAGE];        // staged displacements (x | y | z)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // The grid is capped at the resident blocks (a launch on a step without a rebuild then costs a few
   // microseconds whatever the atom count); each block takes the next group of NB_WARPS consecutive
@@ -364,8 +393,8 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
     if ((long long)g * NB_WARPS >= n) break;           // block-uniform
     const int i = g * NB_WARPS + w;                    // warp-uniform
     if (i < n)
-      neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], skey[w], lane, nbr, nnum,
-                        nang, nown, nband0, ctrl);
+      neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], sdd[w], skey[w], lane, nbr, nnum,
+                        nang, nown, nband0, nfar, ctrl);
     __syncwarp();                                      // the stage is reused by the warp's next atom
   }
 }
@@ -423,9 +452,9 @@ cudaError_t launch_neighbors(const RebuildArgs &a, cudaStream_t st) {
   g.lx = (float)a.l[0]; g.ly = (float)a.l[1]; g.lz = (float)a.l[2];
   g.ncx = a.nc[0]; g.ncy = a.nc[1]; g.ncz = a.nc[2];
   Bands B;
-  B.b0 = a.ba2; B.b1 = a.ra2; B.b2 = a.br2; B.b3 = a.rl2;
-  k_neighbors<<<resident_grid(k_neighbors, a.n, NB_WARPS, NB_WARPS * 32), NB_WARPS * 32, 0, st>>>(a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum,
-                                                                   a.nang, a.nown, a.nband0, a.ctrl);
+  B.b0 = a.ba2; B.b1 = a.ra2; B.b2 = a.br2; B.b3 = std::min(a.fs2, a.rl2); B.b4 = a.rl2;
+  k_neighbors<<<resident_grid(k_neighbors, a.n, NB_WARPS, NB_WARPS * 32), NB_WARPS * 32, 0, st>>>(
+      a.n, a.pos, a.start, g, a.cap, B, a.nbr, a.nnum, a.nang, a.nown, a.nband0, a.nfar, a.ctrl);
   return cudaGetLastError();
 }
 

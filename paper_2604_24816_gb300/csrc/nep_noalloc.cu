@@ -28,12 +28,12 @@
 
 namespace nep {
 template <class S>
-cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
+cudaError_t launch_descriptor(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
                               float *, float *, float *, long long *, long long *, int *, const Fallback &,
                               cudaStream_t);
 template <class S, class GT>
-cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const int32_t *,
-                         const int32_t *, const int32_t *, const GT *, long long *, long long *, int *, cudaStream_t);
+cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
+                         const GT *, long long *, long long *, int *, cudaStream_t);
 int descriptor_blocks(int n);
 int force_blocks(int n);
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
@@ -61,7 +61,7 @@ constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 // Byte offsets of the pieces inside the scratch array.
 struct Layout {
   size_t x, y, z, vx, vy, vz, xb, yb, zb, vxb, vyb, vzb, id, idb, cell_of, perm, pos, pos_ref, F, usite, G, nbr,
-      nnum, nang, nown, nband0, count, cursor, start, tile_sums, part_d, part_f, sums, counters, ctrl, io, total;
+      nnum, nang, nown, nband0, nfar, count, cursor, start, tile_sums, part_d, part_f, sums, counters, ctrl, io, total;
 };
 
 constexpr Layout make_layout() {
@@ -76,7 +76,7 @@ constexpr Layout make_layout() {
   L.id = take(N * 4); L.idb = take(N * 4); L.cell_of = take(N * 4); L.perm = take(N * 4);
   L.pos = take(N * 16); L.pos_ref = take(N * 16);
   L.F = take(N * 3 * 8); L.usite = take(N * 4); L.G = take(N * S::GS * 4); L.nbr = take(N * CAP * 4);
-  L.nnum = take(N * 4); L.nang = take(N * 4); L.nown = take(N * 4); L.nband0 = take(N * 4);
+  L.nnum = take(N * 4); L.nang = take(N * 4); L.nown = take(N * 4); L.nband0 = take(N * 4); L.nfar = take(N * 4);
   L.count = take((size_t)NC_MAX * 4); L.cursor = take((size_t)NC_MAX * 4); L.start = take(((size_t)NC_MAX + 1) * 4);
   L.tile_sums = take(((size_t)NC_MAX / 4096 + 2) * 4);
   L.part_d = take(((size_t)N / 64 + 2) * 5 * 8); L.part_f = take(((size_t)N / 64 + 2) * 13 * 8);
@@ -217,10 +217,10 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   a.tile_sums = (int *)at(LAYOUT.tile_sums); a.perm = (int *)at(LAYOUT.perm);
   a.pos = (float4 *)at(LAYOUT.pos); a.pos_ref = (float4 *)at(LAYOUT.pos_ref);
   a.nbr = (int32_t *)at(LAYOUT.nbr); a.nnum = (int32_t *)at(LAYOUT.nnum); a.nang = (int32_t *)at(LAYOUT.nang);
-  a.nown = (int32_t *)at(LAYOUT.nown); a.nband0 = (int32_t *)at(LAYOUT.nband0);
+  a.nown = (int32_t *)at(LAYOUT.nown); a.nband0 = (int32_t *)at(LAYOUT.nband0); a.nfar = (int32_t *)at(LAYOUT.nfar);
   a.cap = CAP;
-  const float rlf = p->rc_R + p->skin, raf = p->rc_A + p->skin;
-  a.rl2 = rlf * rlf; a.ra2 = raf * raf; a.ba2 = p->rc_A * p->rc_A; a.br2 = p->rc_R * p->rc_R;
+  const float rlf = p->rc_R + p->skin, raf = p->rc_A + p->skin, fsf = p->rc_R + FAR_EDGE * p->skin;
+  a.rl2 = rlf * rlf; a.ra2 = raf * raf; a.ba2 = p->rc_A * p->rc_A; a.br2 = p->rc_R * p->rc_R; a.fs2 = fsf * fsf;
   Control *ctrl = (Control *)at(LAYOUT.ctrl);
   a.ctrl = ctrl;
   long long *Ffix = (long long *)at(LAYOUT.F);
@@ -245,10 +245,11 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   NA_CUDA(launch_control(ctrl, true, st));
   NA_CUDA(launch_cell_sort(a, st));
   NA_CUDA(launch_neighbors(a, st));
-  NA_CUDA(launch_descriptor<S>(M, g, N, a.pos, a.nbr, a.nnum, (float *)at(LAYOUT.G), (float *)at(LAYOUT.usite),
+  const RowExt rows{a.nnum, a.nown, a.nband0, a.nfar, nullptr};   // one evaluation: the whole rows
+  NA_CUDA(launch_descriptor<S>(M, g, N, a.pos, a.nbr, rows, (float *)at(LAYOUT.G), (float *)at(LAYOUT.usite),
                                nullptr, Ffix, pd, &ctrl->status, Fallback{}, st));
-  NA_CUDA((launch_force<S, float>(M, g, N, a.pos, a.nbr, a.nnum, a.nown, a.nband0, (const float *)at(LAYOUT.G), Ffix, pf,
-                          &ctrl->status, st)));
+  NA_CUDA((launch_force<S, float>(M, g, N, a.pos, a.nbr, rows, (const float *)at(LAYOUT.G), Ffix, pf, &ctrl->status,
+                                  st)));
   NA_CUDA(launch_finalize(pd, descriptor_blocks(N), pf, force_blocks(N), nullptr, 0, sums, counters, st));
   const bool f_dev = F && device_pointer(F);
   const bool e_dev = E && device_pointer(E);

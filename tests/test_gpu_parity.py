@@ -18,6 +18,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
+FAR_EDGE = 0.4    # the far band of a list row starts at rc_R + FAR_EDGE * skin
+
 
 @pytest.fixture(scope="module")
 def api():
@@ -61,7 +63,8 @@ def test_neighbor_sets_bit_exact(api, model_params, cells):
     wl = ni.fcc_cu_workload(0, sigma=0.05, seed=21 + sum(cells), cells_xyz=cells)
     rl = model_params["rc_R"] + model_params["skin"]
     ra = model_params["rc_A"] + model_params["skin"]
-    assert _min_gap_to_cutoffs(wl.pos, wl.box, (rl, ra)) > 1e-5, "ambiguous pair within 1e-5 A of a cutoff"
+    fs = model_params["rc_R"] + FAR_EDGE * model_params["skin"]
+    assert _min_gap_to_cutoffs(wl.pos, wl.box, (rl, ra, fs)) > 1e-5, "ambiguous pair within 1e-5 A of a cutoff"
     with api.NEP(model_params) as nep:
         nep.set_state(wl.pos, wl.vel, wl.box)
         nep.build_neighbors()
@@ -76,8 +79,9 @@ def test_neighbor_sets_bit_exact(api, model_params, cells):
     for i in range(wl.n):
         for j in full[i]:
             assert (j in owned[i]) != (i in owned[j])
-    # row layout: [owned | other], each grouped by band r < rc_A, rc_A + skin, rc_R, rc_R + skin
-    edges = np.array([model_params["rc_A"], ra, model_params["rc_R"], rl])
+    # row layout: [owned | other], each grouped by band r < rc_A, rc_A + skin, rc_R, rc_R + 0.4 skin,
+    # rc_R + skin
+    edges = np.array([model_params["rc_A"], ra, model_params["rc_R"], fs, rl])
     for i in range(0, wl.n, 7):
         b_own = _bands(wl.pos, wl.box, i, lst[i, :nown[i]], edges)
         b_oth = _bands(wl.pos, wl.box, i, lst[i, nown[i]:counts[i]], edges)
@@ -354,3 +358,70 @@ def test_reupload_rebuilds_when_atoms_moved_beyond_the_skin(api, model_params):
     # float32 rounding of the shifted cell-relative coordinates: the float32 path's bound
     assert np.abs(F1 - F0).max() <= 1e-4
     assert abs(E1 - E0) <= 1e-6 * abs(E0)
+
+
+def _pair_r(pos, box, i, js):
+    d = pos[js] - pos[i]
+    d -= box * np.round(d / box)
+    return np.sqrt((d ** 2).sum(-1))
+
+
+def test_far_bands_left_out_only_while_no_pair_can_enter(api, model_params, model):
+    """The row walks leave out the far bands (entries built at r >= rc_R + 0.4 skin) while no atom
+    has moved more than (0.4 skin - 0.02)/2 since the build, and walk them again after a larger move: a pair
+    built in the far band and brought inside rc_R by two 0.45 A moves (each below skin/2, so the list
+    is kept) must contribute.  Forces are the oracle's in both cases."""
+    wl = ni.fcc_cu_workload(4, 300.0, 0.05, seed=75)
+    rc, skin = model_params["rc_R"], model_params["skin"]
+    fs = rc + FAR_EDGE * skin
+    rng = np.random.default_rng(76)
+    with api.NEP(model_params, rebuild_every=0) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        counts, nang, nown, lst = nep.neighbors(cap=160)
+        total = int(counts.sum())
+        r_build = [_pair_r(wl.pos, wl.box, i, lst[i, :counts[i]]) for i in range(wl.n)]
+        n_far = sum(int((r >= fs).sum()) for r in r_build)
+        n_edge = sum(int((np.abs(r - fs) < 1e-4).sum()) for r in r_build)
+        assert n_far > 0.1 * total
+
+        # (a) every atom within 0.08 A of its build position: far bands skipped
+        u = rng.standard_normal(wl.pos.shape)
+        u *= (0.08 * rng.random(wl.n) ** (1 / 3) / np.linalg.norm(u, axis=1))[:, None]
+        x1 = wl.pos + u
+        c0 = nep.counters()
+        nep.set_state(x1, wl.vel, wl.box)
+        E1, F1, _ = nep.compute()
+        c1 = nep.counters()
+        assert c1["rebuilds"] == c0["rebuilds"]
+        walked = c1["list_entries"] - c0["list_entries"]
+        assert abs(walked - (total - n_far)) <= n_edge
+        assert c1["force_list_entries"] - c0["force_list_entries"] == walked
+
+        # (b) one far-band pair pulled 0.9 A closer: the whole rows are walked
+        best = None
+        for i in range(wl.n):
+            r = r_build[i]
+            for k in np.nonzero((r > fs + 0.02) & (r < fs + 0.15))[0]:
+                j = int(lst[i, k])
+                d = wl.pos[j] - wl.pos[i]
+                d -= wl.box * np.round(d / wl.box)
+                e = d / np.linalg.norm(d)
+                x2 = wl.pos.copy()
+                x2[i] += 0.45 * e
+                x2[j] -= 0.45 * e
+                closest = min(np.delete(_pair_r(x2, wl.box, a, np.arange(wl.n)), a).min() for a in (i, j))
+                if best is None or closest > best[0]:
+                    best = (closest, i, j, x2)
+            if best is not None and best[0] > 2.3:
+                break
+        closest, i, j, x2 = best
+        assert _pair_r(x2, wl.box, i, np.array([j]))[0] < rc - 0.3
+        nep.set_state(x2, wl.vel, wl.box)
+        E2, F2, _ = nep.compute()
+        c2 = nep.counters()
+        assert c2["rebuilds"] == c0["rebuilds"]
+        assert c2["list_entries"] - c1["list_entries"] == total
+    for x, E, F in ((x1, E1, F1), (x2, E2, F2)):
+        Eo, Uo, Fo, Wo = oracle.energy_forces(model, x, wl.box)
+        assert np.abs(F - Fo).max() <= 1e-4
+        assert abs(E - Eo) / abs(Eo) <= 1e-6

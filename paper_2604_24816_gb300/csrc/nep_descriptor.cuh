@@ -227,7 +227,11 @@ __device__ __forceinline__ float network(const Model<S> &P, const float (&q)[S::
 #pragma unroll
   for (int v = 0; v < S::NDES; ++v) { qt[v] = q[v] * P.qs[v]; dq[v] = 0.f; }
   float U = -P.b1;
-#pragma unroll
+  // The teacher's 30 x 30 network, fully unrolled, is ~2k instructions of straight-line code that the
+  // row-walk loops share the instruction cache with; one neuron per iteration (weights read from the
+  // constant bank with a register offset) measured 2 % faster in the fused kernel.
+  constexpr int UNROLL = S::NNEU * S::NDES > 400 ? 1 : S::NNEU;
+#pragma unroll UNROLL
   for (int mu = 0; mu < S::NNEU; ++mu) {
     float z = -P.b0[mu];
 #pragma unroll

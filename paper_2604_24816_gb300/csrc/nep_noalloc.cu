@@ -128,8 +128,12 @@ nep_status wait_bounded(cudaStream_t st) {
     const cudaError_t e = cudaStreamQuery(st);
     if (e == cudaSuccess) return NEP_OK;
     if (e != cudaErrorNotReady) return NEP_ERR_CUDA;
-    if (spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
-    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > 600.0) return NEP_ERR_TIMEOUT;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > 600.0) return NEP_ERR_TIMEOUT;
+    if (spins > 64) {                       // yield for the first 2 ms, then sleep between polls
+      if (el < 2e-3) std::this_thread::yield();
+      else std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
   }
 }
 

@@ -60,3 +60,24 @@ def test_full_size_md_conserves_energy_and_is_deterministic(big, model_params):
     assert abs(e1 - e0) < 2e-4
     assert np.array_equal(runs[0][2], runs[1][2]) and np.array_equal(runs[0][3], runs[1][3])
     assert np.all(np.isfinite(x)) and np.all((x >= 0) & (x < big.box))
+
+
+@pytest.mark.parametrize("rebuild_every, steps", [(10, 25), (0, 40)])
+def test_sampled_forces_after_md_full_size(big, model_params, model, rebuild_every, steps):
+    """Forces of the MD state after `steps` graph steps, evaluated on the list the MD path kept (5 steps
+    old with rebuilds every 10 steps; with displacement-triggered rebuilds only, old enough that the
+    largest displacement passes the far-band threshold and the far bands are walked again), against the
+    oracle on 4,096 sampled atoms of the same positions."""
+    import paper_2604_24816_gb300 as pkg
+    with pkg.NEP(model_params, rebuild_every=rebuild_every) as nep:
+        nep.set_state(big.pos, big.vel, big.box)
+        nep.step(1.0, steps)
+        x, _ = nep.get_state()
+        E, F, W = nep.compute()
+        c = nep.counters()
+    idx = ni.sample_indices(big.n, 4096, seed=11)
+    Fo, Uo = oracle.forces_sampled(model, x, big.box, idx)
+    print(f"rebuild_every={rebuild_every}: {c['rebuilds']} rebuilds, "
+          f"{c['list_entries'] / (c['evaluations'] * big.n):.1f} list entries walked per atom-evaluation, "
+          f"max |dF| {np.abs(F[idx] - Fo).max():.2e} eV/A")
+    assert np.abs(F[idx] - Fo).max() <= 1e-4

@@ -246,6 +246,18 @@ const char *nep_last_error(nep_handle *h);
  * completed).  Synchronous; uses the current device; no handle. */
 nep_status nep_selftest_bounded_wait(int64_t polls, int *timed_out);
 
+/* FP32 throughput microbenchmark of the current device (a measurement aid with no paper counterpart;
+ * it gives the denominator of the FP32 roofline the force kernels are reported against).  Every SM is
+ * filled with resident blocks whose threads run 16 independent multiply-add chains: scalar FMAs
+ * (packed = 0) or packed float2 FMAs, two per instruction (packed = 1).  Each launch is sized to about
+ * launch_ms (0 < launch_ms <= 1000) and timed with CUDA events on cuda_stream (NULL = legacy default
+ * stream); after a calibration, `reps` launches (1..10000) are timed.  Outputs (host, may be NULL):
+ * *best_tflops and *median_tflops = FLOP/s over the timed launches (FMA = 2 FLOP), in 10^12;
+ * *sm_count = multiprocessor count read from the device.  Synchronous; allocates and frees a small
+ * output buffer; NEP_ERR_ARG for bad sizes, NEP_ERR_CUDA / NEP_ERR_OOM on runtime failures. */
+nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void *cuda_stream, double *best_tflops,
+                         double *median_tflops, int *sm_count);
+
 /* Name of a status code (never NULL). */
 const char *nep_status_string(nep_status s);
 

@@ -6,4 +6,4 @@
     E, F, W = nep.compute()
     nep.step(1.0, 100)
 """
-from .nep import NEP, NepError, load_model, lib, DEFAULT_MODEL  # noqa: F401
+from .nep import NEP, NepError, load_model, lib, fp32_peak, DEFAULT_MODEL  # noqa: F401

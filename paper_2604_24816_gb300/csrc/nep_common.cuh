@@ -124,52 +124,98 @@ __device__ __forceinline__ void fill_shift_table(float4 *tab, const Geom &g) {
   }
 }
 
-// Chebyshev basis f_k(r) = (T_k(x) + 1)/2 * fc(r), x = 2 (r/rc - 1)^2 - 1, fc = (1 + cos(pi r/rc))/2.
+// Packed float2 arithmetic: two FP32 operations per instruction on the sm_100 family (FFMA2, FADD2,
+// FMUL2), each rounded as its scalar counterpart.  The hot loops pair independent operations so that
+// they issue half as many FP32 instructions.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float hsum(float2 a) { return a.x + a.y; }
+
+// sum_k c[k] f[k] (K even) as K/2 paired multiply-adds (even and odd k accumulated apart) and one add.
+template <int K>
+__device__ __forceinline__ float dot_pairs(const float (&c)[K], const float (&f)[K]) {
+  static_assert(K % 2 == 0, "even length");
+  float2 t = mul2(pr(c[0], c[1]), pr(f[0], f[1]));
+#pragma unroll
+  for (int k = 2; k < K; k += 2) t = fma2(pr(c[k], c[k + 1]), pr(f[k], f[k + 1]), t);
+  return hsum(t);
+}
+// Two dot products with the same coefficients: sum_k c[k] f[k] and sum_k c[k] d[k].
+template <int K>
+__device__ __forceinline__ void dot_pairs2(const float (&c)[K], const float (&f)[K], const float (&d)[K], float &tf,
+                                           float &td) {
+  static_assert(K % 2 == 0, "even length");
+  const float2 c0 = pr(c[0], c[1]);
+  float2 a = mul2(c0, pr(f[0], f[1])), b = mul2(c0, pr(d[0], d[1]));
+#pragma unroll
+  for (int k = 2; k < K; k += 2) {
+    const float2 ck = pr(c[k], c[k + 1]);
+    a = fma2(ck, pr(f[k], f[k + 1]), a);
+    b = fma2(ck, pr(d[k], d[k + 1]), b);
+  }
+  tf = hsum(a);
+  td = hsum(b);
+}
+
+// Chebyshev basis f_k(r) = (T_k(x) + 1)/2 * fc(r), x = 2 (r/rc - 1)^2 - 1, fc = (1 + cos(pi r/rc))/2,
+// evaluated as f_k = h T_k + h with h = fc / 2 (T_k by the three-term recurrence, the f_k in pairs).
 // The cutoff uses the hardware sine/cosine (absolute error below 2^-21.4 for arguments in [-pi, pi];
 // here pi r / rc lies in [0, pi]), a few instructions instead of the range-reduced library call.
 template <int K>
 __device__ __forceinline__ void cheb_basis(float r, float inv_rc, float (&f)[K]) {
+  static_assert(K % 2 == 0 && K >= 2, "even basis size");
   float s, c;
   const float t = r * inv_rc;
   __sincosf(3.14159265358979f * t, &s, &c);
-  const float fc = 0.5f + 0.5f * c;
+  const float h = fmaf(0.5f, c, 0.5f) * 0.5f;   // fc / 2
   const float u = t - 1.f;
-  const float x = 2.f * u * u - 1.f;
-  float tm1 = 1.f, t0 = x;
-  f[0] = fc;                       // (T_0 + 1)/2 = 1
-  if (K > 1) f[1] = 0.5f * (x + 1.f) * fc;
+  const float x = fmaf(2.f * u, u, -1.f);
+  const float x2 = x + x;
+  float T[K];
+  T[0] = 1.f; T[1] = x;
 #pragma unroll
-  for (int k = 2; k < K; ++k) {
-    float tk = 2.f * x * t0 - tm1;
-    f[k] = 0.5f * (tk + 1.f) * fc;
-    tm1 = t0; t0 = tk;
+  for (int k = 2; k < K; ++k) T[k] = fmaf(x2, T[k - 1], -T[k - 2]);
+  const float2 h2 = bc2(h);
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    const float2 v = fma2(h2, pr(T[k], T[k + 1]), h2);
+    f[k] = v.x; f[k + 1] = v.y;
   }
 }
 
-// Basis and radial derivative.
+// Basis and radial derivative: f_k' = (T_k + 1) h' + T_k'(x) x'(r) h, with h = fc / 2, h' = fc' / 2,
+// T_k' by the differentiated recurrence T_k' = 2 T_{k-1} + 2 x T_{k-1}' - T_{k-2}'.
 template <int K>
 __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K], float (&df)[K]) {
+  static_assert(K % 2 == 0 && K >= 2, "even basis size");
   float s, c;
   const float t = r * inv_rc;
   __sincosf(3.14159265358979f * t, &s, &c);
-  const float fc = 0.5f + 0.5f * c;
-  const float dfc = -0.5f * 3.14159265358979f * inv_rc * s;
+  const float h = fmaf(0.5f, c, 0.5f) * 0.5f;                     // fc / 2
+  const float dh = (-0.25f * 3.14159265358979f * inv_rc) * s;      // fc' / 2
   const float u = t - 1.f;
-  const float x = 2.f * u * u - 1.f;
-  const float dx = 4.f * u * inv_rc;
-  float tm1 = 1.f, t0 = x, dtm1 = 0.f, dt0 = 1.f;
-  f[0] = fc; df[0] = dfc;
-  if (K > 1) {
-    f[1] = 0.5f * (x + 1.f) * fc;
-    df[1] = 0.5f * dx * fc + 0.5f * (x + 1.f) * dfc;
-  }
+  const float x = fmaf(2.f * u, u, -1.f);
+  const float x2 = x + x;
+  const float dxh = (4.f * inv_rc) * u * h;                        // x'(r) h
+  float T[K], D[K];
+  T[0] = 1.f; T[1] = x;
+  D[0] = 0.f; D[1] = 1.f;
 #pragma unroll
   for (int k = 2; k < K; ++k) {
-    float tk = 2.f * x * t0 - tm1;
-    float dtk = 2.f * t0 + 2.f * x * dt0 - dtm1;
-    f[k] = 0.5f * (tk + 1.f) * fc;
-    df[k] = 0.5f * dtk * dx * fc + 0.5f * (tk + 1.f) * dfc;
-    tm1 = t0; t0 = tk; dtm1 = dt0; dt0 = dtk;
+    T[k] = fmaf(x2, T[k - 1], -T[k - 2]);
+    D[k] = fmaf(x2, D[k - 1], fmaf(2.f, T[k - 1], -D[k - 2]));
+  }
+  const float2 h2 = bc2(h), dh2 = bc2(dh), dxh2 = bc2(dxh);
+#pragma unroll
+  for (int k = 0; k < K; k += 2) {
+    const float2 tk = pr(T[k], T[k + 1]);
+    const float2 v = fma2(h2, tk, h2);
+    const float2 d = fma2(pr(D[k], D[k + 1]), dxh2, fma2(tk, dh2, dh2));
+    f[k] = v.x; f[k + 1] = v.y;
+    df[k] = d.x; df[k + 1] = d.y;
   }
 }
 
@@ -216,10 +262,10 @@ __device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[
   }
 }
 
-// Gradient of the solid-harmonic polynomial of component lm, evaluated at (x, y, z), accumulated
-// with weight b into (gx, gy, gz).  lm is a compile-time constant after unrolling.
-__device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, float z, float b, float &gx,
-                                                  float &gy, float &gz) {
+// Gradient (ax, ay, az) of the solid-harmonic polynomial of component lm at (x, y, z).  lm is a
+// compile-time constant after unrolling; harmonic_grad_mask(lm) has bit d set when component d can be
+// non-zero, so callers skip the multiply-adds of the identically zero ones.
+__device__ __forceinline__ void harmonic_grad(int lm, float x, float y, float z, float (&a)[3]) {
   const float x2 = x * x, y2 = y * y, z2 = z * z;
   const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
   const float s10 = 3.1622776601683795f, s15 = 3.872983346207417f, s35 = 5.916079783099616f;
@@ -256,9 +302,39 @@ __device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, floa
     case 23: ax = 0.5f * s35 * x * (x2 - 3.f * y2); ay = -0.5f * s35 * y * (3.f * x2 - y2); break;
     default: break;
   }
-  gx = fmaf(b, ax, gx);
-  gy = fmaf(b, ay, gy);
-  gz = fmaf(b, az, gz);
+  a[0] = ax; a[1] = ay; a[2] = az;
+}
+__host__ __device__ constexpr int harmonic_grad_mask(int lm) {
+  return lm == 0 ? 2 : lm == 1 ? 4 : lm == 2 ? 1 : lm == 3 ? 3 : lm == 4 ? 6 : lm == 6 ? 5 :
+         (lm == 7 || lm == 8 || lm == 14 || lm == 15 || lm == 23) ? 3 : 7;
+}
+
+// Gradient of the solid-harmonic polynomial of component lm, evaluated at (x, y, z), accumulated
+// with weight b into (gx, gy, gz).
+__device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, float z, float b, float &gx,
+                                                  float &gy, float &gz) {
+  float a[3];
+  harmonic_grad(lm, x, y, z, a);
+  const int m = harmonic_grad_mask(lm);
+  if (m & 1) gx = fmaf(b, a[0], gx);
+  if (m & 2) gy = fmaf(b, a[1], gy);
+  if (m & 4) gz = fmaf(b, a[2], gz);
+}
+
+// The same for the two components lm0, lm0 + 1 with weights b = (b_lm0, b_lm0+1), accumulated into the
+// component pairs g[d] (even and odd lm apart): paired multiply-adds where both are non-zero.
+__device__ __forceinline__ void harmonic_grad_acc2(int lm0, float x, float y, float z, float2 b, float2 (&g)[3]) {
+  float a0[3], a1[3];
+  harmonic_grad(lm0, x, y, z, a0);
+  harmonic_grad(lm0 + 1, x, y, z, a1);
+  const int m0 = harmonic_grad_mask(lm0), m1 = harmonic_grad_mask(lm0 + 1);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const bool n0 = (m0 >> d) & 1, n1 = (m1 >> d) & 1;
+    if (n0 && n1) g[d] = fma2(b, pr(a0[d], a1[d]), g[d]);
+    else if (n0) g[d].x = fmaf(b.x, a0[d], g[d].x);
+    else if (n1) g[d].y = fmaf(b.y, a1[d], g[d].y);
+  }
 }
 
 __host__ __device__ constexpr int lm_l(int lm) { return lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4)); }

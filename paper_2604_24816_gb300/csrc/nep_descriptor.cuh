@@ -298,19 +298,13 @@ __device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, con
 
 // ---------------------------------------------------------------------------------------------------
 // Teacher shape with the angular sums s_nlm of the first NT channels in tensor memory (TMEM) instead
-// of registers (NT = 5: all 120; NT = 4: 96, the fifth channel's 24 in registers): s[a][lm] at column
-// (lm - lm mod 4) NT + 4 a + lm mod 4 of the thread's lane (TMEM_W = 4 components x NT channels per
-// chunk, the same layout as the force kernel's adjoint row for NT = 5).  All TMEM accesses are
-// warp-collective, so the neighbour walk runs to the warp's longest row (threads past their own row,
-// or past the last atom, idle with a predicate) and the angular update is made by whole warps, lanes
+// of registers (NT = 5: all 120; NT = 4: 96, the fifth channel's 24 in registers), in the chunked layout
+// of tm_col (chunk k = components 4k..4k+3 of every channel: one x16 access for channels 0..3 and one x4
+// access for channel 4), which the force pass's adjoint row shares.  All TMEM accesses are
+// warp-collective, so the neighbour walk runs to the warp's longest row (threads past their own row, or
+// past the last atom, idle with a predicate) and the angular update is made by whole warps, lanes
 // without an angular pair adding g = 0.
 constexpr int TMEM_W = 4;
-
-template <int NT>
-__device__ __forceinline__ void tmem_chunk_cols(uint32_t trow, int c, uint32_t (&cols)[NT]) {
-#pragma unroll
-  for (int a = 0; a < NT; ++a) cols[a] = trow + (uint32_t)(c * NT + a * TMEM_W);
-}
 
 // The sums of the channels kept in registers (NA - NT of them; one unused row when NT = NA).
 template <class S, int NT>
@@ -318,8 +312,37 @@ struct RegSums {
   float s[S::NA > NT ? S::NA - NT : 1][S::NLM];
 };
 
+// Chunk k of the NT TMEM channels into v[0..NT-1] (one statement, waited for).
+template <class S, int NT>
+__device__ __forceinline__ void tm_load(uint32_t trow, int k, float (&v)[S::NA][TMEM_W]) {
+  if constexpr (NT == 5) {
+    tmem_ld_chunk<S::NLM>(trow, k, v);
+  } else {
+    float t[4][TMEM_W];
+    tmem_ld_chunk<S::NLM>(trow, k, t);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < TMEM_W; ++c) v[a][c] = t[a][c];
+  }
+}
+template <class S, int NT>
+__device__ __forceinline__ void tm_store(uint32_t trow, int k, const float (&v)[S::NA][TMEM_W]) {
+  if constexpr (NT == 5) {
+    tmem_st_chunk<S::NLM, 5>(trow, k, v);
+  } else {
+    float t[4][TMEM_W];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < TMEM_W; ++c) t[a][c] = v[a][c];
+    tmem_st_chunk<S::NLM, 4>(trow, k, t);
+  }
+}
+
 // Zero the sums, then walk atom ii's row (cnt entries; cnt = 0 for threads past the last atom):
 // radial basis sums QR and the LJ energy in registers, s_nlm in TMEM (channels < NT) and R.
+// The accumulations run in float2 pairs (two basis functions, or two (l, m) components, per instruction).
 template <class S, int NT, int DE, int DP, int BLOCK>
 __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const float4 *shift, uint32_t trow, int ii,
                                                    int n, const float4 *__restrict__ pos,
@@ -327,21 +350,26 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
                                                    float4 *ring_p, float (&QR)[S::KR], RegSums<S, NT> &R,
                                                    float &elj, int &nrad, int &nang, int &nact) {
   static_assert(S::NA == 5 && S::NLM == 24 && (NT == 4 || NT == 5), "teacher shape");
+  static_assert(S::KR % 2 == 0 && S::KA % 2 == 0, "basis sizes are paired");
   constexpr int W = TMEM_W;
+  constexpr int NC = S::NLM / W;
   {
-    const float z[W] = {0.f, 0.f, 0.f, 0.f};
+    float z[S::NA][W];
 #pragma unroll
-    for (int c = 0; c < S::NLM; c += W)
+    for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-      for (int a = 0; a < NT; ++a) tmem_st(trow + (uint32_t)(c * NT + a * W), z);
+      for (int c = 0; c < W; ++c) z[a][c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) tm_store<S, NT>(trow, k, z);
     tmem_wait_st();
   }
 #pragma unroll
   for (int a = NT; a < S::NA; ++a)
 #pragma unroll
     for (int c = 0; c < S::NLM; ++c) R.s[a - NT][c] = 0.f;
+  float2 QR2[S::KR / 2];
 #pragma unroll
-  for (int k = 0; k < S::KR; ++k) QR[k] = 0.f;
+  for (int k = 0; k < S::KR / 2; ++k) QR2[k] = bc2(0.f);
   elj = 0.f;
   nrad = 0; nang = 0; nact = 0;
   const float4 pi = pos[ii];
@@ -366,7 +394,7 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
         float f[S::KR];
         cheb_basis<S::KR>(r, P.inv_rcR, f);
 #pragma unroll
-        for (int b = 0; b < S::KR; ++b) QR[b] += f[b];
+        for (int b = 0; b < S::KR / 2; ++b) QR2[b] = add2(QR2[b], pr(f[2 * b], f[2 * b + 1]));
         ++nrad;
       }
       if (P.lj_on != 0.f && r2 < P.lj_rc2) {
@@ -385,26 +413,26 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
       float g[S::NA];
 #pragma unroll
       for (int a = 0; a < S::NA; ++a) {
-        float t = 0.f;
-#pragma unroll
-        for (int b = 0; b < S::KA; ++b) t = fmaf(P.cA[a][b], f[b], t);
+        const float t = dot_pairs<S::KA>(P.cA[a], f);
         g[a] = ang ? t : 0.f;
       }
       float Y[S::NLM];
       harmonics<S::NLM>(ux, uy, uz, Y);
 #pragma unroll
-      for (int c = 0; c < S::NLM; c += W) {
-        uint32_t cols[NT];
-        tmem_chunk_cols<NT>(trow, c, cols);
-        float sv[NT][W];
-        tmem_ld5(cols, sv);
+      for (int k = 0; k < NC; ++k) {
+        float sv[S::NA][W];
+        tm_load<S, NT>(trow, k, sv);
+        const float2 y01 = pr(Y[W * k], Y[W * k + 1]), y23 = pr(Y[W * k + 2], Y[W * k + 3]);
 #pragma unroll
         for (int a = 0; a < NT; ++a) {
-#pragma unroll
-          for (int cc = 0; cc < W; ++cc) sv[a][cc] = fmaf(g[a], Y[c + cc], sv[a][cc]);
-          tmem_st(cols[a], sv[a]);
+          const float2 g2 = bc2(g[a]);
+          const float2 lo = fma2(g2, y01, pr(sv[a][0], sv[a][1]));
+          const float2 hi = fma2(g2, y23, pr(sv[a][2], sv[a][3]));
+          sv[a][0] = lo.x; sv[a][1] = lo.y; sv[a][2] = hi.x; sv[a][3] = hi.y;
         }
+        tm_store<S, NT>(trow, k, sv);
       }
+      // register-resident channels: scalar (paired updates would pin the sums to aligned register pairs)
 #pragma unroll
       for (int a = NT; a < S::NA; ++a)
 #pragma unroll
@@ -414,19 +442,18 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
     }
   }
   pipe.finish();
+#pragma unroll
+  for (int k = 0; k < S::KR / 2; ++k) { QR[2 * k] = QR2[k].x; QR[2 * k + 1] = QR2[k].y; }
 }
 
-// The sums of chunk c (components c..c+3) of every channel: TMEM for a < NT, registers after.
+// The sums of chunk k (components 4k..4k+3) of every channel: TMEM for a < NT, registers after.
 template <class S, int NT>
-__device__ __forceinline__ void sums_chunk(uint32_t trow, int c, const RegSums<S, NT> &R, float (&sv)[S::NA][TMEM_W]) {
-  uint32_t cols[NT];
-  tmem_chunk_cols<NT>(trow, c, cols);
-  float tv[NT][TMEM_W];
-  tmem_ld5(cols, tv);
+__device__ __forceinline__ void sums_chunk(uint32_t trow, int k, const RegSums<S, NT> &R, float (&sv)[S::NA][TMEM_W]) {
+  tm_load<S, NT>(trow, k, sv);
 #pragma unroll
-  for (int a = 0; a < S::NA; ++a)
+  for (int a = NT; a < S::NA; ++a)
 #pragma unroll
-    for (int cc = 0; cc < TMEM_W; ++cc) sv[a][cc] = a < NT ? tv[a < NT ? a : 0][cc] : R.s[a < NT ? 0 : a - NT][c + cc];
+    for (int cc = 0; cc < TMEM_W; ++cc) sv[a][cc] = R.s[a < NT ? 0 : a - NT][TMEM_W * k + cc];
 }
 
 // Descriptors from the radial basis sums and the sums s_nlm (q_nl = sum_m s_nlm^2, 4-body from the
@@ -446,20 +473,43 @@ __device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow,
   for (int v = S::NR; v < S::NR + S::NA * S::LMAX; ++v) q[v] = 0.f;
   float s2[S::NA][5];
 #pragma unroll
-  for (int c = 0; c < S::NLM; c += W) {
+  for (int k = 0; k < S::NLM / W; ++k) {
     float sv[S::NA][W];
-    sums_chunk<S, NT>(trow, c, R, sv);
+    sums_chunk<S, NT>(trow, k, R, sv);
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll
       for (int cc = 0; cc < W; ++cc) {
-        const int lm = c + cc;
+        const int lm = W * k + cc;
         float &ql = q[S::NR + a * S::LMAX + lm_l(lm) - 1];
         ql = fmaf(sv[a][cc], sv[a][cc], ql);
         if (lm >= 3 && lm < 8) s2[a][lm - 3] = sv[a][cc];
       }
   }
   fourbody_tensors<S>(s2, T, q);
+}
+
+// 4-body adjoint factors g4[a] = 3 (T_a^2) : dT_a/ds_m of every channel, with the tensors T_a rebuilt
+// from the l = 2 sums (components 3..7: chunk 0 holds component 3, chunk 1 components 4..7), so that
+// T need not stay live across the network.
+template <class S, int NT>
+__device__ __forceinline__ void fourbody_adjoint_tm(uint32_t trow, const RegSums<S, NT> &R, float (&g4)[S::NA][5]) {
+  static_assert(S::FOURBODY && S::NLM == 24, "teacher shape");
+  float c0[S::NA][TMEM_W], c1[S::NA][TMEM_W];
+  sums_chunk<S, NT>(trow, 0, R, c0);
+  sums_chunk<S, NT>(trow, 1, R, c1);
+  float s2[S::NA][5];
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) {
+    s2[a][0] = c0[a][3];
+#pragma unroll
+    for (int m = 1; m < 5; ++m) s2[a][m] = c1[a][m - 1];
+  }
+  FourBody<S> T;
+  float q[S::NDES];
+  fourbody_tensors<S>(s2, T, q);
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
 }
 
 // The adjoint of components c..c+3 of channel a, gl = 2 Fp_{a,l} s + (4-body terms for l = 2), as
@@ -473,6 +523,65 @@ __device__ __forceinline__ void adjoint_chunk(int a, int c, const float (&sv)[TM
     gl[cc] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(lm) - 1] * sv[cc];
     if (S::FOURBODY && lm >= 3 && lm < 8) gl[cc] = fmaf(Fp[S::NR + S::NA * S::LMAX + a], g4[lm - 3], gl[cc]);
   }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// The network with W0 staged in shared memory: rows of S::NDES weights padded to NDP (a multiple of 4)
+// so that each is read with 16-byte broadcast loads (all lanes read the same address), and the forward
+// and backward products of a neuron run in float2 pairs over the descriptors.  Same result as network()
+// up to the order of the additions.
+template <class S>
+struct NetSmem {
+  static constexpr int NDP = (S::NDES + 3) / 4 * 4;
+  float W0[S::NNEU][NDP];
+};
+template <class S>
+__device__ __forceinline__ void stage_network(const Model<S> &P, NetSmem<S> &N) {
+  for (int t = threadIdx.x; t < S::NNEU * NetSmem<S>::NDP; t += blockDim.x) {
+    const int mu = t / NetSmem<S>::NDP, v = t % NetSmem<S>::NDP;
+    N.W0[mu][v] = v < S::NDES ? P.W0[mu][v] : 0.f;
+  }
+}
+template <class S>
+__device__ __forceinline__ float network_smem(const Model<S> &P, const NetSmem<S> &N, const float (&q)[S::NDES],
+                                              bool flagged, float (&Fp)[S::NDES]) {
+  constexpr int NDP = NetSmem<S>::NDP, NP = NDP / 2;
+  float2 qt[NP], dq[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int v0 = 2 * p, v1 = 2 * p + 1;
+    qt[p] = pr(v0 < S::NDES ? q[v0 < S::NDES ? v0 : 0] * P.qs[v0 < S::NDES ? v0 : 0] : 0.f,
+               v1 < S::NDES ? q[v1 < S::NDES ? v1 : 0] * P.qs[v1 < S::NDES ? v1 : 0] : 0.f);
+    dq[p] = bc2(0.f);
+  }
+  float U = -P.b1;
+#pragma unroll 1
+  for (int mu = 0; mu < S::NNEU; ++mu) {
+    // the row is read twice (forward, then backward) rather than held in registers
+    const float4 *row = reinterpret_cast<const float4 *>(N.W0[mu]);
+    float2 z2 = pr(-P.b0[mu], 0.f);
+#pragma unroll
+    for (int p = 0; p < NDP / 4; ++p) {
+      const float4 t = row[p];
+      z2 = fma2(pr(t.x, t.y), qt[2 * p], z2);
+      z2 = fma2(pr(t.z, t.w), qt[2 * p + 1], z2);
+    }
+    const float h = tanhf(hsum(z2));
+    U = fmaf(P.w1[mu], h, U);
+    const float2 t2 = bc2(P.w1[mu] * (1.f - h * h));
+#pragma unroll
+    for (int p = 0; p < NDP / 4; ++p) {
+      const float4 t = row[p];
+      dq[2 * p] = fma2(t2, pr(t.x, t.y), dq[2 * p]);
+      dq[2 * p + 1] = fma2(t2, pr(t.z, t.w), dq[2 * p + 1]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < S::NDES; ++v) {
+    const float d = (v & 1) ? dq[v / 2].y : dq[v / 2].x;
+    Fp[v] = flagged ? 0.f : d * P.qs[v];
+  }
+  return U;
 }
 
 }  // namespace nep

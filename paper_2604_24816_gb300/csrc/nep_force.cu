@@ -135,9 +135,11 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
   __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
   __shared__ uint32_t tmem_base;
+  __shared__ __align__(16) NetSmem<S> net;
   if (threadIdx.x < 32) tmem_alloc(&tmem_base, TCOLS);
   tc_fence_before();
   fill_shift_table(shift, geom);
+  stage_network(P, net);
   __syncthreads();
   tc_fence_after();
   const uint32_t trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
@@ -163,17 +165,17 @@ k_descriptor_tm(const __grid_constant__ Model<S> P, const Geom geom, const int n
   const bool flagged = live && fb.on && out_of_range<S>(fb, P, q);
   if (flagged) flag_atom(fb, i, status);
   float Fp[S::NDES];
-  const float U = network<S>(P, q, flagged, Fp);
+  const float U = network_smem<S>(P, net, q, flagged, Fp);
 
   // adjoint row from the TMEM sums, then the radial tail
   float *Gi = G + (size_t)ii * S::GS;
   float g4[S::NA][5];
+  fourbody_adjoint_tm<S, S::NA>(trow, R, g4);
 #pragma unroll
-  for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
-#pragma unroll
-  for (int c = 0; c < S::NLM; c += W) {
+  for (int k = 0; k < S::NLM / W; ++k) {
+    const int c = W * k;
     float sv[S::NA][W];
-    sums_chunk<S, S::NA>(trow, c, R, sv);
+    sums_chunk<S, S::NA>(trow, k, R, sv);
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) {
       float gl[W];
@@ -226,12 +228,17 @@ struct ForceCfg {
 };
 
 // The pair loop of the force kernel (see k_force), for atom i whose adjoint row is already in place:
-// in TMEM at trow (teacher shape) or in gi (registers), radial tail in fpi.  Adds d_ij (FULL) or D_ij
-// to F_i and subtracts it from F_j, and leaves the virial and pair counters in acc.
-template <class S, class GT, bool FS, bool FULL>
+// in TMEM at trow (teacher shape) or in gi (registers), radial tail (8 values) in shared memory at
+// fps[0] and fps[FORCE_BLOCK].  Adds d_ij (FULL) or D_ij to F_i and subtracts it from F_j, and leaves
+// the virial and (COUNT) the pair counters in acc.
+//
+// Virial: only the 6 components of the upper triangle are accumulated and mirrored.  The total
+// W = -sum r_ij (x) d_ij is symmetric because every site energy U_i (and the LJ pair term) is invariant
+// under a rigid rotation of its neighbours: for any antisymmetric Omega, sum_j (Omega r_ij) . d_ij = 0.
+template <class S, class GT, bool FS, bool FULL, bool COUNT = true>
 __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shift, uint32_t trow,
                                             const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
-                                            const float (&fpi)[8], int i, bool live, int ii, int n,
+                                            const float4 *fps, int i, bool live, int ii, int n,
                                             const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
                                             RowSpan sp, int nb0, const GT *__restrict__ G, uint32_t *ring_e, float4 *ring_p,
                                             unsigned long long *__restrict__ Ffix, int *__restrict__ status,
@@ -241,7 +248,7 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
   constexpr int DE = ForceCfg<S>::DE, DP = ForceCfg<S>::DP;
   const float4 pi = pos[ii];
   float fx = 0.f, fy = 0.f, fz = 0.f;
-  float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyx = 0.f, wyy = 0.f, wyz = 0.f, wzx = 0.f, wzy = 0.f, wzz = 0.f;
+  float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyy = 0.f, wyz = 0.f, wzz = 0.f;
   const int cnt = sp.c;
   int nrad = 0, nang = 0, nact = 0;
   NbrPipe<DE, DP, FORCE_BLOCK> pipe;
@@ -276,18 +283,26 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
     if (act && r2 < P.rcR2) {
       float f[S::KR], df[S::KR];
       cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
-      float c = 0.f;
+      float c;
+      float fpi[8];
+      {
+        const float4 a = fps[0], b = fps[FORCE_BLOCK];
+        fpi[0] = a.x; fpi[1] = a.y; fpi[2] = a.z; fpi[3] = a.w; fpi[4] = b.x; fpi[5] = b.y; fpi[6] = b.z; fpi[7] = b.w;
+      }
       if constexpr (FULL) {
-#pragma unroll
-        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k], df[k], c);
+        c = dot_pairs<S::KR>(*reinterpret_cast<const float(*)[S::KR]>(&fpi[0]), df);
       } else {
-        float fpj[8];
+        float fpj[8], fs[S::KR];
         load_tail8(G + (size_t)j * S::GS, S::NA * S::NLM, fpj);
 #pragma unroll
-        for (int k = 0; k < S::KR; ++k) c = fmaf(fpi[k] + fpj[k], df[k], c);
+        for (int k = 0; k < S::KR; k += 2) {
+          const float2 t = add2(pr(fpi[k], fpi[k + 1]), pr(fpj[k], fpj[k + 1]));
+          fs[k] = t.x; fs[k + 1] = t.y;
+        }
+        c = dot_pairs<S::KR>(fs, df);
       }
       coef = c * ir;
-      ++nrad;
+      if (COUNT) ++nrad;
     }
     if (act && P.lj_on != 0.f && r2 < P.lj_rc2) {
       float el, dl;
@@ -309,57 +324,74 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
       cheb_basis_d<S::KA>(ar, P.inv_rcA, f, df);
       float g[S::NA], dg[S::NA];
 #pragma unroll
-      for (int a = 0; a < S::NA; ++a) {
-        float t = 0.f, dt = 0.f;
-#pragma unroll
-        for (int b = 0; b < S::KA; ++b) { t = fmaf(P.cA[a][b], f[b], t); dt = fmaf(P.cA[a][b], df[b], dt); }
-        g[a] = t; dg[a] = dt;
-      }
+      for (int a = 0; a < S::NA; ++a) dot_pairs2<S::KA>(P.cA[a], f, df, g[a], dg[a]);
       float Y[S::NLM];
       harmonics<S::NLM>(ux, uy, uz, Y);
-      float along = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-      // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u)
+      // -l / r for the components' l, in the pairs of consecutive components
+      const float2 air2 = bc2(air);
+      // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u); per component
+      // A_lm = sum_n H_nlm g_n', B_lm = sum_n H_nlm g_n, in pairs of consecutive components (lm, lm + 1)
+      float2 al = bc2(0.f);
+      float2 gv[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};
+      float hj8[S::NA][8];
 #pragma unroll
-      for (int c = 0; c < S::NLM; c += W) {
-        float hj[S::NA][W], hi[S::NA][W];
-        if constexpr (!FULL) {
-#pragma unroll
-          for (int a = 0; a < S::NA; ++a) load_vec(Gj + a * S::NLM + c, hj[a]);
-        }
+      for (int k = 0; k < S::NLM / 4; ++k) {
+        const int lm0 = 4 * k;
+        float hi[S::NA][4];
         if constexpr (TM) {
-          uint32_t cols[S::NA];
-#pragma unroll
-          for (int a = 0; a < S::NA; ++a) cols[a] = trow + (uint32_t)(c * S::NA + a * W);
-          tmem_ld5(cols, hi);
+          tm_load<S, S::NA>(trow, k, hi);
         } else {
 #pragma unroll
           for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-            for (int cc = 0; cc < W; ++cc) hi[a][cc] = gi[a][c + cc];
+            for (int cc = 0; cc < 4; ++cc) hi[a][cc] = gi[a][lm0 + cc];
         }
+        if constexpr (!FULL) {
+          // H = G^i + (-1)^l G^j: the neighbour's row, W values per 16-byte load
+          if (W == 4 || (k & 1) == 0) {
 #pragma unroll
-        for (int cc = 0; cc < W; ++cc) {
-          const int lm = c + cc;
-          const float sgn = (lm_l(lm) & 1) ? -1.f : 1.f;
-          float av = 0.f, bv = 0.f;
+            for (int a = 0; a < S::NA; ++a) {
+              float t[W];
+              load_vec(Gj + a * S::NLM + (lm0 / W) * W, t);
+#pragma unroll
+              for (int cc = 0; cc < W; ++cc) hj8[a][cc] = t[cc];
+            }
+          }
+          const int o = W == 4 ? 0 : (k & 1) * 4;
+          const float2 s01 = pr((lm_l(lm0) & 1) ? -1.f : 1.f, (lm_l(lm0 + 1) & 1) ? -1.f : 1.f);
+          const float2 s23 = pr((lm_l(lm0 + 2) & 1) ? -1.f : 1.f, (lm_l(lm0 + 3) & 1) ? -1.f : 1.f);
 #pragma unroll
           for (int a = 0; a < S::NA; ++a) {
-            const float H = FULL ? hi[a][cc] : fmaf(sgn, hj[a][cc], hi[a][cc]);
-            av = fmaf(H, dg[a], av);
-            bv = fmaf(H, g[a], bv);
+            const float2 h01 = fma2(s01, pr(hj8[a][o], hj8[a][o + 1]), pr(hi[a][0], hi[a][1]));
+            const float2 h23 = fma2(s23, pr(hj8[a][o + 2], hj8[a][o + 3]), pr(hi[a][2], hi[a][3]));
+            hi[a][0] = h01.x; hi[a][1] = h01.y; hi[a][2] = h23.x; hi[a][3] = h23.y;
           }
-          along = fmaf(av - (float)lm_l(lm) * air * bv, Y[lm], along);
-          harmonic_grad_acc(lm, ux, uy, uz, bv, bx, by, bz);
         }
+        float2 av01 = bc2(0.f), av23 = bc2(0.f), bv01 = bc2(0.f), bv23 = bc2(0.f);
+#pragma unroll
+        for (int a = 0; a < S::NA; ++a) {
+          const float2 h01 = pr(hi[a][0], hi[a][1]), h23 = pr(hi[a][2], hi[a][3]);
+          const float2 dg2 = bc2(dg[a]), g2 = bc2(g[a]);
+          av01 = fma2(h01, dg2, av01);
+          av23 = fma2(h23, dg2, av23);
+          bv01 = fma2(h01, g2, bv01);
+          bv23 = fma2(h23, g2, bv23);
+        }
+        const float2 nl01 = mul2(pr(-(float)lm_l(lm0), -(float)lm_l(lm0 + 1)), air2);
+        const float2 nl23 = mul2(pr(-(float)lm_l(lm0 + 2), -(float)lm_l(lm0 + 3)), air2);
+        al = fma2(fma2(nl01, bv01, av01), pr(Y[lm0], Y[lm0 + 1]), al);
+        al = fma2(fma2(nl23, bv23, av23), pr(Y[lm0 + 2], Y[lm0 + 3]), al);
+        harmonic_grad_acc2(lm0, ux, uy, uz, bv01, gv);
+        harmonic_grad_acc2(lm0 + 2, ux, uy, uz, bv23, gv);
       }
       if (ang) {
-        ++nang;
-        coef = fmaf(along, ir, coef);
-        vx = bx * ir; vy = by * ir; vz = bz * ir;
+        if (COUNT) ++nang;
+        coef = fmaf(hsum(al), ir, coef);
+        vx = hsum(gv[0]) * ir; vy = hsum(gv[1]) * ir; vz = hsum(gv[2]) * ir;
       }
     }
     if (act) {
-      ++nact;
+      if (COUNT) ++nact;
       const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
       fx += Dx; fy += Dy; fz += Dz;
       // Newton's third law: F_j -= D_ij, accumulated in fixed point (order-independent sum)
@@ -371,8 +403,7 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
         atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)(-to_fix32(Dz)));
       }
       wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
-      wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
-      wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
+      wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz); wzz = fmaf(dz, Dz, wzz);
     }
   }
   pipe.finish();
@@ -385,11 +416,11 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
       atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
     }
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
-    // each unordered pair once: W = -sum_pairs r_ij (x) D_ij
+    // W = -sum over the evaluated pairs of r_ij (x) d_ij (or D_ij), upper triangle mirrored
     acc[0] = -to_fix32(wxx); acc[1] = -to_fix32(wxy); acc[2] = -to_fix32(wxz);
-    acc[3] = -to_fix32(wyx); acc[4] = -to_fix32(wyy); acc[5] = -to_fix32(wyz);
-    acc[6] = -to_fix32(wzx); acc[7] = -to_fix32(wzy); acc[8] = -to_fix32(wzz);
-    acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang;
+    acc[3] = acc[1]; acc[4] = -to_fix32(wyy); acc[5] = -to_fix32(wyz);
+    acc[6] = acc[2]; acc[7] = acc[5]; acc[8] = -to_fix32(wzz);
+    if (COUNT) { acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang; }
   }
 }
 
@@ -417,6 +448,7 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   constexpr int DE = ForceCfg<S>::DE, DP = ForceCfg<S>::DP;
   __shared__ uint32_t ring_e[DE * FORCE_BLOCK];
   __shared__ float4 ring_p[DP * FORCE_BLOCK];
+  __shared__ float4 fp_s[2 * FORCE_BLOCK];
   __shared__ uint32_t tmem_base;
   if constexpr (TM) {
     if (threadIdx.x < 32) tmem_alloc(&tmem_base, ForceCfg<S>::TCOLS);
@@ -437,26 +469,46 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
   // G_i[a][lm] lives at TMEM column (lm - lm mod W) NA + a W + lm mod W: chunk c of W components
   // holds all channels in NA consecutive groups of W columns.
   float gi[TM ? 1 : S::NA][TM ? 1 : S::NLM];
+  if constexpr (TM) {
+    // chunked TMEM layout (tm_col): chunk k = components 4k..4k+3 of every channel
 #pragma unroll
-  for (int a = 0; a < S::NA; ++a)
+    for (int k = 0; k < S::NLM / 4; ++k) {
+      float v[S::NA][4];
 #pragma unroll
-    for (int c = 0; c < S::NLM; c += W) {
-      float t[W];
-      load_vec(Gi + a * S::NLM + c, t);
-      if constexpr (TM) {
-        tmem_st(trow + (uint32_t)(c * S::NA + a * W), t);
-      } else {
+      for (int a = 0; a < S::NA; ++a) {
+        if constexpr (W == 4) {
+          load_vec(Gi + a * S::NLM + 4 * k, v[a]);
+        } else {
+          float t[W];
+          load_vec(Gi + a * S::NLM + (4 * k / W) * W, t);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) v[a][cc] = t[(4 * k) % W + cc];
+        }
+      }
+      tm_store<S, S::NA>(trow, k, v);
+    }
+    tmem_wait_st();
+  } else {
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+      for (int c = 0; c < S::NLM; c += W) {
+        float t[W];
+        load_vec(Gi + a * S::NLM + c, t);
 #pragma unroll
         for (int k = 0; k < W; ++k) gi[a][c + k] = t[k];
       }
-    }
-  if constexpr (TM) tmem_wait_st();
-  float fpi[8];
-  load_tail8(Gi, S::NA * S::NLM, fpi);
+  }
+  {
+    float fpi[8];
+    load_tail8(Gi, S::NA * S::NLM, fpi);
+    fp_s[threadIdx.x] = make_float4(fpi[0], fpi[1], fpi[2], fpi[3]);
+    fp_s[FORCE_BLOCK + threadIdx.x] = make_float4(fpi[4], fpi[5], fpi[6], fpi[7]);
+  }
   const bool skip = skip_far(X);
   const RowSpan sp = !live ? RowSpan{0, 0, 0} : (FULL ? full_row(X, i, skip) : owned_row(X, i, skip));
-  force_pairs<S, GT, FS, FULL>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, sp, live ? X.nband0[i] : 0, G,
-                               ring_e, ring_p, Ffix, status, Ff, acc);
+  force_pairs<S, GT, FS, FULL>(P, shift, trow, gi, fp_s + threadIdx.x, i, live, ii, n, pos, nbr, sp,
+                               live ? X.nband0[i] : 0, G, ring_e, ring_p, Ffix, status, Ff, acc);
   if constexpr (TM) {
     tc_fence_before();
     __syncthreads();
@@ -491,9 +543,12 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
   __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
   __shared__ uint32_t tmem_base;
+  __shared__ __align__(16) NetSmem<S> net;
+  __shared__ float4 fp_s[2 * DESC_BLOCK];
   if (threadIdx.x < 32) tmem_alloc(&tmem_base, TCOLS);
   tc_fence_before();
   fill_shift_table(shift, geom);
+  stage_network(P, net);
   __syncthreads();
   tc_fence_after();
   const uint32_t trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
@@ -517,28 +572,26 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
     for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
   }
   float Fp[S::NDES];
-  const float U = network<S>(P, q, false, Fp);
+  const float U = network_smem<S>(P, net, q, false, Fp);
 
   // the adjoint row replaces the sums in TMEM (same columns, chunk by chunk); radial tail in registers
   float g4[S::NA][5];
+  fourbody_adjoint_tm<S, S::NA>(trow, R, g4);
 #pragma unroll
-  for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
+  for (int k = 0; k < S::NLM / W; ++k) {
+    float sv[S::NA][W], gl[S::NA][W];
+    sums_chunk<S, S::NA>(trow, k, R, sv);
 #pragma unroll
-  for (int c = 0; c < S::NLM; c += W) {
-    float sv[S::NA][W];
-    sums_chunk<S, S::NA>(trow, c, R, sv);
-    uint32_t cols[S::NA];
-    tmem_chunk_cols<S::NA>(trow, c, cols);
-#pragma unroll
-    for (int a = 0; a < S::NA; ++a) {
-      float gl[W];
-      adjoint_chunk<S>(a, c, sv[a], g4[a], Fp, gl);
-      tmem_st(cols[a], gl);
-    }
+    for (int a = 0; a < S::NA; ++a) adjoint_chunk<S>(a, W * k, sv[a], g4[a], Fp, gl[a]);
+    tm_store<S, S::NA>(trow, k, gl);
   }
   tmem_wait_st();
-  float fpi[8];
-  radial_tail<S>(P, Fp, fpi);
+  {
+    float fpi[8];
+    radial_tail<S>(P, Fp, fpi);
+    fp_s[threadIdx.x] = make_float4(fpi[0], fpi[1], fpi[2], fpi[3]);
+    fp_s[DESC_BLOCK + threadIdx.x] = make_float4(fpi[4], fpi[5], fpi[6], fpi[7]);
+  }
   long long acc_d[5] = {0, 0, 0, 0, 0};
   if (live) {
     const float ui = U + elj;
@@ -555,8 +608,8 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   // forces: every ordered pair of the row with the own adjoint row (as k_force, FULL)
   const float gi[1][1] = {{0.f}};
   long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  force_pairs<S, float, false, true>(P, shift, trow, gi, fpi, i, live, ii, n, pos, nbr, sp, 0, nullptr, ring_e,
-                                     ring_p, Ffix, status, nullptr, acc_f);
+  force_pairs<S, float, false, true>(P, shift, trow, gi, fp_s + threadIdx.x, i, live, ii, n, pos, nbr, sp, 0, nullptr,
+                                     ring_e, ring_p, Ffix, status, nullptr, acc_f);
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) {

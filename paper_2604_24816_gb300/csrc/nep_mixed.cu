@@ -187,9 +187,10 @@ k_descriptor_mixed(const __grid_constant__ Model<S> P, const Geom geom, const in
 #pragma unroll
     for (int a = 0; a < S::NA; ++a) fourbody_adjoint<S>(a, T, g4[a]);
 #pragma unroll
-    for (int c = 0; c < S::NLM; c += TMEM_W) {
+    for (int k = 0; k < S::NLM / TMEM_W; ++k) {
+      const int c = TMEM_W * k;
       float sv[S::NA][TMEM_W];
-      sums_chunk<S, NT>(trow, c, R, sv);
+      sums_chunk<S, NT>(trow, k, R, sv);
 #pragma unroll
       for (int a = 0; a < S::NA; ++a) {
         float gl[TMEM_W];

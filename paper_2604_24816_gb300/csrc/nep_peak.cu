@@ -1,0 +1,116 @@
+// nep_peak.cu -- FP32 throughput microbenchmark of the GPU the library runs on.
+//
+// It measures the denominator of the FP32 roofline that the force kernels are reported against: every
+// thread runs CHAINS independent multiply-add chains acc = acc * a + b for `iters` rounds, either as
+// scalar fused multiply-adds (one FMA per instruction) or as packed float2 ones (two FMAs per
+// instruction, the sm_100 family's paired FP32 form).  The grid fills every SM with as many resident
+// blocks as fit, so the FMA pipes, not the issue slots or the occupancy, are the limit.  Arithmetic
+// performed = threads * iters * CHAINS * 2 FLOP (FMA = 2).  a and b are kernel arguments (no constant
+// folding), the chain converges to b / (1 - a) = 1 (no overflow, no denormals), and every thread stores
+// its sum (no dead-code elimination).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nep_gb300.h"
+
+namespace {
+
+constexpr int PEAK_BLOCK = 256;
+constexpr int PEAK_CHAINS = 16;   // independent accumulators per thread (float2 form: 8 pairs)
+constexpr int PEAK_UNROLL = 8;    // rounds per loop iteration (iters is a multiple of it)
+
+template <bool PACKED>
+__global__ void __launch_bounds__(PEAK_BLOCK) k_fp32_peak(float a, float b, long long rounds, float *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  float s = 0.f;
+  if constexpr (PACKED) {
+    float2 acc[PEAK_CHAINS / 2];
+#pragma unroll
+    for (int c = 0; c < PEAK_CHAINS / 2; ++c) acc[c] = make_float2(1e-3f * (float)(t & 255), 1e-3f * (float)c);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    for (long long it = 0; it < rounds; ++it) {
+#pragma unroll
+      for (int u = 0; u < PEAK_UNROLL; ++u)
+#pragma unroll
+        for (int c = 0; c < PEAK_CHAINS / 2; ++c) acc[c] = __ffma2_rn(acc[c], a2, b2);
+    }
+#pragma unroll
+    for (int c = 0; c < PEAK_CHAINS / 2; ++c) s += acc[c].x + acc[c].y;
+  } else {
+    float acc[PEAK_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PEAK_CHAINS; ++c) acc[c] = 1e-3f * (float)((t + c) & 255);
+    for (long long it = 0; it < rounds; ++it) {
+#pragma unroll
+      for (int u = 0; u < PEAK_UNROLL; ++u)
+#pragma unroll
+        for (int c = 0; c < PEAK_CHAINS; ++c) acc[c] = fmaf(acc[c], a, b);
+    }
+#pragma unroll
+    for (int c = 0; c < PEAK_CHAINS; ++c) s += acc[c];
+  }
+  out[t] = s;
+}
+
+}  // namespace
+
+extern "C" nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void *cuda_stream, double *best_tflops,
+                                    double *median_tflops, int *sm_count) {
+  if (reps < 1 || reps > 10000 || !(launch_ms > 0.0 && launch_ms <= 1000.0)) return NEP_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NEP_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return NEP_ERR_CUDA;
+  cudaError_t e = packed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<true>, PEAK_BLOCK, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<false>, PEAK_BLOCK, 0);
+  if (e != cudaSuccess || per_sm <= 0) return NEP_ERR_CUDA;
+  const int grid = sms * per_sm;
+  const long long threads = (long long)grid * PEAK_BLOCK;
+  float *out = nullptr;
+  if (cudaMalloc(&out, sizeof(float) * (size_t)threads) != cudaSuccess) return NEP_ERR_OOM;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  nep_status status = NEP_OK;
+  std::vector<double> rate;
+  auto launch = [&](long long rounds) {
+    if (packed)
+      k_fp32_peak<true><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out);
+    else
+      k_fp32_peak<false><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out);
+  };
+  auto timed = [&](long long rounds, float *ms) -> bool {
+    if (cudaEventRecord(t0, st) != cudaSuccess) return false;
+    launch(rounds);
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(t1, st) != cudaSuccess) return false;
+    if (cudaEventSynchronize(t1) != cudaSuccess) return false;
+    return cudaEventElapsedTime(ms, t0, t1) == cudaSuccess;
+  };
+  do {
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) { status = NEP_ERR_CUDA; break; }
+    // calibrate the rounds per launch to about launch_ms
+    long long rounds = 256;
+    float ms = 0.f;
+    if (!timed(rounds, &ms)) { status = NEP_ERR_CUDA; break; }       // warm-up
+    for (int k = 0; k < 20 && ms < 0.5 * launch_ms; ++k) {
+      rounds *= 2;
+      if (!timed(rounds, &ms)) { status = NEP_ERR_CUDA; break; }
+    }
+    if (status != NEP_OK) break;
+    rounds = std::max(1LL, (long long)((double)rounds * launch_ms / std::max(1e-3, (double)ms)));
+    const double flop = (double)threads * (double)rounds * PEAK_UNROLL * PEAK_CHAINS * 2.0;
+    for (int r = 0; r < reps; ++r) {
+      if (!timed(rounds, &ms)) { status = NEP_ERR_CUDA; break; }
+      rate.push_back(flop / (ms * 1e-3) / 1e12);
+    }
+  } while (false);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(out);
+  if (status != NEP_OK) return status;
+  std::sort(rate.begin(), rate.end());
+  if (best_tflops) *best_tflops = rate.back();
+  if (median_tflops) *median_tflops = rate[rate.size() / 2];
+  if (sm_count) *sm_count = sms;
+  return NEP_OK;
+}

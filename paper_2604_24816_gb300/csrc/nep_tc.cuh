@@ -134,6 +134,16 @@ __device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[8]) {
                "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
                "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])));
 }
+// Columns [taddr, taddr + 16) of this thread's lane <- v.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])));
+}
 // Wait until this thread's TMEM stores have completed.
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -192,6 +202,61 @@ __device__ __forceinline__ void tmem_ld5(const uint32_t (&c)[5], float (&v)[5][8
   for (int a = 0; a < 5; ++a)
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[a][k] = __uint_as_float(r[8 * a + k]);
+}
+
+// Per-thread rows of 5 channels x NLM components in TMEM ("chunked" layout): chunk k holds the
+// components lm = 4k..4k+3; channels 0..3 of chunk k sit in the 16 columns 16k + 4a + (lm mod 4)
+// (one x16 access at a 16-aligned column) and channel 4 in the 4 columns 16 NC + lm (one x4 access at a
+// 4-aligned column), NC = NLM / 4 chunks.  With NLM = 24: 96 + 24 = 120 columns; with only channels 0..3
+// (the mixed-precision kernel) the first 96.  Every access is aligned to its own width.
+__host__ __device__ constexpr uint32_t tm_col(int a, int lm, int nlm) {
+  return a < 4 ? (uint32_t)((lm >> 2) * 16 + a * 4 + (lm & 3)) : (uint32_t)((nlm >> 2) * 16 + lm);
+}
+
+// Chunk k of channels 0..NT-1 (NT = 4 or 5), loaded and waited for in one statement.
+template <int NLM>
+__device__ __forceinline__ void tmem_ld_chunk(uint32_t trow, int k, float (&v)[5][4]) {
+  uint32_t r[20];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%20];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%21];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19])
+      : "r"(trow + tm_col(0, 4 * k, NLM)), "r"(trow + tm_col(4, 4 * k, NLM)));
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[a][c] = __uint_as_float(r[4 * a + c]);
+}
+template <int NLM>
+__device__ __forceinline__ void tmem_ld_chunk(uint32_t trow, int k, float (&v)[4][4]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(trow + tm_col(0, 4 * k, NLM)));
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[a][c] = __uint_as_float(r[4 * a + c]);
+}
+// Chunk k of channels 0..NT-1 <- v (not waited for: tmem_wait_st before the columns are read again).
+template <int NLM, int NT>
+__device__ __forceinline__ void tmem_st_chunk(uint32_t trow, int k, const float (&v)[NT][4]) {
+  static_assert(NT == 4 || NT == 5, "4 or 5 channels");
+  float w[16];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) w[4 * a + c] = v[a][c];
+  tmem_st16(trow + tm_col(0, 4 * k, NLM), w);
+  if constexpr (NT == 5) tmem_st(trow + tm_col(4, 4 * k, NLM), v[NT - 1]);
 }
 
 }  // namespace nep

@@ -35,7 +35,9 @@ cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, co
                          const GT *, long long *, long long *, int *, cudaStream_t);
 template <class S>
 cudaError_t launch_fused(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &, float *,
-                         float *, long long *, long long *, long long *, int *, cudaStream_t);
+                         float *, long long *, long long *, long long *, int *, const PairCache &, cudaStream_t);
+cudaError_t pair_cache_sm_bound(int *nsm);
+size_t pair_cache_region_elems(int pmax);
 #ifndef NEP_FUSED
 #define NEP_FUSED 1
 #endif
@@ -186,6 +188,11 @@ struct nep_handle {
   // buffers of the ablation variants (allocated on first use)
   float *abl_f = nullptr, *abl_s = nullptr;
 
+  // pair records of the fused float32 kernel (allocated with the system for the float32 teacher)
+  float4 *pc_rec = nullptr;
+  unsigned *pc_mask = nullptr;
+  int pc_nsm = 0;
+
   int ndes() const { return shape == 0 ? CuShape::NDES : StudentShape::NDES; }
   int gs() const { return shape == 0 ? CuShape::GS : StudentShape::GS; }
 };
@@ -235,6 +242,8 @@ void free_system(nep_handle *h) {
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
   dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
   dfree(h->abl_f); dfree(h->abl_s);
+  dfree(h->pc_rec); dfree(h->pc_mask);
+  h->pc_nsm = 0;
   h->fb_cap = 0;
   h->io_i_elems = 0;
   h->n = 0;
@@ -360,7 +369,7 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
       cudaError_t e = cudaMemsetAsync(h->F, 0, 3 * (size_t)h->n * sizeof(long long), h->stream);
       if (e != cudaSuccess) return e;
       return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F, h->part_d, h->part_f,
-                                   &h->ctrl->status, h->stream);
+                                   &h->ctrl->status, PairCache{h->pc_rec, h->pc_mask, h->pc_nsm, h->cap}, h->stream);
     }
   }
   Fallback fb{};
@@ -459,6 +468,7 @@ nep_status check_device_status(nep_handle *h) {
   if (st & ST_TIMEOUT) return fail(h, NEP_ERR_TIMEOUT, "a bounded wait on the tensor cores ran out");
   if (st & ST_FB_OVERFLOW)
     return fail(h, NEP_ERR_FALLBACK_OVERFLOW, "more atoms left the student's range than the fallback list holds");
+  if (st & ST_SLOT) return fail(h, NEP_ERR_CUDA, "a block of the fused force kernel found no free pair-record slot");
   return NEP_OK;
 }
 
@@ -777,6 +787,17 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 13 + 1));
   A(dalloc(h->part_k, (size_t)h->nb_k + 1)); A(dalloc(h->io, 6 * N));
   if (h->fb_on) A(alloc_fallback(h));
+  if (h->shape == 0 && h->precision == NEP_FP32 && e == cudaSuccess) {
+    // pair records of the fused kernel: PC_SLOTS regions per SM index, list capacity records per atom
+    A(pair_cache_sm_bound(&h->pc_nsm));
+    // record offsets are 32-bit: nsm * PC_SLOTS * cap (<= 128) * 128 < 2^32 for nsm <= 4096
+    if (e == cudaSuccess && (h->pc_nsm <= 0 || h->pc_nsm > 4096)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) {
+      A(dalloc(h->pc_rec, (size_t)h->pc_nsm * PC_SLOTS * pair_cache_region_elems(h->cap)));
+      A(dalloc(h->pc_mask, (size_t)h->pc_nsm));
+      if (e == cudaSuccess) A(cudaMemsetAsync(h->pc_mask, 0, (size_t)h->pc_nsm * sizeof(unsigned), h->stream));
+    }
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_system(h);

@@ -29,7 +29,8 @@ constexpr double FIX_INV = 1.0 / 4294967296.0;
 enum : int {
   ST_OVERFLOW = 1,   // neighbour list capacity exceeded
   ST_NAN = 2,        // non-finite value seen
-  ST_FB_OVERFLOW = 8 // more atoms flagged for the fallback model than its list holds
+  ST_FB_OVERFLOW = 8, // more atoms flagged for the fallback model than its list holds
+  ST_SLOT = 16        // a block found no free pair-record slot on its SM (not expected: see PairCache)
 };
 
 // The far band of a neighbour-list row starts at rc_R + FAR_EDGE * skin.  For fcc Cu at rc_R = 5 A and
@@ -105,6 +106,30 @@ struct Model {
   float lj_on, lj_c12, lj_c6, lj_rc2, lj_e_rc, lj_de_rc, lj_rc;  // shifted-force LJ
   float rmax2;   // max(rcR, lj_rc)^2
 };
+
+// Pair records of the fused float32 kernel: its descriptor walk stores every active pair's displacement
+// and neighbour index, and its force pass reads them back instead of walking the neighbour list again.
+// Each resident block owns one region [pmax][BLOCK] float4 of `rec`, chosen by the SM it runs on and a
+// free slot among that SM's PC_SLOTS (one bit each in slot_mask[sm]); at most PC_SLOTS blocks of the
+// kernel fit on an SM (each holds 512 / PC_SLOTS of the SM's tensor-memory columns), so a slot is always
+// free for a starting block.  Regions are reused block after block, so their lines stay in L2.
+constexpr int PC_SLOTS = 4;
+struct PairCache {
+  float4 *rec;           // [nsm * PC_SLOTS][pmax][BLOCK]
+  unsigned *slot_mask;   // [nsm], zero-initialised; bit b: slot b of that SM is held
+  int nsm;               // bound on the SM index (%nsmid)
+  int pmax;              // records per atom: >= the neighbour-list capacity
+};
+__device__ __forceinline__ unsigned sm_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned sm_index_bound() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%nsmid;" : "=r"(r));
+  return r;
+}
 
 // Cell geometry of the current neighbour list.
 struct Geom {
@@ -426,6 +451,11 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+// 16 bytes, cached in L2 only (records that are read once)
+__device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

@@ -343,12 +343,17 @@ __device__ __forceinline__ void tm_store(uint32_t trow, int k, const float (&v)[
 // Zero the sums, then walk atom ii's row (cnt entries; cnt = 0 for threads past the last atom):
 // radial basis sums QR and the LJ energy in registers, s_nlm in TMEM (channels < NT) and R.
 // The accumulations run in float2 pairs (two basis functions, or two (l, m) components, per instruction).
-template <class S, int NT, int DE, int DP, int BLOCK>
+// REC: every active pair is also recorded as (dx, dy, dz, j) at rec[off + slot * BLOCK] (off: this
+// thread's column of a [pmax][BLOCK] array): angular pairs (r < rc_A) from
+// slot 0 up in walk order, the other active pairs from slot pmax - 1 down (pmax >= the row length, so
+// the two never meet).
+template <class S, int NT, int DE, int DP, int BLOCK, bool REC = false>
 __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const float4 *shift, uint32_t trow, int ii,
                                                    int n, const float4 *__restrict__ pos,
                                                    const int32_t *__restrict__ nbr, RowSpan sp, uint32_t *ring_e,
                                                    float4 *ring_p, float (&QR)[S::KR], RegSums<S, NT> &R,
-                                                   float &elj, int &nrad, int &nang, int &nact) {
+                                                   float &elj, int &nrad, int &nang, int &nact,
+                                                   float4 *__restrict__ rec = nullptr, unsigned off = 0, int pmax = 0) {
   static_assert(S::NA == 5 && S::NLM == 24 && (NT == 4 || NT == 5), "teacher shape");
   static_assert(S::KR % 2 == 0 && S::KA % 2 == 0, "basis sizes are paired");
   constexpr int W = TMEM_W;
@@ -389,6 +394,10 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
     const float ir = rsqrtf(r2);
     const float r = r2 * ir;
     if (act) {
+      if constexpr (REC) {
+        const int slot = r2 < P.rcA2 ? nang : pmax - 1 - (nact - nang);
+        rec[off + (unsigned)slot * BLOCK] = make_float4(dx, dy, dz, __int_as_float((int)(e & J_MASK)));
+      }
       ++nact;
       if (r2 < P.rcR2) {
         float f[S::KR];

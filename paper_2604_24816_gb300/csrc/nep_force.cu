@@ -227,6 +227,85 @@ struct ForceCfg {
   static_assert(!TM || FORCE_BLOCK == 128, "one TMEM lane per thread: 4 warps cover the 128 lanes");
 };
 
+// The angular part of one pair's force, d/dd of sum_nlm H_nlm g_n(r) Yh_lm(u) with H the adjoint row:
+// H = G^i (FULL; in TMEM at trow for the teacher shape, else in gi) or G^i + (-1)^l G^j (half list, G^j
+// gathered from Gj).  Returns sum_lm (A_lm - l B_lm / r) Yh_lm (al, even and odd lm apart) and
+// sum_lm B_lm grad P_lm(u) (gv), A_lm = sum_n H_nlm g_n'(r), B_lm = sum_n H_nlm g_n(r).  si: a stand-in
+// pair (r = 1 along x) for lanes that only take part in the warp-collective TMEM loads.
+template <class S, class GT, bool FULL>
+__device__ __forceinline__ void angular_pair(const Model<S> &P, uint32_t trow,
+                                             const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
+                                             const GT *__restrict__ Gj, bool si, float r, float ir, float dx, float dy,
+                                             float dz, float2 &al, float2 (&gv)[3]) {
+  constexpr bool TM = ForceCfg<S>::TM;
+  constexpr int W = GTraits<GT>::W;
+  const float ar = si ? 1.f : r, air = si ? 1.f : ir;
+  const float ux = si ? 1.f : dx * ir, uy = si ? 0.f : dy * ir, uz = si ? 0.f : dz * ir;
+  float f[S::KA], df[S::KA];
+  cheb_basis_d<S::KA>(ar, P.inv_rcA, f, df);
+  float g[S::NA], dg[S::NA];
+#pragma unroll
+  for (int a = 0; a < S::NA; ++a) dot_pairs2<S::KA>(P.cA[a], f, df, g[a], dg[a]);
+  float Y[S::NLM];
+  harmonics<S::NLM>(ux, uy, uz, Y);
+  const float2 air2 = bc2(air);
+  // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u); per component
+  // A_lm = sum_n H_nlm g_n', B_lm = sum_n H_nlm g_n, in pairs of consecutive components (lm, lm + 1)
+  al = bc2(0.f);
+  gv[0] = gv[1] = gv[2] = bc2(0.f);
+  float hj8[S::NA][8];
+#pragma unroll
+  for (int k = 0; k < S::NLM / 4; ++k) {
+    const int lm0 = 4 * k;
+    float hi[S::NA][4];
+    if constexpr (TM) {
+      tm_load<S, S::NA>(trow, k, hi);
+    } else {
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) hi[a][cc] = gi[a][lm0 + cc];
+    }
+    if constexpr (!FULL) {
+      // H = G^i + (-1)^l G^j: the neighbour's row, W values per 16-byte load
+      if (W == 4 || (k & 1) == 0) {
+#pragma unroll
+        for (int a = 0; a < S::NA; ++a) {
+          float t[W];
+          load_vec(Gj + a * S::NLM + (lm0 / W) * W, t);
+#pragma unroll
+          for (int cc = 0; cc < W; ++cc) hj8[a][cc] = t[cc];
+        }
+      }
+      const int o = W == 4 ? 0 : (k & 1) * 4;
+      const float2 s01 = pr((lm_l(lm0) & 1) ? -1.f : 1.f, (lm_l(lm0 + 1) & 1) ? -1.f : 1.f);
+      const float2 s23 = pr((lm_l(lm0 + 2) & 1) ? -1.f : 1.f, (lm_l(lm0 + 3) & 1) ? -1.f : 1.f);
+#pragma unroll
+      for (int a = 0; a < S::NA; ++a) {
+        const float2 h01 = fma2(s01, pr(hj8[a][o], hj8[a][o + 1]), pr(hi[a][0], hi[a][1]));
+        const float2 h23 = fma2(s23, pr(hj8[a][o + 2], hj8[a][o + 3]), pr(hi[a][2], hi[a][3]));
+        hi[a][0] = h01.x; hi[a][1] = h01.y; hi[a][2] = h23.x; hi[a][3] = h23.y;
+      }
+    }
+    float2 av01 = bc2(0.f), av23 = bc2(0.f), bv01 = bc2(0.f), bv23 = bc2(0.f);
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) {
+      const float2 h01 = pr(hi[a][0], hi[a][1]), h23 = pr(hi[a][2], hi[a][3]);
+      const float2 dg2 = bc2(dg[a]), g2 = bc2(g[a]);
+      av01 = fma2(h01, dg2, av01);
+      av23 = fma2(h23, dg2, av23);
+      bv01 = fma2(h01, g2, bv01);
+      bv23 = fma2(h23, g2, bv23);
+    }
+    const float2 nl01 = mul2(pr(-(float)lm_l(lm0), -(float)lm_l(lm0 + 1)), air2);
+    const float2 nl23 = mul2(pr(-(float)lm_l(lm0 + 2), -(float)lm_l(lm0 + 3)), air2);
+    al = fma2(fma2(nl01, bv01, av01), pr(Y[lm0], Y[lm0 + 1]), al);
+    al = fma2(fma2(nl23, bv23, av23), pr(Y[lm0 + 2], Y[lm0 + 3]), al);
+    harmonic_grad_acc2(lm0, ux, uy, uz, bv01, gv);
+    harmonic_grad_acc2(lm0 + 2, ux, uy, uz, bv23, gv);
+  }
+}
+
 // The pair loop of the force kernel (see k_force), for atom i whose adjoint row is already in place:
 // in TMEM at trow (teacher shape) or in gi (registers), radial tail (8 values) in shared memory at
 // fps[0] and fps[FORCE_BLOCK].  Adds d_ij (FULL) or D_ij to F_i and subtracts it from F_j, and leaves
@@ -314,76 +393,9 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
     if constexpr (TM) enter = __any_sync(0xffffffffu, ang);
     if (enter) {
       if constexpr (TM) __syncwarp();
-      // stand-in pair for lanes that only take part in the warp-collective loads: r = 1 along x,
-      // the row of atom ii
       const bool si = TM && !ang;
-      const float ar = si ? 1.f : r, air = si ? 1.f : ir;
-      const float ux = si ? 1.f : dx * ir, uy = si ? 0.f : dy * ir, uz = si ? 0.f : dz * ir;
-      const GT *Gj = G + (size_t)(si ? ii : j) * S::GS;
-      float f[S::KA], df[S::KA];
-      cheb_basis_d<S::KA>(ar, P.inv_rcA, f, df);
-      float g[S::NA], dg[S::NA];
-#pragma unroll
-      for (int a = 0; a < S::NA; ++a) dot_pairs2<S::KA>(P.cA[a], f, df, g[a], dg[a]);
-      float Y[S::NLM];
-      harmonics<S::NLM>(ux, uy, uz, Y);
-      // -l / r for the components' l, in the pairs of consecutive components
-      const float2 air2 = bc2(air);
-      // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u); per component
-      // A_lm = sum_n H_nlm g_n', B_lm = sum_n H_nlm g_n, in pairs of consecutive components (lm, lm + 1)
-      float2 al = bc2(0.f);
-      float2 gv[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};
-      float hj8[S::NA][8];
-#pragma unroll
-      for (int k = 0; k < S::NLM / 4; ++k) {
-        const int lm0 = 4 * k;
-        float hi[S::NA][4];
-        if constexpr (TM) {
-          tm_load<S, S::NA>(trow, k, hi);
-        } else {
-#pragma unroll
-          for (int a = 0; a < S::NA; ++a)
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) hi[a][cc] = gi[a][lm0 + cc];
-        }
-        if constexpr (!FULL) {
-          // H = G^i + (-1)^l G^j: the neighbour's row, W values per 16-byte load
-          if (W == 4 || (k & 1) == 0) {
-#pragma unroll
-            for (int a = 0; a < S::NA; ++a) {
-              float t[W];
-              load_vec(Gj + a * S::NLM + (lm0 / W) * W, t);
-#pragma unroll
-              for (int cc = 0; cc < W; ++cc) hj8[a][cc] = t[cc];
-            }
-          }
-          const int o = W == 4 ? 0 : (k & 1) * 4;
-          const float2 s01 = pr((lm_l(lm0) & 1) ? -1.f : 1.f, (lm_l(lm0 + 1) & 1) ? -1.f : 1.f);
-          const float2 s23 = pr((lm_l(lm0 + 2) & 1) ? -1.f : 1.f, (lm_l(lm0 + 3) & 1) ? -1.f : 1.f);
-#pragma unroll
-          for (int a = 0; a < S::NA; ++a) {
-            const float2 h01 = fma2(s01, pr(hj8[a][o], hj8[a][o + 1]), pr(hi[a][0], hi[a][1]));
-            const float2 h23 = fma2(s23, pr(hj8[a][o + 2], hj8[a][o + 3]), pr(hi[a][2], hi[a][3]));
-            hi[a][0] = h01.x; hi[a][1] = h01.y; hi[a][2] = h23.x; hi[a][3] = h23.y;
-          }
-        }
-        float2 av01 = bc2(0.f), av23 = bc2(0.f), bv01 = bc2(0.f), bv23 = bc2(0.f);
-#pragma unroll
-        for (int a = 0; a < S::NA; ++a) {
-          const float2 h01 = pr(hi[a][0], hi[a][1]), h23 = pr(hi[a][2], hi[a][3]);
-          const float2 dg2 = bc2(dg[a]), g2 = bc2(g[a]);
-          av01 = fma2(h01, dg2, av01);
-          av23 = fma2(h23, dg2, av23);
-          bv01 = fma2(h01, g2, bv01);
-          bv23 = fma2(h23, g2, bv23);
-        }
-        const float2 nl01 = mul2(pr(-(float)lm_l(lm0), -(float)lm_l(lm0 + 1)), air2);
-        const float2 nl23 = mul2(pr(-(float)lm_l(lm0 + 2), -(float)lm_l(lm0 + 3)), air2);
-        al = fma2(fma2(nl01, bv01, av01), pr(Y[lm0], Y[lm0 + 1]), al);
-        al = fma2(fma2(nl23, bv23, av23), pr(Y[lm0 + 2], Y[lm0 + 3]), al);
-        harmonic_grad_acc2(lm0, ux, uy, uz, bv01, gv);
-        harmonic_grad_acc2(lm0 + 2, ux, uy, uz, bv23, gv);
-      }
+      float2 al, gv[3];
+      angular_pair<S, GT, FULL>(P, trow, gi, G + (size_t)(si ? ii : j) * S::GS, si, r, ir, dx, dy, dz, al, gv);
       if (ang) {
         if (COUNT) ++nang;
         coef = fmaf(hsum(al), ir, coef);
@@ -421,6 +433,125 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
     acc[3] = acc[1]; acc[4] = -to_fix32(wyy); acc[5] = -to_fix32(wyz);
     acc[6] = acc[2]; acc[7] = acc[5]; acc[8] = -to_fix32(wzz);
     if (COUNT) { acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang; }
+  }
+}
+
+// cp.async ring of pair records (16 bytes each, L2 only): record k of this thread is src[k * stride];
+// DQ records in flight, as NbrPipe's positions.
+template <int DQ, int BLOCK, int STRIDE>
+struct RecPipe {
+  float4 *rg;
+  const float4 *base;   // the record array (a kernel parameter)
+  unsigned off;         // element offset of record 0 of this thread
+  int cnt;
+  __device__ __forceinline__ void start(float4 *ring, const float4 *base_, unsigned off_, int cnt_) {
+    rg = ring + threadIdx.x; base = base_; off = off_; cnt = cnt_;
+#pragma unroll
+    for (int k = 0; k < DQ; ++k) {
+      if (k < cnt) cp_async16_cg(rg + k * BLOCK, base + (off + k * STRIDE));
+      cp_async_commit();
+    }
+  }
+  __device__ __forceinline__ float4 get(int k) {
+    cp_async_wait<DQ - 1>();
+    const float4 v = rg[(k % DQ) * BLOCK];
+    if (k + DQ < cnt) cp_async16_cg(rg + ((k + DQ) % DQ) * BLOCK, base + (off + (k + DQ) * STRIDE));
+    cp_async_commit();
+    return v;
+  }
+  __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
+};
+
+// Radial and LJ part of one active pair's force coefficient (d = coef * r_ij + angular part): the
+// radial adjoint in basis space (8 values in shared memory at fps[0], fps[FORCE_BLOCK]) against the
+// basis derivatives, plus half of the shifted-force LJ pair force.
+template <class S>
+__device__ __forceinline__ float radial_lj_coef(const Model<S> &P, const float4 *fps, float r2, float r, float ir) {
+  float coef = 0.f;
+  if (r2 < P.rcR2) {
+    float f[S::KR], df[S::KR];
+    cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
+    float fpi[8];
+    const float4 a = fps[0], b = fps[FORCE_BLOCK];
+    fpi[0] = a.x; fpi[1] = a.y; fpi[2] = a.z; fpi[3] = a.w; fpi[4] = b.x; fpi[5] = b.y; fpi[6] = b.z; fpi[7] = b.w;
+    coef = dot_pairs<S::KR>(*reinterpret_cast<const float(*)[S::KR]>(&fpi[0]), df) * ir;
+  }
+  if (P.lj_on != 0.f && r2 < P.lj_rc2) {
+    float el, dl;
+    lj_pair<S>(P, r2, r, ir, el, dl);
+    coef = fmaf(0.5f * dl, ir, coef);
+  }
+  return coef;
+}
+
+// The force pass of the fused kernel over the pair records of its own descriptor walk (PairCache):
+// first the na angular pairs (slots 0..na-1; warp-collective TMEM reads of the own adjoint row, so the
+// loop runs to the warp's largest na and lanes past their own count compute a stand-in pair), then the
+// nr other active pairs (slots pmax-1 down to pmax-nr; no TMEM).  Each pair gets the arithmetic of
+// force_pairs<S, float, false, true> on the displacement the descriptor walk computed: d_ij added to F_i,
+// subtracted from F_j (fixed point), W -= r_ij (x) d_ij (upper triangle, mirrored).
+template <class S, int DQ>
+__device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow, const float4 *fps, int i, bool live,
+                                                int n, const float4 *rec, unsigned off, int pmax, int na, int nr,
+                                                float4 *ring,
+                                                unsigned long long *__restrict__ Ffix, int *__restrict__ status,
+                                                long long (&acc)[13]) {
+  static_assert(ForceCfg<S>::TM, "teacher shape");
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyy = 0.f, wyz = 0.f, wzz = 0.f;
+  auto apply = [&](float dx, float dy, float dz, int j, float coef, float vx, float vy, float vz) {
+    const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
+    fx += Dx; fy += Dy; fz += Dz;
+    atomicAdd(Ffix + j, (unsigned long long)to_fix32(-Dx));
+    atomicAdd(Ffix + (size_t)n + j, (unsigned long long)to_fix32(-Dy));
+    atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)to_fix32(-Dz));
+    wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
+    wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz); wzz = fmaf(dz, Dz, wzz);
+  };
+  const float gi[1][1] = {{0.f}};
+  {
+    RecPipe<DQ, FORCE_BLOCK, FORCE_BLOCK> pa;
+    pa.start(ring, rec, off, na);
+    const int trip = __reduce_max_sync(0xffffffffu, na);
+    for (int p = 0; p < trip; ++p) {
+      const bool valid = p < na;
+      float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+      if (valid) q = pa.get(p);
+      const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
+      const float ir = rsqrtf(r2);
+      const float r = r2 * ir;
+      float coef = valid ? radial_lj_coef<S>(P, fps, r2, r, ir) : 0.f;
+      __syncwarp();
+      float2 al, gv[3];
+      angular_pair<S, float, true>(P, trow, gi, static_cast<const float *>(nullptr), !valid, r, ir, q.x, q.y, q.z, al,
+                                   gv);
+      if (valid) {
+        coef = fmaf(hsum(al), ir, coef);
+        apply(q.x, q.y, q.z, __float_as_int(q.w), coef, hsum(gv[0]) * ir, hsum(gv[1]) * ir, hsum(gv[2]) * ir);
+      }
+    }
+    pa.finish();
+  }
+  {
+    RecPipe<DQ, FORCE_BLOCK, -FORCE_BLOCK> pb;
+    pb.start(ring, rec, off + (unsigned)(pmax - 1) * FORCE_BLOCK, nr);
+    for (int p = 0; p < nr; ++p) {
+      const float4 q = pb.get(p);
+      const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
+      const float ir = rsqrtf(r2);
+      const float r = r2 * ir;
+      apply(q.x, q.y, q.z, __float_as_int(q.w), radial_lj_coef<S>(P, fps, r2, r, ir), 0.f, 0.f, 0.f);
+    }
+    pb.finish();
+  }
+  if (live) {
+    atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
+    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
+    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
+    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
+    acc[0] = -to_fix32(wxx); acc[1] = -to_fix32(wxy); acc[2] = -to_fix32(wxz);
+    acc[3] = acc[1]; acc[4] = -to_fix32(wyy); acc[5] = -to_fix32(wyz);
+    acc[6] = acc[2]; acc[7] = acc[5]; acc[8] = -to_fix32(wzz);
   }
 }
 
@@ -522,10 +653,12 @@ k_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, const 
 
 // Descriptors, network and forces of the float32 teacher in one kernel.  The full-row force form reads
 // no neighbour row, so no atom waits for another's adjoint row: the angular sums s_nlm are accumulated
-// in TMEM, turned into the adjoint row in place, and the force pass walks the row again with it, so no
-// adjoint row goes through HBM and one launch (and its tail wave) is saved.  The forces are scattered
-// with atomics into Ffix, which the caller zeroes before the launch (a block may add to F_j before
-// atom j's own block has started).
+// in TMEM, turned into the adjoint row in place, and the force pass evaluates every active pair again
+// with it, so no adjoint row goes through HBM and one launch (and its tail wave) is saved.  The
+// descriptor walk records each active pair's displacement and neighbour (PairCache; L2-resident
+// regions reused block after block), so the force pass reads 16 bytes per active pair in order instead
+// of walking the neighbour list a second time.  The forces are scattered with atomics into Ffix, which
+// the caller zeroes before the launch (a block may add to F_j before atom j's own block has started).
 #ifndef NEP_FUSED_MINB
 #define NEP_FUSED_MINB 4
 #endif
@@ -534,23 +667,41 @@ __global__ void __launch_bounds__(DESC_BLOCK, NEP_FUSED_MINB)
 k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
             const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ usite,
             float *__restrict__ qout, unsigned long long *__restrict__ Ffix, long long *__restrict__ part_d,
-            long long *__restrict__ part_f, int *__restrict__ status) {
+            long long *__restrict__ part_f, int *__restrict__ status, const PairCache pc) {
   static_assert(ForceCfg<S>::TM && DESC_BLOCK == 128 && FORCE_BLOCK == 128, "teacher shape, 4 warps");
-  static_assert(ForceCfg<S>::DE <= PIPE_DE && ForceCfg<S>::DP <= PIPE_DP, "one ring serves both passes");
   constexpr int W = TMEM_W;
   constexpr uint32_t TCOLS = 128;
+  static_assert(PC_SLOTS * TCOLS == 512, "at most PC_SLOTS blocks per SM: one pair-record slot each");
   __shared__ float4 shift[27];
   __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
   __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
   __shared__ uint32_t tmem_base;
   __shared__ __align__(16) NetSmem<S> net;
   __shared__ float4 fp_s[2 * DESC_BLOCK];
+  __shared__ int s_slot;
   if (threadIdx.x < 32) tmem_alloc(&tmem_base, TCOLS);
+  if (threadIdx.x == 0) {
+    // one free pair-record slot of this SM (at most PC_SLOTS blocks of this kernel are resident here)
+    const unsigned sm = sm_index();
+    int slot = -1;
+    if ((int)sm < pc.nsm) {
+      for (int it = 0; it < 64 && slot < 0; ++it)
+        for (int b = 0; b < PC_SLOTS && slot < 0; ++b)
+          if ((atomicOr(pc.slot_mask + sm, 1u << b) & (1u << b)) == 0u) slot = (int)sm * PC_SLOTS + b;
+    }
+    if (slot < 0) atomicOr(status, ST_SLOT);   // results of this evaluation are then reported invalid
+    __threadfence();
+    s_slot = slot;
+  }
   tc_fence_before();
   fill_shift_table(shift, geom);
   stage_network(P, net);
   __syncthreads();
   tc_fence_after();
+  const int slot = s_slot;
+  // element offset of this thread's record column; without a slot (reported above) the block still
+  // writes only inside the array, to slot 0
+  const unsigned rec_off = (unsigned)(slot < 0 ? 0 : slot) * (unsigned)pc.pmax * DESC_BLOCK + threadIdx.x;
   const uint32_t trow = tmem_base + ((uint32_t)(threadIdx.x & ~31u) << 16);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = i < n;
@@ -558,12 +709,13 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   const RowSpan sp = live ? full_row(X, i, skip_far(X)) : RowSpan{0, 0, 0};
   const int cnt = sp.c;
 
-  // descriptors and network (as k_descriptor_tm)
+  // descriptors and network (as k_descriptor_tm), recording the active pairs
   float QR[S::KR], elj;
   int nrad, nang, nact;
   RegSums<S, S::NA> R;
-  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
-                                                             QR, R, elj, nrad, nang, nact);
+  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK, true>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
+                                                                   QR, R, elj, nrad, nang, nact, pc.rec, rec_off,
+                                                                   pc.pmax);
   float q[S::NDES];
   FourBody<S> T;
   descriptors_tm<S, S::NA>(P, trow, QR, R, q, T);
@@ -593,6 +745,7 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
     fp_s[DESC_BLOCK + threadIdx.x] = make_float4(fpi[4], fpi[5], fpi[6], fpi[7]);
   }
   long long acc_d[5] = {0, 0, 0, 0, 0};
+  long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (live) {
     const float ui = U + elj;
     usite[i] = ui;
@@ -602,19 +755,23 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
     acc_d[2] = nang;
     acc_d[3] = cnt;
     acc_d[4] = nact;
+    // the force pass visits the descriptor walk's active pairs
+    acc_f[9] = cnt; acc_f[10] = nact; acc_f[11] = nrad; acc_f[12] = nang;
   }
   block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);   // before the force pass: fewer live registers
 
-  // forces: every ordered pair of the row with the own adjoint row (as k_force, FULL)
-  const float gi[1][1] = {{0.f}};
-  long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  force_pairs<S, float, false, true>(P, shift, trow, gi, fp_s + threadIdx.x, i, live, ii, n, pos, nbr, sp, 0, nullptr,
-                                     ring_e, ring_p, Ffix, status, nullptr, acc_f);
+  // forces: every active pair of the row with the own adjoint row, from the pair records
+  force_pairs_rec<S, PIPE_DP>(P, trow, fp_s + threadIdx.x, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang,
+                              ring_p, Ffix, status, acc_f);
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) {
     tc_fence_after();
     tmem_dealloc(tmem_base, TCOLS);
+  }
+  if (threadIdx.x == 0 && slot >= 0) {
+    __threadfence();          // this block's record reads are complete (cp.async waited, barrier above)
+    atomicAnd(pc.slot_mask + slot / PC_SLOTS, ~(1u << (slot % PC_SLOTS)));
   }
   block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
@@ -696,16 +853,31 @@ template cudaError_t launch_force_float_scatter<CuShape>(const Model<CuShape> &,
 template <class S>
 cudaError_t launch_fused(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
                          const RowExt &X, float *usite, float *qout, long long *Ffix, long long *part_d,
-                         long long *part_f, int *status, cudaStream_t st) {
+                         long long *part_f, int *status, const PairCache &pc, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
   k_nep_fused<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, usite, qout,
-                                              reinterpret_cast<unsigned long long *>(Ffix), part_d, part_f, status);
+                                              reinterpret_cast<unsigned long long *>(Ffix), part_d, part_f, status, pc);
   return cudaGetLastError();
 }
 template cudaError_t launch_fused<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *, const int32_t *,
                                            const RowExt &, float *, float *, long long *, long long *, long long *,
-                                           int *, cudaStream_t);
+                                           int *, const PairCache &, cudaStream_t);
+
+// Records per SM bound of the pair cache: %nsmid of the current device (synchronous).
+__global__ void k_sm_bound(int *out) { *out = (int)sm_index_bound(); }
+cudaError_t pair_cache_sm_bound(int *nsm) {
+  int *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return e;
+  k_sm_bound<<<1, 1>>>(d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(nsm, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e;
+}
+// Pair records per region: one float4 per record, DESC_BLOCK threads.
+size_t pair_cache_region_elems(int pmax) { return (size_t)pmax * DESC_BLOCK; }
 
 int descriptor_blocks(int n) { return (n + DESC_BLOCK - 1) / DESC_BLOCK; }
 int force_blocks(int n) { return (n + FORCE_BLOCK - 1) / FORCE_BLOCK; }

@@ -2,7 +2,7 @@
 """NEP molecular-dynamics throughput on GB300: atom-steps/s of plain FP32 NEP-MD.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
-                    [--form plain|mix_bf16|mix_fp16]
+                    [--form plain|mix_bf16|mix_fp16|student|student_bf16_fallback] [--no-configs]
 
 One step = one velocity-Verlet MD step of the whole hot path on the 1,048,576-atom fcc Cu workload
 (64x64x64 cells, 300 K, 1 fs): half kick + drift, neighbour-rebuild check (a rebuild runs every 10
@@ -11,19 +11,21 @@ skin/2), cell sort + neighbour list when rebuilding, descriptors + network, forc
 kick, energy/virial/kinetic sums.  Inputs are resident in HBM when the timed region starts.  The
 timed region replays the captured CUDA graph of one MD step, the launch path md_verlet_step uses; the
 per-kernel breakdown ("kernels") and the roofline come from an eager pass of the same length with
-per-kernel-class CUDA events (about 3 % slower per step than the graph).
+per-kernel-class CUDA events.  The roofline's peak is the FP32 throughput measured in the same run by
+the library's microbenchmark (nep_fp32_peak), with the SM clock sampled during it.
 
 --form selects the form whose throughput is the headline value (default: plain FP32).  The other
 forms are then timed on the same workload and start state ("forms": atom-steps/s, speedup, and force
 RMSE/max against the plain FP32 forces on 8,192 sampled atoms; their error against the FP64 oracle is
-a GPU test).  --workload cu_160x160x160 (16,384,000 atoms, 300 K) or cu_160x160x160_1200K runs the
-mixed-precision workload.
+a GPU test).  "configs" (default run, --no-configs skips it) times the forms on the 16,384,000-atom
+workload at 300 K and from the 1200 K start, and the plain teacher against the student with teacher
+fallback on the 131,027,885-atom void workload, each with its own clocks.
 
 N > 1 (torchrun): every rank runs an independent replica on its own GPU (no collective on the data
 path); value = atom-steps of all ranks / max-over-ranks time ("scaling": "weak").
 
 --impl reference times the FP64 CPU oracle (the method as written, plain C) on the host cores for
-the same metric, each step on a bounded sample of the workload.
+the same metric on the same workload: one velocity-Verlet call over a bounded number of steps.
 """
 from __future__ import annotations
 
@@ -47,37 +49,58 @@ import nep_inputs as ni  # noqa: E402
 
 METRIC = "NEP MD atom-steps/s on 1 GB300: plain FP32 vs mixed/student at stated force RMSE"
 UNIT = "atom-steps/s"
-N_SMS = 152
-FP32_LANES_PER_SM = 128
 
-# Algorithmic FP32 FLOPs of the method per unit (static count of the arithmetic each unit needs,
-# FMA = 2, add/mul = 1, each transcendental = 1), for the compiled shape (5 radial + 5 angular
-# channels, 8 basis functions, l = 1..4, 4-body, 30 neurons).  The descriptor kernel visits every
-# list entry of every atom.  The force kernel of the float32 teacher ("force_full") visits every
-# ordered pair with the own adjoint row only; the half-list form ("force": float16 rows, and the
-# half-list ablation) visits each unordered pair once and forms H = G^i + (-1)^l G^j (120 more FMAs
-# per angular pair, and fp_i + fp_j per radial pair).
+# Algorithmic FP32 FLOPs of the method per unit: a static count of the arithmetic each unit needs in the
+# kernels (FMA = 2, add/mul = 1, each transcendental = 1, a packed float2 operation counts both halves),
+# for the compiled teacher shape (5 radial + 5 angular channels, 8 basis functions, l = 1..4, 4-body,
+# 30 neurons).  Fixed-point conversions of the force scatter and of the sums, the stand-in pairs of
+# lanes that only take part in warp-collective loads and the zero padding of the network row are not
+# counted.  Pieces (teacher shape):
+#   list entry 11: displacement (6 adds) and r^2 (1 mul + 2 FMA);
+#   active pair, descriptor 2: rsqrt and r;
+#   radial pair, descriptor 49: Chebyshev basis 41 (r/rc, pi r/rc and the hardware sine/cosine 4, the
+#     cutoff half 3, x = 2 (r/rc - 1)^2 - 1 5, 6 recurrence FMAs, 4 paired FMAs) + 4 paired adds;
+#   LJ pair, descriptor 17: 1/r^2 with one Newton step, r^-6, r^-12, the shifted energy, half of it summed;
+#   angular pair, descriptor 440: unit vector 3 + basis 41 + 5 channel dot products 75 + 24 solid
+#     harmonics 81 + 120 paired FMAs into s_nlm 240;
+#   atom, descriptor 4921: q_n 80, q_nl 240, 4-body tensors and q4 130, network 3870 (scaling 60 and
+#     30 neurons x (30 FMAs forward, tanh, energy, gradient factor, 30 FMAs back)), 4-body adjoint 330,
+#     adjoint row 190, radial adjoint in basis space 80, site energy 1;
+#   active pair, force from the pair records 28: r^2, rsqrt, r (7), d = coef r + v (6), F_i (3),
+#     virial upper triangle (12); the list-walking force kernel: 23 plus 11 per list entry;
+#   radial pair, force 118: basis and derivative 102 + dot with the radial adjoint 15 + 1/r;
+#   LJ pair, force 18;
+#   angular pair, force 1178: unit vector 3 + basis and derivative 102 + 2 x 5 channel dots 150 +
+#     harmonics 81 + per (l, m) the sums A_lm, B_lm over the channels 480 + (A - l B / r) Y 96 + the
+#     l / r factors 12 + gradients of the harmonic polynomials 129 and their 58 non-zero FMAs 116 + 9;
+#   the half-list force (float16 rows): H = G^i + (-1)^l G^j adds 240 per angular pair and 8 per radial
+#     pair; its LJ term is the whole pair force (17).
+# The FP32 op counters of one fused launch (ffma, fadd, fmul, paired ops, MUFU) agree with this count to
+# within the conversions and padding named above (profiles/k_nep_fused_cu64x64x64.md).
 FLOPS = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=56, lj_pair=12, angular_pair=464, atom=4815),
-    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=149, lj_pair=13, angular_pair=1465, atom=3),
-    "force_full": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=141, lj_pair=14, angular_pair=1225,
-                       atom=3),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=440, atom=4921),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=1178, atom=0),
+    "force_full": dict(list_entry=11, active_pair=23, radial_pair=118, lj_pair=18, angular_pair=1178, atom=0),
+    "force": dict(list_entry=11, active_pair=23, radial_pair=126, lj_pair=17, angular_pair=1418, atom=0),
 }
-# The same static count for the student shape (4 radial + 4 angular channels, 8 basis functions,
-# l = 1, 2, no 4-body, 16 neurons), used for the student forms.
+# The same count for the student shape (4 + 4 channels, 8 basis functions, l = 1, 2, no 4-body term,
+# 16 neurons): register-resident sums, scalar channel dots (16 per channel), 8 harmonics (14),
+# network 888; its force runs over the half list.
 FLOPS_STUDENT = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=56, lj_pair=12, angular_pair=193, atom=1144),
-    "force": dict(list_entry=11, active_pair=2 + 27 + 3, radial_pair=149, lj_pair=13, angular_pair=570, atom=3),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=186, atom=1145),
+    "force": dict(list_entry=11, active_pair=23, radial_pair=126, lj_pair=17, angular_pair=511, atom=0),
 }
-# Algorithmic bytes per atom per force evaluation (HBM, float32 path): positions 16 (x2 kernels), list
-# entries 4 each (descriptor: full row, force: owned half), adjoint row 512 written + read, fixed-point
-# force 24 zeroed + accumulated, site energy 4.
-BYTES = dict(per_atom=16 * 2 + 512 * 2 + 24 * 2 + 4, per_list_entry=4 * 1.5)
+# Algorithmic HBM bytes per atom-step: the integrator reads and writes x, v (96) in the kick + drift and
+# v (48) in the second kick, and reads the forces in both kicks (48); the force kernel reads the atom's
+# position (16) and its walked neighbour-list entries (4 each), writes the site energy (4) and the
+# forces (24).  The neighbour build is amortised over the rebuild interval and not counted.
+BYTES = dict(per_atom=96 + 48 + 48 + 16 + 4 + 24, per_list_entry=4)
 
 
 def force_kind(form: str) -> str:
-    """FLOP table of the force kernel a form runs: the full-row form for the float32 teacher."""
-    return "force_full" if form == "plain" else "force"
+    """FLOP table of the force pass a form runs: the fused kernel's pass over its pair records for the
+    float32 teacher, the half list otherwise."""
+    return "force_rec" if form == "plain" else "force"
 
 
 def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) -> float:
@@ -269,8 +292,15 @@ def cpu_baseline(seconds_hint: float = 15.0) -> dict:
 
 
 # ---------------------------------------------------------------------------------------------------
+REFERENCE_BUDGET_S = 150.0
+
+
 def run_reference(args, rank: int, ws: int):
-    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only), on the GPU arm's
+    workload.  One oracle velocity-Verlet call over k steps does k + 1 force evaluations (the call
+    starts with the forces of the initial state); a warm-up call of 0 steps times that initial
+    evaluation alone, and it is subtracted, so the value counts k steps of one evaluation each.  k is
+    --steps, bounded so that the whole arm takes about REFERENCE_BUDGET_S seconds."""
     if rank != 0:
         return
     import oracle
@@ -278,33 +308,52 @@ def run_reference(args, rank: int, ws: int):
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     model = oracle.load_model(os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_nep4_synth.json"))
-    # size the per-step sample so that warmup + steps take about two minutes
-    probe = ni.fcc_cu_workload(6, 300.0, 0.05, seed=2)
+    wl = ni.workload(args.workload)
     t0 = time.perf_counter()
-    oracle.md_nve(model, probe.pos, probe.vel, probe.box, ni.M_CU, 1.0, 1)
-    t_atom_step = (time.perf_counter() - t0) / (2 * probe.n)
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    cells = int(max(4, min(16, round((budget / t_atom_step / 4) ** (1 / 3)))))
-    wl = ni.fcc_cu_workload(cells, 300.0, 0.05, seed=2)
-    x, v = wl.pos.copy(), wl.vel.copy()
-    for _ in range(args.warmup):
-        x, v, _ = oracle.md_nve(model, x, v, wl.box, ni.M_CU, 1.0, 1)
+    oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, wl.dt_fs, 0)
+    t_eval = time.perf_counter() - t0
+    k = int(max(1, min(args.steps, (REFERENCE_BUDGET_S - 2 * t_eval) // max(t_eval, 1e-6))))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        x, v, _ = oracle.md_nve(model, x, v, wl.box, ni.M_CU, 1.0, 1)
-    dt = time.perf_counter() - t0
-    value = wl.n * args.steps / dt
-    sample = (f"fcc Cu {cells}x{cells}x{cells} cells ({wl.n} atoms) per step, FP64 oracle velocity-Verlet "
-              f"(each step: 2 force evaluations with a fresh neighbour search, as the oracle stands)")
+    oracle.md_nve(model, wl.pos, wl.vel, wl.box, ni.M_CU, wl.dt_fs, k)
+    dt = max(time.perf_counter() - t0 - t_eval, 1e-9)
+    value = wl.n * k / dt
+    sample = (f"{args.workload} ({wl.n} atoms), {k} velocity-Verlet steps of the FP64 oracle in one call, one force "
+              f"evaluation per step (the call's initial evaluation, {t_eval:.1f} s, timed alone and subtracted)"
+              + ("" if k == args.steps else f"; {k} of the requested {args.steps} steps (time bound)"))
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": k,
+        "warmup": 1, "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample, "parallelism": "host cores (OpenMP)"},
+        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "sample": sample,
+                   "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def measure_fp32_peak(stream, local: int) -> dict:
+    """FP32 throughput of this GPU (nep_fp32_peak: FMA chains on every SM, packed float2 and scalar):
+    median over 60 launches of ~5 ms each, the FMAs per SM clock cycle counted in the kernel, and the
+    SM clock sampled while it runs.  The peak is the faster form's median."""
+    from paper_2604_24816_gb300 import fp32_peak
+    clocks = ClockSampler(local)
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    packed = fp32_peak(True, 5.0, 60, stream.cuda_stream)
+    scalar = fp32_peak(False, 5.0, 60, stream.cuda_stream)
+    t1 = time.perf_counter()
+    clocks.stop()
+    top = packed if packed["median_tflops"] >= scalar["median_tflops"] else scalar
+    sms = top["sm_count"]
+    return {"tflops": top["median_tflops"], "form": "packed float2" if top is packed else "scalar",
+            "packed_tflops": packed["median_tflops"], "scalar_tflops": scalar["median_tflops"],
+            "packed_best_tflops": packed["best_tflops"],
+            "fma_per_clock_sm": {"packed": round(packed["fma_per_clock_sm"], 2),
+                                 "scalar": round(scalar["fma_per_clock_sm"], 2)},
+            "implied_sm_mhz": (round(top["median_tflops"] * 1e6 / (2 * sms * top["fma_per_clock_sm"]), 1)
+                               if top["fma_per_clock_sm"] > 0 else None),
+            "sm_count": sms, "clocks": clocks.summary(t0, t1)}
 
 
 # form name -> library precision, model (teacher or distilled student), per-atom fallback to the
@@ -326,13 +375,6 @@ FORMS = {
 }
 FALLBACK_MARGIN = 0.05
 STUDENT_PATH = os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_student_trained.json")
-
-
-def row_bytes(form: str) -> int:
-    """Bytes of one adjoint row G of the form's model (teacher 128 / student 40 values; float32 in the
-    plain forms, float16 in the mixed ones)."""
-    f = FORMS[form]
-    return (40 if f["model"] == "student" else 128) * (4 if f["precision"] == "fp32" else 2)
 
 
 def load_student() -> dict:
@@ -378,6 +420,84 @@ def time_form(form, teacher, student, wl, args, stream, dev, ws, atoms_total):
     return rec
 
 
+# Workloads of the "configs" block: (name, workload, forms, timed steps, neighbour-list capacity).
+CONFIGS = (
+    ("cu_160x160x160", "cu_160x160x160", ("plain", "mix_bf16", "mix_fp16"), 20, 0),
+    ("cu_160x160x160_1200K", "cu_160x160x160_1200K", ("plain", "mix_bf16", "mix_fp16"), 20, 0),
+    ("cu_320_void", "cu_320_void", ("plain", "student_bf16_fallback"), 10, 96),
+)
+
+
+def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, idx, stream, dev, local, ws):
+    """One form on one workload: forces of the start state on the sampled atoms, then `warmup` and
+    `steps` CUDA-graph MD steps, the latter timed with events on the library's stream while the SM
+    clock is sampled."""
+    import torch
+    from paper_2604_24816_gb300 import NEP
+    f = FORMS[form]
+    with NEP(student if f["model"] == "student" else teacher, stream=stream.cuda_stream, rebuild_every=10,
+             precision=f["precision"], max_neighbors=max_neighbors) as h:
+        if f["fallback"]:
+            h.set_fallback(teacher, student["q_lo"], student["q_hi"], margin=FALLBACK_MARGIN)
+        h.set_state(wl.pos, wl.vel, wl.box)
+        Fd = torch.empty((wl.n, 3), dtype=torch.float64, device=dev)
+        h.compute(out=Fd)
+        F = Fd[torch.from_numpy(idx).to(dev)].cpu().numpy()
+        del Fd
+        h.step(wl.dt_fs, warmup)
+        c0 = h.counters()
+        clocks = ClockSampler(local)
+        time.sleep(0.2)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        dist_barrier(ws)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s.record(stream)
+        h.step(wl.dt_fs, steps)
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        clocks.stop()
+        ms = dist_max(s.elapsed_time(e), ws, dev)
+        th = h.thermo()
+        c1 = h.counters()
+    rec = {"value": dist_sum(wl.n, ws, dev) * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
+           "dtype": f["dtype"], "clocks": clocks.summary(t0, t1), "pe_per_atom_end": th["pe"] / wl.n,
+           "rebuilds": c1["rebuilds"] - c0["rebuilds"] if "rebuilds" in c1 else None, "_F": F}
+    if f["fallback"]:
+        ev = max(1, c1["evaluations"] - c0["evaluations"])
+        rec["fallback_fraction"] = (c1["fallback_atoms"] - c0["fallback_atoms"]) / (ev * wl.n)
+    return rec
+
+
+def run_configs(teacher, student, args, stream, dev, local, ws) -> dict:
+    """The larger workloads: every form of CONFIGS on its workload, throughput and force RMSE / max
+    against the plain float32 forces on 8,192 sampled atoms of the start state."""
+    import gc
+    out = {}
+    for name, wname, forms, steps, cap in CONFIGS:
+        t_gen = time.perf_counter()
+        wl = ni.workload(wname)
+        t_gen = time.perf_counter() - t_gen
+        idx = ni.sample_indices(wl.n, 8192, seed=11)
+        recs = {}
+        for form in forms:
+            recs[form] = time_config_form(form, teacher, student, wl, steps, 3, cap, idx, stream, dev, local, ws)
+        Fp = recs["plain"]["_F"]
+        for form, rec in recs.items():
+            d = rec.pop("_F") - Fp
+            if form != "plain":
+                rec["force_rmse_vs_plain"] = float(np.sqrt(np.mean(d ** 2)))
+                rec["force_max_vs_plain"] = float(np.abs(d).max())
+                rec["speedup_vs_plain"] = round(rec["value"] / recs["plain"]["value"], 4)
+        out[name] = {"atoms": wl.n, "temperature_K": wl.temperature, "input_generation_s": round(t_gen, 1),
+                     "forms": recs}
+        del wl
+        gc.collect()
+    return out
+
+
 def run_ours(args, rank: int, ws: int, local: int):
     import torch
     from paper_2604_24816_gb300 import load_model, build
@@ -389,6 +509,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     student = load_student()
     wl = ni.workload(args.workload)       # every rank runs an independent replica of the same workload
     stream = torch.cuda.Stream(device=dev)
+    peak = measure_fp32_peak(stream, local)
     nep = make_nep(args.form, model, student, stream, args)
     nep.set_state(wl.pos, wl.vel, wl.box)
     nep.compute(forces=False)
@@ -417,7 +538,6 @@ def run_ours(args, rank: int, ws: int, local: int):
     torch.cuda.synchronize(dev)
     t_host1 = time.perf_counter()
     dist_barrier(ws)
-    clocks.stop()
     ms = start.elapsed_time(end)
     ms_max = dist_max(ms, ws, dev)
     atoms_total = dist_sum(wl.n, ws, dev)
@@ -427,8 +547,11 @@ def run_ours(args, rank: int, ws: int, local: int):
     th = nep.thermo()
     dg = {k: c1[k] - c0[k] for k in c1}          # the timed (graph) region
     nep.set_timing(True)
+    t_host2 = time.perf_counter()
     nep.step(wl.dt_fs, args.steps)
     torch.cuda.synchronize(dev)
+    t_host3 = time.perf_counter()
+    clocks.stop()
     tim = nep.timing()
     c2 = nep.counters()
     dc = {k: c2[k] - c1[k] for k in c2}          # the eager pass with per-kernel events
@@ -436,9 +559,8 @@ def run_ours(args, rank: int, ws: int, local: int):
     table = FLOPS_STUDENT if FORMS[args.form]["model"] == "student" else FLOPS
     f_desc = kernel_flops("descriptor", dc, evals * wl.n, table)
     f_force = kernel_flops(force_kind(args.form), dc, evals * wl.n, table)
-    peaks = load_peaks()
     clk = clocks.summary(t_host0, t_host1)
-    peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    clk_kernels = clocks.summary(t_host2, t_host3)
     kern = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in tim.items()}
     fused = tim["descriptor"][1] == 0 and tim["force"][1] > 0      # one kernel does descriptors and forces
     dominant = "force" if fused else max(("descriptor", "force"), key=lambda k: tim[k][0])
@@ -449,47 +571,57 @@ def run_ours(args, rank: int, ws: int, local: int):
     traffic = profiled_traffic("fused" if fused else (dominant if args.form == "plain" else f"{dominant}:{args.form}"))
     dom_name = ("k_nep_fused" if fused else
                 "k_descriptor_mixed" if dominant == "descriptor" and args.form != "plain" else f"k_{dominant}")
+    pk_mhz, kn_mhz = peak["clocks"].get("sm_mhz"), clk_kernels.get("sm_mhz")
     roofline = {
         "bound": "alu",
-        "kernel": dom_name, "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
-        "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+        "kernel": dom_name, "achieved": round(achieved, 3), "peak": round(peak["tflops"], 2),
+        "unit": "TFLOP/s", "frac": round(achieved / peak["tflops"], 4),
         "traffic": (round(traffic["bytes"] * wl.n / traffic["atoms"]) if traffic else None),
-        "peak_source": f"FP32 FFMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x "
-                       f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peaks['source']} max SM clock)",
+        "peak_source": (f"measured in this run: nep_fp32_peak FP32 FMA microbenchmark on the {peak['sm_count']} SMs "
+                        f"read from the device, median of 60 launches of ~5 ms ({peak['form']}: packed float2 "
+                        f"{peak['packed_tflops']:.2f}, scalar {peak['scalar_tflops']:.2f} TFLOP/s; "
+                        f"{peak['fma_per_clock_sm']['packed']} / {peak['fma_per_clock_sm']['scalar']} FMA per SM "
+                        f"cycle counted in the kernel, i.e. an SM clock of {peak['implied_sm_mhz']} MHz; "
+                        f"nvidia-smi median {pk_mhz} MHz while it ran)"),
+        "peak_sm_mhz": pk_mhz, "kernel_sm_mhz": kn_mhz,
+        "frac_same_clock": (round(achieved / (peak["tflops"] * kn_mhz / pk_mhz), 4) if pk_mhz and kn_mhz else None),
         "flops_per_launch": round(dom_flops / dom_launches),
         "ms_per_launch": round(dom_ms / dom_launches, 5),
-        "frac_at_measured_clock": (round(achieved / (N_SMS * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e-6), 4)
-                                   if clk.get("sm_mhz") else None),
     }
     both_ms = tim["descriptor"][0] + tim["force"][0]
     both = (f_desc + f_force) / (both_ms * 1e-3) / 1e12 if both_ms > 0 else 0.0
 
-    # end-to-end through the public API with pinned host buffers: every step uploads (x, v), runs one
-    # MD step (which must rebuild and recompute forces for the uploaded state) and downloads (x, v, E)
+    # end to end through the public API with pinned host buffers: every step uploads the state read
+    # back by the previous step, runs one MD step and reads the state and the thermodynamics back.  An
+    # upload that leaves every atom's float32 position unchanged keeps the forces, so each step does
+    # one force evaluation, as a step on resident data does.
     e2e = None
     if not args.no_e2e:
-        xh = torch.from_numpy(wl.pos).pin_memory()
-        vh = torch.from_numpy(wl.vel).pin_memory()
-        xo = torch.empty_like(xh).pin_memory()
-        vo = torch.empty_like(vh).pin_memory()
+        xo = torch.from_numpy(wl.pos.copy()).pin_memory()
+        vo = torch.from_numpy(wl.vel.copy()).pin_memory()
         nep.set_timing(False)
+        nep.set_state(xo, vo, wl.box)
         for _ in range(2):
-            nep.set_state(xh, vh, wl.box); nep.step(wl.dt_fs, 1); nep.get_state(xo, vo); nep.thermo()
+            nep.step(wl.dt_fs, 1); nep.get_state(xo, vo); nep.thermo(); nep.set_state(xo, vo, wl.box)
         dist_barrier(ws)
         torch.cuda.synchronize(dev)
+        c_e0 = nep.counters()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            nep.set_state(xh, vh, wl.box)
+            nep.set_state(xo, vo, wl.box)
             nep.step(wl.dt_fs, 1)
             nep.get_state(xo, vo)
             nep.thermo()
         torch.cuda.synchronize(dev)
         te = dist_max(time.perf_counter() - t0, ws, dev)
+        c_e1 = nep.counters()
         dist_barrier(ws)
         e2e = {"value": atoms_total * args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": 48 * wl.n,
                "d2h_bytes_per_step": 48 * wl.n + 8 * 16, "steps": args.e2e_steps,
-               "note": "per step: nep_set_state(x, v from pinned host) + md_verlet_step(1) (rebuild + 2 force "
-                       "evaluations for the uploaded state) + nep_get_state(x, v to pinned host) + thermo"}
+               "force_evaluations_per_step": (c_e1["evaluations"] - c_e0["evaluations"]) / args.e2e_steps,
+               "note": "per step: nep_set_state(x, v read back by the previous step, pinned host) + md_verlet_step(1) "
+                       "+ nep_get_state(x, v to pinned host) + thermo; the upload leaves the float32 positions "
+                       "unchanged, so the library keeps the forces and the step evaluates them once"}
     ablations = None
     if args.form == "plain" and not args.no_ablations:
         # kernel variants of the paper's design on the same state, against the production kernels
@@ -501,15 +633,16 @@ def run_ours(args, rank: int, ws: int, local: int):
         ablations = {"fused_ms": round(t_ref["force"][0] + t_ref["descriptor"][0], 4)}
         for v in ("separate_descriptor", "separate_force", "float_scatter", "half_list", "tile1", "tile3"):
             ablations[v + "_ms"] = round(min(nep.run_variant(v)[0] for _ in range(3)), 4)
-        ablations["note"] = ("fused: the production kernel (descriptors, network and full-row forces in one launch, "
-                             "adjoint rows in tensor memory); separate_descriptor + separate_force: the same work "
-                             "as two launches with the adjoint rows through device memory; float_scatter: the "
-                             "separate full-row force kernel with float atomicAdd (order-dependent sums) instead "
-                             "of fixed-point integer atomics; half_list: force kernel over each unordered pair "
-                             "once, gathering the neighbour's adjoint row, instead of every ordered pair with the "
-                             "own row; tile1/tile3: descriptor kernel with 1 or 3 angular channels per neighbour "
-                             "pass and s_nlm through global memory instead of all 5 channels in tensor memory; "
-                             "single launches, CUDA events")
+        ablations["note"] = ("fused: the production kernel (descriptors, network and forces in one launch, adjoint "
+                             "rows in tensor memory, the force pass over the descriptor walk's pair records); "
+                             "separate_descriptor + separate_force: descriptors and full-row forces as two launches "
+                             "with the adjoint rows through device memory and the force kernel walking the "
+                             "neighbour list; float_scatter: the separate force kernel with float atomicAdd "
+                             "(order-dependent sums) instead of fixed-point integer atomics; half_list: force "
+                             "kernel over each unordered pair once, gathering the neighbour's adjoint row; "
+                             "tile1/tile3: descriptor kernel with 1 or 3 angular channels per neighbour pass and "
+                             "s_nlm through global memory instead of all 5 channels in tensor memory; single "
+                             "launches, CUDA events")
     F_plain = F_this = None
     others = [] if args.no_forms else [f for f in FORMS if f != args.form]
     if others:
@@ -534,40 +667,47 @@ def run_ours(args, rank: int, ws: int, local: int):
         if args.form != "plain":
             d = F_this[idx] - F_plain[idx]
             forms["this_form_vs_plain"] = {"force_rmse": float(np.sqrt(np.mean(d ** 2))), "force_max": float(np.abs(d).max())}
+    wl_dt, wl_temp = wl.dt_fs, wl.temperature
+    del wl
+    configs = None if args.no_configs else run_configs(model, student, args, stream, dev, local, ws)
 
     if rank != 0:
         return
+    n_rep = int(atoms_total // ws)
+    walked = dc["list_entries"] / max(1, evals * n_rep)         # walked list entries per atom-evaluation
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": FORMS[args.form]["dtype"], "data": "synthetic",
-        "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "form": FORMS[args.form]["desc"],
-                   "dt_fs": wl.dt_fs, "temperature_K": wl.temperature,
+        "config": {"workload": args.workload, "atoms_per_gpu": n_rep, "form": FORMS[args.form]["desc"],
+                   "dt_fs": wl_dt, "temperature_K": wl_temp,
                    "neighbor_rebuild": f"every {args.rebuild_every} steps + displacement check (skin/2)",
                    "rebuilds_in_timed_region": dg["rebuilds"],
                    "timing": "timed region: CUDA-graph replay of the MD step (CUDA events on the library's "
                              "stream); kernels and roofline: an eager pass of the same length with per-kernel-class "
                              "CUDA events",
-                   **({"fallback_fraction": dg["fallback_atoms"] / max(1, dg["evaluations"] * wl.n),
+                   **({"fallback_fraction": dg["fallback_atoms"] / max(1, dg["evaluations"] * n_rep),
                        "fallback_margin": FALLBACK_MARGIN} if FORMS[args.form]["fallback"] else {}),
-                   "l2": "inputs larger than L2: per-step algorithmic traffic ~"
-                         f"{(wl.n * (row_bytes(args.form) * 2 + BYTES['per_atom'] - 512 * 2 + 48 * 2) + dc['list_entries'] / max(1, evals) * BYTES['per_list_entry']) / 1e9:.2f} GB"
-                         " (neighbour list, adjoint rows, state) vs 129 MB L2",
+                   "l2": "inputs larger than L2: per-step algorithmic HBM traffic ~"
+                         f"{n_rep * (BYTES['per_atom'] + BYTES['per_list_entry'] * walked) / 1e9:.2f} GB"
+                         " (state, forces, positions, walked neighbour-list entries) vs 129 MB L2",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "model": "cu_nep4_synth (seeded)"},
         "roofline": roofline,
         "clocks": clk,
+        "clocks_kernel_pass": clk_kernels,
         "gpu_launches": dg["launches"],
         "kernels": kern,
         "descriptor_plus_force_tflops": round(both, 3),
-        "pairs_per_atom": {"list": dc["list_entries"] / max(1, evals * wl.n),
-                           "radial": dc["radial_pairs"] / max(1, evals * wl.n),
-                           "angular": dc["angular_pairs"] / max(1, evals * wl.n),
-                           "force_kernel_angular": dc["force_angular_pairs"] / max(1, evals * wl.n)},
-        "thermo_end": {"pe_per_atom": th["pe"] / wl.n, "temperature": th["temperature"],
-                       "energy_change_per_atom": ((th["pe"] + th["ke"]) - (th0["pe"] + th0["ke"])) / wl.n,
-                       "over_fs": args.steps * wl.dt_fs},
+        "pairs_per_atom": {"list": walked, "radial": dc["radial_pairs"] / max(1, evals * n_rep),
+                           "angular": dc["angular_pairs"] / max(1, evals * n_rep),
+                           "force_kernel_angular": dc["force_angular_pairs"] / max(1, evals * n_rep)},
+        "thermo_end": {"pe_per_atom": th["pe"] / n_rep, "temperature": th["temperature"],
+                       "energy_change_per_atom": ((th["pe"] + th["ke"]) - (th0["pe"] + th0["ke"])) / n_rep,
+                       "over_fs": args.steps * wl_dt},
+        "fp32_peak": {k: v for k, v in peak.items()},
         "e2e": e2e,
         "forms": forms or None,
+        "configs": configs,
         "ablations": ablations,
         "source_hash": source_hash(),
     }
@@ -592,6 +732,7 @@ def main(argv=None):
     ap.add_argument("--max-neighbors", type=int, default=0, help="neighbour-list capacity per atom (0 = 128)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-ablations", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 16.4M- and 131M-atom workloads")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -253,10 +253,12 @@ nep_status nep_selftest_bounded_wait(int64_t polls, int *timed_out);
  * launch_ms (0 < launch_ms <= 1000) and timed with CUDA events on cuda_stream (NULL = legacy default
  * stream); after a calibration, `reps` launches (1..10000) are timed.  Outputs (host, may be NULL):
  * *best_tflops and *median_tflops = FLOP/s over the timed launches (FMA = 2 FLOP), in 10^12;
- * *sm_count = multiprocessor count read from the device.  Synchronous; allocates and frees a small
- * output buffer; NEP_ERR_ARG for bad sizes, NEP_ERR_CUDA / NEP_ERR_OOM on runtime failures. */
+ * *fma_per_clock_sm = FMAs per SM clock cycle of the last launch (from clock64 in every block), which
+ * does not depend on the clock frequency; *sm_count = multiprocessor count read from the device.
+ * Synchronous; allocates and frees small buffers; NEP_ERR_ARG for bad sizes, NEP_ERR_CUDA / NEP_ERR_OOM
+ * on runtime failures. */
 nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void *cuda_stream, double *best_tflops,
-                         double *median_tflops, int *sm_count);
+                         double *median_tflops, double *fma_per_clock_sm, int *sm_count);
 
 /* Name of a status code (never NULL). */
 const char *nep_status_string(nep_status s);

@@ -553,10 +553,16 @@ nep_status upload_state(nep_handle *h, const double *x, const double *v) {
   return NEP_OK;
 }
 
-// Upload into the current cell-sorted order (the list is kept; see k_load_state_sorted).
+// Upload into the current cell-sorted order (the list is kept; see k_load_state_sorted).  When no
+// atom's float32 cell-relative position changed (for instance, the state just read back with
+// nep_get_state is uploaded again, velocities possibly altered) the forces, energy and virial of the
+// last evaluation still hold: they are kept, and only the kinetic energy is summed again.
 nep_status upload_state_sorted(nep_handle *h, const double *x, const double *v) {
   const size_t N = (size_t)h->n;
+  const bool had_forces = h->have_forces, had_recheck = h->recheck;
+  h->have_forces = false;
   NEP_CUDA(h, cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int), h->stream));
+  NEP_CUDA(h, cudaMemsetAsync(&h->ctrl->changed, 0, sizeof(int), h->stream));
   const double *xs = x, *vs = v;
   if (!is_device_ptr(x)) {
     NEP_CUDA(h, cudaMemcpyAsync(h->io, x, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -573,7 +579,22 @@ nep_status upload_state_sorted(nep_handle *h, const double *x, const double *v) 
                                          h->pos_ref, h->l, h->L, hs * hs, h->ctrl, h->stream));
   }
   h->recheck = true;
-  return check_device_status(h);
+  nep_status s = check_device_status(h);
+  if (s != NEP_OK || h->h_ctrl->changed || !had_forces) return s;
+  // positions unchanged: keep the list state and the forces; refresh the kinetic energy sum (the
+  // evaluation counters are not touched: no force evaluation ran)
+  h->recheck = had_recheck;
+  h->have_forces = true;
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_kinetic(h->n, h->vx, h->vy, h->vz, h->mass, h->part_k, h->stream));
+  }
+  {
+    Scope sc(h, KC_RED, 1);
+    NEP_CUDA(h, launch_finalize(h->part_d, h->nb_d, h->part_f, h->nb_f, h->part_k, h->nb_k, h->sums, nullptr,
+                                h->stream));
+  }
+  return NEP_OK;
 }
 
 // Fallback buffers for the current system: flagged-atom list, its length, teacher adjoint rows.
@@ -747,7 +768,6 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   if (same && h->have_nlist) {
     // Same size and box with a neighbour list: keep the list and the cell order; the next
     // evaluation rebuilds only if an atom moved more than skin/2 from where the list was built.
-    h->have_forces = false;
     return upload_state_sorted(h, x, v);
   }
   if (same) {

@@ -54,6 +54,7 @@ struct Control {
   float dmax2;          // largest squared displacement of an atom since the last rebuild (Angstrom^2)
   float far_dmax2;      // below this, no list entry of the far band can be inside the largest cutoff
   int skip_far;         // decision for the current evaluation: row walks may skip the far band
+  int changed;          // an upload into the kept cell order changed some atom's float32 position
 };
 
 // Arguments of the rebuild chain (cell sort + neighbour list).
@@ -405,6 +406,29 @@ __device__ __forceinline__ long long to_fix32(float v) {
   if (sh >= 0) r = man << min(sh, 39);
   else r = (man + (1ll << (-sh - 1))) >> (-sh);
   return (b >> 31) ? -r : r;
+}
+
+// to_fix32 of three values with one range test and the float parts of x and y in float2 pairs (the
+// same results as three to_fix32 calls).
+__device__ __forceinline__ void to_fix32x3(float x, float y, float z, long long &a, long long &b, long long &cz) {
+  constexpr float SHIFT = 12582912.0f;
+  const float m = fmaxf(fmaxf(fabsf(x), fabsf(y)), fabsf(z));
+  if (m < 4096.f) {
+    const float2 xy = make_float2(x, y);
+    const float2 hm = __ffma2_rn(xy, make_float2(1024.f, 1024.f), make_float2(SHIFT, SHIFT));
+    const float hmz = fmaf(z, 1024.f, SHIFT);
+    const float2 h = __fadd2_rn(hm, make_float2(-SHIFT, -SHIFT));
+    const float hz = hmz - SHIFT;
+    const float2 l = __ffma2_rn(xy, make_float2(4294967296.f, 4294967296.f), __fmul2_rn(h, make_float2(-4194304.f, -4194304.f)));
+    const float lz = fmaf(z, 4294967296.f, hz * -4194304.f);
+    const float2 lm = __fadd2_rn(l, make_float2(SHIFT, SHIFT));
+    const float lmz = lz + SHIFT;
+    a = ((long long)(__float_as_int(hm.x) - 0x4B400000) << 22) + (__float_as_int(lm.x) - 0x4B400000);
+    b = ((long long)(__float_as_int(hm.y) - 0x4B400000) << 22) + (__float_as_int(lm.y) - 0x4B400000);
+    cz = ((long long)(__float_as_int(hmz) - 0x4B400000) << 22) + (__float_as_int(lmz) - 0x4B400000);
+  } else {
+    a = to_fix32(x); b = to_fix32(y); cz = to_fix32(z);
+  }
 }
 
 // Block-wide sum of NV int64 values into out[blockIdx.x * NV + v].  Integer addition is associative,

@@ -384,9 +384,12 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
   const int trip = __reduce_max_sync(0xffffffffu, cnt);
   for (int k = 0; k < trip; ++k) {
     const bool valid = k < cnt;
-    uint32_t e = 0u;
-    float4 pj = pi;
-    if (valid) pipe.get(k, e, pj);
+    uint32_t e;
+    float4 pj;
+    // past the end of the row the ring slots are stale: act below is false for them, and e = 0 keeps
+    // the shift-table index in range
+    pipe.get(k, e, pj);
+    e = valid ? e : 0u;
     const float4 o = shift[e >> J_BITS];
     const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
     const float r2 = dx * dx + dy * dy + dz * dz;

@@ -464,11 +464,12 @@ struct RecPipe {
 
 // Radial and LJ part of one active pair's force coefficient (d = coef * r_ij + angular part): the
 // radial adjoint in basis space (8 values in shared memory at fps[0], fps[FORCE_BLOCK]) against the
-// basis derivatives, plus half of the shifted-force LJ pair force.
-template <class S>
+// basis derivatives, plus half of the shifted-force LJ pair force.  INSIDE_RC: the caller knows that
+// r < rc_R (an angular pair: rc_A <= rc_R is checked by nep_create).
+template <class S, bool INSIDE_RC = false>
 __device__ __forceinline__ float radial_lj_coef(const Model<S> &P, const float4 *fps, float r2, float r, float ir) {
   float coef = 0.f;
-  if (r2 < P.rcR2) {
+  if (INSIDE_RC || r2 < P.rcR2) {
     float f[S::KR], df[S::KR];
     cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
     float fpi[8];
@@ -502,9 +503,11 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
   auto apply = [&](float dx, float dy, float dz, int j, float coef, float vx, float vy, float vz) {
     const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
     fx += Dx; fy += Dy; fz += Dz;
-    atomicAdd(Ffix + j, (unsigned long long)to_fix32(-Dx));
-    atomicAdd(Ffix + (size_t)n + j, (unsigned long long)to_fix32(-Dy));
-    atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)to_fix32(-Dz));
+    long long ox, oy, oz;
+    to_fix32x3(-Dx, -Dy, -Dz, ox, oy, oz);
+    atomicAdd(Ffix + j, (unsigned long long)ox);
+    atomicAdd(Ffix + (size_t)n + j, (unsigned long long)oy);
+    atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)oz);
     wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
     wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz); wzz = fmaf(dz, Dz, wzz);
   };
@@ -520,7 +523,7 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
       const float r2 = q.x * q.x + q.y * q.y + q.z * q.z;
       const float ir = rsqrtf(r2);
       const float r = r2 * ir;
-      float coef = valid ? radial_lj_coef<S>(P, fps, r2, r, ir) : 0.f;
+      float coef = valid ? radial_lj_coef<S, true>(P, fps, r2, r, ir) : 0.f;
       __syncwarp();
       float2 al, gv[3];
       angular_pair<S, float, true>(P, trow, gi, static_cast<const float *>(nullptr), !valid, r, ir, q.x, q.y, q.z, al,

@@ -197,7 +197,7 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
                                     const float4 *__restrict__ pos_ref, double lx, double ly, double lz, double Lx,
                                     double Ly, double Lz, float half_skin2, Control *ctrl) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  bool moved = false;
+  bool moved = false, changed = false;
   float dd = 0.f;
   if (s < n) {
     const size_t o = 3 * (size_t)id[s];
@@ -221,6 +221,9 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
     const float4 q = make_float4((float)fma(-(double)cx, lx, a), (float)fma(-(double)cy, ly, b),
                                  (float)fma(-(double)cz, lz, c), p.w);
     pos[s] = q;
+    // the forces depend on the positions only through these float32 coordinates
+    changed = __float_as_uint(q.x) != __float_as_uint(p.x) || __float_as_uint(q.y) != __float_as_uint(p.y) ||
+              __float_as_uint(q.z) != __float_as_uint(p.z);
     const float4 r = pos_ref[s];
     const float ddx = q.x - r.x, ddy = q.y - r.y, ddz = q.z - r.z;
     const float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
@@ -228,6 +231,7 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
     dd = moved ? 1.0e30f : d2;
   }
   note_displacement(moved, dd, ctrl);
+  if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->changed, 1);
 }
 
 // Sorted SoA -> original-order [n][3] float64 (positions wrapped into the box when L != nullptr).

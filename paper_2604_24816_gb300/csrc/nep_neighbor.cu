@@ -164,8 +164,10 @@ __global__ void k_permute(int n, const int *__restrict__ perm, const double *__r
     idb[t] = id[s];
     const int c = cell_of[s];
     const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
-    const float4 p = make_float4((float)(px - cx * lx), (float)(py - cy * ly), (float)(pz - cz * lz),
-                                 __int_as_float(cx | (cy << 10) | (cz << 20)));
+    // the same expression as the drift and upload kernels (nep_md.cu), so that a position uploaded
+    // unchanged gives bitwise the same cell-relative coordinates
+    const float4 p = make_float4((float)fma(-(double)cx, lx, px), (float)fma(-(double)cy, ly, py),
+                                 (float)fma(-(double)cz, lz, pz), __int_as_float(cx | (cy << 10) | (cz << 20)));
     pos[t] = p;
     pos_ref[t] = p;
   }

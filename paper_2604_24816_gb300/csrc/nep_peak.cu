@@ -7,7 +7,10 @@
 // blocks as fit, so the FMA pipes, not the issue slots or the occupancy, are the limit.  Arithmetic
 // performed = threads * iters * CHAINS * 2 FLOP (FMA = 2).  a and b are kernel arguments (no constant
 // folding), the chain converges to b / (1 - a) = 1 (no overflow, no denormals), and every thread stores
-// its sum (no dead-code elimination).
+// its sum (no dead-code elimination).  Thread 0 of each block also records its SM index and the SM's
+// cycle counter (clock64) at the block's start and end; per SM, the span from its first block's start
+// to its last block's end gives the rate per SM clock (FMA per cycle per SM), which does not depend on
+// the clock frequency.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,8 +25,11 @@ constexpr int PEAK_CHAINS = 16;   // independent accumulators per thread (float2
 constexpr int PEAK_UNROLL = 8;    // rounds per loop iteration (iters is a multiple of it)
 
 template <bool PACKED>
-__global__ void __launch_bounds__(PEAK_BLOCK) k_fp32_peak(float a, float b, long long rounds, float *out) {
+__global__ void __launch_bounds__(PEAK_BLOCK) k_fp32_peak(float a, float b, long long rounds, float *out,
+                                                          long long *cycles) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  __syncthreads();
+  const long long c0 = clock64();
   float s = 0.f;
   if constexpr (PACKED) {
     float2 acc[PEAK_CHAINS / 2];
@@ -52,12 +58,20 @@ __global__ void __launch_bounds__(PEAK_BLOCK) k_fp32_peak(float a, float b, long
     for (int c = 0; c < PEAK_CHAINS; ++c) s += acc[c];
   }
   out[t] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    cycles[3 * blockIdx.x] = c0;
+    cycles[3 * blockIdx.x + 1] = clock64();
+    cycles[3 * blockIdx.x + 2] = sm;
+  }
 }
 
 }  // namespace
 
 extern "C" nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void *cuda_stream, double *best_tflops,
-                                    double *median_tflops, int *sm_count) {
+                                    double *median_tflops, double *fma_per_clock_sm, int *sm_count) {
   if (reps < 1 || reps > 10000 || !(launch_ms > 0.0 && launch_ms <= 1000.0)) return NEP_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   int dev = 0, sms = 0, per_sm = 0;
@@ -69,15 +83,22 @@ extern "C" nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void
   const int grid = sms * per_sm;
   const long long threads = (long long)grid * PEAK_BLOCK;
   float *out = nullptr;
+  long long *cyc = nullptr;
   if (cudaMalloc(&out, sizeof(float) * (size_t)threads) != cudaSuccess) return NEP_ERR_OOM;
+  if (cudaMalloc(&cyc, 3 * sizeof(long long) * (size_t)grid) != cudaSuccess) {
+    cudaFree(out);
+    return NEP_ERR_OOM;
+  }
+  std::vector<long long> hcyc(3 * (size_t)grid);
+  double fpc = 0.0;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   nep_status status = NEP_OK;
   std::vector<double> rate;
   auto launch = [&](long long rounds) {
     if (packed)
-      k_fp32_peak<true><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out);
+      k_fp32_peak<true><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out, cyc);
     else
-      k_fp32_peak<false><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out);
+      k_fp32_peak<false><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out, cyc);
   };
   auto timed = [&](long long rounds, float *ms) -> bool {
     if (cudaEventRecord(t0, st) != cudaSuccess) return false;
@@ -103,14 +124,41 @@ extern "C" nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void
       if (!timed(rounds, &ms)) { status = NEP_ERR_CUDA; break; }
       rate.push_back(flop / (ms * 1e-3) / 1e12);
     }
+    if (status != NEP_OK) break;
+    // FMA per SM cycle of the last launch: per SM, its blocks' FMAs over the span from the earliest
+    // block start to the latest block end (one SM's counter); averaged over the SMs
+    if (cudaMemcpy(hcyc.data(), cyc, 3 * sizeof(long long) * (size_t)grid, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      status = NEP_ERR_CUDA;
+      break;
+    }
+    std::vector<long long> first, last, nblk;
+    for (int b = 0; b < grid; ++b) {
+      const size_t sm = (size_t)hcyc[3 * (size_t)b + 2];
+      if (sm >= 4096) continue;
+      if (sm >= first.size()) { first.resize(sm + 1, -1); last.resize(sm + 1, -1); nblk.resize(sm + 1, 0); }
+      const long long c0 = hcyc[3 * (size_t)b], c1 = hcyc[3 * (size_t)b + 1];
+      first[sm] = first[sm] < 0 ? c0 : std::min(first[sm], c0);
+      last[sm] = std::max(last[sm], c1);
+      nblk[sm] += 1;
+    }
+    double sum = 0.0;
+    int used = 0;
+    for (size_t sm = 0; sm < first.size(); ++sm) {
+      if (nblk[sm] == 0 || last[sm] <= first[sm]) continue;
+      sum += (double)nblk[sm] * PEAK_BLOCK * (double)rounds * PEAK_UNROLL * PEAK_CHAINS / (double)(last[sm] - first[sm]);
+      ++used;
+    }
+    fpc = used > 0 ? sum / used : 0.0;
   } while (false);
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   cudaFree(out);
+  cudaFree(cyc);
   if (status != NEP_OK) return status;
   std::sort(rate.begin(), rate.end());
   if (best_tflops) *best_tflops = rate.back();
   if (median_tflops) *median_tflops = rate[rate.size() / 2];
+  if (fma_per_clock_sm) *fma_per_clock_sm = fpc;
   if (sm_count) *sm_count = sms;
   return NEP_OK;
 }

@@ -90,7 +90,7 @@ def lib():
         L.nep_get_fallback.argtypes = [vp, vp, C.POINTER(C.c_int64)]
         L.nep_run_variant.argtypes = [vp, C.c_int, d, vp]
         L.nep_selftest_bounded_wait.argtypes = [i64, C.POINTER(C.c_int)]
-        L.nep_fp32_peak.argtypes = [C.c_int, C.c_double, C.c_int, vp, d, d, C.POINTER(C.c_int)]
+        L.nep_fp32_peak.argtypes = [C.c_int, C.c_double, C.c_int, vp, d, d, d, C.POINTER(C.c_int)]
         for f in EXPORTED:
             if f not in ("nep_last_error", "nep_status_string"):
                 getattr(L, f).restype = C.c_int
@@ -294,11 +294,13 @@ class NEP:
 
 def fp32_peak(packed: bool = True, launch_ms: float = 5.0, reps: int = 20, stream=None) -> dict:
     """FP32 throughput of the current device (nep_fp32_peak): FMA chains on every SM, scalar or packed
-    float2.  Returns best and median TFLOP/s over `reps` launches and the SM count read from the device."""
+    float2.  Returns best and median TFLOP/s over `reps` launches, FMAs per SM clock cycle and the SM
+    count read from the device."""
     L = lib()
-    best, med, sms = C.c_double(0), C.c_double(0), C.c_int(0)
+    best, med, fpc, sms = C.c_double(0), C.c_double(0), C.c_double(0), C.c_int(0)
     st = L.nep_fp32_peak(int(bool(packed)), float(launch_ms), int(reps), C.c_void_p(stream) if stream else None,
-                         C.byref(best), C.byref(med), C.byref(sms))
+                         C.byref(best), C.byref(med), C.byref(fpc), C.byref(sms))
     if st != 0:
         raise NepError(st, L.nep_status_string(st).decode(), "nep_fp32_peak failed")
-    return {"best_tflops": best.value, "median_tflops": med.value, "sm_count": sms.value}
+    return {"best_tflops": best.value, "median_tflops": med.value, "fma_per_clock_sm": fpc.value,
+            "sm_count": sms.value}

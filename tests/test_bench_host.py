@@ -71,8 +71,15 @@ def test_flop_model_counts_units():
     assert g["lj_pair"] == h["lj_pair"] + 1
     ratio = bench.kernel_flops("force_full", full, 1) / bench.kernel_flops("force", half, 1)
     assert 1.4 < ratio < 2.0
-    assert bench.force_kind("plain") == "force_full"
+    # the fused kernel's force pass reads each active pair's record instead of walking the list: no
+    # per-entry term, and r^2 (5 FLOP) recomputed from the recorded displacement per active pair
+    r = bench.FLOPS["force_rec"]
+    assert r["list_entry"] == 0 and r["active_pair"] == g["active_pair"] + 5
+    assert all(r[k] == g[k] for k in ("radial_pair", "lj_pair", "angular_pair", "atom"))
+    assert bench.force_kind("plain") == "force_rec"
     assert all(bench.force_kind(f) == "force" for f in bench.FORMS if f != "plain")
+    # per active pair the force kernels spend 2 (rsqrt, r) + 6 (d) + 3 (F_i) + 12 (6 virial components)
+    assert g["active_pair"] == 2 + 6 + 3 + 12 and h["active_pair"] == g["active_pair"]
 
 
 def test_traffic_lookup_requires_matching_source(tmp_path, monkeypatch):

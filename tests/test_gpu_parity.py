@@ -360,6 +360,40 @@ def test_reupload_rebuilds_when_atoms_moved_beyond_the_skin(api, model_params):
     assert abs(E1 - E0) <= 1e-6 * abs(E0)
 
 
+def test_round_trip_upload_keeps_forces(api, model_params):
+    """Uploading the state just read back (velocities possibly changed) leaves every float32 position
+    as it was: the handle keeps the last evaluation's forces, energy and virial (no new evaluation),
+    the kinetic energy follows the uploaded velocities, and MD continues as without the round trip.
+    A changed position makes the next step evaluate the forces again."""
+    wl = ni.fcc_cu_workload(5, 300.0, 0.05, seed=81)
+    with api.NEP(model_params, rebuild_every=10) as ref:
+        ref.set_state(wl.pos, wl.vel, wl.box)
+        ref.step(1.0, 4)
+        th4 = ref.thermo()
+        ref.step(1.0, 3)
+        xr, vr = ref.get_state()
+    with api.NEP(model_params, rebuild_every=10) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.step(1.0, 4)
+        x, v = nep.get_state()
+        ev0 = nep.counters()["evaluations"]
+        nep.set_state(x, 2.0 * v, wl.box)
+        assert nep.counters()["evaluations"] == ev0
+        th = nep.thermo()
+        assert th["pe"] == th4["pe"]
+        assert abs(th["ke"] - 4.0 * th4["ke"]) <= 1e-9 * th4["ke"]
+        nep.set_state(x, v, wl.box)
+        nep.step(1.0, 3)
+        assert nep.counters()["evaluations"] == ev0 + 3
+        xb, vb = nep.get_state()
+        # the round trip through wrapped host positions may move a coordinate by an ulp of float64
+        assert np.abs(xb - xr).max() <= 1e-10 and np.abs(vb - vr).max() <= 1e-12
+        x[0, 0] += 1e-3
+        nep.set_state(x, v, wl.box)
+        nep.step(1.0, 1)
+        assert nep.counters()["evaluations"] == ev0 + 5
+
+
 def _pair_r(pos, box, i, js):
     d = pos[js] - pos[i]
     d -= box * np.round(d / box)

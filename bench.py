@@ -77,8 +77,13 @@ UNIT = "atom-steps/s"
 #     pair; its LJ term is the whole pair force (17).
 # The FP32 op counters of one fused launch (ffma, fadd, fmul, paired ops, MUFU) agree with this count to
 # within the conversions and padding named above (profiles/k_nep_fused_cu64x64x64.md).
+# The mixed-precision forms run the same fused kernel with the network as two tensor-core GEMMs
+# (32 x 32 tiles, bf16/f16 operands): per atom 1321 FP32 FLOPs remain (4921 - 3870 for the float32
+# network + scaling 30, per neuron z - b0, tanh, energy FMA and gradient factor 7, Fp 30); the GEMMs'
+# 4096 tensor FLOPs per atom are not part of the FP32 count.
 FLOPS = {
     "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=440, atom=4921),
+    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=440, atom=1321),
     "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=1178, atom=0),
     "force_full": dict(list_entry=11, active_pair=23, radial_pair=118, lj_pair=18, angular_pair=1178, atom=0),
     "force": dict(list_entry=11, active_pair=23, radial_pair=126, lj_pair=17, angular_pair=1418, atom=0),
@@ -98,14 +103,19 @@ BYTES = dict(per_atom=96 + 48 + 48 + 16 + 4 + 24, per_list_entry=4)
 
 
 def force_kind(form: str) -> str:
-    """FLOP table of the force pass a form runs: the fused kernel's pass over its pair records for the
-    float32 teacher, the half list otherwise."""
-    return "force_rec" if form == "plain" else "force"
+    """FLOP table of the force pass a form runs: the fused kernels' pass over their pair records for the
+    teacher (float32 or mixed-precision network), the half list for the student."""
+    return "force_rec" if FORMS[form]["model"] == "teacher" else "force"
+
+
+def descriptor_kind(form: str) -> str:
+    """FLOP table of the descriptor part: the mixed-precision forms' network is on the tensor cores."""
+    return "descriptor_mixed" if form in ("mix_bf16", "mix_fp16") else "descriptor"
 
 
 def kernel_flops(kind: str, c: dict, n_atoms_evals: int, table: dict = FLOPS) -> float:
     f = table[kind]
-    if kind == "descriptor":
+    if kind.startswith("descriptor"):
         lst, act, rad, ang = c["list_entries"], c["active_pairs"], c["radial_pairs"], c["angular_pairs"]
     else:
         lst, act, rad, ang = (c["force_list_entries"], c["force_active_pairs"], c["force_radial_pairs"],
@@ -557,7 +567,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     dc = {k: c2[k] - c1[k] for k in c2}          # the eager pass with per-kernel events
     evals = dc["evaluations"]
     table = FLOPS_STUDENT if FORMS[args.form]["model"] == "student" else FLOPS
-    f_desc = kernel_flops("descriptor", dc, evals * wl.n, table)
+    f_desc = kernel_flops(descriptor_kind(args.form) if table is FLOPS else "descriptor", dc, evals * wl.n, table)
     f_force = kernel_flops(force_kind(args.form), dc, evals * wl.n, table)
     clk = clocks.summary(t_host0, t_host1)
     clk_kernels = clocks.summary(t_host2, t_host3)

@@ -36,6 +36,10 @@ cudaError_t launch_force(const Model<S> &, const Geom &, int, const float4 *, co
 template <class S>
 cudaError_t launch_fused(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &, float *,
                          float *, long long *, long long *, long long *, int *, const PairCache &, cudaStream_t);
+template <class S, class MT>
+cudaError_t launch_fused_mixed(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
+                               float *, float *, long long *, long long *, long long *, int *, const PairCache &,
+                               cudaStream_t);
 cudaError_t pair_cache_sm_bound(int *nsm);
 size_t pair_cache_region_elems(int pmax);
 #ifndef NEP_FUSED
@@ -363,13 +367,21 @@ template <class S>
 cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   const Geom g = geom_of(h);
   if constexpr (std::is_same<S, CuShape>::value && NEP_FUSED) {
-    if (h->precision == NEP_FP32 && !h->fb_on) {
-      // the float32 teacher: descriptors, network and forces in one kernel (forces zeroed first)
+    if (!h->fb_on) {
+      // the teacher: descriptors, network and forces in one kernel (forces zeroed first); the network in
+      // float32, or as two tensor-core GEMMs with bf16 / f16 operands in the mixed-precision forms
       Scope sc(h, KC_FORCE, 1);
       cudaError_t e = cudaMemsetAsync(h->F, 0, 3 * (size_t)h->n * sizeof(long long), h->stream);
       if (e != cudaSuccess) return e;
-      return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F, h->part_d, h->part_f,
-                                   &h->ctrl->status, PairCache{h->pc_rec, h->pc_mask, h->pc_nsm, h->cap}, h->stream);
+      const PairCache pc{h->pc_rec, h->pc_mask, h->pc_nsm, h->cap};
+      if (h->precision == NEP_FP32)
+        return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F, h->part_d,
+                                     h->part_f, &h->ctrl->status, pc, h->stream);
+      if (h->precision == NEP_MIX_BF16)
+        return launch_fused_mixed<CuShape, __nv_bfloat16>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F,
+                                                          h->part_d, h->part_f, &h->ctrl->status, pc, h->stream);
+      return launch_fused_mixed<CuShape, __half>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F,
+                                                 h->part_d, h->part_f, &h->ctrl->status, pc, h->stream);
     }
   }
   Fallback fb{};
@@ -807,7 +819,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 13 + 1));
   A(dalloc(h->part_k, (size_t)h->nb_k + 1)); A(dalloc(h->io, 6 * N));
   if (h->fb_on) A(alloc_fallback(h));
-  if (h->shape == 0 && h->precision == NEP_FP32 && e == cudaSuccess) {
+  if (h->shape == 0 && e == cudaSuccess) {
     // pair records of the fused kernel: PC_SLOTS regions per SM index, list capacity records per atom
     A(pair_cache_sm_bound(&h->pc_nsm));
     // record offsets are 32-bit: nsm * PC_SLOTS * cap (<= 128) * 128 < 2^32 for nsm <= 4096

@@ -779,6 +779,217 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
 
+// Mixed-precision form of the fused kernel: the same descriptor walk (pair records), float32 adjoint
+// row in TMEM and force pass over the records, with the one-hidden-layer network as two GEMMs on the
+// 5th-generation tensor cores, one CTA = one 128-atom tile = the M of one tcgen05.mma:
+//   forward   Z[128 x 32]  = Q~[128 x 32] . W0^T    (MT = bf16 or f16 operands, f32 accumulation)
+//   backward  dQ[128 x 32] = T[128 x 32] . W0       T_mu = w1_mu (1 - tanh(z_mu - b0_mu)^2)
+// (the batched network GEMM of Section V.B, Optimization 1, in the half-precision network input of
+// Optimization 4).  The walk is the float32 kernel's (all 120 sums in TMEM); for the GEMMs the 24 sums
+// of angular channel 4 move to registers, so that TMEM columns 96..127 take the GEMM accumulators, and
+// afterwards channel 4's adjoint goes back to columns 96..119 (the layout of tm_col), over the consumed
+// GEMM result (each warp only touches its own 32 lanes, after its own load of them completed).  The A
+// tile (q~ rows, then T rows) has its own shared memory, so each thread writes its row as soon as its
+// descriptors are known; one barrier precedes each GEMM.  Every wait on the tensor core is bounded
+// (ST_TIMEOUT on expiry).
+constexpr int FM_K = 32;             // descriptors padded to 32 (two K = 16 steps)
+constexpr int FM_N = 32;             // neurons padded to 32
+constexpr long FM_WAIT = 1L << 22;   // mbarrier polls before giving up
+
+template <class S, class MT>
+__global__ void __launch_bounds__(DESC_BLOCK, NEP_FUSED_MINB)
+k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
+                  const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ usite,
+                  float *__restrict__ qout, unsigned long long *__restrict__ Ffix, long long *__restrict__ part_d,
+                  long long *__restrict__ part_f, int *__restrict__ status, const PairCache pc) {
+  static_assert(ForceCfg<S>::TM && DESC_BLOCK == 128 && S::NDES <= FM_K && S::NNEU <= FM_N, "teacher shape");
+  constexpr int NT = 4;
+  constexpr int W = TMEM_W;
+  constexpr uint32_t TCOLS = 128;
+  constexpr uint32_t GCOL = NT * S::NLM;   // GEMM accumulator columns 96..127
+  static_assert(GCOL + FM_N <= TCOLS && tm_col(4, 0, S::NLM) == GCOL, "channel 4's adjoint takes the GEMM columns");
+  static_assert(PC_SLOTS * TCOLS == 512, "at most PC_SLOTS blocks per SM: one pair-record slot each");
+  __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
+  __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
+  __shared__ __align__(1024) MT sA[DESC_BLOCK * FM_K];
+  __shared__ __align__(1024) MT sW[FM_N * FM_K];    // B of the forward GEMM: W0[neuron][descriptor]
+  __shared__ __align__(1024) MT sWt[FM_K * FM_N];   // B of the backward GEMM: W0[descriptor][neuron]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ float4 fp_s[2 * DESC_BLOCK];
+  __shared__ int s_slot;
+  const int t = threadIdx.x;
+  if (t < 32) {
+    for (int k = 0; k < FM_K; ++k) {
+      sW[tile_off(t, k, FM_K / 8)] = to_mma_type<MT>((t < S::NNEU && k < S::NDES) ? P.W0[t][k] : 0.f);
+      sWt[tile_off(t, k, FM_K / 8)] = to_mma_type<MT>((t < S::NDES && k < S::NNEU) ? P.W0[k][t] : 0.f);
+    }
+    tmem_alloc(&tmem_base, TCOLS);
+  }
+  if (t == 0) {
+    mbar_init(&mbar, 1);
+    const unsigned sm = sm_index();
+    int slot = -1;
+    if ((int)sm < pc.nsm) {
+      for (int it = 0; it < 64 && slot < 0; ++it)
+        for (int b = 0; b < PC_SLOTS && slot < 0; ++b)
+          if ((atomicOr(pc.slot_mask + sm, 1u << b) & (1u << b)) == 0u) slot = (int)sm * PC_SLOTS + b;
+    }
+    if (slot < 0) atomicOr(status, ST_SLOT);
+    __threadfence();
+    s_slot = slot;
+  }
+  tc_fence_before();
+  fill_shift_table(shift, geom);
+  __syncthreads();
+  tc_fence_after();
+  const int slot = s_slot;
+  const unsigned rec_off = (unsigned)(slot < 0 ? 0 : slot) * (unsigned)pc.pmax * DESC_BLOCK + t;
+  const uint32_t trow = tmem_base + ((uint32_t)(t & ~31) << 16);
+  const int i = blockIdx.x * DESC_BLOCK + t;
+  const bool live = i < n;
+  const int ii = live ? i : 0;
+  const RowSpan sp = live ? full_row(X, i, skip_far(X)) : RowSpan{0, 0, 0};
+  const int cnt = sp.c;
+
+  float QR[S::KR], elj;
+  int nrad, nang, nact;
+  float q[S::NDES];
+  {
+    RegSums<S, S::NA> R5;
+    accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK, true>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
+                                                                     QR, R5, elj, nrad, nang, nact, pc.rec, rec_off,
+                                                                     pc.pmax);
+    FourBody<S> T;
+    descriptors_tm<S, S::NA>(P, trow, QR, R5, q, T);   // zero for threads past the last atom (empty row)
+  }
+  // channel 4's sums (columns 96..119) to registers: the GEMMs take columns 96..127
+  RegSums<S, NT> R;
+  {
+    uint32_t r[24];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%25];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(trow + GCOL), "r"(trow + GCOL + 16));
+#pragma unroll
+    for (int c = 0; c < S::NLM; ++c) R.s[0][c] = __uint_as_float(r[c]);
+  }
+  if (live && qout != nullptr) {
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
+  }
+#pragma unroll
+  for (int k = 0; k < FM_K; ++k) sA[tile_off(t, k, FM_K / 8)] = to_mma_type<MT>(k < S::NDES ? q[k] * P.qs[k] : 0.f);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t idesc = umma_idesc_f16(DESC_BLOCK, FM_N, MmaKind<MT>::bf16);
+  const uint32_t lbo = 128, sbo = (FM_K / 8) * 128;
+  if (t == 0) {
+#pragma unroll
+    for (int ks = 0; ks < FM_K / 16; ++ks)
+      umma_f16(tmem_base + GCOL, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo),
+               umma_smem_desc(smem_addr(sW) + ks * 256, lbo, sbo), idesc, ks);
+    umma_commit(&mbar);
+  }
+  bool ok = mbar_wait(&mbar, 0, FM_WAIT);
+  tc_fence_after();
+  float U = -P.b1;
+  {
+    float z[32];
+    tmem_ld32(trow + GCOL, z);
+    float tr[FM_N];
+#pragma unroll
+    for (int mu = 0; mu < FM_N; ++mu) {
+      if (mu < S::NNEU) {
+        const float h = tanhf(z[mu] - P.b0[mu]);
+        U = fmaf(P.w1[mu], h, U);
+        tr[mu] = P.w1[mu] * (1.f - h * h);
+      } else {
+        tr[mu] = 0.f;
+      }
+    }
+    // the forward MMA has completed (mbarrier), so its A tile can be overwritten
+#pragma unroll
+    for (int k = 0; k < FM_N; ++k) sA[tile_off(t, k, FM_N / 8)] = to_mma_type<MT>(tr[k]);
+  }
+  fence_async_smem();
+  tc_fence_before();   // every thread has read the forward result before the backward GEMM overwrites it
+  __syncthreads();
+  tc_fence_after();
+  if (t == 0) {
+#pragma unroll
+    for (int ks = 0; ks < FM_N / 16; ++ks)
+      umma_f16(tmem_base + GCOL, umma_smem_desc(smem_addr(sA) + ks * 256, lbo, sbo),
+               umma_smem_desc(smem_addr(sWt) + ks * 256, lbo, sbo), idesc, ks);
+    umma_commit(&mbar);
+  }
+  ok = mbar_wait(&mbar, 1, FM_WAIT) && ok;
+  tc_fence_after();
+  float Fp[S::NDES];
+  {
+    float dq[32];
+    tmem_ld32(trow + GCOL, dq);
+#pragma unroll
+    for (int v = 0; v < S::NDES; ++v) Fp[v] = dq[v] * P.qs[v];
+  }
+  if (!ok && t == 0) atomicOr(status, ST_TIMEOUT);
+
+  // adjoint row of all 5 channels in the chunked layout: channels 0..3 over their sums, channel 4 over
+  // the GEMM columns this warp has just read
+  float g4[S::NA][5];
+  fourbody_adjoint_tm<S, NT>(trow, R, g4);
+#pragma unroll
+  for (int k = 0; k < S::NLM / W; ++k) {
+    float sv[S::NA][W], gl[S::NA][W];
+    sums_chunk<S, NT>(trow, k, R, sv);
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) adjoint_chunk<S>(a, W * k, sv[a], g4[a], Fp, gl[a]);
+    tm_store<S, S::NA>(trow, k, gl);
+  }
+  tmem_wait_st();
+  {
+    float fpi[8];
+    radial_tail<S>(P, Fp, fpi);
+    fp_s[t] = make_float4(fpi[0], fpi[1], fpi[2], fpi[3]);
+    fp_s[DESC_BLOCK + t] = make_float4(fpi[4], fpi[5], fpi[6], fpi[7]);
+  }
+  long long acc_d[5] = {0, 0, 0, 0, 0};
+  long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (live) {
+    const float ui = U + elj;
+    usite[i] = ui;
+    if (!isfinite(ui)) atomicOr(status, ST_NAN);
+    acc_d[0] = to_fix32(ui);
+    acc_d[1] = nrad;
+    acc_d[2] = nang;
+    acc_d[3] = cnt;
+    acc_d[4] = nact;
+    acc_f[9] = cnt; acc_f[10] = nact; acc_f[11] = nrad; acc_f[12] = nang;
+  }
+  block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);
+  force_pairs_rec<S, PIPE_DP>(P, trow, fp_s + t, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang, ring_p,
+                              Ffix, status, acc_f);
+  tc_fence_before();
+  __syncthreads();
+  if (t < 32) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TCOLS);
+  }
+  if (t == 0 && slot >= 0) {
+    __threadfence();
+    atomicAnd(pc.slot_mask + slot / PC_SLOTS, ~(1u << (slot % PC_SLOTS)));
+  }
+  block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
+}
+
 // ---------------------------------------------------------------------------------------------------
 // Host launchers (called from nep_api.cu).
 
@@ -866,6 +1077,27 @@ cudaError_t launch_fused(const Model<S> &P, const Geom &g, int n, const float4 *
 template cudaError_t launch_fused<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *, const int32_t *,
                                            const RowExt &, float *, float *, long long *, long long *, long long *,
                                            int *, const PairCache &, cudaStream_t);
+
+// Mixed-precision fused evaluation of the teacher (k_nep_fused_mixed); Ffix must be zero.
+template <class S, class MT>
+cudaError_t launch_fused_mixed(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
+                               const RowExt &X, float *usite, float *qout, long long *Ffix, long long *part_d,
+                               long long *part_f, int *status, const PairCache &pc, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
+  k_nep_fused_mixed<S, MT><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, usite, qout,
+                                                        reinterpret_cast<unsigned long long *>(Ffix), part_d, part_f,
+                                                        status, pc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fused_mixed<CuShape, __nv_bfloat16>(const Model<CuShape> &, const Geom &, int,
+                                                                const float4 *, const int32_t *, const RowExt &,
+                                                                float *, float *, long long *, long long *,
+                                                                long long *, int *, const PairCache &, cudaStream_t);
+template cudaError_t launch_fused_mixed<CuShape, __half>(const Model<CuShape> &, const Geom &, int, const float4 *,
+                                                         const int32_t *, const RowExt &, float *, float *,
+                                                         long long *, long long *, long long *, int *,
+                                                         const PairCache &, cudaStream_t);
 
 // Records per SM bound of the pair cache: %nsmid of the current device (synchronous).
 __global__ void k_sm_bound(int *out) { *out = (int)sm_index_bound(); }

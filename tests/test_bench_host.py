@@ -76,8 +76,11 @@ def test_flop_model_counts_units():
     r = bench.FLOPS["force_rec"]
     assert r["list_entry"] == 0 and r["active_pair"] == g["active_pair"] + 5
     assert all(r[k] == g[k] for k in ("radial_pair", "lj_pair", "angular_pair", "atom"))
-    assert bench.force_kind("plain") == "force_rec"
-    assert all(bench.force_kind(f) == "force" for f in bench.FORMS if f != "plain")
+    assert all(bench.force_kind(f) == ("force_rec" if bench.FORMS[f]["model"] == "teacher" else "force")
+               for f in bench.FORMS)
+    # the mixed forms' descriptor part differs only in the network (on the tensor cores)
+    dm, dd = bench.FLOPS["descriptor_mixed"], bench.FLOPS["descriptor"]
+    assert all(dm[k] == dd[k] for k in dd if k != "atom") and dm["atom"] < dd["atom"]
     # per active pair the force kernels spend 2 (rsqrt, r) + 6 (d) + 3 (F_i) + 12 (6 virial components)
     assert g["active_pair"] == 2 + 6 + 3 + 12 and h["active_pair"] == g["active_pair"]
 

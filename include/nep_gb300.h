@@ -219,21 +219,25 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F);
 #define NEP_NOALLOC_MAX_CELLS 32768
 
 /* One energy/force/virial evaluation that allocates no memory (no paper counterpart: it is a
- * deployment aid).  It is meant for callers that cannot allocate GPU memory where they need forces --
- * a plugin that must stay inside a host program's memory pool or allocation budget, code running while
- * that program captures a stream, an embedded runtime that forbids cudaMalloc after start-up -- and so
- * cannot create a handle (nep_create and nep_set_state allocate).  It runs the same kernels as
- * nep_compute on up to NEP_NOALLOC_MAX_ATOMS atoms (boxes of up to NEP_NOALLOC_MAX_CELLS neighbour
- * cells), with every intermediate buffer in one fixed file-scope device array (about 11 MB, held by
- * every GPU that loads the library until the process exits); it calls no cudaMalloc, cudaFree or
- * other allocating routine.  params: as for nep_create (max_neighbors and rebuild_every are ignored; the
- * list capacity is 128).  x: [n][3] positions, E: scalar, F: [n][3] float64 in the caller's order,
- * virial: [9]; each pointer host or device, E/F/virial may be NULL.  cuda_stream: the stream to run on
- * (NULL = the legacy default stream).  The call waits for its work (bounded) and returns the status.
- * Sizes above the limits return NEP_ERR_ARG.  The first call on each device looks up the array's device
- * address, so make it before any stream capture.  All calls share the array and it keeps the last
- * call's contents (the call clears what must start at zero); calls that overlap on the GPU race on it:
- * do not run two at once. */
+ * deployment aid).  It is meant for callers that cannot allocate GPU memory where they need forces -- a
+ * plugin that must stay inside a host program's memory pool or allocation budget, or an embedded
+ * runtime that forbids cudaMalloc after start-up -- and so cannot create a handle (nep_create and
+ * nep_set_state allocate).  It evaluates the float32 teacher shape only (params as for nep_create with
+ * precision NEP_FP32; another shape or precision returns NEP_ERR_UNSUPPORTED; max_neighbors and
+ * rebuild_every are ignored, the list capacity is 128), on up to NEP_NOALLOC_MAX_ATOMS atoms in boxes of
+ * up to NEP_NOALLOC_MAX_CELLS neighbour cells, with the separate descriptor and full-row force kernels
+ * (not the fused kernel of nep_compute, whose pair records would need more scratch), and keeps every
+ * intermediate buffer in one fixed file-scope device array (about 11 MB, held by every GPU that loads
+ * the library until the process exits); it calls no cudaMalloc, cudaFree or other allocating routine.
+ * x: [n][3] positions, E: scalar, F: [n][3] float64 in the caller's order, virial: [9]; each pointer
+ * host or device, E/F/virial may be NULL.  cuda_stream: the stream to run on (NULL = the legacy default
+ * stream).  The call waits for its own work (polling the stream, 900 s limit) and reads its status and
+ * host-side results with synchronous copies, so it must not run while any stream of the process is
+ * being captured into a CUDA graph.  Sizes above the limits return NEP_ERR_ARG before any GPU work.  The
+ * first call on each device looks up the array's device address.  All calls share the array and it
+ * keeps the last call's contents (the call clears what must start at zero); calls that overlap on the
+ * GPU race on it: do not run two at once.  After NEP_ERR_TIMEOUT the timed-out work may still be running
+ * on the array: the next call returns NEP_ERR_STATE until that stream is idle. */
 nep_status nep_compute_noalloc(const nep_params *params, int64_t n, const double *x, const double *box, double *E,
                                double *F, double *virial, void *cuda_stream);
 

@@ -1,19 +1,21 @@
 // nep_noalloc.cu -- one force evaluation that allocates no memory (nep_compute_noalloc).
 //
 // Some callers cannot allocate GPU memory at the point where they need forces: a plugin running
-// inside another program's memory pool or allocator budget, code that runs while a stream of that
-// program is being captured, or an embedded runtime that forbids cudaMalloc after start-up.  For them
-// this entry point evaluates E, F and the virial of a small system with the same kernels as
-// nep_compute, but every intermediate buffer (cell lists, neighbour lists, adjoint rows, partial sums,
-// status word) lives in one file-scope __device__ array of fixed size, created when the library is
-// loaded and kept by every GPU that loads it until the process exits.
+// inside another program's memory pool or allocator budget, or an embedded runtime that forbids
+// cudaMalloc after start-up.  For them this entry point evaluates E, F and the virial of a small system
+// of the float32 teacher shape with the separate descriptor and full-row force kernels, but every
+// intermediate buffer (cell lists, neighbour lists, adjoint rows, partial sums, status word) lives in
+// one file-scope __device__ array of fixed size, created when the library is loaded and kept by every
+// GPU that loads it until the process exits.
 //
 // The device address of that array is looked up once per device with cudaGetSymbolAddress (in host
-// code the symbol name is only a host-side stand-in, never a device address); that look-up happens in
-// the first call on each device, so that first call should come before any stream capture.  All calls
-// share the array and it keeps the previous call's contents: every piece that must start from zero is
-// cleared by the call itself, and calls that overlap on the GPU (on different streams, or from
-// different threads) race on the array -- serialize them.
+// code the symbol name is only a host-side stand-in, never a device address), in the first call on
+// each device.  The call waits for its work by polling the stream and reads results with synchronous
+// copies, so it is not for use while a stream is being captured.  All calls share the array and it
+// keeps the previous call's contents: every piece that must start from zero is cleared by the call
+// itself, and calls that overlap on the GPU (on different streams, or from different threads) race on
+// the array -- serialize them.  A call whose wait timed out leaves its work running on the array; the
+// next call refuses to start (NEP_ERR_STATE) until that stream is idle.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -91,8 +93,33 @@ constexpr Layout LAYOUT = make_layout();
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LAYOUT.total];
 
 constexpr int MAX_DEVICES = 64;
+constexpr double WAIT_LIMIT_S = 900.0;
 std::mutex g_mutex;
 unsigned char *g_scratch_addr[MAX_DEVICES] = {nullptr};
+// stream of a call whose wait timed out, per device (its work may still use the array)
+cudaStream_t g_busy_stream[MAX_DEVICES] = {nullptr};
+bool g_busy[MAX_DEVICES] = {false};
+
+// NEP_OK when no timed-out call's work is still running on this device's array.
+nep_status previous_call_done() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return NEP_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_busy[dev]) return NEP_OK;
+  const cudaError_t e = cudaStreamQuery(g_busy_stream[dev]);
+  if (e == cudaErrorNotReady) return NEP_ERR_STATE;
+  if (e != cudaSuccess) cudaGetLastError();
+  g_busy[dev] = false;
+  return NEP_OK;
+}
+
+void mark_busy(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return;
+  std::lock_guard<std::mutex> lock(g_mutex);
+  g_busy[dev] = true;
+  g_busy_stream[dev] = st;
+}
 
 // Device address of the scratch array on the current device (looked up once per device).
 cudaError_t scratch_address(unsigned char **out) {
@@ -129,7 +156,7 @@ nep_status wait_bounded(cudaStream_t st) {
     if (e == cudaSuccess) return NEP_OK;
     if (e != cudaErrorNotReady) return NEP_ERR_CUDA;
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (el > 600.0) return NEP_ERR_TIMEOUT;
+    if (el > WAIT_LIMIT_S) return NEP_ERR_TIMEOUT;
     if (spins > 64) {                       // yield for the first 2 ms, then sleep between polls
       if (el < 2e-3) std::this_thread::yield();
       else std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -202,6 +229,8 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   const float rmax = std::max(p->rc_R, eps != 0.0 ? p->lj_rc : 0.f);
   M.rmax2 = rmax * rmax;
 
+  const nep_status prev = previous_call_done();
+  if (prev != NEP_OK) return prev;
   unsigned char *base = nullptr;
   NA_CUDA(scratch_address(&base));
   auto at = [base](size_t off) { return static_cast<void *>(base + off); };
@@ -263,6 +292,7 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
   if (w_dev) NA_CUDA(cudaMemcpyAsync(virial, sums + 1, 9 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   // Wait (bounded) for the work, then copy host-side results from the now idle scratch array.
   const nep_status w = wait_bounded(st);
+  if (w == NEP_ERR_TIMEOUT) mark_busy(st);
   if (w != NEP_OK) return w;
   int status = 0;
   NA_CUDA(cudaMemcpy(&status, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -222,15 +222,16 @@ def test_atoms_crossing_the_boundary_and_rebuilds(api, model_params, model):
 
 
 def test_nve_energy_drift_gpu(api, model_params, c1):
-    """Plain FP32 forces with FP64 integration: drift below 1e-5 eV/atom/ps over 2 ps."""
+    """Plain FP32 forces with FP64 integration: the slope of a linear fit of the total energy over 10 ps
+    (10^4 steps, sampled every 50) is below 1e-5 eV/atom/ps."""
     with api.NEP(model_params) as nep:
         nep.set_state(c1.pos, c1.vel, c1.box)
         et = []
-        for _ in range(40):
+        for _ in range(200):
             nep.step(1.0, 50)
             th = nep.thermo()
             et.append((th["pe"] + th["ke"]) / c1.n)
-    t_ps = np.arange(1, 41) * 0.05
+    t_ps = np.arange(1, 201) * 0.05
     assert abs(np.polyfit(t_ps, np.array(et), 1)[0]) < 1e-5
 
 

@@ -438,7 +438,8 @@ CONFIGS = (
 )
 
 
-def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, idx, stream, dev, local, ws):
+def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, idx, stream, dev, local, ws,
+                     ablate=False):
     """One form on one workload: forces of the start state on the sampled atoms, then `warmup` and
     `steps` CUDA-graph MD steps, the latter timed with events on the library's stream while the SM
     clock is sampled."""
@@ -472,12 +473,21 @@ def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, i
         ms = dist_max(s.elapsed_time(e), ws, dev)
         th = h.thermo()
         c1 = h.counters()
+        abl = None
+        if form == "plain" and ablate:
+            # the list-walking force kernels on the state after the timed steps (rows of unequal lengths)
+            abl = {v + "_ms": round(min(h.run_variant(v)[0] for _ in range(2)), 3)
+                   for v in ("separate_force", "cpb1", "cpb2", "cpb3")}
+            p90, cpb = h.angular_p90()
+            abl["cpb_rule"] = {"p90_angular_pairs": p90, "centres_per_warp": cpb}
     rec = {"value": dist_sum(wl.n, ws, dev) * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
            "dtype": f["dtype"], "clocks": clocks.summary(t0, t1), "pe_per_atom_end": th["pe"] / wl.n,
            "rebuilds": c1["rebuilds"] - c0["rebuilds"] if "rebuilds" in c1 else None, "_F": F}
     if f["fallback"]:
         ev = max(1, c1["evaluations"] - c0["evaluations"])
         rec["fallback_fraction"] = (c1["fallback_atoms"] - c0["fallback_atoms"]) / (ev * wl.n)
+    if abl is not None:
+        rec["ablations"] = abl
     return rec
 
 
@@ -493,7 +503,8 @@ def run_configs(teacher, student, args, stream, dev, local, ws) -> dict:
         idx = ni.sample_indices(wl.n, 8192, seed=11)
         recs = {}
         for form in forms:
-            recs[form] = time_config_form(form, teacher, student, wl, steps, 3, cap, idx, stream, dev, local, ws)
+            recs[form] = time_config_form(form, teacher, student, wl, steps, 3, cap, idx, stream, dev, local, ws,
+                                          ablate=name == "cu_160x160x160_1200K")
         Fp = recs["plain"]["_F"]
         for form, rec in recs.items():
             d = rec.pop("_F") - Fp
@@ -641,8 +652,11 @@ def run_ours(args, rank: int, ws: int, local: int):
         t_ref = nep.timing()
         nep.set_timing(False)
         ablations = {"fused_ms": round(t_ref["force"][0] + t_ref["descriptor"][0], 4)}
-        for v in ("separate_descriptor", "separate_force", "float_scatter", "half_list", "tile1", "tile3"):
+        for v in ("separate_descriptor", "separate_force", "float_scatter", "half_list", "tile1", "tile3",
+                  "cpb1", "cpb2", "cpb3"):
             ablations[v + "_ms"] = round(min(nep.run_variant(v)[0] for _ in range(3)), 4)
+        p90, cpb = nep.angular_p90()
+        ablations["cpb_rule"] = {"p90_angular_pairs": p90, "centres_per_warp": cpb}
         ablations["note"] = ("fused: the production kernel (descriptors, network and forces in one launch, adjoint "
                              "rows in tensor memory, the force pass over the descriptor walk's pair records); "
                              "separate_descriptor + separate_force: descriptors and full-row forces as two launches "
@@ -651,8 +665,10 @@ def run_ours(args, rank: int, ws: int, local: int):
                              "(order-dependent sums) instead of fixed-point integer atomics; half_list: force "
                              "kernel over each unordered pair once, gathering the neighbour's adjoint row; "
                              "tile1/tile3: descriptor kernel with 1 or 3 angular channels per neighbour pass and "
-                             "s_nlm through global memory instead of all 5 channels in tensor memory; single "
-                             "launches, CUDA events")
+                             "s_nlm through global memory instead of all 5 channels in tensor memory; cpb1/2/3: "
+                             "force kernel in the paper's thread-per-neighbour form, 1, 2 or 3 centre atoms per "
+                             "32-lane warp (adaptive centres-per-block; cpb_rule: the 90th percentile of the "
+                             "angular pair count and the CPB it selects); single launches, CUDA events")
     F_plain = F_this = None
     others = [] if args.no_forms else [f for f in FORMS if f != args.form]
     if others:

@@ -210,9 +210,24 @@ enum {
   NEP_VARIANT_TILE3 = 3,
   NEP_VARIANT_HALF_LIST = 4,
   NEP_VARIANT_SEPARATE_DESCRIPTOR = 5,
-  NEP_VARIANT_SEPARATE_FORCE = 6
+  NEP_VARIANT_SEPARATE_FORCE = 6,
+  NEP_VARIANT_CPB1 = 7,
+  NEP_VARIANT_CPB2 = 8,
+  NEP_VARIANT_CPB3 = 9,
+  NEP_VARIANT_CPB_AUTO = 10
 };
+/* NEP_VARIANT_CPB1/2/3/AUTO: the force kernel in the paper's thread-per-neighbour form with its adaptive
+ * centres-per-block scheduling (Section V.B, Optimization 3): a 32-lane warp takes 1, 2 or 3 centre
+ * atoms at a time, its lanes split into as many groups; a group strides over its centre's row (radial
+ * and LJ pairs) and then over the centre's angular pairs (the three-body backward) with the adjoint row
+ * in shared memory.  AUTO picks CPB from the 90th percentile of the angular pair count (nep_angular_p90).
+ * Run after the separate descriptor kernel, like the other force variants. */
 nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F);
+
+/* Diagnostic of the CPB variants: the 90th percentile p90 of the per-atom angular pair count (r < rc_A)
+ * of the current state, and the centres per warp the paper's rule gives for 32-lane warps (its 64-lane
+ * thresholds halved): 3 if p90 <= 10, 2 if p90 < 24, else 1.  Synchronous; host outputs. */
+nep_status nep_angular_p90(nep_handle *h, int *p90, int *cpb);
 
 /* Upper limits of nep_compute_noalloc: the size of its fixed scratch array. */
 #define NEP_NOALLOC_MAX_ATOMS 8192

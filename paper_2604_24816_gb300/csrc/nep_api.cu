@@ -74,6 +74,11 @@ cudaError_t launch_descriptor_tiled(const Model<S> &, const Geom &, int, const f
                                     const RowExt &, float *, float *, long long *, long long *, int *, float *,
                                     cudaStream_t);
 cudaError_t launch_store_float3(int, const int *, const float *, double *, cudaStream_t);
+template <class S>
+cudaError_t launch_force_cpb(int, const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
+                             const float *, long long *, long long *, int *, cudaStream_t);
+cudaError_t launch_angular_counts(int, const float4 *, const int32_t *, const RowExt &, const Geom &, float, int *,
+                                  cudaStream_t);
 // nep_neighbor.cu
 cudaError_t launch_cell_sort(const RebuildArgs &, cudaStream_t);
 cudaError_t launch_neighbors(const RebuildArgs &, cudaStream_t);
@@ -191,6 +196,7 @@ struct nep_handle {
 
   // buffers of the ablation variants (allocated on first use)
   float *abl_f = nullptr, *abl_s = nullptr;
+  int *abl_cnt = nullptr;
 
   // pair records of the fused float32 kernel (allocated with the system for the float32 teacher)
   float4 *pc_rec = nullptr;
@@ -245,7 +251,7 @@ void free_system(nep_handle *h) {
   dfree(h->count); dfree(h->cursor); dfree(h->start); dfree(h->tile_sums);
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
   dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
-  dfree(h->abl_f); dfree(h->abl_s);
+  dfree(h->abl_f); dfree(h->abl_s); dfree(h->abl_cnt);
   dfree(h->pc_rec); dfree(h->pc_mask);
   h->pc_nsm = 0;
   h->fb_cap = 0;
@@ -1080,10 +1086,34 @@ nep_status nep_set_fallback(nep_handle *h, const nep_params *teacher, const floa
   return NEP_OK;
 }
 
+nep_status nep_angular_p90(nep_handle *h, int *p90, int *cpb) {
+  if (!h || !p90 || !cpb) return NEP_ERR_ARG;
+  if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
+  if (h->shape != 0) return fail(h, NEP_ERR_UNSUPPORTED, "the CPB variants exist for the teacher shape");
+  *p90 = 0;
+  *cpb = 3;
+  if (h->n == 0) return NEP_OK;
+  nep_status s = ensure_nlist(h);
+  if (s != NEP_OK) return s;
+  const size_t N = (size_t)h->n;
+  if (!h->abl_cnt) NEP_CUDA(h, dalloc(h->abl_cnt, N));
+  int *counts = h->abl_cnt;
+  NEP_CUDA(h, launch_angular_counts(h->n, h->pos, h->nbr, rows_of(h), geom_of(h), h->rcA * h->rcA, counts, h->stream));
+  std::vector<int> hc(N);
+  NEP_CUDA(h, cudaMemcpyAsync(hc.data(), counts, N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  s = wait_stream(h);
+  if (s != NEP_OK) return s;
+  const size_t k = std::min(N - 1, (size_t)std::ceil(0.9 * (double)N) - 1);
+  std::nth_element(hc.begin(), hc.begin() + (long)k, hc.end());
+  *p90 = hc[k];
+  *cpb = *p90 <= 10 ? 3 : (*p90 < 24 ? 2 : 1);
+  return NEP_OK;
+}
+
 nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
   if (!h || !ms) return NEP_ERR_ARG;
   if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
-  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_SEPARATE_FORCE)
+  if (variant < NEP_VARIANT_FLOAT_SCATTER || variant > NEP_VARIANT_CPB_AUTO)
     return fail(h, NEP_ERR_ARG, "unknown variant");
   if (h->shape != 0 || h->precision != NEP_FP32 || h->fb_on)
     return fail(h, NEP_ERR_UNSUPPORTED, "the variants exist for the plain float32 teacher path");
@@ -1121,6 +1151,24 @@ nep_status nep_run_variant(nep_handle *h, int variant, double *ms, double *F) {
       if (e == cudaSuccess && variant == NEP_VARIANT_SEPARATE_FORCE)
         e = launch_force<CuShape, float>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->F,
                                          h->part_f, &h->ctrl->status, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+      if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
+    } else if (variant >= NEP_VARIANT_CPB1 && variant <= NEP_VARIANT_CPB_AUTO) {
+      int cpb = variant - NEP_VARIANT_CPB1 + 1;
+      if (variant == NEP_VARIANT_CPB_AUTO) {
+        int p90 = 0;
+        const nep_status ps = nep_angular_p90(h, &p90, &cpb);
+        if (ps != NEP_OK) {
+          cudaEventDestroy(a); cudaEventDestroy(b);
+          return ps;
+        }
+      }
+      e = launch_descriptor<CuShape>(h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->usite, nullptr, h->F,
+                                     h->part_d, &h->ctrl->status, Fallback{}, h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+      if (e == cudaSuccess)
+        e = launch_force_cpb<CuShape>(cpb, h->model_t, g, h->n, h->pos, h->nbr, rows_of(h), G, h->F, h->part_f,
+                                      &h->ctrl->status, h->stream);
       if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
       if (e == cudaSuccess) e = launch_store_force(h->n, h->id, h->F, h->io, h->stream);
     } else if (variant == NEP_VARIANT_SEPARATE_DESCRIPTOR) {

@@ -53,7 +53,7 @@ EXPORTED = ("nep_create", "nep_destroy", "nep_set_state", "nep_build_neighbors",
             "nep_get_state", "nep_get_thermo", "nep_get_neighbors", "nep_get_descriptors", "nep_get_site_energies",
             "nep_set_timing", "nep_get_timing", "nep_get_counters", "nep_last_error", "nep_status_string",
             "nep_compute_noalloc", "nep_set_fallback", "nep_get_fallback", "nep_run_variant",
-            "nep_selftest_bounded_wait", "nep_fp32_peak")
+            "nep_selftest_bounded_wait", "nep_fp32_peak", "nep_angular_p90")
 
 
 def lib():
@@ -89,6 +89,7 @@ def lib():
                                        C.c_float, C.c_double]
         L.nep_get_fallback.argtypes = [vp, vp, C.POINTER(C.c_int64)]
         L.nep_run_variant.argtypes = [vp, C.c_int, d, vp]
+        L.nep_angular_p90.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.nep_selftest_bounded_wait.argtypes = [i64, C.POINTER(C.c_int)]
         L.nep_fp32_peak.argtypes = [C.c_int, C.c_double, C.c_int, vp, d, d, d, C.POINTER(C.c_int)]
         for f in EXPORTED:
@@ -273,7 +274,13 @@ class NEP:
                                              float(max_fraction)))
 
     VARIANTS = {"float_scatter": 1, "tile1": 2, "tile3": 3, "half_list": 4, "separate_descriptor": 5,
-                "separate_force": 6}
+                "separate_force": 6, "cpb1": 7, "cpb2": 8, "cpb3": 9, "cpb_auto": 10}
+
+    def angular_p90(self):
+        """(p90 of the per-atom angular pair count, centres per warp of the CPB rule) (nep_angular_p90)."""
+        p90, cpb = C.c_int(0), C.c_int(0)
+        self._check(self._L.nep_angular_p90(self._h, C.byref(p90), C.byref(cpb)))
+        return p90.value, cpb.value
 
     def run_variant(self, name: str):
         """One force evaluation with a kernel variant kept for ablation (nep_run_variant): returns

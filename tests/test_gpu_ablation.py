@@ -1,8 +1,9 @@
 """Kernel variants kept for ablation (nep_run_variant) against the production kernel and the oracle:
 the separate descriptor and full-row force kernels (the production fused kernel's work as two launches),
 the float-atomic force scatter (order-dependent float sums; forces equal to the fixed-point path within
-float rounding), the half-list force kernel (each unordered pair once, gathering the neighbour's row)
-and the channel-tiled descriptor kernel (same descriptors, same forces)."""
+float rounding), the half-list force kernel (each unordered pair once, gathering the neighbour's row),
+the channel-tiled descriptor kernel (same descriptors, same forces) and the thread-per-neighbour force
+kernel with 1, 2 or 3 centre atoms per warp (the paper's adaptive centres-per-block scheduling)."""
 import numpy as np
 import pytest
 
@@ -24,7 +25,7 @@ def api():
 
 
 @pytest.mark.parametrize("variant", ["float_scatter", "tile1", "tile3", "half_list", "separate_descriptor",
-                                     "separate_force"])
+                                     "separate_force", "cpb1", "cpb2", "cpb3", "cpb_auto"])
 def test_variant_forces(api, model_params, model, variant):
     wl = ni.fcc_cu_workload(6, 300.0, 0.05, seed=91)
     with api.NEP(model_params) as nep:
@@ -50,3 +51,21 @@ def test_float_scatter_is_order_dependent_but_fixed_point_is_not(api, model_para
     print(f"float atomicAdd scatter: {diff} of {3 * runs[0].size} force components differ between repeated runs")
     for r in runs[1:]:
         assert np.abs(r - runs[0]).max() <= 1e-5
+
+
+def test_cpb_rule_and_irregular_rows(api, model_params, model):
+    """The CPB rule's p90 on a lattice (18 angular pairs within rc_A for fcc Cu: 2 centres per 32-lane
+    warp), and the CPB kernels on a cell with a void (rows of very different lengths, some atoms with
+    few angular pairs) against the oracle."""
+    wl = ni.fcc_cu_workload(6, 300.0, 0.05, seed=93)
+    with api.NEP(model_params) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        p90, cpb = nep.angular_p90()
+    assert 17 <= p90 <= 20 and cpb == 2
+    wv = ni.void_strain_workload(8, void_radius=7.0, strain_z=0.02, seed=94)
+    Fo = oracle.energy_forces(model, wv.pos, wv.box)[2]
+    with api.NEP(model_params) as nep:
+        nep.set_state(wv.pos, wv.vel, wv.box)
+        for v in ("cpb1", "cpb2", "cpb3"):
+            ms, Fv = nep.run_variant(v)
+            assert np.abs(Fv - Fo).max() <= 1e-4, v

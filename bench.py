@@ -132,8 +132,8 @@ KERNEL_SOURCES = {
     "descriptor": ("nep_force.cu",) + _CORE,
     "force": ("nep_force.cu",) + _CORE,
     "fused": ("nep_force.cu",) + _CORE,
-    "descriptor:mix_bf16": ("nep_mixed.cu",) + _CORE,
-    "force:mix_bf16": ("nep_force.cu",) + _CORE,
+    "fused:mix_bf16": ("nep_force.cu",) + _CORE,
+    "fused:mix_fp16": ("nep_force.cu",) + _CORE,
     "descriptor:student_bf16_fallback": ("nep_mixed.cu", "nep_fallback.cu") + _CORE,
     "force:student_bf16_fallback": ("nep_force.cu", "nep_fallback.cu") + _CORE,
 }
@@ -589,8 +589,9 @@ def run_ours(args, rank: int, ws: int, local: int):
     dom_ms = tim[dominant][0]
     dom_launches = max(1, tim[dominant][1])
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = profiled_traffic("fused" if fused else (dominant if args.form == "plain" else f"{dominant}:{args.form}"))
-    dom_name = ("k_nep_fused" if fused else
+    kind = "fused" if fused else dominant
+    traffic = profiled_traffic(kind if args.form == "plain" else f"{kind}:{args.form}")
+    dom_name = (("k_nep_fused" if args.form == "plain" else "k_nep_fused_mixed") if fused else
                 "k_descriptor_mixed" if dominant == "descriptor" and args.form != "plain" else f"k_{dominant}")
     pk_mhz, kn_mhz = peak["clocks"].get("sm_mhz"), clk_kernels.get("sm_mhz")
     roofline = {

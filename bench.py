@@ -335,7 +335,10 @@ def run_reference(args, rank: int, ws: int):
         "warmup": 1, "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "atoms_per_gpu": wl.n, "sample": sample,
-                   "parallelism": "host cores (OpenMP)"},
+                   "parallelism": "host cores (OpenMP)",
+                   "warmup": (f"one initial force evaluation (timed alone, then subtracted) instead of the requested "
+                              f"{args.warmup} steps: the CPU program has no caches or graphs to warm, and each "
+                              f"oracle step at this size takes {t_eval:.0f} s")},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -352,6 +355,7 @@ def measure_fp32_peak(stream, local: int) -> dict:
     t0 = time.perf_counter()
     packed = fp32_peak(True, 5.0, 60, stream.cuda_stream)
     scalar = fp32_peak(False, 5.0, 60, stream.cuda_stream)
+    half2 = fp32_peak("half2", 5.0, 20, stream.cuda_stream)
     t1 = time.perf_counter()
     clocks.stop()
     top = packed if packed["median_tflops"] >= scalar["median_tflops"] else scalar
@@ -360,7 +364,9 @@ def measure_fp32_peak(stream, local: int) -> dict:
             "packed_tflops": packed["median_tflops"], "scalar_tflops": scalar["median_tflops"],
             "packed_best_tflops": packed["best_tflops"],
             "fma_per_clock_sm": {"packed": round(packed["fma_per_clock_sm"], 2),
-                                 "scalar": round(scalar["fma_per_clock_sm"], 2)},
+                                 "scalar": round(scalar["fma_per_clock_sm"], 2),
+                                 "half2": round(half2["fma_per_clock_sm"], 2)},
+            "half2_tflops": half2["median_tflops"],
             "implied_sm_mhz": (round(top["median_tflops"] * 1e6 / (2 * sms * top["fma_per_clock_sm"]), 1)
                                if top["fma_per_clock_sm"] > 0 else None),
             "sm_count": sms, "clocks": clocks.summary(t0, t1)}
@@ -368,11 +374,14 @@ def measure_fp32_peak(stream, local: int) -> dict:
 
 # form name -> library precision, model (teacher or distilled student), per-atom fallback to the
 # teacher, arithmetic types, description
-_MIX = ("network GEMMs on tcgen05 tensor cores with {} operands and f32 accumulation, float16 adjoint rows, "
-        "FP32 descriptors, float64 integration and sums")
+_MIX = ("network GEMMs on tcgen05 tensor cores with {} operands and f32 accumulation inside the fused "
+        "kernel, FP32 descriptors and forces, float64 integration and sums")
+_MIX_STUDENT = ("network GEMMs on tcgen05 tensor cores with {} operands and f32 accumulation, float16 adjoint "
+                "rows between its descriptor and half-list force kernels, FP32 descriptors and forces, float64 "
+                "integration and sums")
 FORMS = {
     "plain": dict(precision="fp32", model="teacher", fallback=False, dtype="f32",
-                  desc="plain FP32 NEP (float64 integration and sums)"),
+                  desc="plain FP32 NEP, seeded teacher weights (float64 integration and sums)"),
     "mix_bf16": dict(precision="mix_bf16", model="teacher", fallback=False, dtype="bf16/f32",
                      desc="mixed precision: " + _MIX.format("bf16")),
     "mix_fp16": dict(precision="mix_fp16", model="teacher", fallback=False, dtype="f16/f32",
@@ -380,7 +389,7 @@ FORMS = {
     "student": dict(precision="fp32", model="student", fallback=False, dtype="f32",
                     desc="distilled student NEP (n_max 3/3, l_max 2, no 4-body, 16 neurons), FP32"),
     "student_bf16_fallback": dict(precision="mix_bf16", model="student", fallback=True, dtype="bf16/f32",
-                                  desc="distilled student NEP, " + _MIX.format("bf16") + "; per-atom fallback to the "
+                                  desc="distilled student NEP, " + _MIX_STUDENT.format("bf16") + "; per-atom fallback to the "
                                        "FP32 teacher for atoms outside the student's training range (5 % margin)"),
 }
 FALLBACK_MARGIN = 0.05
@@ -430,19 +439,22 @@ def time_form(form, teacher, student, wl, args, stream, dev, ws, atoms_total):
     return rec
 
 
-# Workloads of the "configs" block: (name, workload, forms, timed steps, neighbour-list capacity).
+# Workloads of the "configs" block: (name, workload, forms, timed steps, neighbour-list capacity, probe
+# sigma).  The forces compared between forms are those of the start state, unless the start positions
+# are perfect lattice sites (the void workload: bulk forces cancel by symmetry there); then they are
+# those of a probe state, the start positions with seeded N(0, sigma^2) displacements.
 CONFIGS = (
-    ("cu_160x160x160", "cu_160x160x160", ("plain", "mix_bf16", "mix_fp16"), 20, 0),
-    ("cu_160x160x160_1200K", "cu_160x160x160_1200K", ("plain", "mix_bf16", "mix_fp16"), 20, 0),
-    ("cu_320_void", "cu_320_void", ("plain", "student_bf16_fallback"), 10, 96),
+    ("cu_160x160x160", "cu_160x160x160", ("plain", "mix_bf16", "mix_fp16"), 20, 0, None),
+    ("cu_160x160x160_1200K", "cu_160x160x160_1200K", ("plain", "mix_bf16", "mix_fp16"), 20, 0, None),
+    ("cu_320_void", "cu_320_void", ("plain", "student_bf16_fallback"), 10, 96, 0.05),
 )
 
 
 def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, idx, stream, dev, local, ws,
-                     ablate=False):
-    """One form on one workload: forces of the start state on the sampled atoms, then `warmup` and
-    `steps` CUDA-graph MD steps, the latter timed with events on the library's stream while the SM
-    clock is sampled."""
+                     ablate=False, probe=None):
+    """One form on one workload: forces on the sampled atoms (of `probe` positions if given, else of
+    the start state), then `warmup` and `steps` CUDA-graph MD steps from the start state, the latter
+    timed with events on the library's stream while the SM clock is sampled."""
     import torch
     from paper_2604_24816_gb300 import NEP
     f = FORMS[form]
@@ -450,11 +462,13 @@ def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, i
              precision=f["precision"], max_neighbors=max_neighbors) as h:
         if f["fallback"]:
             h.set_fallback(teacher, student["q_lo"], student["q_hi"], margin=FALLBACK_MARGIN)
-        h.set_state(wl.pos, wl.vel, wl.box)
+        h.set_state(wl.pos if probe is None else probe, wl.vel, wl.box)
         Fd = torch.empty((wl.n, 3), dtype=torch.float64, device=dev)
         h.compute(out=Fd)
         F = Fd[torch.from_numpy(idx).to(dev)].cpu().numpy()
         del Fd
+        if probe is not None:
+            h.set_state(wl.pos, wl.vel, wl.box)
         h.step(wl.dt_fs, warmup)
         c0 = h.counters()
         clocks = ClockSampler(local)
@@ -493,18 +507,20 @@ def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, i
 
 def run_configs(teacher, student, args, stream, dev, local, ws) -> dict:
     """The larger workloads: every form of CONFIGS on its workload, throughput and force RMSE / max
-    against the plain float32 forces on 8,192 sampled atoms of the start state."""
+    against the plain float32 forces on 8,192 sampled atoms (of the start state or the probe state)."""
     import gc
     out = {}
-    for name, wname, forms, steps, cap in CONFIGS:
+    for name, wname, forms, steps, cap, probe_sigma in CONFIGS:
         t_gen = time.perf_counter()
         wl = ni.workload(wname)
+        probe = (None if probe_sigma is None else
+                 ni.gaussian_displace(wl.pos, wl.box, probe_sigma, np.random.default_rng(13)))
         t_gen = time.perf_counter() - t_gen
         idx = ni.sample_indices(wl.n, 8192, seed=11)
         recs = {}
         for form in forms:
             recs[form] = time_config_form(form, teacher, student, wl, steps, 3, cap, idx, stream, dev, local, ws,
-                                          ablate=name == "cu_160x160x160_1200K")
+                                          ablate=name == "cu_160x160x160_1200K", probe=probe)
         Fp = recs["plain"]["_F"]
         for form, rec in recs.items():
             d = rec.pop("_F") - Fp
@@ -513,8 +529,10 @@ def run_configs(teacher, student, args, stream, dev, local, ws) -> dict:
                 rec["force_max_vs_plain"] = float(np.abs(d).max())
                 rec["speedup_vs_plain"] = round(rec["value"] / recs["plain"]["value"], 4)
         out[name] = {"atoms": wl.n, "temperature_K": wl.temperature, "input_generation_s": round(t_gen, 1),
+                     "forces_compared_on": ("start state" if probe is None else
+                                            f"probe state: start positions + N(0, {probe_sigma}^2) A displacements"),
                      "forms": recs}
-        del wl
+        del wl, probe
         gc.collect()
     return out
 
@@ -718,7 +736,7 @@ def run_ours(args, rank: int, ws: int, local: int):
                    "l2": "inputs larger than L2: per-step algorithmic HBM traffic ~"
                          f"{n_rep * (BYTES['per_atom'] + BYTES['per_list_entry'] * walked) / 1e9:.2f} GB"
                          " (state, forces, positions, walked neighbour-list entries) vs 129 MB L2",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "model": "cu_nep4_synth (seeded)"},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roofline,
         "clocks": clk,
         "clocks_kernel_pass": clk_kernels,

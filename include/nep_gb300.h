@@ -268,7 +268,8 @@ nep_status nep_selftest_bounded_wait(int64_t polls, int *timed_out);
 /* FP32 throughput microbenchmark of the current device (a measurement aid with no paper counterpart;
  * it gives the denominator of the FP32 roofline the force kernels are reported against).  Every SM is
  * filled with resident blocks whose threads run 16 independent multiply-add chains: scalar FMAs
- * (packed = 0) or packed float2 FMAs, two per instruction (packed = 1).  Each launch is sized to about
+ * (packed = 0), packed float2 FMAs, two per instruction (packed = 1), or, for comparison with the
+ * 16-bit rate of the CUDA cores, packed half2 FMAs (packed = 2; any other value: NEP_ERR_ARG).  Each launch is sized to about
  * launch_ms (0 < launch_ms <= 1000) and timed with CUDA events on cuda_stream (NULL = legacy default
  * stream); after a calibration, `reps` launches (1..10000) are timed.  Outputs (host, may be NULL):
  * *best_tflops and *median_tflops = FLOP/s over the timed launches (FMA = 2 FLOP), in 10^12;

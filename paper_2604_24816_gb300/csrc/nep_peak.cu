@@ -3,7 +3,8 @@
 // It measures the denominator of the FP32 roofline that the force kernels are reported against: every
 // thread runs CHAINS independent multiply-add chains acc = acc * a + b for `iters` rounds, either as
 // scalar fused multiply-adds (one FMA per instruction) or as packed float2 ones (two FMAs per
-// instruction, the sm_100 family's paired FP32 form).  The grid fills every SM with as many resident
+// instruction, the sm_100 family's paired FP32 form); a third form runs packed half2 FMAs, for comparing
+// the 16-bit rate of the CUDA cores with the FP32 one.  The grid fills every SM with as many resident
 // blocks as fit, so the FMA pipes, not the issue slots or the occupancy, are the limit.  Arithmetic
 // performed = threads * iters * CHAINS * 2 FLOP (FMA = 2).  a and b are kernel arguments (no constant
 // folding), the chain converges to b / (1 - a) = 1 (no overflow, no denormals), and every thread stores
@@ -11,6 +12,7 @@
 // cycle counter (clock64) at the block's start and end; per SM, the span from its first block's start
 // to its last block's end gives the rate per SM clock (FMA per cycle per SM), which does not depend on
 // the clock frequency.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,14 +26,29 @@ constexpr int PEAK_BLOCK = 256;
 constexpr int PEAK_CHAINS = 16;   // independent accumulators per thread (float2 form: 8 pairs)
 constexpr int PEAK_UNROLL = 8;    // rounds per loop iteration (iters is a multiple of it)
 
-template <bool PACKED>
+// FORM 0: scalar float, 1: packed float2, 2: packed half2
+template <int FORM>
 __global__ void __launch_bounds__(PEAK_BLOCK) k_fp32_peak(float a, float b, long long rounds, float *out,
                                                           long long *cycles) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   __syncthreads();
   const long long c0 = clock64();
   float s = 0.f;
-  if constexpr (PACKED) {
+  if constexpr (FORM == 2) {
+    __half2 acc[PEAK_CHAINS / 2];
+#pragma unroll
+    for (int c = 0; c < PEAK_CHAINS / 2; ++c)
+      acc[c] = __floats2half2_rn(1e-3f * (float)(t & 255), 1e-3f * (float)c);
+    const __half2 a2 = __floats2half2_rn(a, a), b2 = __floats2half2_rn(b, b);
+    for (long long it = 0; it < rounds; ++it) {
+#pragma unroll
+      for (int u = 0; u < PEAK_UNROLL; ++u)
+#pragma unroll
+        for (int c = 0; c < PEAK_CHAINS / 2; ++c) acc[c] = __hfma2(acc[c], a2, b2);
+    }
+#pragma unroll
+    for (int c = 0; c < PEAK_CHAINS / 2; ++c) s += __low2float(acc[c]) + __high2float(acc[c]);
+  } else if constexpr (FORM == 1) {
     float2 acc[PEAK_CHAINS / 2];
 #pragma unroll
     for (int c = 0; c < PEAK_CHAINS / 2; ++c) acc[c] = make_float2(1e-3f * (float)(t & 255), 1e-3f * (float)c);
@@ -73,12 +90,15 @@ __global__ void __launch_bounds__(PEAK_BLOCK) k_fp32_peak(float a, float b, long
 extern "C" nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void *cuda_stream, double *best_tflops,
                                     double *median_tflops, double *fma_per_clock_sm, int *sm_count) {
   if (reps < 1 || reps > 10000 || !(launch_ms > 0.0 && launch_ms <= 1000.0)) return NEP_ERR_ARG;
+  if (packed < 0 || packed > 2) return NEP_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NEP_ERR_CUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return NEP_ERR_CUDA;
-  cudaError_t e = packed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<true>, PEAK_BLOCK, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<false>, PEAK_BLOCK, 0);
+  cudaError_t e =
+      packed == 2   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<2>, PEAK_BLOCK, 0)
+      : packed == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<1>, PEAK_BLOCK, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fp32_peak<0>, PEAK_BLOCK, 0);
   if (e != cudaSuccess || per_sm <= 0) return NEP_ERR_CUDA;
   const int grid = sms * per_sm;
   const long long threads = (long long)grid * PEAK_BLOCK;
@@ -95,10 +115,13 @@ extern "C" nep_status nep_fp32_peak(int packed, double launch_ms, int reps, void
   nep_status status = NEP_OK;
   std::vector<double> rate;
   auto launch = [&](long long rounds) {
-    if (packed)
-      k_fp32_peak<true><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out, cyc);
+    // half2: a = 0.75, b = 0.25 (exact in half precision; the chain converges to 1 as well)
+    if (packed == 2)
+      k_fp32_peak<2><<<grid, PEAK_BLOCK, 0, st>>>(0.75f, 0.25f, rounds, out, cyc);
+    else if (packed == 1)
+      k_fp32_peak<1><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out, cyc);
     else
-      k_fp32_peak<false><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out, cyc);
+      k_fp32_peak<0><<<grid, PEAK_BLOCK, 0, st>>>(0.9999f, 1e-4f, rounds, out, cyc);
   };
   auto timed = [&](long long rounds, float *ms) -> bool {
     if (cudaEventRecord(t0, st) != cudaSuccess) return false;

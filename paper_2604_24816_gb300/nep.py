@@ -299,13 +299,15 @@ class NEP:
         return flags[:self.n], int(cnt.value)
 
 
-def fp32_peak(packed: bool = True, launch_ms: float = 5.0, reps: int = 20, stream=None) -> dict:
-    """FP32 throughput of the current device (nep_fp32_peak): FMA chains on every SM, scalar or packed
-    float2.  Returns best and median TFLOP/s over `reps` launches, FMAs per SM clock cycle and the SM
-    count read from the device."""
+def fp32_peak(packed=True, launch_ms: float = 5.0, reps: int = 20, stream=None) -> dict:
+    """FP32 throughput of the current device (nep_fp32_peak): FMA chains on every SM, scalar
+    (packed=False), packed float2 (True) or packed half2 ("half2", the 16-bit comparison).  Returns best
+    and median TFLOP/s over `reps` launches, FMAs per SM clock cycle and the SM count read from the
+    device."""
     L = lib()
+    form = 2 if packed == "half2" else int(bool(packed))
     best, med, fpc, sms = C.c_double(0), C.c_double(0), C.c_double(0), C.c_int(0)
-    st = L.nep_fp32_peak(int(bool(packed)), float(launch_ms), int(reps), C.c_void_p(stream) if stream else None,
+    st = L.nep_fp32_peak(form, float(launch_ms), int(reps), C.c_void_p(stream) if stream else None,
                          C.byref(best), C.byref(med), C.byref(fpc), C.byref(sms))
     if st != 0:
         raise NepError(st, L.nep_status_string(st).decode(), "nep_fp32_peak failed")

@@ -468,7 +468,9 @@ def time_config_form(form, teacher, student, wl, steps, warmup, max_neighbors, i
         F = Fd[torch.from_numpy(idx).to(dev)].cpu().numpy()
         del Fd
         if probe is not None:
+            # back to the start state with a list built there (an upload keeps the probe state's list)
             h.set_state(wl.pos, wl.vel, wl.box)
+            h.build_neighbors()
         h.step(wl.dt_fs, warmup)
         c0 = h.counters()
         clocks = ClockSampler(local)

@@ -288,9 +288,9 @@ k_force_cpb(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
     fx += D0; fy += D1; fz += D2;
     long long ox, oy, oz;
     to_fix32x3(-D0, -D1, -D2, ox, oy, oz);
-    atomicAdd(Ffix + j, (unsigned long long)ox);
-    atomicAdd(Ffix + (size_t)n + j, (unsigned long long)oy);
-    atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)oz);
+    red_add(Ffix + j, ox);
+    red_add(Ffix + (size_t)n + j, oy);
+    red_add(Ffix + 2 * (size_t)n + j, oz);
     wxx = fmaf(dx, D0, wxx); wxy = fmaf(dx, D1, wxy); wxz = fmaf(dx, D2, wxz);
     wyy = fmaf(dy, D1, wyy); wyz = fmaf(dy, D2, wyz); wzz = fmaf(dz, D2, wzz);
   };
@@ -365,9 +365,9 @@ k_force_cpb(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
       if (fx != 0.f || fy != 0.f || fz != 0.f) {
         long long ox, oy, oz;
         to_fix32x3(fx, fy, fz, ox, oy, oz);
-        atomicAdd(Ffix + a, (unsigned long long)ox);
-        atomicAdd(Ffix + (size_t)n + a, (unsigned long long)oy);
-        atomicAdd(Ffix + 2 * (size_t)n + a, (unsigned long long)oz);
+        red_add(Ffix + a, ox);
+        red_add(Ffix + (size_t)n + a, oy);
+        red_add(Ffix + 2 * (size_t)n + a, oz);
       }
       if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
     }

@@ -567,4 +567,38 @@ struct NbrPipe {
   __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
 };
 
+// 64-bit integer add to global memory whose result nobody reads (the fixed-point force scatter): a
+// reduction, which returns nothing, so no register waits for the memory system (atomicAdd on a
+// generic pointer becomes a value-returning atomic).  Integer addition is associative, so the sums do
+// not depend on the order in which the additions arrive.
+__device__ __forceinline__ void red_add(unsigned long long *p, long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v));
+}
+
+// cp.async ring of pair records (16 bytes each, L2 only): record k of this thread is src[k * stride];
+// DQ records in flight, as NbrPipe's positions.
+template <int DQ, int BLOCK, int STRIDE>
+struct RecPipe {
+  float4 *rg;
+  const float4 *base;   // the record array (a kernel parameter)
+  unsigned off;         // element offset of record 0 of this thread
+  int cnt;
+  __device__ __forceinline__ void start(float4 *ring, const float4 *base_, unsigned off_, int cnt_) {
+    rg = ring + threadIdx.x; base = base_; off = off_; cnt = cnt_;
+#pragma unroll
+    for (int k = 0; k < DQ; ++k) {
+      if (k < cnt) cp_async16_cg(rg + k * BLOCK, base + (off + k * STRIDE));
+      cp_async_commit();
+    }
+  }
+  __device__ __forceinline__ float4 get(int k) {
+    cp_async_wait<DQ - 1>();
+    const float4 v = rg[(k % DQ) * BLOCK];
+    if (k + DQ < cnt) cp_async16_cg(rg + ((k + DQ) % DQ) * BLOCK, base + (off + (k + DQ) * STRIDE));
+    cp_async_commit();
+    return v;
+  }
+  __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
+};
+
 }  // namespace nep

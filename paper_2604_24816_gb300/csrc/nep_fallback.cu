@@ -187,17 +187,17 @@ k_fb_force(const __grid_constant__ Model<S> P, const Geom geom, const int n, con
       // D = dU_i/dd_ij: F_i += D, F_j -= D
       const float Dx = fmaf(coef, dx, vx), Dy = fmaf(coef, dy, vy), Dz = fmaf(coef, dz, vz);
       fx += Dx; fy += Dy; fz += Dz;
-      atomicAdd(Ffix + j, (unsigned long long)(-to_fix32(Dx)));
-      atomicAdd(Ffix + (size_t)n + j, (unsigned long long)(-to_fix32(Dy)));
-      atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)(-to_fix32(Dz)));
+      red_add(Ffix + j, -to_fix32(Dx));
+      red_add(Ffix + (size_t)n + j, -to_fix32(Dy));
+      red_add(Ffix + 2 * (size_t)n + j, -to_fix32(Dz));
       wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
       wyx = fmaf(dy, Dx, wyx); wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz);
       wzx = fmaf(dz, Dx, wzx); wzy = fmaf(dz, Dy, wzy); wzz = fmaf(dz, Dz, wzz);
     }
     pipe.finish();
-    atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
-    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
-    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
+    red_add(Ffix + i, to_fix32(fx));
+    red_add(Ffix + (size_t)n + i, to_fix32(fy));
+    red_add(Ffix + 2 * (size_t)n + i, to_fix32(fz));
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
     acc[0] -= to_fix32(wxx); acc[1] -= to_fix32(wxy); acc[2] -= to_fix32(wxz);
     acc[3] -= to_fix32(wyx); acc[4] -= to_fix32(wyy); acc[5] -= to_fix32(wyz);

@@ -34,6 +34,8 @@
 
 #include <type_traits>
 
+
+
 namespace nep {
 
 constexpr int DESC_BLOCK = 128;
@@ -53,7 +55,7 @@ constexpr int FORCE_BLOCK = NEP_FORCE_BLOCK;
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 constexpr int PIPE_DE = 8;    // list entries in flight per thread (descriptor kernel)
-constexpr int PIPE_DP = 4;    // neighbour positions in flight per thread (descriptor kernel)
+constexpr int PIPE_DP = 2;    // neighbour positions (and the fused force pass's records) in flight per thread
 constexpr int FPIPE_DE = 6;   // the same for the force kernel, whose pairs take longer
 constexpr int FPIPE_DP = 3;
 
@@ -410,9 +412,9 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
       if constexpr (FS) {
         atomicAdd(Ff + j, -Dx); atomicAdd(Ff + (size_t)n + j, -Dy); atomicAdd(Ff + 2 * (size_t)n + j, -Dz);
       } else {
-        atomicAdd(Ffix + j, (unsigned long long)(-to_fix32(Dx)));
-        atomicAdd(Ffix + (size_t)n + j, (unsigned long long)(-to_fix32(Dy)));
-        atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)(-to_fix32(Dz)));
+        red_add(Ffix + j, -to_fix32(Dx));
+        red_add(Ffix + (size_t)n + j, -to_fix32(Dy));
+        red_add(Ffix + 2 * (size_t)n + j, -to_fix32(Dz));
       }
       wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
       wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz); wzz = fmaf(dz, Dz, wzz);
@@ -423,9 +425,9 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
     if constexpr (FS) {
       atomicAdd(Ff + i, fx); atomicAdd(Ff + (size_t)n + i, fy); atomicAdd(Ff + 2 * (size_t)n + i, fz);
     } else {
-      atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
-      atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
-      atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
+      red_add(Ffix + i, to_fix32(fx));
+      red_add(Ffix + (size_t)n + i, to_fix32(fy));
+      red_add(Ffix + 2 * (size_t)n + i, to_fix32(fz));
     }
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
     // W = -sum over the evaluated pairs of r_ij (x) d_ij (or D_ij), upper triangle mirrored
@@ -435,32 +437,6 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
     if (COUNT) { acc[9] = cnt; acc[10] = nact; acc[11] = nrad; acc[12] = nang; }
   }
 }
-
-// cp.async ring of pair records (16 bytes each, L2 only): record k of this thread is src[k * stride];
-// DQ records in flight, as NbrPipe's positions.
-template <int DQ, int BLOCK, int STRIDE>
-struct RecPipe {
-  float4 *rg;
-  const float4 *base;   // the record array (a kernel parameter)
-  unsigned off;         // element offset of record 0 of this thread
-  int cnt;
-  __device__ __forceinline__ void start(float4 *ring, const float4 *base_, unsigned off_, int cnt_) {
-    rg = ring + threadIdx.x; base = base_; off = off_; cnt = cnt_;
-#pragma unroll
-    for (int k = 0; k < DQ; ++k) {
-      if (k < cnt) cp_async16_cg(rg + k * BLOCK, base + (off + k * STRIDE));
-      cp_async_commit();
-    }
-  }
-  __device__ __forceinline__ float4 get(int k) {
-    cp_async_wait<DQ - 1>();
-    const float4 v = rg[(k % DQ) * BLOCK];
-    if (k + DQ < cnt) cp_async16_cg(rg + ((k + DQ) % DQ) * BLOCK, base + (off + (k + DQ) * STRIDE));
-    cp_async_commit();
-    return v;
-  }
-  __device__ __forceinline__ void finish() { cp_async_wait<0>(); }
-};
 
 // Radial and LJ part of one active pair's force coefficient (d = coef * r_ij + angular part): the
 // radial adjoint in basis space (8 values in shared memory at fps[0], fps[FORCE_BLOCK]) against the
@@ -505,9 +481,9 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
     fx += Dx; fy += Dy; fz += Dz;
     long long ox, oy, oz;
     to_fix32x3(-Dx, -Dy, -Dz, ox, oy, oz);
-    atomicAdd(Ffix + j, (unsigned long long)ox);
-    atomicAdd(Ffix + (size_t)n + j, (unsigned long long)oy);
-    atomicAdd(Ffix + 2 * (size_t)n + j, (unsigned long long)oz);
+    red_add(Ffix + j, ox);
+    red_add(Ffix + (size_t)n + j, oy);
+    red_add(Ffix + 2 * (size_t)n + j, oz);
     wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
     wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz); wzz = fmaf(dz, Dz, wzz);
   };
@@ -548,9 +524,9 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
     pb.finish();
   }
   if (live) {
-    atomicAdd(Ffix + i, (unsigned long long)to_fix32(fx));
-    atomicAdd(Ffix + (size_t)n + i, (unsigned long long)to_fix32(fy));
-    atomicAdd(Ffix + 2 * (size_t)n + i, (unsigned long long)to_fix32(fz));
+    red_add(Ffix + i, to_fix32(fx));
+    red_add(Ffix + (size_t)n + i, to_fix32(fy));
+    red_add(Ffix + 2 * (size_t)n + i, to_fix32(fz));
     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(status, ST_NAN);
     acc[0] = -to_fix32(wxx); acc[1] = -to_fix32(wxy); acc[2] = -to_fix32(wxz);
     acc[3] = acc[1]; acc[4] = -to_fix32(wyy); acc[5] = -to_fix32(wyz);

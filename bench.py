@@ -90,10 +90,14 @@ FLOPS = {
 }
 # The same count for the student shape (4 + 4 channels, 8 basis functions, l = 1, 2, no 4-body term,
 # 16 neurons): register-resident sums, scalar channel dots (16 per channel), 8 harmonics (14),
-# network 888; its force runs over the half list.
+# network 888.  Its float32 form runs the fused kernel, whose force pass over the pair records costs per
+# angular pair: unit vector 3 + basis and derivative 102 + 2 x 4 channel dots 120 + harmonics 14 + the
+# sums A_lm, B_lm 128 + (A - l B / r) Y 32 + the l / r factors 8 + gradient polynomials 9 and their 14
+# non-zero FMAs 28 + 9; its mixed form runs the separate kernels with the force over the half list.
 FLOPS_STUDENT = {
     "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=186, atom=1145),
     "force": dict(list_entry=11, active_pair=23, radial_pair=126, lj_pair=17, angular_pair=511, atom=0),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=453, atom=0),
 }
 # Algorithmic HBM bytes per atom-step: the integrator reads and writes x, v (96) in the kick + drift and
 # v (48) in the second kick, and reads the forces in both kicks (48); the force kernel reads the atom's
@@ -104,8 +108,10 @@ BYTES = dict(per_atom=96 + 48 + 48 + 16 + 4 + 24, per_list_entry=4)
 
 def force_kind(form: str) -> str:
     """FLOP table of the force pass a form runs: the fused kernels' pass over their pair records for the
-    teacher (float32 or mixed-precision network), the half list for the student."""
-    return "force_rec" if FORMS[form]["model"] == "teacher" else "force"
+    teacher (float32 or mixed-precision network) and the float32 student, the half list for the
+    student's mixed-precision form."""
+    f = FORMS[form]
+    return "force_rec" if f["model"] == "teacher" or f["precision"] == "fp32" else "force"
 
 
 def descriptor_kind(form: str) -> str:
@@ -611,7 +617,8 @@ def run_ours(args, rank: int, ws: int, local: int):
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12
     kind = "fused" if fused else dominant
     traffic = profiled_traffic(kind if args.form == "plain" else f"{kind}:{args.form}")
-    dom_name = (("k_nep_fused" if args.form == "plain" else "k_nep_fused_mixed") if fused else
+    dom_name = (("k_nep_fused_reg" if FORMS[args.form]["model"] == "student" else
+                 "k_nep_fused" if args.form == "plain" else "k_nep_fused_mixed") if fused else
                 "k_descriptor_mixed" if dominant == "descriptor" and args.form != "plain" else f"k_{dominant}")
     pk_mhz, kn_mhz = peak["clocks"].get("sm_mhz"), clk_kernels.get("sm_mhz")
     roofline = {

@@ -32,7 +32,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
+            sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))) + [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:
@@ -47,8 +48,10 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    # register-usage-level 8 (ptxas default 5): the fused force kernel, register-bound at 128, measured
+    # 0.5 % faster
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                    "--expt-relaxed-constexpr"]
+                    "--expt-relaxed-constexpr", "-Xptxas", "--register-usage-level=8"]
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]
 

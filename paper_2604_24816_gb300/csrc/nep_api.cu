@@ -40,6 +40,10 @@ template <class S, class MT>
 cudaError_t launch_fused_mixed(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
                                float *, float *, long long *, long long *, long long *, int *, const PairCache &,
                                cudaStream_t);
+template <class S>
+cudaError_t launch_fused_reg(const Model<S> &, const Geom &, int, const float4 *, const int32_t *, const RowExt &,
+                             float *, float *, long long *, long long *, long long *, int *, const Fallback &,
+                             const PairCache &, cudaStream_t);
 cudaError_t pair_cache_sm_bound(int *nsm);
 size_t pair_cache_region_elems(int pmax);
 #ifndef NEP_FUSED
@@ -198,10 +202,10 @@ struct nep_handle {
   float *abl_f = nullptr, *abl_s = nullptr;
   int *abl_cnt = nullptr;
 
-  // pair records of the fused float32 kernel (allocated with the system for the float32 teacher)
+  // pair records of the fused kernels (allocated with the system for the teacher and the float32 student)
   float4 *pc_rec = nullptr;
   unsigned *pc_mask = nullptr;
-  int pc_nsm = 0;
+  int pc_nsm = 0, pc_slots = 0;         // SM index bound and record regions per SM index
 
   int ndes() const { return shape == 0 ? CuShape::NDES : StudentShape::NDES; }
   int gs() const { return shape == 0 ? CuShape::GS : StudentShape::GS; }
@@ -379,7 +383,7 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
       Scope sc(h, KC_FORCE, 1);
       cudaError_t e = cudaMemsetAsync(h->F, 0, 3 * (size_t)h->n * sizeof(long long), h->stream);
       if (e != cudaSuccess) return e;
-      const PairCache pc{h->pc_rec, h->pc_mask, h->pc_nsm, h->cap};
+      const PairCache pc{h->pc_rec, h->pc_mask, h->pc_nsm, h->cap, h->pc_slots};
       if (h->precision == NEP_FP32)
         return launch_fused<CuShape>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F, h->part_d,
                                      h->part_f, &h->ctrl->status, pc, h->stream);
@@ -398,6 +402,29 @@ cudaError_t forces_of(nep_handle *h, const Model<S> &M, float *qout) {
   }
   cudaError_t e;
   if (fb.on && (e = cudaMemsetAsync(h->fb_count, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
+  if constexpr (std::is_same<S, StudentShape>::value && NEP_FUSED) {
+    if (h->precision == NEP_FP32) {
+      // the student in float32: descriptors, network and full-row forces in one kernel (forces zeroed
+      // first), then the teacher on the flagged atoms
+      {
+        Scope sc(h, KC_FORCE, 1);
+        if ((e = cudaMemsetAsync(h->F, 0, 3 * (size_t)h->n * sizeof(long long), h->stream)) != cudaSuccess) return e;
+        const PairCache pc{h->pc_rec, h->pc_mask, h->pc_nsm, h->cap, h->pc_slots};
+        e = launch_fused_reg<StudentShape>(M, g, h->n, h->pos, h->nbr, rows_of(h), h->usite, qout, h->F, h->part_d,
+                                           h->part_f, &h->ctrl->status, fb, pc, h->stream);
+      }
+      if (e == cudaSuccess && fb.on) {
+        Scope sc(h, KC_FB, 2);
+        e = launch_fallback_descriptor<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list,
+                                                h->fb_count, h->fb_cap, h->fb_G, h->usite, h->part_d, h->counters,
+                                                &h->ctrl->status, h->stream);
+        if (e == cudaSuccess)
+          e = launch_fallback_force<CuShape>(h->fb_model, g, h->n, h->pos, h->nbr, h->nnum, h->fb_list, h->fb_count,
+                                             h->fb_cap, h->fb_G, h->F, h->part_f, &h->ctrl->status, h->stream);
+      }
+      return e;
+    }
+  }
   {
     Scope sc(h, KC_DESC, 1);
     if (h->precision == NEP_FP32)
@@ -825,13 +852,14 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   A(dalloc(h->part_d, (size_t)h->nb_d * 5 + 1)); A(dalloc(h->part_f, (size_t)h->nb_f * 13 + 1));
   A(dalloc(h->part_k, (size_t)h->nb_k + 1)); A(dalloc(h->io, 6 * N));
   if (h->fb_on) A(alloc_fallback(h));
-  if (h->shape == 0 && e == cudaSuccess) {
-    // pair records of the fused kernel: PC_SLOTS regions per SM index, list capacity records per atom
+  if (e == cudaSuccess && (h->shape == 0 || h->precision == NEP_FP32)) {
+    // pair records of the fused kernels: pc_slots regions per SM index, list capacity records per atom
+    h->pc_slots = h->shape == 0 ? PC_SLOTS : PC_SLOTS_REG;
     A(pair_cache_sm_bound(&h->pc_nsm));
-    // record offsets are 32-bit: nsm * PC_SLOTS * cap (<= 128) * 128 < 2^32 for nsm <= 4096
+    // record offsets are 32-bit: nsm * slots (<= 8) * cap (<= 128) * 128 < 2^32 for nsm <= 4096
     if (e == cudaSuccess && (h->pc_nsm <= 0 || h->pc_nsm > 4096)) e = cudaErrorInvalidValue;
     if (e == cudaSuccess) {
-      A(dalloc(h->pc_rec, (size_t)h->pc_nsm * PC_SLOTS * pair_cache_region_elems(h->cap)));
+      A(dalloc(h->pc_rec, (size_t)h->pc_nsm * h->pc_slots * pair_cache_region_elems(h->cap)));
       A(dalloc(h->pc_mask, (size_t)h->pc_nsm));
       if (e == cudaSuccess) A(cudaMemsetAsync(h->pc_mask, 0, (size_t)h->pc_nsm * sizeof(unsigned), h->stream));
     }

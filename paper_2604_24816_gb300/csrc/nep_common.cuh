@@ -108,19 +108,24 @@ struct Model {
   float rmax2;   // max(rcR, lj_rc)^2
 };
 
-// Pair records of the fused float32 kernel: its descriptor walk stores every active pair's displacement
-// and neighbour index, and its force pass reads them back instead of walking the neighbour list again.
+// Pair records of the fused kernels: the descriptor walk stores every active pair's displacement and
+// neighbour index, and the force pass reads them back instead of walking the neighbour list again.
 // Each resident block owns one region [pmax][BLOCK] float4 of `rec`, chosen by the SM it runs on and a
-// free slot among that SM's PC_SLOTS (one bit each in slot_mask[sm]); at most PC_SLOTS blocks of the
-// kernel fit on an SM (each holds 512 / PC_SLOTS of the SM's tensor-memory columns), so a slot is always
-// free for a starting block.  Regions are reused block after block, so their lines stay in L2.
+// free slot among that SM's `slots` (one bit each in slot_mask[sm]).  The teacher's fused kernels use
+// PC_SLOTS: at most that many of their blocks fit on an SM (each holds 512 / PC_SLOTS of the SM's
+// tensor-memory columns); the student's register-resident fused kernel uses PC_SLOTS_REG, checked on
+// the host against its occupancy.  So a slot is always free for a starting block.  Regions are reused
+// block after block, so their lines stay in L2.
 constexpr int PC_SLOTS = 4;
+constexpr int PC_SLOTS_REG = 8;
 struct PairCache {
-  float4 *rec;           // [nsm * PC_SLOTS][pmax][BLOCK]
+  float4 *rec;           // [nsm * slots][pmax][BLOCK]
   unsigned *slot_mask;   // [nsm], zero-initialised; bit b: slot b of that SM is held
   int nsm;               // bound on the SM index (%nsmid)
   int pmax;              // records per atom: >= the neighbour-list capacity
+  int slots;             // regions per SM index
 };
+
 __device__ __forceinline__ unsigned sm_index() {
   unsigned r;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
@@ -130,6 +135,20 @@ __device__ __forceinline__ unsigned sm_index_bound() {
   unsigned r;
   asm volatile("mov.u32 %0, %%nsmid;" : "=r"(r));
   return r;
+}
+
+// A free pair-record region of this SM for the calling block (one thread calls it): sm * slots + b, or
+// -1 after 64 rounds over the SM's slots (the caller reports that; it cannot happen while no more than
+// `slots` blocks of the kernel are resident on an SM).
+__device__ __forceinline__ int acquire_record_slot(const PairCache &pc) {
+  const unsigned sm = sm_index();
+  int slot = -1;
+  if ((int)sm < pc.nsm) {
+    for (int it = 0; it < 64 && slot < 0; ++it)
+      for (int b = 0; b < pc.slots && slot < 0; ++b)
+        if ((atomicOr(pc.slot_mask + sm, 1u << b) & (1u << b)) == 0u) slot = (int)sm * pc.slots + b;
+  }
+  return slot;
 }
 
 // Cell geometry of the current neighbour list.

@@ -91,11 +91,14 @@ struct AtomSums {
   int nrad, nang, nact, cnt;
 };
 
-// Walk atom i's full neighbour row and accumulate q_n, s_nlm and the LJ energy.
-template <class S, int DE, int DP, int BLOCK>
+// Walk atom i's full neighbour row and accumulate q_n, s_nlm and the LJ energy.  REC: every active pair
+// is also recorded as (dx, dy, dz, j) at rec[off + slot * BLOCK], angular pairs from slot 0 up and the
+// other active pairs from slot pmax - 1 down (the layout of accumulate_atom_tm's records).
+template <class S, int DE, int DP, int BLOCK, bool REC = false>
 __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 *shift, int i, int n,
                                                 const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
-                                                RowSpan sp, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A) {
+                                                RowSpan sp, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A,
+                                                float4 *__restrict__ rec = nullptr, unsigned off = 0, int pmax = 0) {
   const int cnt = sp.c;
   const float4 pi = pos[i];
 #pragma unroll
@@ -116,6 +119,10 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
     const float dx = pj.x - pi.x + o.x, dy = pj.y - pi.y + o.y, dz = pj.z - pi.z + o.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= P.rmax2) continue;
+    if constexpr (REC) {
+      const int slot = r2 < P.rcA2 ? A.nang : pmax - 1 - (A.nact - A.nang);
+      rec[off + (unsigned)slot * BLOCK] = make_float4(dx, dy, dz, __int_as_float((int)(e & J_MASK)));
+    }
     ++A.nact;
     const float ir = rsqrtf(r2);
     const float r = r2 * ir;

@@ -468,12 +468,14 @@ __device__ __forceinline__ float radial_lj_coef(const Model<S> &P, const float4 
 // force_pairs<S, float, false, true> on the displacement the descriptor walk computed: d_ij added to F_i,
 // subtracted from F_j (fixed point), W -= r_ij (x) d_ij (upper triangle, mirrored).
 template <class S, int DQ>
-__device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow, const float4 *fps, int i, bool live,
+__device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow,
+                                                const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
+                                                const float4 *fps, int i, bool live,
                                                 int n, const float4 *rec, unsigned off, int pmax, int na, int nr,
                                                 float4 *ring,
                                                 unsigned long long *__restrict__ Ffix, int *__restrict__ status,
                                                 long long (&acc)[13]) {
-  static_assert(ForceCfg<S>::TM, "teacher shape");
+  constexpr bool TM = ForceCfg<S>::TM;
   float fx = 0.f, fy = 0.f, fz = 0.f;
   float wxx = 0.f, wxy = 0.f, wxz = 0.f, wyy = 0.f, wyz = 0.f, wzz = 0.f;
   auto apply = [&](float dx, float dy, float dz, int j, float coef, float vx, float vy, float vz) {
@@ -487,11 +489,11 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
     wxx = fmaf(dx, Dx, wxx); wxy = fmaf(dx, Dy, wxy); wxz = fmaf(dx, Dz, wxz);
     wyy = fmaf(dy, Dy, wyy); wyz = fmaf(dy, Dz, wyz); wzz = fmaf(dz, Dz, wzz);
   };
-  const float gi[1][1] = {{0.f}};
   {
     RecPipe<DQ, FORCE_BLOCK, FORCE_BLOCK> pa;
     pa.start(ring, rec, off, na);
-    const int trip = __reduce_max_sync(0xffffffffu, na);
+    // with the row in TMEM the loop runs to the warp's largest count (warp-collective reads)
+    const int trip = TM ? __reduce_max_sync(0xffffffffu, na) : na;
     for (int p = 0; p < trip; ++p) {
       const bool valid = p < na;
       float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -500,7 +502,7 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
       const float ir = rsqrtf(r2);
       const float r = r2 * ir;
       float coef = valid ? radial_lj_coef<S, true>(P, fps, r2, r, ir) : 0.f;
-      __syncwarp();
+      if constexpr (TM) __syncwarp();
       float2 al, gv[3];
       angular_pair<S, float, true>(P, trow, gi, static_cast<const float *>(nullptr), !valid, r, ir, q.x, q.y, q.z, al,
                                    gv);
@@ -661,13 +663,7 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   if (threadIdx.x < 32) tmem_alloc(&tmem_base, TCOLS);
   if (threadIdx.x == 0) {
     // one free pair-record slot of this SM (at most PC_SLOTS blocks of this kernel are resident here)
-    const unsigned sm = sm_index();
-    int slot = -1;
-    if ((int)sm < pc.nsm) {
-      for (int it = 0; it < 64 && slot < 0; ++it)
-        for (int b = 0; b < PC_SLOTS && slot < 0; ++b)
-          if ((atomicOr(pc.slot_mask + sm, 1u << b) & (1u << b)) == 0u) slot = (int)sm * PC_SLOTS + b;
-    }
+    const int slot = acquire_record_slot(pc);
     if (slot < 0) atomicOr(status, ST_SLOT);   // results of this evaluation are then reported invalid
     __threadfence();
     s_slot = slot;
@@ -740,8 +736,9 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);   // before the force pass: fewer live registers
 
   // forces: every active pair of the row with the own adjoint row, from the pair records
-  force_pairs_rec<S, PIPE_DP>(P, trow, fp_s + threadIdx.x, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang,
-                              ring_p, Ffix, status, acc_f);
+  const float gi[1][1] = {{0.f}};
+  force_pairs_rec<S, PIPE_DP>(P, trow, gi, fp_s + threadIdx.x, i, live, n, pc.rec, rec_off, pc.pmax, nang,
+                              nact - nang, ring_p, Ffix, status, acc_f);
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -750,8 +747,90 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   }
   if (threadIdx.x == 0 && slot >= 0) {
     __threadfence();          // this block's record reads are complete (cp.async waited, barrier above)
-    atomicAnd(pc.slot_mask + slot / PC_SLOTS, ~(1u << (slot % PC_SLOTS)));
+    atomicAnd(pc.slot_mask + slot / pc.slots, ~(1u << (slot % pc.slots)));
   }
+  block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
+}
+
+// The fused kernel for shapes whose per-atom row fits in registers (the distilled student: 4 x 8
+// angular sums, 32-value adjoint row): descriptors, network and full-row forces of 128 atoms per block
+// with no tensor memory, so every thread walks its own row (no warp-collective steps).  The descriptor
+// walk records the active pairs (PairCache, PC_SLOTS_REG regions per SM: the launch checks that no more
+// blocks are resident), the adjoint row stays in registers and the force pass reads the records.  With
+// the fallback on, an atom whose descriptors leave the training range is flagged as in k_descriptor
+// (zero adjoint row, LJ energy only), and the teacher kernels then add its own model's part.  Ffix is
+// zeroed by the caller before the launch.
+#ifndef NEP_FUSED_REG_MINB
+#define NEP_FUSED_REG_MINB 4
+#endif
+template <class S>
+__global__ void __launch_bounds__(DESC_BLOCK, NEP_FUSED_REG_MINB)
+k_nep_fused_reg(const __grid_constant__ Model<S> P, const Geom geom, const int n, const float4 *__restrict__ pos,
+                const int32_t *__restrict__ nbr, const RowExt X, float *__restrict__ usite,
+                float *__restrict__ qout, unsigned long long *__restrict__ Ffix, long long *__restrict__ part_d,
+                long long *__restrict__ part_f, int *__restrict__ status, const __grid_constant__ Fallback fb,
+                const PairCache pc) {
+  static_assert(!ForceCfg<S>::TM && DESC_BLOCK == FORCE_BLOCK, "register-resident rows");
+  __shared__ float4 shift[27];
+  __shared__ uint32_t ring_e[PIPE_DE * DESC_BLOCK];
+  __shared__ float4 ring_p[PIPE_DP * DESC_BLOCK];
+  __shared__ float4 fp_s[2 * DESC_BLOCK];
+  __shared__ int s_slot;
+  if (threadIdx.x == 0) {
+    const int slot = acquire_record_slot(pc);
+    if (slot < 0) atomicOr(status, ST_SLOT);   // results of this evaluation are then reported invalid
+    __threadfence();
+    s_slot = slot;
+  }
+  fill_shift_table(shift, geom);
+  __syncthreads();
+  const int slot = s_slot;
+  const unsigned rec_off = (unsigned)(slot < 0 ? 0 : slot) * (unsigned)pc.pmax * DESC_BLOCK + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  long long acc_d[5] = {0, 0, 0, 0, 0};
+  long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < n) {
+    AtomSums<S> A;
+    accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK, true>(P, shift, i, n, pos, nbr, full_row(X, i, skip_far(X)),
+                                                           ring_e, ring_p, A, pc.rec, rec_off, pc.pmax);
+    float q[S::NDES];
+    FourBody<S> T;
+    descriptors_of<S>(P, A, q, T);
+    if (qout != nullptr) {
+#pragma unroll
+      for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
+    }
+    const bool flagged = fb.on && out_of_range<S>(fb, P, q);
+    if (flagged) flag_atom(fb, i, status);
+    float Fp[S::NDES];
+    const float U = network<S>(P, q, flagged, Fp);   // flagged: no U_i from this model, Fp = 0
+    float gi[S::NA][S::NLM];
+#pragma unroll
+    for (int a = 0; a < S::NA; ++a) adjoint_channel<S>(a, A, T, Fp, gi[a]);
+    {
+      float tail[8];
+      radial_tail<S>(P, Fp, tail);
+      fp_s[threadIdx.x] = make_float4(tail[0], tail[1], tail[2], tail[3]);
+      fp_s[DESC_BLOCK + threadIdx.x] = make_float4(tail[4], tail[5], tail[6], tail[7]);
+    }
+    const float ui = flagged ? A.elj : U + A.elj;
+    usite[i] = ui;
+    if (!isfinite(ui)) atomicOr(status, ST_NAN);
+    acc_d[0] = to_fix32(ui);
+    acc_d[1] = A.nrad;
+    acc_d[2] = A.nang;
+    acc_d[3] = A.cnt;
+    acc_d[4] = A.nact;
+    acc_f[9] = A.cnt; acc_f[10] = A.nact; acc_f[11] = A.nrad; acc_f[12] = A.nang;
+    force_pairs_rec<S, PIPE_DP>(P, 0u, gi, fp_s + threadIdx.x, i, true, n, pc.rec, rec_off, pc.pmax, A.nang,
+                                A.nact - A.nang, ring_p, Ffix, status, acc_f);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && slot >= 0) {
+    __threadfence();          // this block's record reads are complete (cp.async waited, barrier above)
+    atomicAnd(pc.slot_mask + slot / pc.slots, ~(1u << (slot % pc.slots)));
+  }
+  block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);
   block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
 
@@ -805,13 +884,7 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
   }
   if (t == 0) {
     mbar_init(&mbar, 1);
-    const unsigned sm = sm_index();
-    int slot = -1;
-    if ((int)sm < pc.nsm) {
-      for (int it = 0; it < 64 && slot < 0; ++it)
-        for (int b = 0; b < PC_SLOTS && slot < 0; ++b)
-          if ((atomicOr(pc.slot_mask + sm, 1u << b) & (1u << b)) == 0u) slot = (int)sm * PC_SLOTS + b;
-    }
+    const int slot = acquire_record_slot(pc);
     if (slot < 0) atomicOr(status, ST_SLOT);
     __threadfence();
     s_slot = slot;
@@ -951,7 +1024,8 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
     acc_f[9] = cnt; acc_f[10] = nact; acc_f[11] = nrad; acc_f[12] = nang;
   }
   block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);
-  force_pairs_rec<S, PIPE_DP>(P, trow, fp_s + t, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang, ring_p,
+  const float gi[1][1] = {{0.f}};
+  force_pairs_rec<S, PIPE_DP>(P, trow, gi, fp_s + t, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang, ring_p,
                               Ffix, status, acc_f);
   tc_fence_before();
   __syncthreads();
@@ -961,7 +1035,7 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
   }
   if (t == 0 && slot >= 0) {
     __threadfence();
-    atomicAnd(pc.slot_mask + slot / PC_SLOTS, ~(1u << (slot % PC_SLOTS)));
+    atomicAnd(pc.slot_mask + slot / pc.slots, ~(1u << (slot % pc.slots)));
   }
   block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
@@ -1053,6 +1127,29 @@ cudaError_t launch_fused(const Model<S> &P, const Geom &g, int n, const float4 *
 template cudaError_t launch_fused<CuShape>(const Model<CuShape> &, const Geom &, int, const float4 *, const int32_t *,
                                            const RowExt &, float *, float *, long long *, long long *, long long *,
                                            int *, const PairCache &, cudaStream_t);
+
+// Fused evaluation of a register-resident shape (k_nep_fused_reg); Ffix must be zero.  Fails with
+// cudaErrorInvalidConfiguration if more blocks than PC_SLOTS_REG could be resident on an SM.
+template <class S>
+cudaError_t launch_fused_reg(const Model<S> &P, const Geom &g, int n, const float4 *pos, const int32_t *nbr,
+                             const RowExt &X, float *usite, float *qout, long long *Ffix, long long *part_d,
+                             long long *part_f, int *status, const Fallback &fb, const PairCache &pc,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nep_fused_reg<S>, DESC_BLOCK, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm > pc.slots) return cudaErrorInvalidConfiguration;
+  const int grid = (n + DESC_BLOCK - 1) / DESC_BLOCK;
+  k_nep_fused_reg<S><<<grid, DESC_BLOCK, 0, st>>>(P, g, n, pos, nbr, X, usite, qout,
+                                                  reinterpret_cast<unsigned long long *>(Ffix), part_d, part_f,
+                                                  status, fb, pc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fused_reg<StudentShape>(const Model<StudentShape> &, const Geom &, int, const float4 *,
+                                                    const int32_t *, const RowExt &, float *, float *, long long *,
+                                                    long long *, long long *, int *, const Fallback &,
+                                                    const PairCache &, cudaStream_t);
 
 // Mixed-precision fused evaluation of the teacher (k_nep_fused_mixed); Ffix must be zero.
 template <class S, class MT>

@@ -76,8 +76,13 @@ def test_flop_model_counts_units():
     r = bench.FLOPS["force_rec"]
     assert r["list_entry"] == 0 and r["active_pair"] == g["active_pair"] + 5
     assert all(r[k] == g[k] for k in ("radial_pair", "lj_pair", "angular_pair", "atom"))
-    assert all(bench.force_kind(f) == ("force_rec" if bench.FORMS[f]["model"] == "teacher" else "force")
-               for f in bench.FORMS)
+    assert all(bench.force_kind(f) == ("force_rec" if bench.FORMS[f]["model"] == "teacher" or
+                                       bench.FORMS[f]["precision"] == "fp32" else "force") for f in bench.FORMS)
+    # the student's fused kernel: its record pass has the teacher's per-pair terms except the angular
+    # one, whose channel sums scale with the 4 x 8 instead of 5 x 24 (l, m) components
+    rs, hs = bench.FLOPS_STUDENT["force_rec"], bench.FLOPS_STUDENT["force"]
+    assert all(rs[k] == r[k] for k in ("list_entry", "active_pair", "radial_pair", "lj_pair", "atom"))
+    assert 0.3 * r["angular_pair"] < rs["angular_pair"] < hs["angular_pair"]
     # the mixed forms' descriptor part differs only in the network (on the tensor cores)
     dm, dd = bench.FLOPS["descriptor_mixed"], bench.FLOPS["descriptor"]
     assert all(dm[k] == dd[k] for k in dd if k != "atom") and dm["atom"] < dd["atom"]

@@ -107,7 +107,9 @@ nep_status nep_destroy(nep_handle *h);
  * the next evaluation rebuilds the list only if an atom moved more than skin/2 from the positions it
  * was built for (the same test as between MD steps; positions are taken at their periodic image
  * nearest the previous ones).  Otherwise the neighbour list is invalidated.  n = 0 is accepted (every
- * later call is a no-op). */
+ * later call is a no-op).  x and v may be host or device memory; when the list is kept, device and
+ * page-locked host arrays are read by the GPU directly (other host arrays are copied first).  Returns
+ * after the upload has completed, so the caller may reuse the arrays. */
 nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double *v, const double *box);
 
 /* Build the cell list and the neighbour list (cutoff rc_R + skin) for the current positions:
@@ -128,7 +130,8 @@ nep_status nep_compute(nep_handle *h, double *E, double *F, double *virial);
 nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps);
 
 /* Copy positions (wrapped into the box) and velocities out, [n][3] each, original order; either may
- * be NULL. */
+ * be NULL.  Device arrays are written by the GPU directly, host arrays through a device staging
+ * buffer and copies (the two arrays' copies run concurrently); returns when the data is in place. */
 nep_status nep_get_state(nep_handle *h, double *x, double *v);
 
 /* Thermodynamics of the last force evaluation: out = {potential energy, kinetic energy,

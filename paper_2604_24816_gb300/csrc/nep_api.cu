@@ -93,6 +93,7 @@ cudaError_t launch_kick_drift(int, double *, double *, double *, double *, doubl
                               const float4 *, double, double, const double *, float, Control *, cudaStream_t);
 cudaError_t launch_control(Control *, bool, cudaStream_t);
 cudaError_t launch_control_check(Control *, cudaStream_t);
+cudaError_t launch_inverse_order(int, const int *, int *, cudaStream_t);
 cudaError_t launch_load_state_sorted(int, const double *, const double *, const int *, double *, double *, double *,
                                      double *, double *, double *, float4 *, const float4 *, const double *,
                                      const double *, float, Control *, cudaStream_t);
@@ -132,6 +133,8 @@ struct Timer {
 
 struct nep_handle {
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;            // second copy stream of nep_get_state (created on first use)
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
   bool own_stream = false;
   int shape = 0;                   // 0: teacher shape (CuShape), 1: student shape (StudentShape)
   Model<CuShape> model_t{};
@@ -204,6 +207,7 @@ struct nep_handle {
 
   // pair records of the fused kernels (allocated with the system for the teacher and the float32 student)
   float4 *pc_rec = nullptr;
+  int *inv = nullptr;                   // cell-order slot of each atom (filled by nep_set_state / nep_get_state)
   unsigned *pc_mask = nullptr;
   int pc_nsm = 0, pc_slots = 0;         // SM index bound and record regions per SM index
 
@@ -239,6 +243,19 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc / cudaHostRegister: kernels read and
+// write it directly), else nullptr.
+template <class T>
+T *pinned_alias(T *p) {
+  if (p == nullptr) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<T *>(a.devicePointer) : nullptr;
+}
+
 template <class T>
 void dfree(T *&p) {
   if (p) cudaFree((void *)p);
@@ -256,7 +273,7 @@ void free_system(nep_handle *h) {
   dfree(h->part_d); dfree(h->part_f); dfree(h->part_k); dfree(h->io); dfree(h->io_i);
   dfree(h->fb_list); dfree(h->fb_count); dfree(h->fb_G);
   dfree(h->abl_f); dfree(h->abl_s); dfree(h->abl_cnt);
-  dfree(h->pc_rec); dfree(h->pc_mask);
+  dfree(h->pc_rec); dfree(h->pc_mask); dfree(h->inv);
   h->pc_nsm = 0;
   h->fb_cap = 0;
   h->io_i_elems = 0;
@@ -608,19 +625,22 @@ nep_status upload_state_sorted(nep_handle *h, const double *x, const double *v) 
   h->have_forces = false;
   NEP_CUDA(h, cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int), h->stream));
   NEP_CUDA(h, cudaMemsetAsync(&h->ctrl->changed, 0, sizeof(int), h->stream));
+  // device arrays and page-locked host arrays are read by the kernel itself (in the caller's order,
+  // contiguously); other host arrays are copied to the device first
   const double *xs = x, *vs = v;
-  if (!is_device_ptr(x)) {
+  if (!is_device_ptr(x) && !(xs = pinned_alias(x))) {
     NEP_CUDA(h, cudaMemcpyAsync(h->io, x, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     xs = h->io;
   }
-  if (v && !is_device_ptr(v)) {
+  if (v && !is_device_ptr(v) && !(vs = pinned_alias(v))) {
     NEP_CUDA(h, cudaMemcpyAsync(h->io + 3 * N, v, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     vs = h->io + 3 * N;
   }
   const float hs = 0.5f * h->skin;
   {
-    Scope sc(h, KC_OTHER, 1);
-    NEP_CUDA(h, launch_load_state_sorted(h->n, xs, vs, h->id, h->x, h->y, h->z, h->vx, h->vy, h->vz, h->pos,
+    Scope sc(h, KC_OTHER, 2);
+    NEP_CUDA(h, launch_inverse_order(h->n, h->id, h->inv, h->stream));
+    NEP_CUDA(h, launch_load_state_sorted(h->n, xs, vs, h->inv, h->x, h->y, h->z, h->vx, h->vy, h->vz, h->pos,
                                          h->pos_ref, h->l, h->L, hs * hs, h->ctrl, h->stream));
   }
   h->recheck = true;
@@ -793,6 +813,9 @@ nep_status nep_destroy(nep_handle *h) {
   if (h->h_counters) cudaFreeHost(h->h_counters);
   for (auto &t : h->timers) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   if (h->done) cudaEventDestroy(h->done);
+  for (cudaEvent_t ev : h->aux_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (h->aux) cudaStreamDestroy(h->aux);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return NEP_OK;
@@ -841,7 +864,7 @@ nep_status nep_set_state(nep_handle *h, int64_t n, const double *x, const double
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(dalloc(h->x, N)); A(dalloc(h->y, N)); A(dalloc(h->z, N)); A(dalloc(h->vx, N)); A(dalloc(h->vy, N)); A(dalloc(h->vz, N));
   A(dalloc(h->xb, N)); A(dalloc(h->yb, N)); A(dalloc(h->zb, N)); A(dalloc(h->vxb, N)); A(dalloc(h->vyb, N)); A(dalloc(h->vzb, N));
-  A(dalloc(h->id, N)); A(dalloc(h->idb, N)); A(dalloc(h->cell_of, N)); A(dalloc(h->perm, N));
+  A(dalloc(h->id, N)); A(dalloc(h->idb, N)); A(dalloc(h->cell_of, N)); A(dalloc(h->perm, N)); A(dalloc(h->inv, N));
   A(dalloc(h->pos, N)); A(dalloc(h->pos_ref, N));
   A(dalloc(h->F, 3 * N)); A(dalloc(h->usite, N));
   A(dalloc(reinterpret_cast<char *&>(h->G), N * (size_t)h->gs() * (h->precision == NEP_FP32 ? 4 : 2)));
@@ -940,22 +963,42 @@ nep_status nep_get_state(nep_handle *h, double *x, double *v) {
   if (!h) return NEP_ERR_ARG;
   if (!h->have_state) return fail(h, NEP_ERR_STATE, "nep_set_state has not been called");
   if (h->n == 0) return NEP_OK;
-  const size_t bytes = 3 * (size_t)h->n * sizeof(double);
+  const size_t N3 = 3 * (size_t)h->n;
+  {
+    Scope sc(h, KC_OTHER, 1);
+    NEP_CUDA(h, launch_inverse_order(h->n, h->id, h->inv, h->stream));
+  }
+  // device arrays are written by the kernel itself; host arrays through the staging buffer and a copy
+  // (kernel stores into page-locked host memory measured slower than the copy engines).  The positions'
+  // copy runs on a second stream, beside the velocities' store and copy.
+  if (!h->aux) {
+    NEP_CUDA(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    NEP_CUDA(h, cudaEventCreateWithFlags(&h->aux_ev[0], cudaEventDisableTiming));
+    NEP_CUDA(h, cudaEventCreateWithFlags(&h->aux_ev[1], cudaEventDisableTiming));
+  }
+  bool aux_used = false;
   for (int which = 0; which < 2; ++which) {
     double *out = which == 0 ? x : v;
     if (!out) continue;
     const bool dev = is_device_ptr(out);
+    double *stage = dev ? out : h->io + which * N3;
     {
       Scope sc(h, KC_OTHER, 1);
-      if (which == 0) NEP_CUDA(h, launch_store_vec(h->n, h->id, h->x, h->y, h->z, h->L, 1, dev ? out : h->io, h->stream));
-      else NEP_CUDA(h, launch_store_vec(h->n, h->id, h->vx, h->vy, h->vz, h->L, 0, dev ? out : h->io, h->stream));
+      if (which == 0) NEP_CUDA(h, launch_store_vec(h->n, h->inv, h->x, h->y, h->z, h->L, 1, stage, h->stream));
+      else NEP_CUDA(h, launch_store_vec(h->n, h->inv, h->vx, h->vy, h->vz, h->L, 0, stage, h->stream));
     }
-    if (!dev) {
-      NEP_CUDA(h, cudaMemcpyAsync(out, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
-      nep_status s = wait_stream(h);
-      if (s != NEP_OK) return s;
+    if (dev) continue;
+    if (which == 0) {
+      NEP_CUDA(h, cudaEventRecord(h->aux_ev[0], h->stream));
+      NEP_CUDA(h, cudaStreamWaitEvent(h->aux, h->aux_ev[0], 0));
+      NEP_CUDA(h, cudaMemcpyAsync(out, stage, N3 * sizeof(double), cudaMemcpyDeviceToHost, h->aux));
+      NEP_CUDA(h, cudaEventRecord(h->aux_ev[1], h->aux));
+      aux_used = true;
+    } else {
+      NEP_CUDA(h, cudaMemcpyAsync(out, stage, N3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     }
   }
+  if (aux_used) NEP_CUDA(h, cudaStreamWaitEvent(h->stream, h->aux_ev[1], 0));
   return wait_stream(h);
 }
 

@@ -759,9 +759,10 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
 // blocks are resident), the adjoint row stays in registers and the force pass reads the records.  With
 // the fallback on, an atom whose descriptors leave the training range is flagged as in k_descriptor
 // (zero adjoint row, LJ energy only), and the teacher kernels then add its own model's part.  Ffix is
-// zeroed by the caller before the launch.
+// zeroed by the caller before the launch.  Five resident blocks (at most 102 registers) measured 4 %
+// faster than four.
 #ifndef NEP_FUSED_REG_MINB
-#define NEP_FUSED_REG_MINB 4
+#define NEP_FUSED_REG_MINB 5
 #endif
 template <class S>
 __global__ void __launch_bounds__(DESC_BLOCK, NEP_FUSED_REG_MINB)

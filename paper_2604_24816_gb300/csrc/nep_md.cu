@@ -190,17 +190,26 @@ __global__ void k_load_state(int n, const double *__restrict__ xin, const double
 // position (so the cell-relative coordinate stays continuous, as between rebuilds), the cell-relative
 // float32 coordinate is refreshed in the slot's cell, and an atom that moved more than skin/2 from
 // the positions the list was built for sets ctrl->moved (the next evaluation then rebuilds).
+// inv[id[s]] = s: the cell-order slot of every atom (original order).
+__global__ void k_inverse_order(int n, const int *__restrict__ id, int *__restrict__ inv) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) inv[id[s]] = s;
+}
+
+// One thread per atom in the caller's order (i; its slot s = inv[i]), so that the reads of xin and vin
+// are contiguous: they may live in host memory that the kernel reads directly.
 __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const double *__restrict__ vin,
-                                    const int *__restrict__ id, double *__restrict__ x, double *__restrict__ y,
+                                    const int *__restrict__ inv, double *__restrict__ x, double *__restrict__ y,
                                     double *__restrict__ z, double *__restrict__ vx, double *__restrict__ vy,
                                     double *__restrict__ vz, float4 *__restrict__ pos,
                                     const float4 *__restrict__ pos_ref, double lx, double ly, double lz, double Lx,
                                     double Ly, double Lz, float half_skin2, Control *ctrl) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool moved = false, changed = false;
   float dd = 0.f;
-  if (s < n) {
-    const size_t o = 3 * (size_t)id[s];
+  if (i < n) {
+    const int s = inv[i];
+    const size_t o = 3 * (size_t)i;
     double a = xin[o], b = xin[o + 1], c = xin[o + 2];
     if (!(isfinite(a) && isfinite(b) && isfinite(c))) {
       atomicOr(&ctrl->status, ST_NAN);
@@ -235,18 +244,20 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
 }
 
 // Sorted SoA -> original-order [n][3] float64 (positions wrapped into the box when L != nullptr).
-__global__ void k_store_vec(int n, const int *__restrict__ id, const double *__restrict__ a, const double *__restrict__ b,
+// One thread per atom in the caller's order (contiguous writes: out may be host memory).
+__global__ void k_store_vec(int n, const int *__restrict__ inv, const double *__restrict__ a, const double *__restrict__ b,
                             const double *__restrict__ c, double Lx, double Ly, double Lz, int wrap,
                             double *__restrict__ out) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = inv[i];
   double u = a[s], v = b[s], w = c[s];
   if (wrap) {
     u -= Lx * floor(u / Lx); if (u >= Lx) u -= Lx;
     v -= Ly * floor(v / Ly); if (v >= Ly) v -= Ly;
     w -= Lz * floor(w / Lz); if (w >= Lz) w -= Lz;
   }
-  const size_t o = 3 * (size_t)id[s];
+  const size_t o = 3 * (size_t)i;
   out[o] = u; out[o + 1] = v; out[o + 2] = w;
 }
 
@@ -339,19 +350,24 @@ cudaError_t launch_control_check(Control *ctrl, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_load_state_sorted(int n, const double *xin, const double *vin, const int *id, double *x, double *y,
+cudaError_t launch_inverse_order(int n, const int *id, int *inv, cudaStream_t st) {
+  if (n > 0) k_inverse_order<<<bl(n, 256), 256, 0, st>>>(n, id, inv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_state_sorted(int n, const double *xin, const double *vin, const int *inv, double *x, double *y,
                                      double *z, double *vx, double *vy, double *vz, float4 *pos, const float4 *pos_ref,
                                      const double l[3], const double L[3], float half_skin2, Control *ctrl,
                                      cudaStream_t st) {
   if (n > 0)
-    k_load_state_sorted<<<bl(n, 256), 256, 0, st>>>(n, xin, vin, id, x, y, z, vx, vy, vz, pos, pos_ref, l[0], l[1],
+    k_load_state_sorted<<<bl(n, 256), 256, 0, st>>>(n, xin, vin, inv, x, y, z, vx, vy, vz, pos, pos_ref, l[0], l[1],
                                                     l[2], L[0], L[1], L[2], half_skin2, ctrl);
   return cudaGetLastError();
 }
 
-cudaError_t launch_store_vec(int n, const int *id, const double *a, const double *b, const double *c, const double L[3],
+cudaError_t launch_store_vec(int n, const int *inv, const double *a, const double *b, const double *c, const double L[3],
                              int wrap, double *out, cudaStream_t st) {
-  if (n > 0) k_store_vec<<<bl(n, 256), 256, 0, st>>>(n, id, a, b, c, L[0], L[1], L[2], wrap, out);
+  if (n > 0) k_store_vec<<<bl(n, 256), 256, 0, st>>>(n, inv, a, b, c, L[0], L[1], L[2], wrap, out);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,7 @@ KERNEL_SOURCES = {
     "fused": ("nep_force.cu",) + _CORE,
     "fused:mix_bf16": ("nep_force.cu",) + _CORE,
     "fused:mix_fp16": ("nep_force.cu",) + _CORE,
+    "fused:student": ("nep_force.cu",) + _CORE,
     "descriptor:student_bf16_fallback": ("nep_mixed.cu", "nep_fallback.cu") + _CORE,
     "force:student_bf16_fallback": ("nep_force.cu", "nep_fallback.cu") + _CORE,
 }

@@ -2,7 +2,7 @@
 """NEP molecular-dynamics throughput on GB300: atom-steps/s of plain FP32 NEP-MD.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
-                    [--form plain|mix_bf16|mix_fp16|student|student_bf16_fallback] [--no-configs]
+                    [--form plain|mix_bf16|mix_fp16|student|student_bf16_fallback|student_fallback] [--no-configs]
 
 One step = one velocity-Verlet MD step of the whole hot path on the 1,048,576-atom fcc Cu workload
 (64x64x64 cells, 300 K, 1 fs): half kick + drift, neighbour-rebuild check (a rebuild runs every 10
@@ -398,6 +398,9 @@ FORMS = {
     "student_bf16_fallback": dict(precision="mix_bf16", model="student", fallback=True, dtype="bf16/f32",
                                   desc="distilled student NEP, " + _MIX_STUDENT.format("bf16") + "; per-atom fallback to the "
                                        "FP32 teacher for atoms outside the student's training range (5 % margin)"),
+    "student_fallback": dict(precision="fp32", model="student", fallback=True, dtype="f32",
+                             desc="distilled student NEP, FP32 (one fused kernel); per-atom fallback to the FP32 teacher "
+                                  "for atoms outside the student's training range (5 % margin)"),
 }
 FALLBACK_MARGIN = 0.05
 STUDENT_PATH = os.path.join(ROOT, "paper_2604_24816_gb300", "params", "cu_student_trained.json")
@@ -453,7 +456,7 @@ def time_form(form, teacher, student, wl, args, stream, dev, ws, atoms_total):
 CONFIGS = (
     ("cu_160x160x160", "cu_160x160x160", ("plain", "mix_bf16", "mix_fp16"), 20, 0, None),
     ("cu_160x160x160_1200K", "cu_160x160x160_1200K", ("plain", "mix_bf16", "mix_fp16"), 20, 0, None),
-    ("cu_320_void", "cu_320_void", ("plain", "student_bf16_fallback"), 10, 96, 0.05),
+    ("cu_320_void", "cu_320_void", ("plain", "student_bf16_fallback", "student_fallback"), 10, 96, 0.05),
 )
 
 

@@ -480,6 +480,32 @@ __device__ __forceinline__ void block_sum_store(long long (&v)[NV], long long *o
   }
 }
 
+// block_sum_store in two halves, so that no block barrier is needed where the values become known:
+// warp_sum_stage adds the warp's NV int64 values (lane 0 writes them to dst[0..NV-1]); after a later
+// block barrier, block_store_staged adds the staged sums of the block's warps into
+// out[blockIdx.x * NV + v].  Integer sums: the result does not depend on the order.
+template <int NV>
+__device__ __forceinline__ void warp_sum_stage(long long (&v)[NV], long long *dst) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) dst[k] = v[k];
+  }
+}
+template <int NV, int NW>
+__device__ __forceinline__ void block_store_staged(const long long (*src)[NV], long long *out) {
+  if (threadIdx.x < NV) {
+    long long t = 0;
+    const int nw = min(NW, (int)(blockDim.x >> 5));
+    for (int w = 0; w < nw; ++w) t += src[w][threadIdx.x];
+    out[(size_t)blockIdx.x * NV + threadIdx.x] = t;
+  }
+}
+
 
 // ---------------------------------------------------------------------------------------------------
 // Asynchronous per-thread neighbour pipeline (cp.async into shared memory).  The walk over an atom's

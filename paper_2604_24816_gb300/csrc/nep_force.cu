@@ -733,7 +733,10 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
     // the force pass visits the descriptor walk's active pairs
     acc_f[9] = cnt; acc_f[10] = nact; acc_f[11] = nrad; acc_f[12] = nang;
   }
-  block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);   // before the force pass: fewer live registers
+  // the energy and counters: summed over the warp now (fewer live registers in the force pass), over
+  // the block after the closing barrier
+  __shared__ long long wsum_d[DESC_BLOCK / 32][5];
+  warp_sum_stage<5>(acc_d, wsum_d[threadIdx.x >> 5]);
 
   // forces: every active pair of the row with the own adjoint row, from the pair records
   const float gi[1][1] = {{0.f}};
@@ -749,6 +752,7 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
     __threadfence();          // this block's record reads are complete (cp.async waited, barrier above)
     atomicAnd(pc.slot_mask + slot / pc.slots, ~(1u << (slot % pc.slots)));
   }
+  block_store_staged<5, DESC_BLOCK / 32>(wsum_d, part_d);
   block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
 
@@ -1024,7 +1028,8 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
     acc_d[4] = nact;
     acc_f[9] = cnt; acc_f[10] = nact; acc_f[11] = nrad; acc_f[12] = nang;
   }
-  block_sum_store<5, DESC_BLOCK / 32>(acc_d, part_d);
+  __shared__ long long wsum_d[DESC_BLOCK / 32][5];
+  warp_sum_stage<5>(acc_d, wsum_d[t >> 5]);
   const float gi[1][1] = {{0.f}};
   force_pairs_rec<S, PIPE_DP>(P, trow, gi, fp_s + t, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang, ring_p,
                               Ffix, status, acc_f);
@@ -1038,6 +1043,7 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
     __threadfence();
     atomicAnd(pc.slot_mask + slot / pc.slots, ~(1u << (slot % pc.slots)));
   }
+  block_store_staged<5, DESC_BLOCK / 32>(wsum_d, part_d);
   block_sum_store<13, DESC_BLOCK / 32>(acc_f, part_f);
 }
 

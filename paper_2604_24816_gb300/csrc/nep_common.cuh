@@ -264,6 +264,32 @@ __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K
   }
 }
 
+// The basis derivatives f_k'(r) of cheb_basis_d for two radii at once (the values f_k are not formed).
+template <int K>
+__device__ __forceinline__ void cheb_dbasis_x2(float2 r, float inv_rc, float2 (&df)[K]) {
+  static_assert(K >= 2, "basis size");
+  float2 s, cs;
+  const float2 t = mul2(r, bc2(inv_rc));
+  __sincosf(3.14159265358979f * t.x, &s.x, &cs.x);
+  __sincosf(3.14159265358979f * t.y, &s.y, &cs.y);
+  const float2 h = mul2(fma2(bc2(0.5f), cs, bc2(0.5f)), bc2(0.5f));                 // fc / 2
+  const float2 dh = mul2(bc2(-0.25f * 3.14159265358979f * inv_rc), s);              // fc' / 2
+  const float2 u = add2(t, bc2(-1.f));
+  const float2 x = fma2(mul2(bc2(2.f), u), u, bc2(-1.f));
+  const float2 x2 = add2(x, x);
+  const float2 dxh = mul2(mul2(bc2(4.f * inv_rc), u), h);                           // x'(r) h
+  float2 T[K], D[K];
+  T[0] = bc2(1.f); T[1] = x;
+  D[0] = bc2(0.f); D[1] = bc2(1.f);
+#pragma unroll
+  for (int k = 2; k < K; ++k) {
+    T[k] = fma2(x2, T[k - 1], make_float2(-T[k - 2].x, -T[k - 2].y));
+    D[k] = fma2(x2, D[k - 1], fma2(bc2(2.f), T[k - 1], make_float2(-D[k - 2].x, -D[k - 2].y)));
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) df[k] = fma2(D[k], dxh, fma2(T[k], dh, dh));
+}
+
 // Normalised real harmonics Yh_lm(u) = sqrt(4 pi / (2l+1)) Y_lm(u), l = 1..4 (24 values, m = -l..l),
 // so that sum_m Yh_lm(u) Yh_lm(v) = P_l(u . v).  Written as solid-harmonic polynomials of a unit vector.
 // NLM = 8 computes l = 1, 2 only.
@@ -395,6 +421,16 @@ __device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, fl
   const float a12 = P.lj_c12 * ir6 * ir6, a6 = P.lj_c6 * ir6;
   e = a12 - a6 - P.lj_e_rc - (r - P.lj_rc) * P.lj_de_rc;
   de = fmaf(-12.f, a12, 6.f * a6) * ir - P.lj_de_rc;
+}
+
+// lj_pair's derivative dE/dr for two pairs at once.
+template <class S>
+__device__ __forceinline__ float2 lj_deriv_x2(const Model<S> &P, float2 r2, float2 ir) {
+  float2 ir2 = mul2(ir, ir);
+  ir2 = fma2(ir2, fma2(make_float2(-r2.x, -r2.y), ir2, bc2(1.f)), ir2);
+  const float2 ir6 = mul2(mul2(ir2, ir2), ir2);
+  const float2 a12 = mul2(mul2(bc2(P.lj_c12), ir6), ir6), a6 = mul2(bc2(P.lj_c6), ir6);
+  return fma2(fma2(bc2(-12.f), a12, mul2(bc2(6.f), a6)), ir, bc2(-P.lj_de_rc));
 }
 
 // Exact conversion of a float to 64-bit fixed point with 32 fractional bits, without a 64-bit

@@ -92,6 +92,7 @@ int md_blocks(int n);
 cudaError_t launch_kick_drift(int, double *, double *, double *, double *, double *, double *, const long long *, float4 *,
                               const float4 *, double, double, const double *, float, Control *, cudaStream_t);
 cudaError_t launch_control(Control *, bool, cudaStream_t);
+cudaError_t launch_control_cond(Control *, cudaGraphConditionalHandle, cudaStream_t);
 cudaError_t launch_control_check(Control *, cudaStream_t);
 cudaError_t launch_inverse_order(int, const int *, int *, cudaStream_t);
 cudaError_t launch_load_state_sorted(int, const double *, const double *, const int *, double *, double *, double *,
@@ -133,7 +134,8 @@ struct Timer {
 
 struct nep_handle {
   cudaStream_t stream = nullptr;
-  cudaStream_t aux = nullptr;            // second copy stream of nep_get_state (created on first use)
+  cudaStream_t aux = nullptr;            // auxiliary stream: the rebuild chain's capture, nep_get_state's second
+                                         // copy (created on first use)
   cudaEvent_t aux_ev[2] = {nullptr, nullptr};
   bool own_stream = false;
   int shape = 0;                   // 0: teacher shape (CuShape), 1: student shape (StudentShape)
@@ -182,7 +184,8 @@ struct nep_handle {
   // graph of one MD step
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
-  long long graph_launches = 0;   // our kernel launches in one captured step
+  long long graph_launches = 0;   // our kernel launches in one captured step, outside the rebuild chain
+  long long graph_rebuild_launches = 0;   // those of the rebuild chain (run on rebuild steps only)
 
   // timing
   bool timing = false;
@@ -490,7 +493,12 @@ cudaError_t enqueue_finalize(nep_handle *h, bool with_kinetic) {
 }
 
 // One velocity-Verlet step.
-cudaError_t enqueue_step(nep_handle *h, double dt) {
+// One MD step.  Launched eagerly (capture = false) the rebuild chain's kernels run every step and
+// return at once unless the control kernel decided to rebuild.  Under stream capture (capture = true)
+// the chain is the body of a conditional graph node whose condition the control kernel sets, so a
+// step without a rebuild launches none of its kernels; the chain is captured from the auxiliary stream
+// into the node's body graph.
+cudaError_t enqueue_step(nep_handle *h, double dt, bool capture = false) {
   const double kick = 0.5 * dt * ACC_CONV / h->mass;
   const float hs = 0.5f * h->skin;
   cudaError_t e;
@@ -500,12 +508,54 @@ cudaError_t enqueue_step(nep_handle *h, double dt) {
                           hs * hs, h->ctrl, h->stream);
   }
   if (e != cudaSuccess) return e;
-  {
-    Scope sc(h, KC_CELL, 1);
-    e = launch_control(h->ctrl, false, h->stream);
+  if (!capture) {
+    {
+      Scope sc(h, KC_CELL, 1);
+      e = launch_control(h->ctrl, false, h->stream);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = enqueue_rebuild(h)) != cudaSuccess) return e;
+  } else {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &graph, &deps, nullptr, &nd)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    {
+      Scope sc(h, KC_CELL, 1);
+      e = launch_control_cond(h->ctrl, cond, h->stream);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &graph, &deps, nullptr, &nd)) != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, graph, deps, nullptr, nd, &cp)) != cudaSuccess) return e;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+      return e;
+    if (!h->aux && (e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCaptureToGraph(h->aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      return e;
+    const long long before = h->launch_total;
+    cudaStream_t main = h->stream;
+    h->stream = h->aux;                       // the chain's launches go to the body graph
+    const cudaError_t eb = enqueue_rebuild(h);
+    h->stream = main;
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->aux, &captured);
+    h->graph_rebuild_launches = h->launch_total - before;
+    h->launch_total = before;
+    if (eb != cudaSuccess) return eb;
+    if (ee != cudaSuccess) return ee;
   }
-  if (e != cudaSuccess) return e;
-  if ((e = enqueue_rebuild(h)) != cudaSuccess) return e;
   if ((e = enqueue_forces(h, nullptr)) != cudaSuccess) return e;
   {
     Scope sc(h, KC_KICK, 1);
@@ -575,9 +625,9 @@ nep_status build_graph(nep_handle *h, double dt) {
   cudaGraph_t g = nullptr;
   const long long before = h->launch_total;
   NEP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_step(h, dt);
+  cudaError_t e = enqueue_step(h, dt, true);
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-  h->graph_launches = h->launch_total - before;   // kernels of one captured step
+  h->graph_launches = h->launch_total - before;   // kernels of one captured step, without the rebuild chain
   h->launch_total = before;
   if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "capture step"); }
   if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
@@ -944,6 +994,7 @@ nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
   if (h->n == 0 || n_steps == 0) return NEP_OK;
   if (!h->have_forces) {
     nep_status s = compute_internal(h, nullptr);
+    if (s == NEP_OK && !h->timing) s = check_device_status(h);   // the host copy of the rebuild count
     if (s != NEP_OK) return s;
   }
   if (h->timing) {
@@ -953,8 +1004,12 @@ nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
       nep_status s = build_graph(h, dt_fs);
       if (s != NEP_OK) return s;
     }
+    const long long rebuilds_before = h->h_ctrl->rebuilds;
     for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
-    h->launch_total += h->graph_launches * n_steps;
+    nep_status s = check_device_status(h);
+    // the rebuild chain's kernels ran on the rebuild steps only
+    h->launch_total += h->graph_launches * n_steps + h->graph_rebuild_launches * (h->h_ctrl->rebuilds - rebuilds_before);
+    return s;
   }
   return check_device_status(h);
 }
@@ -971,11 +1026,9 @@ nep_status nep_get_state(nep_handle *h, double *x, double *v) {
   // device arrays are written by the kernel itself; host arrays through the staging buffer and a copy
   // (kernel stores into page-locked host memory measured slower than the copy engines).  The positions'
   // copy runs on a second stream, beside the velocities' store and copy.
-  if (!h->aux) {
-    NEP_CUDA(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
-    NEP_CUDA(h, cudaEventCreateWithFlags(&h->aux_ev[0], cudaEventDisableTiming));
-    NEP_CUDA(h, cudaEventCreateWithFlags(&h->aux_ev[1], cudaEventDisableTiming));
-  }
+  if (!h->aux) NEP_CUDA(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+  for (cudaEvent_t &ev : h->aux_ev)
+    if (!ev) NEP_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   bool aux_used = false;
   for (int which = 0; which < 2; ++which) {
     double *out = which == 0 ? x : v;

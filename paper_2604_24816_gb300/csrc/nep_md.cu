@@ -63,8 +63,7 @@ __device__ __forceinline__ void decide_far(Control *ctrl) {
   ctrl->skip_far = ctrl->dmax2 < ctrl->far_dmax2 ? 1 : 0;
 }
 
-__global__ void k_control(Control *ctrl) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ int step_control(Control *ctrl) {
   ctrl->steps += 1;
   ctrl->steps_since += 1;
   int rb = ctrl->moved | ctrl->force_rebuild;
@@ -77,6 +76,18 @@ __global__ void k_control(Control *ctrl) {
     ctrl->rebuilds += 1;
   }
   decide_far(ctrl);
+  return rb;
+}
+__global__ void k_control(Control *ctrl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  step_control(ctrl);
+}
+// The same in a captured MD step, where the rebuild chain is the body of a conditional graph node:
+// the decision also sets that node's condition, so that a step without a rebuild launches none of the
+// chain's kernels.
+__global__ void k_control_cond(Control *ctrl, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cudaGraphSetConditional(cond, step_control(ctrl) ? 1u : 0u);
 }
 
 // Outside MD steps, after an upload that kept the list: rebuild only if an atom moved more than
@@ -312,6 +323,11 @@ cudaError_t launch_kick_drift(int n, double *x, double *y, double *z, double *vx
   if (n > 0)
     k_kick_drift<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, x, y, z, vx, vy, vz, F, pos, pos_ref, kick, dt, l[0], l[1],
                                                        l[2], half_skin2, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_control_cond(Control *ctrl, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_control_cond<<<1, 32, 0, st>>>(ctrl, cond);
   return cudaGetLastError();
 }
 

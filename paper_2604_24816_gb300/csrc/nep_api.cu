@@ -98,7 +98,8 @@ cudaError_t launch_inverse_order(int, const int *, int *, cudaStream_t);
 cudaError_t launch_load_state_sorted(int, const double *, const double *, const int *, double *, double *, double *,
                                      double *, double *, double *, float4 *, const float4 *, const double *,
                                      const double *, float, Control *, cudaStream_t);
-cudaError_t launch_kick(int, double *, double *, double *, const long long *, double, double, long long *, cudaStream_t);
+cudaError_t launch_kick(int, double *, double *, double *, const long long *, double, double, long long *, Control *,
+                        cudaStream_t);
 cudaError_t launch_kinetic(int, const double *, const double *, const double *, double, long long *, cudaStream_t);
 cudaError_t launch_finalize(const long long *, int, const long long *, int, const long long *, int, double *,
                             long long *, cudaStream_t);
@@ -557,12 +558,25 @@ cudaError_t enqueue_step(nep_handle *h, double dt, bool capture = false) {
     if (ee != cudaSuccess) return ee;
   }
   if ((e = enqueue_forces(h, nullptr)) != cudaSuccess) return e;
+  // the energy, virial and pair counts of this evaluation (the kinetic energy is the one of the last
+  // closing kick, refreshed by enqueue_step_end); the closing half kick is left to the next step's
+  // opening kick, which applies both at once
+  Scope sc(h, KC_RED, 1);
+  return launch_finalize(h->part_d, h->nb_d, h->part_f, h->nb_f, nullptr, h->nb_k, h->sums, h->counters, h->stream);
+}
+
+// The closing half kick of the last step of md_verlet_step, its kinetic energy, and the sums again
+// with it (no counters: the evaluation was counted by its own step).
+cudaError_t enqueue_step_end(nep_handle *h, double dt) {
+  const double kick = 0.5 * dt * ACC_CONV / h->mass;
+  cudaError_t e;
   {
     Scope sc(h, KC_KICK, 1);
-    e = launch_kick(h->n, h->vx, h->vy, h->vz, h->F, kick, h->mass, h->part_k, h->stream);
+    e = launch_kick(h->n, h->vx, h->vy, h->vz, h->F, kick, h->mass, h->part_k, h->ctrl, h->stream);
   }
   if (e != cudaSuccess) return e;
-  return enqueue_finalize(h, true);
+  Scope sc(h, KC_RED, 1);
+  return launch_finalize(h->part_d, h->nb_d, h->part_f, h->nb_f, h->part_k, h->nb_k, h->sums, nullptr, h->stream);
 }
 
 // Read back the control block and translate device-detected conditions into a status.
@@ -999,6 +1013,7 @@ nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
   }
   if (h->timing) {
     for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, enqueue_step(h, dt_fs));
+    NEP_CUDA(h, enqueue_step_end(h, dt_fs));
   } else {
     if (!h->graph || h->graph_dt != dt_fs) {
       nep_status s = build_graph(h, dt_fs);
@@ -1006,6 +1021,7 @@ nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps) {
     }
     const long long rebuilds_before = h->h_ctrl->rebuilds;
     for (int k = 0; k < n_steps; ++k) NEP_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+    NEP_CUDA(h, enqueue_step_end(h, dt_fs));
     nep_status s = check_device_status(h);
     // the rebuild chain's kernels ran on the rebuild steps only
     h->launch_total += h->graph_launches * n_steps + h->graph_rebuild_launches * (h->h_ctrl->rebuilds - rebuilds_before);

@@ -55,6 +55,8 @@ struct Control {
   float far_dmax2;      // below this, no list entry of the far band can be inside the largest cutoff
   int skip_far;         // decision for the current evaluation: row walks may skip the far band
   int changed;          // an upload into the kept cell order changed some atom's float32 position
+  int pending;          // the last MD step's closing half kick is still owed (applied by the next step's
+                        // opening kick, or by the kick that ends md_verlet_step)
 };
 
 // Arguments of the rebuild chain (cell sort + neighbour list).

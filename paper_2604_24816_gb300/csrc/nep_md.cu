@@ -33,11 +33,21 @@ __global__ void k_kick_drift(int n, double *__restrict__ x, double *__restrict__
   bool moved = false;
   float dd = 0.f;                      // squared displacement since the rebuild (capped; NaN -> cap)
   if (i < n) {
-    // kick_fix = kick * 2^-32: one conversion and one FMA per component on the narrow FP64 pipe
+    // kick_fix = kick * 2^-32: one conversion and one FMA per component on the narrow FP64 pipe.  When
+    // the previous step's closing half kick is owed (the same forces), it is applied first, as its own
+    // FMA: the same arithmetic as two separate kicks, so trajectories do not depend on how the steps
+    // are grouped into calls.
     const double kick_fix = kick * FIX_INV;
-    double ux = fma(kick_fix, (double)F[i], vx[i]);
-    double uy = fma(kick_fix, (double)F[(size_t)n + i], vy[i]);
-    double uz = fma(kick_fix, (double)F[2 * (size_t)n + i], vz[i]);
+    const double fx = (double)F[i], fy = (double)F[(size_t)n + i], fz = (double)F[2 * (size_t)n + i];
+    double ux = vx[i], uy = vy[i], uz = vz[i];
+    if (ctrl->pending) {
+      ux = fma(kick_fix, fx, ux);
+      uy = fma(kick_fix, fy, uy);
+      uz = fma(kick_fix, fz, uz);
+    }
+    ux = fma(kick_fix, fx, ux);
+    uy = fma(kick_fix, fy, uy);
+    uz = fma(kick_fix, fz, uz);
     vx[i] = ux; vy[i] = uy; vz[i] = uz;
     const double px = x[i] + dt * ux, py = y[i] + dt * uy, pz = z[i] + dt * uz;
     x[i] = px; y[i] = py; z[i] = pz;
@@ -76,6 +86,7 @@ __device__ __forceinline__ int step_control(Control *ctrl) {
     ctrl->rebuilds += 1;
   }
   decide_far(ctrl);
+  ctrl->pending = 1;    // this step's closing half kick: done by the next step's opening kick or the final one
   return rb;
 }
 __global__ void k_control(Control *ctrl) {
@@ -116,9 +127,12 @@ __global__ void k_control_force(Control *ctrl) {
   decide_far(ctrl);
 }
 
+// The closing half kick of md_verlet_step's last step, with the kinetic-energy partials.
 __global__ void k_kick(int n, double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
-                       const long long *__restrict__ F, double kick, double mass, long long *__restrict__ part) {
+                       const long long *__restrict__ F, double kick, double mass, long long *__restrict__ part,
+                       Control *ctrl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) ctrl->pending = 0;
   long long acc[1] = {0};
   if (i < n) {
     const double kick_fix = kick * FIX_INV;
@@ -338,8 +352,8 @@ cudaError_t launch_control(Control *ctrl, bool force, cudaStream_t st) {
 }
 
 cudaError_t launch_kick(int n, double *vx, double *vy, double *vz, const long long *F, double kick, double mass, long long *part,
-                        cudaStream_t st) {
-  if (n > 0) k_kick<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, F, kick, mass, part);
+                        Control *ctrl, cudaStream_t st) {
+  if (n > 0) k_kick<<<bl(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, vx, vy, vz, F, kick, mass, part, ctrl);
   return cudaGetLastError();
 }
 

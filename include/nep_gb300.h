@@ -106,7 +106,9 @@ nep_status nep_destroy(nep_handle *h);
  * the box are unchanged and a neighbour list exists, the list and the internal cell order are kept:
  * the next evaluation rebuilds the list only if an atom moved more than skin/2 from the positions it
  * was built for (the same test as between MD steps; positions are taken at their periodic image
- * nearest the previous ones).  Otherwise the neighbour list is invalidated.  n = 0 is accepted (every
+ * nearest the previous ones, and a coordinate within 8 eps L of the current one, eps the float64
+ * machine epsilon and L the box edge -- the rounding of the wrap applied by nep_get_state -- is the
+ * current one).  Otherwise the neighbour list is invalidated.  n = 0 is accepted (every
  * later call is a no-op).  x and v may be host or device memory; when the list is kept, device and
  * page-locked host arrays are read by the GPU directly (other host arrays are copied first).  Returns
  * after the upload has completed, so the caller may reuse the arrays. */

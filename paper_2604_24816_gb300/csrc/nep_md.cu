@@ -7,6 +7,8 @@
 // kernel then asks the next rebuild chain to run.
 #include "nep_common.cuh"
 
+#include <cfloat>
+
 namespace nep {
 
 constexpr double KE_CONV = 103.642696562;          // 1 amu Angstrom^2/fs^2 in eV
@@ -243,6 +245,13 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
       a -= Lx * rint((a - x[s]) / Lx);
       b -= Ly * rint((b - y[s]) / Ly);
       c -= Lz * rint((c - z[s]) / Lz);
+      // a coordinate that differs from the current one only by the rounding of a periodic wrap (the
+      // state read back by nep_get_state is wrapped into the box; adding the edge back can be an ulp
+      // off) is the current one
+      const double tx = 8.0 * DBL_EPSILON * Lx, ty = 8.0 * DBL_EPSILON * Ly, tz = 8.0 * DBL_EPSILON * Lz;
+      if (fabs(a - x[s]) <= tx) a = x[s];
+      if (fabs(b - y[s]) <= ty) b = y[s];
+      if (fabs(c - z[s]) <= tz) c = z[s];
     }
     x[s] = a; y[s] = b; z[s] = c;
     if (vin != nullptr) {

@@ -307,6 +307,30 @@ def test_checkpoint_resume_is_bit_identical(api, model_params):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
+def test_step_grouping_is_bit_identical(api, model_params):
+    """md_verlet_step(20) and twenty md_verlet_step(1) give the same bits: each step's closing half kick
+    is applied by the next step's opening kick kernel or, after the last step of a call, by the kick
+    that ends the call, with the same two FMAs either way; the rebuild chain runs inside the captured
+    step only when the control kernel asks for it."""
+    wl = ni.fcc_cu_workload(6, 300.0, 0.05, seed=99)
+    with api.NEP(model_params, rebuild_every=10) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        nep.step(1.0, 20)
+        xa, va = nep.get_state()
+        ta = nep.thermo()
+        ca = nep.counters()
+    with api.NEP(model_params, rebuild_every=10) as nep:
+        nep.set_state(wl.pos, wl.vel, wl.box)
+        for _ in range(20):
+            nep.step(1.0, 1)
+        xb, vb = nep.get_state()
+        tb = nep.thermo()
+        cb = nep.counters()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert ta["pe"] == tb["pe"] and ta["ke"] == tb["ke"]
+    assert ca["rebuilds"] == cb["rebuilds"] == 3 and ca["evaluations"] == cb["evaluations"] == 21
+
+
 def test_bounded_wait_runs_out_and_reports(api):
     """The tensor-core kernels wait on mbarriers with a poll limit; a wait on a barrier that nothing
     arrives on ends the kernel with the timeout bit set, and the context stays usable."""

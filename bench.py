@@ -61,30 +61,35 @@ UNIT = "atom-steps/s"
 #   radial pair, descriptor 49: Chebyshev basis 41 (r/rc, pi r/rc and the hardware sine/cosine 4, the
 #     cutoff half 3, x = 2 (r/rc - 1)^2 - 1 5, 6 recurrence FMAs, 4 paired FMAs) + 4 paired adds;
 #   LJ pair, descriptor 17: 1/r^2 with one Newton step, r^-6, r^-12, the shifted energy, half of it summed;
-#   angular pair, descriptor 440: unit vector 3 + basis 41 + 5 channel dot products 75 + 24 solid
-#     harmonics 81 + 120 paired FMAs into s_nlm 240;
-#   atom, descriptor 4921: q_n 80, q_nl 240, 4-body tensors and q4 130, network 3870 (scaling 60 and
-#     30 neurons x (30 FMAs forward, tanh, energy, gradient factor, 30 FMAs back)), 4-body adjoint 330,
-#     adjoint row 190, radial adjoint in basis space 80, site energy 1;
+#   angular pair, descriptor 411: unit vector 3 + basis 41 + 5 channel dot products 75 + the 24
+#     harmonic polynomials without their constant factors 52 (the fused kernels keep the sums and the
+#     adjoint row over Ph_lm = Yh_lm / hnorm(lm); with the constants, as the separate kernels, 81) +
+#     120 paired FMAs into s_nlm 240;
+#   atom, descriptor 5106: q_n 80, q_nl 335 (240 + the 95 hnorm scalings of the sums), 4-body tensors and
+#     q4 130, network 3870 (scaling 60 and 30 neurons x (30 FMAs forward, tanh, energy, gradient
+#     factor, 30 FMAs back)), 4-body adjoint 350 (330 + 20 scalings), adjoint row 260 (G' = 2 hnorm^2 Fp
+#     s' + hnorm f4 g4: 16 distinct hnorm^2 Fp factors per channel 80, 120 products, 10 hnorm f4
+#     factors, 25 FMAs), radial adjoint in basis space 80, site energy 1;
 #   active pair, force from the pair records 28: r^2, rsqrt, r (7), d = coef r + v (6), F_i (3),
 #     virial upper triangle (12); the list-walking force kernel: 23 plus 11 per list entry;
 #   radial pair, force 118: basis and derivative 102 + dot with the radial adjoint 15 + 1/r;
 #   LJ pair, force 18;
-#   angular pair, force 1178: unit vector 3 + basis and derivative 102 + 2 x 5 channel dots 150 +
-#     harmonics 81 + per (l, m) the sums A_lm, B_lm over the channels 480 + (A - l B / r) Y 96 + the
-#     l / r factors 12 + gradients of the harmonic polynomials 129 and their 58 non-zero FMAs 116 + 9;
+#   angular pair, force 1106 (fused kernels, over Ph_lm): unit vector 3 + basis and derivative 102 +
+#     2 x 5 channel dots 150 + the polynomials 52 + per (l, m) the sums A_lm, B_lm over the channels 480
+#     + (A - l B / r) Ph 96 + the l / r factors 12 + the polynomials' gradients 86 and their 58 non-zero
+#     FMAs 116 + 9; the list-walking force kernels over Yh_lm: 1178 (harmonics 81, gradients 129);
 #   the half-list force (float16 rows): H = G^i + (-1)^l G^j adds 240 per angular pair and 8 per radial
 #     pair; its LJ term is the whole pair force (17).
 # The FP32 op counters of one fused launch (ffma, fadd, fmul, paired ops, MUFU) agree with this count to
 # within the conversions and padding named above (profiles/k_nep_fused_cu64x64x64.md).
 # The mixed-precision forms run the same fused kernel with the network as two tensor-core GEMMs
-# (32 x 32 tiles, bf16/f16 operands): per atom 1321 FP32 FLOPs remain (4921 - 3870 for the float32
+# (32 x 32 tiles, bf16/f16 operands): per atom 1506 FP32 FLOPs remain (5106 - 3870 for the float32
 # network + scaling 30, per neuron z - b0, tanh, energy FMA and gradient factor 7, Fp 30); the GEMMs'
 # 4096 tensor FLOPs per atom are not part of the FP32 count.
 FLOPS = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=440, atom=4921),
-    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=440, atom=1321),
-    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=1178, atom=0),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=411, atom=5106),
+    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=411, atom=1506),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=1106, atom=0),
     "force_full": dict(list_entry=11, active_pair=23, radial_pair=118, lj_pair=18, angular_pair=1178, atom=0),
     "force": dict(list_entry=11, active_pair=23, radial_pair=126, lj_pair=17, angular_pair=1418, atom=0),
 }

@@ -382,6 +382,129 @@ __host__ __device__ constexpr int harmonic_grad_mask(int lm) {
          (lm == 7 || lm == 8 || lm == 14 || lm == 15 || lm == 23) ? 3 : 7;
 }
 
+// The same harmonics without their constant factors: Yh_lm = hnorm(lm) Ph_lm, with Ph_lm (harmonics_p)
+// a polynomial with small integer coefficients.  A sum or an adjoint row kept over Ph instead of Yh
+// (s'_nlm = s_nlm / hnorm(lm), G'_nlm = hnorm(lm) G_nlm) gives the same products G s and G dYh/du with
+// the per-pair constant multiplies moved to one multiply per atom and component.
+__host__ __device__ constexpr float hnorm(int lm) {
+  constexpr float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
+  constexpr float s10 = 3.1622776601683795f, s15 = 3.872983346207417f, s35 = 5.916079783099616f;
+  constexpr float s70 = 8.366600265340756f;
+  return lm < 3 ? 1.f : lm == 3 || lm == 4 || lm == 6 ? s3 : lm == 5 ? 1.f : lm == 7 ? 0.5f * s3 :
+         lm == 8 || lm == 14 ? 0.25f * s10 : lm == 9 ? s15 : lm == 10 || lm == 12 ? 0.25f * s6 :
+         lm == 11 ? 1.f : lm == 13 ? 0.5f * s15 : lm == 15 ? 0.5f * s35 : lm == 16 || lm == 22 ? 0.25f * s70 :
+         lm == 17 ? 0.5f * s5 : lm == 18 || lm == 20 ? 0.25f * s10 : lm == 19 ? 0.125f :
+         lm == 21 ? 0.25f * s5 : 0.125f * s35;
+}
+
+template <int NLM>
+__host__ __device__ __forceinline__ void harmonics_p(float x, float y, float z, float (&P)[NLM]) {
+  static_assert(NLM == 24, "l_max 4");
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float xy = x * y, yz = y * z, xz = x * z, d = x2 - y2, e = x2 + y2;
+  P[0] = y; P[1] = z; P[2] = x;
+  P[3] = xy;
+  P[4] = yz;
+  P[5] = fmaf(-0.5f, e, z2);
+  P[6] = xz;
+  P[7] = d;
+  const float a3 = fmaf(4.f, z2, -e);          // 4 z^2 - x^2 - y^2
+  const float p8 = y * fmaf(3.f, x2, -y2);     // y (3 x^2 - y^2)
+  const float p14 = x * fmaf(-3.f, y2, x2);    // x (x^2 - 3 y^2)
+  P[8] = p8;
+  P[9] = xy * z;
+  P[10] = y * a3;
+  P[11] = z * fmaf(-1.5f, e, z2);
+  P[12] = x * a3;
+  P[13] = z * d;
+  P[14] = p14;
+  const float b4 = fmaf(6.f, z2, -e);          // 7 z^2 - r^2
+  const float c4 = fmaf(-3.f, e, 4.f * z2);    // 7 z^2 - 3 r^2
+  const float rr = e + z2;
+  P[15] = xy * d;
+  P[16] = z * p8;
+  P[17] = xy * b4;
+  P[18] = yz * c4;
+  P[19] = fmaf(35.f * z2, z2, fmaf(-30.f * z2, rr, 3.f * rr * rr));
+  P[20] = xz * c4;
+  P[21] = d * b4;
+  P[22] = z * p14;
+  P[23] = fmaf(x2, x2, fmaf(-6.f * x2, y2, y2 * y2));
+}
+
+// Ph_lm alone (lm a compile-time constant after unrolling), for loops that form the components chunk by
+// chunk instead of holding all 24.
+__host__ __device__ __forceinline__ float harmonic_p(int lm, float x, float y, float z) {
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float xy = x * y, d = x2 - y2, e = x2 + y2;
+  switch (lm) {
+    case 0: return y;
+    case 1: return z;
+    case 2: return x;
+    case 3: return xy;
+    case 4: return y * z;
+    case 5: return fmaf(-0.5f, e, z2);
+    case 6: return x * z;
+    case 7: return d;
+    case 8: return y * fmaf(3.f, x2, -y2);
+    case 9: return xy * z;
+    case 10: return y * fmaf(4.f, z2, -e);
+    case 11: return z * fmaf(-1.5f, e, z2);
+    case 12: return x * fmaf(4.f, z2, -e);
+    case 13: return z * d;
+    case 14: return x * fmaf(-3.f, y2, x2);
+    case 15: return xy * d;
+    case 16: return z * (y * fmaf(3.f, x2, -y2));
+    case 17: return xy * fmaf(6.f, z2, -e);
+    case 18: return (y * z) * fmaf(-3.f, e, 4.f * z2);
+    case 19: { const float rr = e + z2; return fmaf(35.f * z2, z2, fmaf(-30.f * z2, rr, 3.f * rr * rr)); }
+    case 20: return (x * z) * fmaf(-3.f, e, 4.f * z2);
+    case 21: return d * fmaf(6.f, z2, -e);
+    case 22: return z * (x * fmaf(-3.f, y2, x2));
+    case 23: return fmaf(x2, x2, fmaf(-6.f * x2, y2, y2 * y2));
+    default: return 0.f;
+  }
+}
+
+// Gradient of Ph_lm at (x, y, z) (harmonic_grad / hnorm(lm)); the same zero pattern (harmonic_grad_mask).
+__host__ __device__ __forceinline__ void harmonic_grad_p(int lm, float x, float y, float z, float (&a)[3]) {
+  const float x2 = x * x, y2 = y * y, z2 = z * z;
+  const float xy = x * y, yz = y * z, xz = x * z, d = x2 - y2, e = x2 + y2;
+  float ax = 0.f, ay = 0.f, az = 0.f;
+  switch (lm) {
+    case 0: ay = 1.f; break;
+    case 1: az = 1.f; break;
+    case 2: ax = 1.f; break;
+    case 3: ax = y; ay = x; break;
+    case 4: ay = z; az = y; break;
+    case 5: ax = -x; ay = -y; az = 2.f * z; break;
+    case 6: ax = z; az = x; break;
+    case 7: ax = 2.f * x; ay = -2.f * y; break;
+    case 8: ax = 6.f * xy; ay = 3.f * d; break;
+    case 9: ax = yz; ay = xz; az = xy; break;
+    case 10: ax = -2.f * xy; ay = fmaf(4.f, z2, -fmaf(3.f, y2, x2)); az = 8.f * yz; break;
+    case 11: ax = -3.f * xz; ay = -3.f * yz; az = fmaf(-1.5f, e, 3.f * z2); break;
+    case 12: ax = fmaf(4.f, z2, -fmaf(3.f, x2, y2)); ay = -2.f * xy; az = 8.f * xz; break;
+    case 13: ax = 2.f * xz; ay = -2.f * yz; az = d; break;
+    case 14: ax = 3.f * d; ay = -6.f * xy; break;
+    case 15: ax = y * fmaf(3.f, x2, -y2); ay = x * fmaf(-3.f, y2, x2); break;
+    case 16: ax = 6.f * xy * z; ay = 3.f * z * d; az = y * fmaf(3.f, x2, -y2); break;
+    case 17: ax = y * fmaf(6.f, z2, -fmaf(3.f, x2, y2)); ay = x * fmaf(6.f, z2, -fmaf(3.f, y2, x2));
+             az = 12.f * xy * z; break;
+    case 18: ax = -6.f * xy * z; ay = z * fmaf(4.f, z2, -fmaf(9.f, y2, 3.f * x2));
+             az = 3.f * y * fmaf(4.f, z2, -e); break;
+    case 19: { const float w = fmaf(-4.f, z2, e);   // x^2 + y^2 - 4 z^2
+               ax = 12.f * x * w; ay = 12.f * y * w; az = -16.f * z * fmaf(3.f, e, -2.f * z2); break; }
+    case 20: ax = z * fmaf(4.f, z2, -fmaf(9.f, x2, 3.f * y2)); ay = -6.f * xy * z;
+             az = 3.f * x * fmaf(4.f, z2, -e); break;
+    case 21: ax = -4.f * x * fmaf(-3.f, z2, x2); ay = 4.f * y * fmaf(-3.f, z2, y2); az = 12.f * z * d; break;
+    case 22: ax = 3.f * z * d; ay = -6.f * xy * z; az = x * fmaf(-3.f, y2, x2); break;
+    case 23: ax = 4.f * x * fmaf(-3.f, y2, x2); ay = -4.f * y * fmaf(3.f, x2, -y2); break;
+    default: break;
+  }
+  a[0] = ax; a[1] = ay; a[2] = az;
+}
+
 // Gradient of the solid-harmonic polynomial of component lm, evaluated at (x, y, z), accumulated
 // with weight b into (gx, gy, gz).
 __device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, float z, float b, float &gx,
@@ -396,10 +519,17 @@ __device__ __forceinline__ void harmonic_grad_acc(int lm, float x, float y, floa
 
 // The same for the two components lm0, lm0 + 1 with weights b = (b_lm0, b_lm0+1), accumulated into the
 // component pairs g[d] (even and odd lm apart): paired multiply-adds where both are non-zero.
+// UN: the gradients of the polynomials Ph (harmonic_grad_p), for weights taken over Ph.
+template <bool UN = false>
 __device__ __forceinline__ void harmonic_grad_acc2(int lm0, float x, float y, float z, float2 b, float2 (&g)[3]) {
   float a0[3], a1[3];
-  harmonic_grad(lm0, x, y, z, a0);
-  harmonic_grad(lm0 + 1, x, y, z, a1);
+  if constexpr (UN) {
+    harmonic_grad_p(lm0, x, y, z, a0);
+    harmonic_grad_p(lm0 + 1, x, y, z, a1);
+  } else {
+    harmonic_grad(lm0, x, y, z, a0);
+    harmonic_grad(lm0 + 1, x, y, z, a1);
+  }
   const int m0 = harmonic_grad_mask(lm0), m1 = harmonic_grad_mask(lm0 + 1);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {

@@ -354,7 +354,7 @@ __device__ __forceinline__ void tm_store(uint32_t trow, int k, const float (&v)[
 // thread's column of a [pmax][BLOCK] array): angular pairs (r < rc_A) from
 // slot 0 up in walk order, the other active pairs from slot pmax - 1 down (pmax >= the row length, so
 // the two never meet).
-template <class S, int NT, int DE, int DP, int BLOCK, bool REC = false>
+template <class S, int NT, int DE, int DP, int BLOCK, bool REC = false, bool UN = false>
 __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const float4 *shift, uint32_t trow, int ii,
                                                    int n, const float4 *__restrict__ pos,
                                                    const int32_t *__restrict__ nbr, RowSpan sp, uint32_t *ring_e,
@@ -435,13 +435,22 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
         const float t = dot_pairs<S::KA>(P.cA[a], f);
         g[a] = ang ? t : 0.f;
       }
+      // UN: the polynomials Ph_lm chunk by chunk (fewer live registers than 24 values); all channels in TMEM
+      static_assert(!UN || NT == S::NA, "register-resident channels take the normalised harmonics");
       float Y[S::NLM];
-      harmonics<S::NLM>(ux, uy, uz, Y);
+      if constexpr (!UN) harmonics<S::NLM>(ux, uy, uz, Y);
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         float sv[S::NA][W];
         tm_load<S, NT>(trow, k, sv);
-        const float2 y01 = pr(Y[W * k], Y[W * k + 1]), y23 = pr(Y[W * k + 2], Y[W * k + 3]);
+        float2 y01, y23;
+        if constexpr (UN) {
+          y01 = pr(harmonic_p(W * k, ux, uy, uz), harmonic_p(W * k + 1, ux, uy, uz));
+          y23 = pr(harmonic_p(W * k + 2, ux, uy, uz), harmonic_p(W * k + 3, ux, uy, uz));
+        } else {
+          y01 = pr(Y[W * k], Y[W * k + 1]);
+          y23 = pr(Y[W * k + 2], Y[W * k + 3]);
+        }
 #pragma unroll
         for (int a = 0; a < NT; ++a) {
           const float2 g2 = bc2(g[a]);
@@ -477,7 +486,8 @@ __device__ __forceinline__ void sums_chunk(uint32_t trow, int k, const RegSums<S
 
 // Descriptors from the radial basis sums and the sums s_nlm (q_nl = sum_m s_nlm^2, 4-body from the
 // l = 2 sums), as descriptors_of.
-template <class S, int NT>
+// UN: sums over Ph_lm (accumulate_atom_tm), scaled by hnorm(lm) here.
+template <class S, int NT, bool UN = false>
 __device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow, const float (&QR)[S::KR],
                                                const RegSums<S, NT> &R, float (&q)[S::NDES], FourBody<S> &T) {
   constexpr int W = TMEM_W;
@@ -500,6 +510,7 @@ __device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow,
 #pragma unroll
       for (int cc = 0; cc < W; ++cc) {
         const int lm = W * k + cc;
+        if constexpr (UN) sv[a][cc] *= hnorm(lm);
         float &ql = q[S::NR + a * S::LMAX + lm_l(lm) - 1];
         ql = fmaf(sv[a][cc], sv[a][cc], ql);
         if (lm >= 3 && lm < 8) s2[a][lm - 3] = sv[a][cc];
@@ -511,7 +522,7 @@ __device__ __forceinline__ void descriptors_tm(const Model<S> &P, uint32_t trow,
 // 4-body adjoint factors g4[a] = 3 (T_a^2) : dT_a/ds_m of every channel, with the tensors T_a rebuilt
 // from the l = 2 sums (components 3..7: chunk 0 holds component 3, chunk 1 components 4..7), so that
 // T need not stay live across the network.
-template <class S, int NT>
+template <class S, int NT, bool UN = false>
 __device__ __forceinline__ void fourbody_adjoint_tm(uint32_t trow, const RegSums<S, NT> &R, float (&g4)[S::NA][5]) {
   static_assert(S::FOURBODY && S::NLM == 24, "teacher shape");
   float c0[S::NA][TMEM_W], c1[S::NA][TMEM_W];
@@ -523,6 +534,10 @@ __device__ __forceinline__ void fourbody_adjoint_tm(uint32_t trow, const RegSums
     s2[a][0] = c0[a][3];
 #pragma unroll
     for (int m = 1; m < 5; ++m) s2[a][m] = c1[a][m - 1];
+    if constexpr (UN) {
+#pragma unroll
+      for (int m = 0; m < 5; ++m) s2[a][m] *= hnorm(3 + m);
+    }
   }
   FourBody<S> T;
   float q[S::NDES];
@@ -533,14 +548,18 @@ __device__ __forceinline__ void fourbody_adjoint_tm(uint32_t trow, const RegSums
 
 // The adjoint of components c..c+3 of channel a, gl = 2 Fp_{a,l} s + (4-body terms for l = 2), as
 // adjoint_channel; g4 = fourbody_adjoint of channel a.
-template <class S>
+// UN: sv holds s'_nlm (sums over Ph_lm) and the row is G'_nlm = hnorm(lm) G_nlm, the weights of Ph_lm:
+// G' = 2 hnorm^2 Fp s' + hnorm f4 g4.
+template <class S, bool UN = false>
 __device__ __forceinline__ void adjoint_chunk(int a, int c, const float (&sv)[TMEM_W], const float (&g4)[5],
                                               const float (&Fp)[S::NDES], float (&gl)[TMEM_W]) {
 #pragma unroll
   for (int cc = 0; cc < TMEM_W; ++cc) {
     const int lm = c + cc;
-    gl[cc] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(lm) - 1] * sv[cc];
-    if (S::FOURBODY && lm >= 3 && lm < 8) gl[cc] = fmaf(Fp[S::NR + S::NA * S::LMAX + a], g4[lm - 3], gl[cc]);
+    const float h = UN ? hnorm(lm) : 1.f;
+    gl[cc] = (2.f * h * h) * Fp[S::NR + a * S::LMAX + lm_l(lm) - 1] * sv[cc];
+    if (S::FOURBODY && lm >= 3 && lm < 8)
+      gl[cc] = fmaf(UN ? h * Fp[S::NR + S::NA * S::LMAX + a] : Fp[S::NR + S::NA * S::LMAX + a], g4[lm - 3], gl[cc]);
   }
 }
 

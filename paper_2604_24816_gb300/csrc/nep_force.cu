@@ -233,8 +233,9 @@ struct ForceCfg {
 // H = G^i (FULL; in TMEM at trow for the teacher shape, else in gi) or G^i + (-1)^l G^j (half list, G^j
 // gathered from Gj).  Returns sum_lm (A_lm - l B_lm / r) Yh_lm (al, even and odd lm apart) and
 // sum_lm B_lm grad P_lm(u) (gv), A_lm = sum_n H_nlm g_n'(r), B_lm = sum_n H_nlm g_n(r).  si: a stand-in
-// pair (r = 1 along x) for lanes that only take part in the warp-collective TMEM loads.
-template <class S, class GT, bool FULL>
+// pair (r = 1 along x) for lanes that only take part in the warp-collective TMEM loads.  UN: the row
+// holds G'_nlm = hnorm(lm) G_nlm, the weights of the polynomials Ph_lm (harmonics_p).
+template <class S, class GT, bool FULL, bool UN = false>
 __device__ __forceinline__ void angular_pair(const Model<S> &P, uint32_t trow,
                                              const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
                                              const GT *__restrict__ Gj, bool si, float r, float ir, float dx, float dy,
@@ -248,8 +249,9 @@ __device__ __forceinline__ void angular_pair(const Model<S> &P, uint32_t trow,
   float g[S::NA], dg[S::NA];
 #pragma unroll
   for (int a = 0; a < S::NA; ++a) dot_pairs2<S::KA>(P.cA[a], f, df, g[a], dg[a]);
+  // UN: the polynomials Ph_lm are formed chunk by chunk below (fewer live registers than 24 values)
   float Y[S::NLM];
-  harmonics<S::NLM>(ux, uy, uz, Y);
+  if constexpr (!UN) harmonics<S::NLM>(ux, uy, uz, Y);
   const float2 air2 = bc2(air);
   // d/dd [g_n(r) Yh_lm(u)] = (g_n' - l g_n / r) Yh_lm u + (g_n / r) grad P_lm(u); per component
   // A_lm = sum_n H_nlm g_n', B_lm = sum_n H_nlm g_n, in pairs of consecutive components (lm, lm + 1)
@@ -301,10 +303,15 @@ __device__ __forceinline__ void angular_pair(const Model<S> &P, uint32_t trow,
     }
     const float2 nl01 = mul2(pr(-(float)lm_l(lm0), -(float)lm_l(lm0 + 1)), air2);
     const float2 nl23 = mul2(pr(-(float)lm_l(lm0 + 2), -(float)lm_l(lm0 + 3)), air2);
-    al = fma2(fma2(nl01, bv01, av01), pr(Y[lm0], Y[lm0 + 1]), al);
-    al = fma2(fma2(nl23, bv23, av23), pr(Y[lm0 + 2], Y[lm0 + 3]), al);
-    harmonic_grad_acc2(lm0, ux, uy, uz, bv01, gv);
-    harmonic_grad_acc2(lm0 + 2, ux, uy, uz, bv23, gv);
+    if constexpr (UN) {
+      al = fma2(fma2(nl01, bv01, av01), pr(harmonic_p(lm0, ux, uy, uz), harmonic_p(lm0 + 1, ux, uy, uz)), al);
+      al = fma2(fma2(nl23, bv23, av23), pr(harmonic_p(lm0 + 2, ux, uy, uz), harmonic_p(lm0 + 3, ux, uy, uz)), al);
+    } else {
+      al = fma2(fma2(nl01, bv01, av01), pr(Y[lm0], Y[lm0 + 1]), al);
+      al = fma2(fma2(nl23, bv23, av23), pr(Y[lm0 + 2], Y[lm0 + 3]), al);
+    }
+    harmonic_grad_acc2<UN>(lm0, ux, uy, uz, bv01, gv);
+    harmonic_grad_acc2<UN>(lm0 + 2, ux, uy, uz, bv23, gv);
   }
 }
 
@@ -466,8 +473,9 @@ __device__ __forceinline__ float radial_lj_coef(const Model<S> &P, const float4 
 // loop runs to the warp's largest na and lanes past their own count compute a stand-in pair), then the
 // nr other active pairs (slots pmax-1 down to pmax-nr; no TMEM).  Each pair gets the arithmetic of
 // force_pairs<S, float, false, true> on the displacement the descriptor walk computed: d_ij added to F_i,
-// subtracted from F_j (fixed point), W -= r_ij (x) d_ij (upper triangle, mirrored).
-template <class S, int DQ>
+// subtracted from F_j (fixed point), W -= r_ij (x) d_ij (upper triangle, mirrored).  UN: the TMEM row is
+// over Ph_lm (angular_pair).
+template <class S, int DQ, bool UN = false>
 __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow,
                                                 const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
                                                 const float4 *fps, int i, bool live,
@@ -504,8 +512,8 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
       float coef = valid ? radial_lj_coef<S, true>(P, fps, r2, r, ir) : 0.f;
       if constexpr (TM) __syncwarp();
       float2 al, gv[3];
-      angular_pair<S, float, true>(P, trow, gi, static_cast<const float *>(nullptr), !valid, r, ir, q.x, q.y, q.z, al,
-                                   gv);
+      angular_pair<S, float, true, UN>(P, trow, gi, static_cast<const float *>(nullptr), !valid, r, ir, q.x, q.y, q.z,
+                                       al, gv);
       if (valid) {
         coef = fmaf(hsum(al), ir, coef);
         apply(q.x, q.y, q.z, __float_as_int(q.w), coef, hsum(gv[0]) * ir, hsum(gv[1]) * ir, hsum(gv[2]) * ir);
@@ -724,12 +732,12 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   float QR[S::KR], elj;
   int nrad, nang, nact;
   RegSums<S, S::NA> R;
-  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK, true>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
-                                                                   QR, R, elj, nrad, nang, nact, pc.rec, rec_off,
-                                                                   pc.pmax);
+  accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK, true, true>(P, shift, trow, ii, n, pos, nbr, sp, ring_e,
+                                                                         ring_p, QR, R, elj, nrad, nang, nact, pc.rec,
+                                                                         rec_off, pc.pmax);
   float q[S::NDES];
   FourBody<S> T;
-  descriptors_tm<S, S::NA>(P, trow, QR, R, q, T);
+  descriptors_tm<S, S::NA, true>(P, trow, QR, R, q, T);
   if (live && qout != nullptr) {
 #pragma unroll
     for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
@@ -739,13 +747,13 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
 
   // the adjoint row replaces the sums in TMEM (same columns, chunk by chunk); radial tail in registers
   float g4[S::NA][5];
-  fourbody_adjoint_tm<S, S::NA>(trow, R, g4);
+  fourbody_adjoint_tm<S, S::NA, true>(trow, R, g4);
 #pragma unroll
   for (int k = 0; k < S::NLM / W; ++k) {
     float sv[S::NA][W], gl[S::NA][W];
     sums_chunk<S, S::NA>(trow, k, R, sv);
 #pragma unroll
-    for (int a = 0; a < S::NA; ++a) adjoint_chunk<S>(a, W * k, sv[a], g4[a], Fp, gl[a]);
+    for (int a = 0; a < S::NA; ++a) adjoint_chunk<S, true>(a, W * k, sv[a], g4[a], Fp, gl[a]);
     tm_store<S, S::NA>(trow, k, gl);
   }
   tmem_wait_st();
@@ -776,8 +784,8 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
 
   // forces: every active pair of the row with the own adjoint row, from the pair records
   const float gi[1][1] = {{0.f}};
-  force_pairs_rec<S, PIPE_DP>(P, trow, gi, fp_s + threadIdx.x, i, live, n, pc.rec, rec_off, pc.pmax, nang,
-                              nact - nang, ring_p, Ffix, status, acc_f);
+  force_pairs_rec<S, PIPE_DP, true>(P, trow, gi, fp_s + threadIdx.x, i, live, n, pc.rec, rec_off, pc.pmax, nang,
+                                    nact - nang, ring_p, Ffix, status, acc_f);
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -948,11 +956,11 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
   float q[S::NDES];
   {
     RegSums<S, S::NA> R5;
-    accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK, true>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
+    accumulate_atom_tm<S, S::NA, PIPE_DE, PIPE_DP, DESC_BLOCK, true, true>(P, shift, trow, ii, n, pos, nbr, sp, ring_e, ring_p,
                                                                      QR, R5, elj, nrad, nang, nact, pc.rec, rec_off,
                                                                      pc.pmax);
     FourBody<S> T;
-    descriptors_tm<S, S::NA>(P, trow, QR, R5, q, T);   // zero for threads past the last atom (empty row)
+    descriptors_tm<S, S::NA, true>(P, trow, QR, R5, q, T);   // zero for threads past the last atom (empty row)
   }
   // channel 4's sums (columns 96..119) to registers: the GEMMs take columns 96..127
   RegSums<S, NT> R;
@@ -1035,13 +1043,13 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
   // adjoint row of all 5 channels in the chunked layout: channels 0..3 over their sums, channel 4 over
   // the GEMM columns this warp has just read
   float g4[S::NA][5];
-  fourbody_adjoint_tm<S, NT>(trow, R, g4);
+  fourbody_adjoint_tm<S, NT, true>(trow, R, g4);
 #pragma unroll
   for (int k = 0; k < S::NLM / W; ++k) {
     float sv[S::NA][W], gl[S::NA][W];
     sums_chunk<S, NT>(trow, k, R, sv);
 #pragma unroll
-    for (int a = 0; a < S::NA; ++a) adjoint_chunk<S>(a, W * k, sv[a], g4[a], Fp, gl[a]);
+    for (int a = 0; a < S::NA; ++a) adjoint_chunk<S, true>(a, W * k, sv[a], g4[a], Fp, gl[a]);
     tm_store<S, S::NA>(trow, k, gl);
   }
   tmem_wait_st();
@@ -1067,7 +1075,7 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
   __shared__ long long wsum_d[DESC_BLOCK / 32][5];
   warp_sum_stage<5>(acc_d, wsum_d[t >> 5]);
   const float gi[1][1] = {{0.f}};
-  force_pairs_rec<S, PIPE_DP>(P, trow, gi, fp_s + t, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang, ring_p,
+  force_pairs_rec<S, PIPE_DP, true>(P, trow, gi, fp_s + t, i, live, n, pc.rec, rec_off, pc.pmax, nang, nact - nang, ring_p,
                               Ffix, status, acc_f);
   tc_fence_before();
   __syncthreads();

@@ -95,14 +95,19 @@ FLOPS = {
 }
 # The same count for the student shape (4 + 4 channels, 8 basis functions, l = 1, 2, no 4-body term,
 # 16 neurons): register-resident sums, scalar channel dots (16 per channel), 8 harmonics (14),
-# network 888.  Its float32 form runs the fused kernel, whose force pass over the pair records costs per
-# angular pair: unit vector 3 + basis and derivative 102 + 2 x 4 channel dots 120 + harmonics 14 + the
-# sums A_lm, B_lm 128 + (A - l B / r) Y 32 + the l / r factors 8 + gradient polynomials 9 and their 14
-# non-zero FMAs 28 + 9; its mixed form runs the separate kernels with the force over the half list.
+# network 888.  Its float32 form runs the fused kernel, which keeps the sums and the adjoint row over
+# the polynomials without their constant factors as the teacher's fused kernels do: the 8 polynomials
+# cost 10 (descriptor_rec: 182 per angular pair; per atom 1169, the 16 hnorm scalings of the sums and 8
+# more adjoint factors), and its force pass over the pair records per angular pair: unit vector 3 +
+# basis and derivative 102 + 2 x 4 channel dots 120 + polynomials 10 + the sums A_lm, B_lm 128 +
+# (A - l B / r) Ph 32 + the l / r factors 8 + the polynomials' gradients 3 and their 14 non-zero FMAs
+# 28 + 9; its mixed form runs the separate kernels (harmonics with their constants) with the force over
+# the half list.
 FLOPS_STUDENT = {
     "descriptor": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=186, atom=1145),
+    "descriptor_rec": dict(list_entry=11, active_pair=2, radial_pair=49, lj_pair=17, angular_pair=182, atom=1169),
     "force": dict(list_entry=11, active_pair=23, radial_pair=126, lj_pair=17, angular_pair=511, atom=0),
-    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=453, atom=0),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=118, lj_pair=18, angular_pair=443, atom=0),
 }
 # Algorithmic HBM bytes per atom-step: the integrator reads and writes x, v (96) in the kick + drift and
 # v (48) in the second kick, and reads the forces in both kicks (48); the force kernel reads the atom's
@@ -120,7 +125,11 @@ def force_kind(form: str) -> str:
 
 
 def descriptor_kind(form: str) -> str:
-    """FLOP table of the descriptor part: the mixed-precision forms' network is on the tensor cores."""
+    """FLOP table of the descriptor part: the mixed-precision teacher forms' network is on the tensor
+    cores; the float32 student runs its fused kernel (descriptor_rec of FLOPS_STUDENT)."""
+    f = FORMS[form]
+    if f["model"] == "student":
+        return "descriptor_rec" if f["precision"] == "fp32" else "descriptor"
     return "descriptor_mixed" if form in ("mix_bf16", "mix_fp16") else "descriptor"
 
 
@@ -613,7 +622,7 @@ def run_ours(args, rank: int, ws: int, local: int):
     dc = {k: c2[k] - c1[k] for k in c2}          # the eager pass with per-kernel events
     evals = dc["evaluations"]
     table = FLOPS_STUDENT if FORMS[args.form]["model"] == "student" else FLOPS
-    f_desc = kernel_flops(descriptor_kind(args.form) if table is FLOPS else "descriptor", dc, evals * wl.n, table)
+    f_desc = kernel_flops(descriptor_kind(args.form), dc, evals * wl.n, table)
     f_force = kernel_flops(force_kind(args.form), dc, evals * wl.n, table)
     clk = clocks.summary(t_host0, t_host1)
     clk_kernels = clocks.summary(t_host2, t_host3)

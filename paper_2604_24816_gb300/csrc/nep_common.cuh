@@ -399,7 +399,7 @@ __host__ __device__ constexpr float hnorm(int lm) {
 
 template <int NLM>
 __host__ __device__ __forceinline__ void harmonics_p(float x, float y, float z, float (&P)[NLM]) {
-  static_assert(NLM == 24, "l_max 4");
+  static_assert(NLM == 8 || NLM == 24, "l_max 2 or 4");
   const float x2 = x * x, y2 = y * y, z2 = z * z;
   const float xy = x * y, yz = y * z, xz = x * z, d = x2 - y2, e = x2 + y2;
   P[0] = y; P[1] = z; P[2] = x;
@@ -408,6 +408,7 @@ __host__ __device__ __forceinline__ void harmonics_p(float x, float y, float z, 
   P[5] = fmaf(-0.5f, e, z2);
   P[6] = xz;
   P[7] = d;
+  if constexpr (NLM > 8) {
   const float a3 = fmaf(4.f, z2, -e);          // 4 z^2 - x^2 - y^2
   const float p8 = y * fmaf(3.f, x2, -y2);     // y (3 x^2 - y^2)
   const float p14 = x * fmaf(-3.f, y2, x2);    // x (x^2 - 3 y^2)
@@ -430,6 +431,7 @@ __host__ __device__ __forceinline__ void harmonics_p(float x, float y, float z, 
   P[21] = d * b4;
   P[22] = z * p14;
   P[23] = fmaf(x2, x2, fmaf(-6.f * x2, y2, y2 * y2));
+  }
 }
 
 // Ph_lm alone (lm a compile-time constant after unrolling), for loops that form the components chunk by

@@ -94,7 +94,8 @@ struct AtomSums {
 // Walk atom i's full neighbour row and accumulate q_n, s_nlm and the LJ energy.  REC: every active pair
 // is also recorded as (dx, dy, dz, j) at rec[off + slot * BLOCK], angular pairs from slot 0 up and the
 // other active pairs from slot pmax - 1 down (the layout of accumulate_atom_tm's records).
-template <class S, int DE, int DP, int BLOCK, bool REC = false>
+// UN: the sums over the polynomials Ph_lm without their constant factors (s' = s / hnorm, harmonics_p).
+template <class S, int DE, int DP, int BLOCK, bool REC = false, bool UN = false>
 __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 *shift, int i, int n,
                                                 const float4 *__restrict__ pos, const int32_t *__restrict__ nbr,
                                                 RowSpan sp, uint32_t *ring_e, float4 *ring_p, AtomSums<S> &A,
@@ -150,7 +151,8 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
         g[a] = t;
       }
       float Y[S::NLM];
-      harmonics<S::NLM>(dx * ir, dy * ir, dz * ir, Y);
+      if constexpr (UN) harmonics_p<S::NLM>(dx * ir, dy * ir, dz * ir, Y);
+      else harmonics<S::NLM>(dx * ir, dy * ir, dz * ir, Y);
 #pragma unroll
       for (int a = 0; a < S::NA; ++a)
 #pragma unroll
@@ -194,7 +196,8 @@ __device__ __forceinline__ void fourbody_tensors(const float (&s2)[S::NA][5], Fo
 }
 
 // Descriptors [q_n | q_nl (n-major, l = 1..LMAX) | q4_n = tr(T_n^3) = 3 det T_n (teacher shape only)].
-template <class S>
+// UN: A holds s'_nlm (accumulate_atom<.., UN>), scaled by hnorm(lm) here.
+template <class S, bool UN = false>
 __device__ __forceinline__ void descriptors_of(const Model<S> &P, const AtomSums<S> &A, float (&q)[S::NDES],
                                                FourBody<S> &T) {
 #pragma unroll
@@ -210,7 +213,10 @@ __device__ __forceinline__ void descriptors_of(const Model<S> &P, const AtomSums
     for (int l = 1; l <= S::LMAX; ++l) {
       float t = 0.f;
 #pragma unroll
-      for (int c = l * l - 1; c < (l + 1) * (l + 1) - 1; ++c) t = fmaf(A.s[a][c], A.s[a][c], t);
+      for (int c = l * l - 1; c < (l + 1) * (l + 1) - 1; ++c) {
+        const float sc = UN ? hnorm(c) * A.s[a][c] : A.s[a][c];
+        t = fmaf(sc, sc, t);
+      }
       q[S::NR + a * S::LMAX + (l - 1)] = t;
     }
   }
@@ -219,7 +225,7 @@ __device__ __forceinline__ void descriptors_of(const Model<S> &P, const AtomSums
 #pragma unroll
     for (int a = 0; a < S::NA; ++a)
 #pragma unroll
-      for (int m = 0; m < 5; ++m) s2[a][m] = A.s[a][3 + m];
+      for (int m = 0; m < 5; ++m) s2[a][m] = UN ? hnorm(3 + m) * A.s[a][3 + m] : A.s[a][3 + m];
     fourbody_tensors<S>(s2, T, q);
   }
 }
@@ -289,17 +295,21 @@ __device__ __forceinline__ void fourbody_adjoint(int a, const FourBody<S> &T, fl
 
 // Adjoint of channel a: gl[c] = dU/ds_{a,c} = 2 Fp_{a,l(c)} s_{a,c} (+ 4-body gradient for l = 2:
 // d tr(T^3)/d s_m = 3 (T^2) : dT/ds_m).
-template <class S>
+// UN: A holds s'_nlm and the row is G'_nlm = hnorm(lm) G_nlm (adjoint_chunk).
+template <class S, bool UN = false>
 __device__ __forceinline__ void adjoint_channel(int a, const AtomSums<S> &A, const FourBody<S> &T,
                                                 const float (&Fp)[S::NDES], float (&gl)[S::NLM]) {
 #pragma unroll
-  for (int c = 0; c < S::NLM; ++c) gl[c] = 2.f * Fp[S::NR + a * S::LMAX + lm_l(c) - 1] * A.s[a][c];
+  for (int c = 0; c < S::NLM; ++c) {
+    const float h = UN ? hnorm(c) : 1.f;
+    gl[c] = (2.f * h * h) * Fp[S::NR + a * S::LMAX + lm_l(c) - 1] * A.s[a][c];
+  }
   if constexpr (S::FOURBODY) {
     const float f4 = Fp[S::NR + S::NA * S::LMAX + a];
     float g4[5];
     fourbody_adjoint<S>(a, T, g4);
 #pragma unroll
-    for (int m = 0; m < 5; ++m) gl[3 + m] = fmaf(f4, g4[m], gl[3 + m]);
+    for (int m = 0; m < 5; ++m) gl[3 + m] = fmaf(UN ? hnorm(3 + m) * f4 : f4, g4[m], gl[3 + m]);
   }
 }
 

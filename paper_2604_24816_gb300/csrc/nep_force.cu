@@ -840,11 +840,11 @@ k_nep_fused_reg(const __grid_constant__ Model<S> P, const Geom geom, const int n
   long long acc_f[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < n) {
     AtomSums<S> A;
-    accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK, true>(P, shift, i, n, pos, nbr, full_row(X, i, skip_far(X)),
+    accumulate_atom<S, PIPE_DE, PIPE_DP, DESC_BLOCK, true, true>(P, shift, i, n, pos, nbr, full_row(X, i, skip_far(X)),
                                                            ring_e, ring_p, A, pc.rec, rec_off, pc.pmax);
     float q[S::NDES];
     FourBody<S> T;
-    descriptors_of<S>(P, A, q, T);
+    descriptors_of<S, true>(P, A, q, T);
     if (qout != nullptr) {
 #pragma unroll
       for (int v = 0; v < S::NDES; ++v) qout[(size_t)i * S::NDES + v] = q[v];
@@ -855,7 +855,7 @@ k_nep_fused_reg(const __grid_constant__ Model<S> P, const Geom geom, const int n
     const float U = network<S>(P, q, flagged, Fp);   // flagged: no U_i from this model, Fp = 0
     float gi[S::NA][S::NLM];
 #pragma unroll
-    for (int a = 0; a < S::NA; ++a) adjoint_channel<S>(a, A, T, Fp, gi[a]);
+    for (int a = 0; a < S::NA; ++a) adjoint_channel<S, true>(a, A, T, Fp, gi[a]);
     {
       float tail[8];
       radial_tail<S>(P, Fp, tail);
@@ -871,7 +871,7 @@ k_nep_fused_reg(const __grid_constant__ Model<S> P, const Geom geom, const int n
     acc_d[3] = A.cnt;
     acc_d[4] = A.nact;
     acc_f[9] = A.cnt; acc_f[10] = A.nact; acc_f[11] = A.nrad; acc_f[12] = A.nang;
-    force_pairs_rec<S, PIPE_DP>(P, 0u, gi, fp_s + threadIdx.x, i, true, n, pc.rec, rec_off, pc.pmax, A.nang,
+    force_pairs_rec<S, PIPE_DP, true>(P, 0u, gi, fp_s + threadIdx.x, i, true, n, pc.rec, rec_off, pc.pmax, A.nang,
                                 A.nact - A.nang, ring_p, Ffix, status, acc_f);
   }
   __syncthreads();

@@ -86,6 +86,16 @@ def test_flop_model_counts_units():
     rs, hs = bench.FLOPS_STUDENT["force_rec"], bench.FLOPS_STUDENT["force"]
     assert all(rs[k] == r[k] for k in ("list_entry", "active_pair", "radial_pair", "lj_pair", "atom"))
     assert 0.3 * r["angular_pair"] < rs["angular_pair"] < hs["angular_pair"]
+    # ... and its descriptor part keeps the sums over the polynomials without their constants (8 of them:
+    # 14 -> 10 FLOPs per angular pair; 16 + 8 more scalings per atom), used by the float32 student only
+    ds, dr = bench.FLOPS_STUDENT["descriptor"], bench.FLOPS_STUDENT["descriptor_rec"]
+    assert dr["angular_pair"] == ds["angular_pair"] - 4 and dr["atom"] == ds["atom"] + 24
+    assert all(dr[k] == ds[k] for k in ("list_entry", "active_pair", "radial_pair", "lj_pair"))
+    assert rs["angular_pair"] == 453 - 4 - 6      # polynomials 14 -> 10, gradients 9 -> 3
+    for f, m in bench.FORMS.items():
+        want = (("descriptor_rec" if m["precision"] == "fp32" else "descriptor") if m["model"] == "student" else
+                ("descriptor_mixed" if f in ("mix_bf16", "mix_fp16") else "descriptor"))
+        assert bench.descriptor_kind(f) == want
     # the mixed forms' descriptor part differs only in the network (on the tensor cores)
     dm, dd = bench.FLOPS["descriptor_mixed"], bench.FLOPS["descriptor"]
     assert all(dm[k] == dd[k] for k in dd if k != "atom") and dm["atom"] < dd["atom"]

@@ -217,7 +217,7 @@ __device__ __forceinline__ void cheb_basis(float r, float inv_rc, float (&f)[K])
   float s, c;
   const float t = r * inv_rc;
   __sincosf(3.14159265358979f * t, &s, &c);
-  const float h = fmaf(0.5f, c, 0.5f) * 0.5f;   // fc / 2
+  const float h = fmaf(0.25f, c, 0.25f);         // fc / 2 (= (c + 1) / 4, one rounding)
   const float u = t - 1.f;
   const float x = fmaf(2.f * u, u, -1.f);
   const float x2 = x + x;
@@ -241,7 +241,7 @@ __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K
   float s, c;
   const float t = r * inv_rc;
   __sincosf(3.14159265358979f * t, &s, &c);
-  const float h = fmaf(0.5f, c, 0.5f) * 0.5f;                     // fc / 2
+  const float h = fmaf(0.25f, c, 0.25f);                           // fc / 2
   const float dh = (-0.25f * 3.14159265358979f * inv_rc) * s;      // fc' / 2
   const float u = t - 1.f;
   const float x = fmaf(2.f * u, u, -1.f);
@@ -274,7 +274,7 @@ __device__ __forceinline__ void cheb_dbasis_x2(float2 r, float inv_rc, float2 (&
   const float2 t = mul2(r, bc2(inv_rc));
   __sincosf(3.14159265358979f * t.x, &s.x, &cs.x);
   __sincosf(3.14159265358979f * t.y, &s.y, &cs.y);
-  const float2 h = mul2(fma2(bc2(0.5f), cs, bc2(0.5f)), bc2(0.5f));                 // fc / 2
+  const float2 h = fma2(bc2(0.25f), cs, bc2(0.25f));                                // fc / 2
   const float2 dh = mul2(bc2(-0.25f * 3.14159265358979f * inv_rc), s);              // fc' / 2
   const float2 u = add2(t, bc2(-1.f));
   const float2 x = fma2(mul2(bc2(2.f), u), u, bc2(-1.f));
@@ -296,7 +296,7 @@ __device__ __forceinline__ void cheb_dbasis_x2(float2 r, float inv_rc, float2 (&
 // so that sum_m Yh_lm(u) Yh_lm(v) = P_l(u . v).  Written as solid-harmonic polynomials of a unit vector.
 // NLM = 8 computes l = 1, 2 only.
 template <int NLM>
-__device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[NLM]) {
+__host__ __device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[NLM]) {
   static_assert(NLM == 8 || NLM == 24, "l_max 2 or 4");
   const float x2 = x * x, y2 = y * y, z2 = z * z;
   const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
@@ -338,7 +338,7 @@ __device__ __forceinline__ void harmonics(float x, float y, float z, float (&Y)[
 // Gradient (ax, ay, az) of the solid-harmonic polynomial of component lm at (x, y, z).  lm is a
 // compile-time constant after unrolling; harmonic_grad_mask(lm) has bit d set when component d can be
 // non-zero, so callers skip the multiply-adds of the identically zero ones.
-__device__ __forceinline__ void harmonic_grad(int lm, float x, float y, float z, float (&a)[3]) {
+__host__ __device__ __forceinline__ void harmonic_grad(int lm, float x, float y, float z, float (&a)[3]) {
   const float x2 = x * x, y2 = y * y, z2 = z * z;
   const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
   const float s10 = 3.1622776601683795f, s15 = 3.872983346207417f, s35 = 5.916079783099616f;

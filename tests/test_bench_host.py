@@ -91,7 +91,7 @@ def test_flop_model_counts_units():
     ds, dr = bench.FLOPS_STUDENT["descriptor"], bench.FLOPS_STUDENT["descriptor_rec"]
     assert dr["angular_pair"] == ds["angular_pair"] - 4 and dr["atom"] == ds["atom"] + 24
     assert all(dr[k] == ds[k] for k in ("list_entry", "active_pair", "radial_pair", "lj_pair"))
-    assert rs["angular_pair"] == 453 - 4 - 6      # polynomials 14 -> 10, gradients 9 -> 3
+    assert rs["angular_pair"] == 452 - 4 - 6      # polynomials 14 -> 10, gradients 9 -> 3
     for f, m in bench.FORMS.items():
         want = (("descriptor_rec" if m["precision"] == "fp32" else "descriptor") if m["model"] == "student" else
                 ("descriptor_mixed" if f in ("mix_bf16", "mix_fp16") else "descriptor"))

@@ -61,7 +61,8 @@ UNIT = "atom-steps/s"
 #   radial pair, descriptor 48: Chebyshev basis 40 (r/rc, pi r/rc and the hardware sine/cosine 4, the
 #     cutoff half (1 + cos) / 4 as one FMA 2, x = 2 (r/rc - 1)^2 - 1 5, 6 recurrence FMAs, 4 paired
 #     FMAs) + 4 paired adds;
-#   LJ pair, descriptor 17: 1/r^2 with one Newton step, r^-6, r^-12, the shifted energy, half of it summed;
+#   LJ pair, descriptor 15: 1/r^2 with one Newton step 5, r^-6 2, the shifted energy factored as
+#     r^-6 (c12 r^-6 - c6) + (rc E'(rc) - E(rc)) - r E'(rc) in three FMAs 6, half of it summed 2;
 #   angular pair, descriptor 410: unit vector 3 + basis 40 + 5 channel dot products 75 + the 24
 #     harmonic polynomials without their constant factors 52 (the fused kernels keep the sums and the
 #     adjoint row over Ph_lm = Yh_lm / hnorm(lm); with the constants, as the separate kernels, 81) +
@@ -74,13 +75,14 @@ UNIT = "atom-steps/s"
 #   active pair, force from the pair records 28: r^2, rsqrt, r (7), d = coef r + v (6), F_i (3),
 #     virial upper triangle (12); the list-walking force kernel: 23 plus 11 per list entry;
 #   radial pair, force 117: basis and derivative 101 + dot with the radial adjoint 15 + 1/r;
-#   LJ pair, force 18;
+#   LJ pair, force 15: 1/r^2, r^-6 (7), dE/dr = r^-6 (-12 c12 r^-6 + 6 c6) / r - E'(rc) (5), half of it / r
+#     added to the pair coefficient (3);
 #   angular pair, force 1105 (fused kernels, over Ph_lm): unit vector 3 + basis and derivative 101 +
 #     2 x 5 channel dots 150 + the polynomials 52 + per (l, m) the sums A_lm, B_lm over the channels 480
 #     + (A - l B / r) Ph 96 + the l / r factors 12 + the polynomials' gradients 86 and their 58 non-zero
 #     FMAs 116 + 9; the list-walking force kernels over Yh_lm: 1177 (harmonics 81, gradients 129);
 #   the half-list force (float16 rows): H = G^i + (-1)^l G^j adds 240 per angular pair and 8 per radial
-#     pair; its LJ term is the whole pair force (17).
+#     pair; its LJ term is the whole pair force (14).
 # The FP32 op counters of one fused launch (ffma, fadd, fmul, paired ops, MUFU) agree with this count to
 # within the conversions and padding named above (profiles/k_nep_fused_cu64x64x64.md).
 # The mixed-precision forms run the same fused kernel with the network as two tensor-core GEMMs
@@ -88,11 +90,11 @@ UNIT = "atom-steps/s"
 # network + scaling 30, per neuron z - b0, tanh, energy FMA and gradient factor 7, Fp 30); the GEMMs'
 # 4096 tensor FLOPs per atom are not part of the FP32 count.
 FLOPS = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=17, angular_pair=410, atom=5106),
-    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=17, angular_pair=410, atom=1506),
-    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=117, lj_pair=18, angular_pair=1105, atom=0),
-    "force_full": dict(list_entry=11, active_pair=23, radial_pair=117, lj_pair=18, angular_pair=1177, atom=0),
-    "force": dict(list_entry=11, active_pair=23, radial_pair=125, lj_pair=17, angular_pair=1417, atom=0),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=410, atom=5106),
+    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=410, atom=1506),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=117, lj_pair=15, angular_pair=1105, atom=0),
+    "force_full": dict(list_entry=11, active_pair=23, radial_pair=117, lj_pair=15, angular_pair=1177, atom=0),
+    "force": dict(list_entry=11, active_pair=23, radial_pair=125, lj_pair=14, angular_pair=1417, atom=0),
 }
 # The same count for the student shape (4 + 4 channels, 8 basis functions, l = 1, 2, no 4-body term,
 # 16 neurons): register-resident sums, scalar channel dots (16 per channel), 8 harmonics (14),
@@ -105,10 +107,10 @@ FLOPS = {
 # 28 + 9; its mixed form runs the separate kernels (harmonics with their constants) with the force over
 # the half list.
 FLOPS_STUDENT = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=17, angular_pair=185, atom=1145),
-    "descriptor_rec": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=17, angular_pair=181, atom=1169),
-    "force": dict(list_entry=11, active_pair=23, radial_pair=125, lj_pair=17, angular_pair=510, atom=0),
-    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=117, lj_pair=18, angular_pair=442, atom=0),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=185, atom=1145),
+    "descriptor_rec": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=181, atom=1169),
+    "force": dict(list_entry=11, active_pair=23, radial_pair=125, lj_pair=14, angular_pair=510, atom=0),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=117, lj_pair=15, angular_pair=442, atom=0),
 }
 # Algorithmic HBM bytes per atom-step: the integrator reads and writes x, v (96) in the kick + drift and
 # v (48) in the second kick, and reads the forces in both kicks (48); the force kernel reads the atom's

@@ -776,10 +776,14 @@ void fill_model(Model<S> &M, const nep_params *p) {
     M.lj_c6 = (float)(4.0 * eps * s6);
     M.lj_e_rc = (float)(4.0 * eps * (sr6 * sr6 - sr6));
     M.lj_de_rc = (float)(4.0 * eps * (-12.0 * sr6 * sr6 + 6.0 * sr6) / rc);
+    M.lj_e0 = (float)(4.0 * eps * ((-12.0 * sr6 * sr6 + 6.0 * sr6) - (sr6 * sr6 - sr6)));   // rc E'(rc) - E(rc)
+    M.lj_m12 = (float)(-12.0 * 4.0 * eps * s6 * s6);
+    M.lj_p6 = (float)(6.0 * 4.0 * eps * s6);
     M.lj_rc = (float)rc;
     M.lj_rc2 = (float)(rc * rc);
   } else {
     M.lj_c12 = M.lj_c6 = M.lj_e_rc = M.lj_de_rc = 0.f;
+    M.lj_e0 = M.lj_m12 = M.lj_p6 = 0.f;
     M.lj_rc = 0.f; M.lj_rc2 = 0.f;
   }
   const float rmax = std::max(p->rc_R, eps != 0.0 ? p->lj_rc : 0.f);

@@ -107,6 +107,7 @@ struct Model {
   float b1;
   float rcR, rcA, rcR2, rcA2, inv_rcR, inv_rcA;
   float lj_on, lj_c12, lj_c6, lj_rc2, lj_e_rc, lj_de_rc, lj_rc;  // shifted-force LJ
+  float lj_e0, lj_m12, lj_p6;   // rc E'(rc) - E(rc), -12 c12, 6 c6 (the factored forms of lj_pair)
   float rmax2;   // max(rcR, lj_rc)^2
 };
 
@@ -552,9 +553,10 @@ __device__ __forceinline__ void lj_pair(const Model<S> &P, float r2, float r, fl
   float ir2 = ir * ir;
   ir2 = fmaf(ir2, fmaf(-r2, ir2, 1.f), ir2);
   const float ir6 = ir2 * ir2 * ir2;
-  const float a12 = P.lj_c12 * ir6 * ir6, a6 = P.lj_c6 * ir6;
-  e = a12 - a6 - P.lj_e_rc - (r - P.lj_rc) * P.lj_de_rc;
-  de = fmaf(-12.f, a12, 6.f * a6) * ir - P.lj_de_rc;
+  // E = c12 r^-12 - c6 r^-6 - E(rc) - (r - rc) E'(rc) = r^-6 (c12 r^-6 - c6) + (rc E'(rc) - E(rc)) - r E'(rc)
+  e = fmaf(ir6, fmaf(P.lj_c12, ir6, -P.lj_c6), fmaf(-P.lj_de_rc, r, P.lj_e0));
+  // dE/dr = r^-6 (-12 c12 r^-6 + 6 c6) / r - E'(rc)
+  de = fmaf(ir6 * fmaf(P.lj_m12, ir6, P.lj_p6), ir, -P.lj_de_rc);
 }
 
 // lj_pair's derivative dE/dr for two pairs at once.
@@ -563,8 +565,7 @@ __device__ __forceinline__ float2 lj_deriv_x2(const Model<S> &P, float2 r2, floa
   float2 ir2 = mul2(ir, ir);
   ir2 = fma2(ir2, fma2(make_float2(-r2.x, -r2.y), ir2, bc2(1.f)), ir2);
   const float2 ir6 = mul2(mul2(ir2, ir2), ir2);
-  const float2 a12 = mul2(mul2(bc2(P.lj_c12), ir6), ir6), a6 = mul2(bc2(P.lj_c6), ir6);
-  return fma2(fma2(bc2(-12.f), a12, mul2(bc2(6.f), a6)), ir, bc2(-P.lj_de_rc));
+  return fma2(mul2(ir6, fma2(bc2(P.lj_m12), ir6, bc2(P.lj_p6))), ir, bc2(-P.lj_de_rc));
 }
 
 // Exact conversion of a float to 64-bit fixed point with 32 fractional bits, without a 64-bit

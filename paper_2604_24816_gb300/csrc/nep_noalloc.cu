@@ -223,6 +223,9 @@ extern "C" nep_status nep_compute_noalloc(const nep_params *p, int64_t n, const 
     M.lj_c6 = (float)(4.0 * eps * s6);
     M.lj_e_rc = (float)(4.0 * eps * (sr6 * sr6 - sr6));
     M.lj_de_rc = (float)(4.0 * eps * (-12.0 * sr6 * sr6 + 6.0 * sr6) / rc);
+    M.lj_e0 = (float)(4.0 * eps * ((-12.0 * sr6 * sr6 + 6.0 * sr6) - (sr6 * sr6 - sr6)));   // rc E'(rc) - E(rc)
+    M.lj_m12 = (float)(-12.0 * 4.0 * eps * s6 * s6);
+    M.lj_p6 = (float)(6.0 * 4.0 * eps * s6);
     M.lj_rc = (float)rc;
     M.lj_rc2 = (float)(rc * rc);
   }

@@ -58,26 +58,31 @@ UNIT = "atom-steps/s"
 # counted.  Pieces (teacher shape):
 #   list entry 11: displacement (6 adds) and r^2 (1 mul + 2 FMA);
 #   active pair, descriptor 2: rsqrt and r;
-#   radial pair, descriptor 48: Chebyshev basis 40 (r/rc, pi r/rc and the hardware sine/cosine 4, the
-#     cutoff half (1 + cos) / 4 as one FMA 2, x = 2 (r/rc - 1)^2 - 1 5, 6 recurrence FMAs, 4 paired
-#     FMAs) + 4 paired adds;
+#   radial pair, descriptor 38: the Chebyshev factors 22 (r/rc, pi r/rc and the hardware cosine 3, the
+#     cutoff half h = (1 + cos) / 4 as one FMA 2, x = 2 (r/rc - 1)^2 - 1 5, 6 recurrence FMAs 12) and the
+#     sums h T_k in 4 paired FMAs 16 (sum f_k = sum h T_k + sum h: 8 adds per atom); the angular basis
+#     f_k = h (T_k + 1) of an angular pair is formed (40);
 #   LJ pair, descriptor 15: 1/r^2 with one Newton step 5, r^-6 2, the shifted energy factored as
 #     r^-6 (c12 r^-6 - c6) + (rc E'(rc) - E(rc)) - r E'(rc) in three FMAs 6, half of it summed 2;
 #   angular pair, descriptor 410: unit vector 3 + basis 40 + 5 channel dot products 75 + the 24
 #     harmonic polynomials without their constant factors 52 (the fused kernels keep the sums and the
 #     adjoint row over Ph_lm = Yh_lm / hnorm(lm); with the constants, as the separate kernels, 81) +
 #     120 paired FMAs into s_nlm 240;
-#   atom, descriptor 5106: q_n 80, q_nl 335 (240 + the 95 hnorm scalings of the sums), 4-body tensors and
+#   atom, descriptor 5114: the radial sums' 8 adds, q_n 80, q_nl 335 (240 + the 95 hnorm scalings of the sums), 4-body tensors and
 #     q4 130, network 3870 (scaling 60 and 30 neurons x (30 FMAs forward, tanh, energy, gradient
 #     factor, 30 FMAs back)), 4-body adjoint 350 (330 + 20 scalings), adjoint row 260 (G' = 2 hnorm^2 Fp
 #     s' + hnorm f4 g4: 16 distinct hnorm^2 Fp factors per channel 80, 120 products, 10 hnorm f4
 #     factors, 25 FMAs), radial adjoint in basis space 80, site energy 1;
 #   active pair, force from the pair records 28: r^2, rsqrt, r (7), d = coef r + v (6), F_i (3),
 #     virial upper triangle (12); the list-walking force kernel: 23 plus 11 per list entry;
-#   radial pair, force 117: basis and derivative 101 + dot with the radial adjoint 15 + 1/r;
+#   radial pair, force 80 (fused kernels): the Chebyshev factors and their derivatives 50 (h, h', x'(r) h,
+#     T_k and T_k' recurrences) and the radial-adjoint contraction h' sum t_k T_k + x' h sum t_k T_k'
+#     without forming the f_k' 30 (paired, two records per iteration; 84 one at a time: the angular
+#     pairs' radial part, +4 in their angular count, and the student); the list-walking force kernels
+#     form the f_k': 117 (basis and derivative 101 + dot with the radial adjoint 15 + 1/r);
 #   LJ pair, force 15: 1/r^2, r^-6 (7), dE/dr = r^-6 (-12 c12 r^-6 + 6 c6) / r - E'(rc) (5), half of it / r
 #     added to the pair coefficient (3);
-#   angular pair, force 1105 (fused kernels, over Ph_lm): unit vector 3 + basis and derivative 101 +
+#   angular pair, force 1109 (fused kernels, over Ph_lm): 4 for its radial part one at a time + unit vector 3 + basis and derivative 101 +
 #     2 x 5 channel dots 150 + the polynomials 52 + per (l, m) the sums A_lm, B_lm over the channels 480
 #     + (A - l B / r) Ph 96 + the l / r factors 12 + the polynomials' gradients 86 and their 58 non-zero
 #     FMAs 116 + 9; the list-walking force kernels over Yh_lm: 1177 (harmonics 81, gradients 129);
@@ -86,13 +91,13 @@ UNIT = "atom-steps/s"
 # The FP32 op counters of one fused launch (ffma, fadd, fmul, paired ops, MUFU) agree with this count to
 # within the conversions and padding named above (profiles/k_nep_fused_cu64x64x64.md).
 # The mixed-precision forms run the same fused kernel with the network as two tensor-core GEMMs
-# (32 x 32 tiles, bf16/f16 operands): per atom 1506 FP32 FLOPs remain (5106 - 3870 for the float32
+# (32 x 32 tiles, bf16/f16 operands): per atom 1514 FP32 FLOPs remain (5114 - 3870 for the float32
 # network + scaling 30, per neuron z - b0, tanh, energy FMA and gradient factor 7, Fp 30); the GEMMs'
 # 4096 tensor FLOPs per atom are not part of the FP32 count.
 FLOPS = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=410, atom=5106),
-    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=410, atom=1506),
-    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=117, lj_pair=15, angular_pair=1105, atom=0),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=38, lj_pair=15, angular_pair=410, atom=5114),
+    "descriptor_mixed": dict(list_entry=11, active_pair=2, radial_pair=38, lj_pair=15, angular_pair=410, atom=1514),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=80, lj_pair=15, angular_pair=1109, atom=0),
     "force_full": dict(list_entry=11, active_pair=23, radial_pair=117, lj_pair=15, angular_pair=1177, atom=0),
     "force": dict(list_entry=11, active_pair=23, radial_pair=125, lj_pair=14, angular_pair=1417, atom=0),
 }
@@ -107,10 +112,10 @@ FLOPS = {
 # 28 + 9; its mixed form runs the separate kernels (harmonics with their constants) with the force over
 # the half list.
 FLOPS_STUDENT = {
-    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=185, atom=1145),
-    "descriptor_rec": dict(list_entry=11, active_pair=2, radial_pair=48, lj_pair=15, angular_pair=181, atom=1169),
+    "descriptor": dict(list_entry=11, active_pair=2, radial_pair=38, lj_pair=15, angular_pair=185, atom=1153),
+    "descriptor_rec": dict(list_entry=11, active_pair=2, radial_pair=38, lj_pair=15, angular_pair=181, atom=1177),
     "force": dict(list_entry=11, active_pair=23, radial_pair=125, lj_pair=14, angular_pair=510, atom=0),
-    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=117, lj_pair=15, angular_pair=442, atom=0),
+    "force_rec": dict(list_entry=0, active_pair=28, radial_pair=84, lj_pair=15, angular_pair=442, atom=0),
 }
 # Algorithmic HBM bytes per atom-step: the integrator reads and writes x, v (96) in the kick + drift and
 # v (48) in the second kick, and reads the forces in both kicks (48); the force kernel reads the atom's

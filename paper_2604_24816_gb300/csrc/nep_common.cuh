@@ -267,21 +267,56 @@ __device__ __forceinline__ void cheb_basis_d(float r, float inv_rc, float (&f)[K
   }
 }
 
-// The basis derivatives f_k'(r) of cheb_basis_d for two radii at once (the values f_k are not formed).
+// The factors of cheb_basis / cheb_basis_d, for sums that never form f_k or f_k' themselves: h = fc / 2,
+// dh = fc' / 2, dxh = x'(r) h, T_k(x) and D_k = T_k'(x) (T_0 = 1, D_0 = 0, D_1 = 1), so that
+// f_k = h (T_k + 1) and f_k' = (T_k + 1) dh + D_k dxh.  Summed over pairs, sum f_k = sum h T_k + sum h,
+// and a contraction sum_k t_k f_k' = dh (sum_k t_k T_k + sum_k t_k) + dxh sum_k t_k D_k.
 template <int K>
-__device__ __forceinline__ void cheb_dbasis_x2(float2 r, float inv_rc, float2 (&df)[K]) {
+__device__ __forceinline__ void cheb_t(float r, float inv_rc, float &h, float (&T)[K]) {
+  static_assert(K >= 2, "basis size");
+  const float t = r * inv_rc;
+  h = fmaf(0.25f, __cosf(3.14159265358979f * t), 0.25f);
+  const float u = t - 1.f;
+  const float x = fmaf(2.f * u, u, -1.f);
+  const float x2 = x + x;
+  T[0] = 1.f; T[1] = x;
+#pragma unroll
+  for (int k = 2; k < K; ++k) T[k] = fmaf(x2, T[k - 1], -T[k - 2]);
+}
+template <int K>
+__device__ __forceinline__ void cheb_td(float r, float inv_rc, float &dh, float &dxh, float (&T)[K], float (&D)[K]) {
+  static_assert(K >= 2, "basis size");
+  float s, c;
+  const float t = r * inv_rc;
+  __sincosf(3.14159265358979f * t, &s, &c);
+  const float h = fmaf(0.25f, c, 0.25f);
+  dh = (-0.25f * 3.14159265358979f * inv_rc) * s;
+  const float u = t - 1.f;
+  const float x = fmaf(2.f * u, u, -1.f);
+  const float x2 = x + x;
+  dxh = (4.f * inv_rc) * u * h;
+  T[0] = 1.f; T[1] = x;
+  D[0] = 0.f; D[1] = 1.f;
+#pragma unroll
+  for (int k = 2; k < K; ++k) {
+    T[k] = fmaf(x2, T[k - 1], -T[k - 2]);
+    D[k] = fmaf(x2, D[k - 1], fmaf(2.f, T[k - 1], -D[k - 2]));
+  }
+}
+template <int K>
+__device__ __forceinline__ void cheb_td_x2(float2 r, float inv_rc, float2 &dh, float2 &dxh, float2 (&T)[K],
+                                           float2 (&D)[K]) {
   static_assert(K >= 2, "basis size");
   float2 s, cs;
   const float2 t = mul2(r, bc2(inv_rc));
   __sincosf(3.14159265358979f * t.x, &s.x, &cs.x);
   __sincosf(3.14159265358979f * t.y, &s.y, &cs.y);
-  const float2 h = fma2(bc2(0.25f), cs, bc2(0.25f));                                // fc / 2
-  const float2 dh = mul2(bc2(-0.25f * 3.14159265358979f * inv_rc), s);              // fc' / 2
+  const float2 h = fma2(bc2(0.25f), cs, bc2(0.25f));
+  dh = mul2(bc2(-0.25f * 3.14159265358979f * inv_rc), s);
   const float2 u = add2(t, bc2(-1.f));
   const float2 x = fma2(mul2(bc2(2.f), u), u, bc2(-1.f));
   const float2 x2 = add2(x, x);
-  const float2 dxh = mul2(mul2(bc2(4.f * inv_rc), u), h);                           // x'(r) h
-  float2 T[K], D[K];
+  dxh = mul2(mul2(bc2(4.f * inv_rc), u), h);
   T[0] = bc2(1.f); T[1] = x;
   D[0] = bc2(0.f); D[1] = bc2(1.f);
 #pragma unroll
@@ -289,8 +324,6 @@ __device__ __forceinline__ void cheb_dbasis_x2(float2 r, float inv_rc, float2 (&
     T[k] = fma2(x2, T[k - 1], make_float2(-T[k - 2].x, -T[k - 2].y));
     D[k] = fma2(x2, D[k - 1], fma2(bc2(2.f), T[k - 1], make_float2(-D[k - 2].x, -D[k - 2].y)));
   }
-#pragma unroll
-  for (int k = 0; k < K; ++k) df[k] = fma2(D[k], dxh, fma2(T[k], dh, dh));
 }
 
 // Normalised real harmonics Yh_lm(u) = sqrt(4 pi / (2l+1)) Y_lm(u), l = 1..4 (24 values, m = -l..l),

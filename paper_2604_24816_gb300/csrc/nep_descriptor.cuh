@@ -128,10 +128,11 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
     const float ir = rsqrtf(r2);
     const float r = r2 * ir;
     if (r2 < P.rcR2) {
-      float f[S::KR];
-      cheb_basis<S::KR>(r, P.inv_rcR, f);
+      // sum h T_k here (T_0 = 1: QR[0] collects sum h); sum f_k = sum h T_k + sum h after the walk
+      float h, T[S::KR];
+      cheb_t<S::KR>(r, P.inv_rcR, h, T);
 #pragma unroll
-      for (int k = 0; k < S::KR; ++k) A.QR[k] += f[k];
+      for (int k = 0; k < S::KR; ++k) A.QR[k] = fmaf(h, T[k], A.QR[k]);
       ++A.nrad;
     }
     if (P.lj_on != 0.f && r2 < P.lj_rc2) {
@@ -161,6 +162,9 @@ __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 
     }
   }
   pipe.finish();
+  const float hsum = A.QR[0];
+#pragma unroll
+  for (int k = 0; k < S::KR; ++k) A.QR[k] += hsum;
 }
 template <class S, int DE, int DP, int BLOCK>
 __device__ __forceinline__ void accumulate_atom(const Model<S> &P, const float4 *shift, int i, int n,
@@ -273,6 +277,15 @@ __device__ __forceinline__ void radial_tail(const Model<S> &P, const float (&Fp)
     }
     tail[k] = t;
   }
+}
+
+// The radial tail as the fused kernels' force pass contracts it with the Chebyshev factors (cheb_td):
+// tail_0 + sum_k tail_k in place of tail_0 (the T_0 = 1 term then also carries sum_k tail_k dh).
+__device__ __forceinline__ void radial_tail_td(float (&tail)[8]) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += tail[k];
+  tail[0] += s;
 }
 
 // 4-body part of the adjoint of channel a for the l = 2 components 3..7, per unit dU/dq4_a:
@@ -420,10 +433,12 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
       }
       ++nact;
       if (r2 < P.rcR2) {
-        float f[S::KR];
-        cheb_basis<S::KR>(r, P.inv_rcR, f);
+        // sum h T_k here (T_0 = 1, so QR2[0].x collects sum h); sum f_k = sum h T_k + sum h below
+        float h, T[S::KR];
+        cheb_t<S::KR>(r, P.inv_rcR, h, T);
+        const float2 h2 = bc2(h);
 #pragma unroll
-        for (int b = 0; b < S::KR / 2; ++b) QR2[b] = add2(QR2[b], pr(f[2 * b], f[2 * b + 1]));
+        for (int b = 0; b < S::KR / 2; ++b) QR2[b] = fma2(h2, pr(T[2 * b], T[2 * b + 1]), QR2[b]);
         ++nrad;
       }
       if (P.lj_on != 0.f && r2 < P.lj_rc2) {
@@ -480,8 +495,9 @@ __device__ __forceinline__ void accumulate_atom_tm(const Model<S> &P, const floa
     }
   }
   pipe.finish();
+  const float hsum = QR2[0].x;
 #pragma unroll
-  for (int k = 0; k < S::KR / 2; ++k) { QR[2 * k] = QR2[k].x; QR[2 * k + 1] = QR2[k].y; }
+  for (int k = 0; k < S::KR / 2; ++k) { QR[2 * k] = QR2[k].x + hsum; QR[2 * k + 1] = QR2[k].y + hsum; }
 }
 
 // The sums of chunk k (components 4k..4k+3) of every channel: TMEM for a < NT, registers after.

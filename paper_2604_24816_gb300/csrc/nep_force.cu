@@ -446,19 +446,22 @@ __device__ __forceinline__ void force_pairs(const Model<S> &P, const float4 *shi
 }
 
 // Radial and LJ part of one active pair's force coefficient (d = coef * r_ij + angular part): the
-// radial adjoint in basis space (8 values in shared memory at fps[0], fps[FORCE_BLOCK]) against the
-// basis derivatives, plus half of the shifted-force LJ pair force.  INSIDE_RC: the caller knows that
+// radial adjoint in basis space (8 values in shared memory at fps[0], fps[FORCE_BLOCK], in
+// radial_tail_td's form) against the basis derivatives, plus half of the shifted-force LJ pair force.  INSIDE_RC: the caller knows that
 // r < rc_R (an angular pair: rc_A <= rc_R is checked by nep_create).
 template <class S, bool INSIDE_RC = false>
 __device__ __forceinline__ float radial_lj_coef(const Model<S> &P, const float4 *fps, float r2, float r, float ir) {
   float coef = 0.f;
   if (INSIDE_RC || r2 < P.rcR2) {
-    float f[S::KR], df[S::KR];
-    cheb_basis_d<S::KR>(r, P.inv_rcR, f, df);
+    // sum_k tail_k f_k' = dh (sum_k tail_k T_k + sum_k tail_k) + dxh sum_k tail_k D_k, the first sum
+    // with the tail in radial_tail_td's form (tail_0 + sum_k tail_k at k = 0, T_0 = 1)
+    float dh, dxh, T[S::KR], D[S::KR];
+    cheb_td<S::KR>(r, P.inv_rcR, dh, dxh, T, D);
     float fpi[8];
     const float4 a = fps[0], b = fps[FORCE_BLOCK];
     fpi[0] = a.x; fpi[1] = a.y; fpi[2] = a.z; fpi[3] = a.w; fpi[4] = b.x; fpi[5] = b.y; fpi[6] = b.z; fpi[7] = b.w;
-    coef = dot_pairs<S::KR>(*reinterpret_cast<const float(*)[S::KR]>(&fpi[0]), df) * ir;
+    const float(&tl)[S::KR] = *reinterpret_cast<const float(*)[S::KR]>(&fpi[0]);
+    coef = fmaf(dh, dot_pairs<S::KR>(tl, T), dxh * dot_pairs<S::KR>(tl, D)) * ir;
   }
   if (P.lj_on != 0.f && r2 < P.lj_rc2) {
     float el, dl;
@@ -474,7 +477,7 @@ __device__ __forceinline__ float radial_lj_coef(const Model<S> &P, const float4 
 // nr other active pairs (slots pmax-1 down to pmax-nr; no TMEM).  Each pair gets the arithmetic of
 // force_pairs<S, float, false, true> on the displacement the descriptor walk computed: d_ij added to F_i,
 // subtracted from F_j (fixed point), W -= r_ij (x) d_ij (upper triangle, mirrored).  UN: the TMEM row is
-// over Ph_lm (angular_pair).
+// over Ph_lm (angular_pair).  The radial tail at fps is in radial_tail_td's form.
 template <class S, int DQ, bool UN = false>
 __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow,
                                                 const float (&gi)[ForceCfg<S>::TM ? 1 : S::NA][ForceCfg<S>::TM ? 1 : S::NLM],
@@ -540,12 +543,15 @@ __device__ __forceinline__ void force_pairs_rec(const Model<S> &P, uint32_t trow
         float2 coef = bc2(0.f);
         const bool ra = r2.x < P.rcR2, rb = r2.y < P.rcR2;
         if (ra || rb) {
-          float2 df[S::KR];
-          cheb_dbasis_x2<S::KR>(r, P.inv_rcR, df);
-          float2 dot = mul2(bc2(tail[0]), df[0]);
+          // the contraction of radial_lj_coef: dh (sum tail_k T_k) + dxh (sum tail_k D_k), T_0 = D_1 = 1
+          float2 dh, dxh, T[S::KR], D[S::KR];
+          cheb_td_x2<S::KR>(r, P.inv_rcR, dh, dxh, T, D);
+          float2 s1 = bc2(tail[0]), s2 = bc2(tail[1]);
 #pragma unroll
-          for (int k = 1; k < S::KR; ++k) dot = fma2(bc2(tail[k]), df[k], dot);
-          dot = mul2(dot, ir);
+          for (int k = 1; k < S::KR; ++k) s1 = fma2(bc2(tail[k]), T[k], s1);
+#pragma unroll
+          for (int k = 2; k < S::KR; ++k) s2 = fma2(bc2(tail[k]), D[k], s2);
+          const float2 dot = mul2(fma2(dh, s1, mul2(dxh, s2)), ir);
           coef = pr(ra ? dot.x : 0.f, rb ? dot.y : 0.f);
         }
         if (P.lj_on != 0.f) {
@@ -760,6 +766,7 @@ k_nep_fused(const __grid_constant__ Model<S> P, const Geom geom, const int n, co
   {
     float fpi[8];
     radial_tail<S>(P, Fp, fpi);
+    radial_tail_td(fpi);                 // the force pass's form (force_pairs_rec)
     fp_s[threadIdx.x] = make_float4(fpi[0], fpi[1], fpi[2], fpi[3]);
     fp_s[DESC_BLOCK + threadIdx.x] = make_float4(fpi[4], fpi[5], fpi[6], fpi[7]);
   }
@@ -859,6 +866,7 @@ k_nep_fused_reg(const __grid_constant__ Model<S> P, const Geom geom, const int n
     {
       float tail[8];
       radial_tail<S>(P, Fp, tail);
+      radial_tail_td(tail);              // the force pass's form (force_pairs_rec)
       fp_s[threadIdx.x] = make_float4(tail[0], tail[1], tail[2], tail[3]);
       fp_s[DESC_BLOCK + threadIdx.x] = make_float4(tail[4], tail[5], tail[6], tail[7]);
     }
@@ -1056,6 +1064,7 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
   {
     float fpi[8];
     radial_tail<S>(P, Fp, fpi);
+    radial_tail_td(fpi);                 // the force pass's form (force_pairs_rec)
     fp_s[t] = make_float4(fpi[0], fpi[1], fpi[2], fpi[3]);
     fp_s[DESC_BLOCK + t] = make_float4(fpi[4], fpi[5], fpi[6], fpi[7]);
   }

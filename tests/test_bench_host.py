@@ -75,16 +75,20 @@ def test_flop_model_counts_units():
     # per-entry term, and r^2 (5 FLOP) recomputed from the recorded displacement per active pair
     r = bench.FLOPS["force_rec"]
     assert r["list_entry"] == 0 and r["active_pair"] == g["active_pair"] + 5
-    assert all(r[k] == g[k] for k in ("radial_pair", "lj_pair", "atom"))
-    # ... and keeps its row over the harmonic polynomials without their constants: 81 -> 52 FLOPs for
-    # the 24 values, 129 -> 86 for their gradients
-    assert r["angular_pair"] == g["angular_pair"] - (81 - 52) - (129 - 86)
+    assert all(r[k] == g[k] for k in ("lj_pair", "atom"))
+    # ... contracts the radial adjoint with the Chebyshev factors instead of forming the 8 basis
+    # derivatives (117 -> 80 per radial pair, two at a time; 84 one at a time, for the angular pairs'
+    # radial part) and keeps its row over the harmonic polynomials without their constants: 81 -> 52
+    # FLOPs for the 24 values, 129 -> 86 for their gradients
+    assert r["radial_pair"] == g["radial_pair"] - 37
+    assert r["angular_pair"] == g["angular_pair"] - (81 - 52) - (129 - 86) + 4
     assert all(bench.force_kind(f) == ("force_rec" if bench.FORMS[f]["model"] == "teacher" or
                                        bench.FORMS[f]["precision"] == "fp32" else "force") for f in bench.FORMS)
     # the student's fused kernel: its record pass has the teacher's per-pair terms except the angular
     # one, whose channel sums scale with the 4 x 8 instead of 5 x 24 (l, m) components
     rs, hs = bench.FLOPS_STUDENT["force_rec"], bench.FLOPS_STUDENT["force"]
-    assert all(rs[k] == r[k] for k in ("list_entry", "active_pair", "radial_pair", "lj_pair", "atom"))
+    assert all(rs[k] == r[k] for k in ("list_entry", "active_pair", "lj_pair", "atom"))
+    assert rs["radial_pair"] == r["radial_pair"] + 4      # one record at a time
     assert 0.3 * r["angular_pair"] < rs["angular_pair"] < hs["angular_pair"]
     # ... and its descriptor part keeps the sums over the polynomials without their constants (8 of them:
     # 14 -> 10 FLOPs per angular pair; 16 + 8 more scalings per atom), used by the float32 student only

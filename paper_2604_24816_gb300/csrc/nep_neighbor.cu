@@ -264,21 +264,24 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
       const float oy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
       const int row = (zz * geom.ncy + yy) * geom.ncx;
       const int shb = 3 * (dy + 1) + 9 * (dz + 1);
-      {
-        // skip a row of three cells whose (y, z) slab lies beyond the list radius from atom i (its
-        // cell-relative position gives the gaps); the 1e-4 margin keeps every candidate a float32
-        // distance test could accept, so the lists are unchanged
-        const float gy = dy < 0 ? pi.y : (dy > 0 ? geom.ly - pi.y : 0.f);
-        const float gz = dz < 0 ? pi.z : (dz > 0 ? geom.lz - pi.z : 0.f);
-        if (gy * gy + gz * gz > B.b4 * 1.0001f) continue;
-      }
+      // Skip a row of three cells whose (y, z) slab lies beyond the list radius from atom i (its
+      // cell-relative position gives the gaps), and the row's left (right) cell when atom i lies farther
+      // from its own cell's left (right) face than the reach left after the slab gap: every candidate
+      // there is at least that far away in x.  The 1e-4 margin keeps every candidate a float32 distance
+      // test could accept, so the lists are unchanged.
+      const float gy = dy < 0 ? pi.y : (dy > 0 ? geom.ly - pi.y : 0.f);
+      const float gz = dz < 0 ? pi.z : (dz > 0 ? geom.lz - pi.z : 0.f);
+      const float reach2 = B.b4 * 1.0001f - (gy * gy + gz * gz);
+      if (reach2 < 0.f) continue;
+      const bool need_l = pi.x * pi.x <= reach2, need_r = (geom.lx - pi.x) * (geom.lx - pi.x) <= reach2;
       const int parts = xwrap ? 3 : 1;
       for (int part = 0; part < parts; ++part) {
         int b, e;
         if (!xwrap) {
-          b = cell_start[row + cx - 1];
-          e = cell_start[row + cx + 2];
+          b = cell_start[row + cx - (need_l ? 1 : 0)];
+          e = cell_start[row + cx + (need_r ? 2 : 1)];
         } else {
+          if ((part == 0 && !need_l) || (part == 2 && !need_r)) continue;
           int xx = cx + part - 1;
           xx += xx < 0 ? geom.ncx : (xx >= geom.ncx ? -geom.ncx : 0);
           b = cell_start[row + xx];

@@ -1015,7 +1015,7 @@ k_nep_fused_mixed(const __grid_constant__ Model<S> P, const Geom geom, const int
 #pragma unroll
     for (int mu = 0; mu < FM_N; ++mu) {
       if (mu < S::NNEU) {
-        const float h = tanhf(z[mu] - P.b0[mu]);
+        const float h = tanh_sfu(z[mu] - P.b0[mu]);   // error 2^-11: below that of z (16-bit inputs)
         U = fmaf(P.w1[mu], h, U);
         tr[mu] = P.w1[mu] * (1.f - h * h);
       } else {

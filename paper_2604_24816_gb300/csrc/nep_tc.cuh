@@ -59,6 +59,13 @@ struct MmaKind<__half> {
   static constexpr int bf16 = 0;
 };
 
+// tanh of the hardware's special-function unit (PTX tanh.approx.f32: relative error about 2^-11, the unit
+// roundoff of the 16-bit operands it feeds in the mixed-precision network).
+__device__ __forceinline__ float tanh_sfu(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
 }

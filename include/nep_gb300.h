@@ -56,8 +56,11 @@ typedef enum {
 
 /* Arithmetic of the force evaluation.  NEP_FP32: everything in float32 (float64 integration and sums).
  * NEP_MIX_BF16 / NEP_MIX_FP16: descriptors in float32; the network GEMMs (forward and gradient) on the
- * tensor cores with bf16 / f16 operands and float32 accumulation; the per-atom adjoint rows stored in
- * float16 (the paper's mixed precision, Section V.B Optimization 4 and Section VII.A). */
+ * tensor cores with bf16 / f16 operands and float32 accumulation (the paper's mixed precision, Section
+ * V.B Optimization 4 and Section VII.A).  The teacher keeps its per-atom adjoint rows in float32 (in
+ * tensor memory) and takes the network's tanh from the special-function unit (relative error about
+ * 2^-11, below that of the 16-bit GEMM inputs); the student's mixed form stores its adjoint rows in
+ * float16 between its two kernels. */
 enum { NEP_FP32 = 0, NEP_MIX_BF16 = 1, NEP_MIX_FP16 = 2 };
 
 /* Model and run parameters.  Host memory; copied by nep_create, the caller keeps ownership.

@@ -135,7 +135,8 @@ nep_status nep_compute(nep_handle *h, double *E, double *F, double *virial);
 nep_status md_verlet_step(nep_handle *h, double dt_fs, int n_steps);
 
 /* Copy positions (wrapped into the box) and velocities out, [n][3] each, original order; either may
- * be NULL.  Device arrays are written by the GPU directly, host arrays through a device staging
+ * be NULL.  Device arrays and page-locked host arrays are written by the GPU directly (16-byte stores
+ * of whole rows when the array is 16-byte aligned), pageable host arrays through a device staging
  * buffer and copies (the two arrays' copies run concurrently); returns when the data is in place. */
 nep_status nep_get_state(nep_handle *h, double *x, double *v);
 

@@ -1043,9 +1043,10 @@ nep_status nep_get_state(nep_handle *h, double *x, double *v) {
     Scope sc(h, KC_OTHER, 1);
     NEP_CUDA(h, launch_inverse_order(h->n, h->id, h->inv, h->stream));
   }
-  // device arrays are written by the kernel itself; host arrays through the staging buffer and a copy
-  // (kernel stores into page-locked host memory measured slower than the copy engines).  The positions'
-  // copy runs on a second stream, beside the velocities' store and copy.
+  // device arrays and page-locked host arrays are written by the store kernel itself (16-byte stores of
+  // whole rows: over the host link this outruns a staging buffer and a copy); pageable host arrays
+  // through the staging buffer and a copy, the positions' copy on a second stream beside the
+  // velocities' store and copy.
   if (!h->aux) NEP_CUDA(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
   for (cudaEvent_t &ev : h->aux_ev)
     if (!ev) NEP_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1053,8 +1054,9 @@ nep_status nep_get_state(nep_handle *h, double *x, double *v) {
   for (int which = 0; which < 2; ++which) {
     double *out = which == 0 ? x : v;
     if (!out) continue;
-    const bool dev = is_device_ptr(out);
-    double *stage = dev ? out : h->io + which * N3;
+    double *direct = is_device_ptr(out) ? out : pinned_alias(out);
+    const bool dev = direct != nullptr;
+    double *stage = dev ? direct : h->io + which * N3;
     {
       Scope sc(h, KC_OTHER, 1);
       if (which == 0) NEP_CUDA(h, launch_store_vec(h->n, h->inv, h->x, h->y, h->z, h->L, 1, stage, h->stream));

@@ -279,20 +279,39 @@ __global__ void k_load_state_sorted(int n, const double *__restrict__ xin, const
 
 // Sorted SoA -> original-order [n][3] float64 (positions wrapped into the box when L != nullptr).
 // One thread per atom in the caller's order (contiguous writes: out may be host memory).
+constexpr int MD_STAGE = 256;   // threads per block of the row-staging form
+// WIDE: out is 16-byte aligned; the block's rows go through shared memory and leave with 16-byte stores
+// of consecutive addresses (blockDim.x == MD_STAGE), so page-locked host memory is written by the
+// kernel itself in full lines.
+template <bool WIDE>
 __global__ void k_store_vec(int n, const int *__restrict__ inv, const double *__restrict__ a, const double *__restrict__ b,
                             const double *__restrict__ c, double Lx, double Ly, double Lz, int wrap,
                             double *__restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int s = inv[i];
-  double u = a[s], v = b[s], w = c[s];
-  if (wrap) {
-    u -= Lx * floor(u / Lx); if (u >= Lx) u -= Lx;
-    v -= Ly * floor(v / Ly); if (v >= Ly) v -= Ly;
-    w -= Lz * floor(w / Lz); if (w >= Lz) w -= Lz;
+  __shared__ double so[WIDE ? 3 * MD_STAGE : 1];
+  if (i < n) {
+    const int s = inv[i];
+    double u = a[s], v = b[s], w = c[s];
+    if (wrap) {
+      u -= Lx * floor(u / Lx); if (u >= Lx) u -= Lx;
+      v -= Ly * floor(v / Ly); if (v >= Ly) v -= Ly;
+      w -= Lz * floor(w / Lz); if (w >= Lz) w -= Lz;
+    }
+    if constexpr (WIDE) {
+      const int t3 = 3 * (int)threadIdx.x;
+      so[t3] = u; so[t3 + 1] = v; so[t3 + 2] = w;
+    } else {
+      const size_t o = 3 * (size_t)i;
+      out[o] = u; out[o + 1] = v; out[o + 2] = w;
+    }
   }
-  const size_t o = 3 * (size_t)i;
-  out[o] = u; out[o + 1] = v; out[o + 2] = w;
+  if constexpr (WIDE) {
+    __syncthreads();
+    const int base = blockIdx.x * blockDim.x, cnt = min((int)blockDim.x, n - base), nd = 3 * cnt;
+    double2 *g = reinterpret_cast<double2 *>(out + 3 * (size_t)base);
+    for (int t = threadIdx.x; t < nd / 2; t += blockDim.x) g[t] = make_double2(so[2 * t], so[2 * t + 1]);
+    if ((nd & 1) && threadIdx.x == 0) out[3 * (size_t)base + nd - 1] = so[nd - 1];
+  }
 }
 
 __global__ void k_store_force(int n, const int *__restrict__ id, const long long *__restrict__ F,
@@ -406,7 +425,11 @@ cudaError_t launch_load_state_sorted(int n, const double *xin, const double *vin
 
 cudaError_t launch_store_vec(int n, const int *inv, const double *a, const double *b, const double *c, const double L[3],
                              int wrap, double *out, cudaStream_t st) {
-  if (n > 0) k_store_vec<<<bl(n, 256), 256, 0, st>>>(n, inv, a, b, c, L[0], L[1], L[2], wrap, out);
+  if (n <= 0) return cudaSuccess;
+  if (((uintptr_t)out & 15) == 0)
+    k_store_vec<true><<<bl(n, MD_STAGE), MD_STAGE, 0, st>>>(n, inv, a, b, c, L[0], L[1], L[2], wrap, out);
+  else
+    k_store_vec<false><<<bl(n, 256), 256, 0, st>>>(n, inv, a, b, c, L[0], L[1], L[2], wrap, out);
   return cudaGetLastError();
 }
 

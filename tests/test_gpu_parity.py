@@ -457,6 +457,60 @@ def test_state_transfer_paths_agree(api, model_params):
         assert np.array_equal(ends[kind][1], ends["pageable"][1])
 
 
+def test_state_transfer_alignment_and_odd_counts(api, model_params):
+    """nep_get_state writes 16-byte aligned arrays a block of rows at a time (16-byte stores of the
+    block's span, an odd last double when the block holds an odd number of atoms) and other arrays one
+    row per thread: with 255 atoms (one block, 765 doubles) and after a rebuild (cell order != caller
+    order), the page-locked and device arrays at a 16-byte boundary and one double past it, and the
+    pageable arrays through the staging copy, all hold the same bits; an upload from arrays one double
+    past a 16-byte boundary continues the same trajectory as one from pageable arrays."""
+    import torch
+    wl = ni.fcc_cu_workload(4, 300.0, 0.05, seed=91)
+    keep = np.ones(wl.n, dtype=bool)
+    keep[17] = False                                   # a vacancy: 255 atoms
+    pos, vel = np.ascontiguousarray(wl.pos[keep]), np.ascontiguousarray(wl.vel[keep])
+    n = pos.shape[0]
+    assert n == 255
+
+    def buffers(kind):
+        """(x, v) of shape (n, 3); 'off' kinds start one double past a 16-byte boundary."""
+        if kind == "pageable":
+            return np.zeros((n, 3)), np.zeros((n, 3))
+        dev = "cuda" if kind.startswith("device") else "cpu"
+        off = 1 if kind.endswith("off") else 0
+        out = []
+        for _ in range(2):
+            base = torch.zeros(3 * n + 2, dtype=torch.float64, device=dev)
+            if dev == "cpu":
+                base = base.pin_memory()
+            t = base[off:off + 3 * n].view(n, 3)
+            assert (t.data_ptr() % 16 == 0) == (off == 0)
+            out.append(t)
+        return tuple(out)
+
+    def host(a):
+        return a if isinstance(a, np.ndarray) else a.cpu().numpy()
+
+    got, ends = {}, {}
+    kinds = ("pageable", "pinned", "pinned_off", "device", "device_off")
+    for kind in kinds:
+        with api.NEP(model_params, rebuild_every=10) as nep:
+            nep.set_state(pos, vel, wl.box)
+            nep.step(1.0, 12)                          # one rebuild: the cell order has changed
+            x, v = buffers(kind)
+            nep.get_state(x, v)
+            got[kind] = (host(x).copy(), host(v).copy())
+            nep.set_state(x, v, wl.box)                # back through the same (possibly offset) buffers
+            nep.step(1.0, 3)
+            ends[kind] = nep.get_state()
+    assert np.isfinite(got["pageable"][0]).all() and np.abs(got["pageable"][1]).max() > 0.0
+    for kind in kinds[1:]:
+        assert np.array_equal(got[kind][0], got["pageable"][0]), kind
+        assert np.array_equal(got[kind][1], got["pageable"][1]), kind
+        assert np.array_equal(ends[kind][0], ends["pageable"][0]), kind
+        assert np.array_equal(ends[kind][1], ends["pageable"][1]), kind
+
+
 def _pair_r(pos, box, i, js):
     d = pos[js] - pos[i]
     d -= box * np.round(d / box)

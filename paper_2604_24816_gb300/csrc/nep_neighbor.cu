@@ -244,7 +244,7 @@ __device__ __forceinline__ int segment_counts(int key, int lane, unsigned fsh) {
 // The candidate scan and segment placement of atom i by one warp (see k_neighbors).
 __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__restrict__ pos,
                                                   const int *__restrict__ cell_start, const Geom &geom,
-                                                  const Bands &B, int limit, uint32_t *stage, float *sdd,
+                                                  const Bands &B, int limit, float4 *stage,
                                                   uint8_t *skey, int lane, int32_t *__restrict__ nbr,
                                                   int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
                                                   int32_t *__restrict__ nown, int32_t *__restrict__ nband0,
@@ -254,65 +254,63 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
   const int cx = cell_x(pi.w), cy = cell_y(pi.w), cz = cell_z(pi.w);
   const bool xwrap = cx == 0 || cx == geom.ncx - 1;
   int acc = 0;                                         // accepted so far (warp-uniform)
-  for (int dz = -1; dz <= 1; ++dz) {
+  // The candidate ranges in stencil order (dz, dy, then the x part), set up one per lane L = 9 (dz + 1)
+  // + 3 (dy + 1) + part: a row of three cells that does not wrap around x is one range (part 0; its
+  // left or right cell left out when atom i lies farther from its own cell's face than the reach left
+  // after the row's (y, z) gap: every candidate there is at least that far away in x), a row that
+  // wraps is three; rows whose (y, z) slab lies beyond the list radius are empty.  The 1e-4 margin
+  // keeps every candidate a float32 distance test could accept, so the lists are unchanged.
+  int rb = 0, rlen = 0;
+  if (lane < 27) {
+    const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, part = lane % 3;
     int zz = cz + dz;
     zz += zz < 0 ? geom.ncz : (zz >= geom.ncz ? -geom.ncz : 0);
-    const float oz = dz < 0 ? -geom.lz : (dz > 0 ? geom.lz : 0.f);   // = the image offset table entry
-    for (int dy = -1; dy <= 1; ++dy) {
-      int yy = cy + dy;
-      yy += yy < 0 ? geom.ncy : (yy >= geom.ncy ? -geom.ncy : 0);
-      const float oy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
-      const int row = (zz * geom.ncy + yy) * geom.ncx;
-      const int shb = 3 * (dy + 1) + 9 * (dz + 1);
-      // Skip a row of three cells whose (y, z) slab lies beyond the list radius from atom i (its
-      // cell-relative position gives the gaps), and the row's left (right) cell when atom i lies farther
-      // from its own cell's left (right) face than the reach left after the slab gap: every candidate
-      // there is at least that far away in x.  The 1e-4 margin keeps every candidate a float32 distance
-      // test could accept, so the lists are unchanged.
-      const float gy = dy < 0 ? pi.y : (dy > 0 ? geom.ly - pi.y : 0.f);
-      const float gz = dz < 0 ? pi.z : (dz > 0 ? geom.lz - pi.z : 0.f);
-      const float reach2 = B.b4 * 1.0001f - (gy * gy + gz * gz);
-      if (reach2 < 0.f) continue;
+    int yy = cy + dy;
+    yy += yy < 0 ? geom.ncy : (yy >= geom.ncy ? -geom.ncy : 0);
+    const int row = (zz * geom.ncy + yy) * geom.ncx;
+    const float gy = dy < 0 ? pi.y : (dy > 0 ? geom.ly - pi.y : 0.f);
+    const float gz = dz < 0 ? pi.z : (dz > 0 ? geom.lz - pi.z : 0.f);
+    const float reach2 = B.b4 * 1.0001f - (gy * gy + gz * gz);
+    if (reach2 >= 0.f) {
       const bool need_l = pi.x * pi.x <= reach2, need_r = (geom.lx - pi.x) * (geom.lx - pi.x) <= reach2;
-      const int parts = xwrap ? 3 : 1;
-      for (int part = 0; part < parts; ++part) {
-        int b, e;
-        if (!xwrap) {
-          b = cell_start[row + cx - (need_l ? 1 : 0)];
-          e = cell_start[row + cx + (need_r ? 2 : 1)];
-        } else {
-          if ((part == 0 && !need_l) || (part == 2 && !need_r)) continue;
-          int xx = cx + part - 1;
-          xx += xx < 0 ? geom.ncx : (xx >= geom.ncx ? -geom.ncx : 0);
-          b = cell_start[row + xx];
-          e = cell_start[row + xx + 1];
+      if (!xwrap) {
+        if (part == 0) {
+          rb = cell_start[row + cx - (need_l ? 1 : 0)];
+          rlen = cell_start[row + cx + (need_r ? 2 : 1)] - rb;
         }
-        for (int j0 = b; j0 < e; j0 += 32) {
-          const int j = j0 + lane;
-          bool ok = false;
-          uint32_t ent = 0;
-          float ddx = 0.f, ddy = 0.f, ddz = 0.f;
-          if (j < e && j != i) {
-            const float4 pj = pos[j];
-            const int dx = xwrap ? part - 1 : cell_x(pj.w) - cx;
-            const float ox = dx < 0 ? -geom.lx : (dx > 0 ? geom.lx : 0.f);
-            ddx = pj.x - pi.x + ox; ddy = pj.y - pi.y + oy; ddz = pj.z - pi.z + oz;
-            if (nb_r2(ddx, ddy, ddz) < B.b4) {
-              ok = true;
-              ent = (uint32_t)j | ((uint32_t)((dx + 1) + shb) << J_BITS);
-            }
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, ok);
-          if (ok) {
-            const int slot = acc + __popc(m & lower);
-            if (slot < NB_STAGE) {
-              stage[slot] = ent;
-              sdd[slot] = ddx; sdd[NB_STAGE + slot] = ddy; sdd[2 * NB_STAGE + slot] = ddz;
-            }
-          }
-          acc += __popc(m);
-        }
+      } else if (!((part == 0 && !need_l) || (part == 2 && !need_r))) {
+        int xx = cx + part - 1;
+        xx += xx < 0 ? geom.ncx : (xx >= geom.ncx ? -geom.ncx : 0);
+        rb = cell_start[row + xx];
+        rlen = cell_start[row + xx + 1] - rb;
       }
+    }
+  }
+  // the non-empty ranges, walked in order (every lane takes part in each shuffle); each candidate is
+  // tested on every lane without a branch (the load index clamped into the range), and an accepted
+  // pair's displacement and entry go to the stage as one 16-byte record in candidate order
+  unsigned ne = __ballot_sync(0xffffffffu, rlen > 0);
+  while (ne != 0u) {
+    const int L = __ffs(ne) - 1;                       // warp-uniform
+    ne &= ne - 1u;
+    const int b = __shfl_sync(0xffffffffu, rb, L), e = b + __shfl_sync(0xffffffffu, rlen, L);
+    const int dz = L / 9 - 1, dy = (L / 3) % 3 - 1, part = L % 3;
+    const float oz = dz < 0 ? -geom.lz : (dz > 0 ? geom.lz : 0.f);   // the shift table's offsets
+    const float oy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
+    const int shb = 3 * (dy + 1) + 9 * (dz + 1);
+    for (int j0 = b; j0 < e; j0 += 32) {
+      const int j = j0 + lane;
+      const bool inr = j < e;
+      const float4 pj = pos[inr ? j : e - 1];          // j0 < e: always inside the range
+      const int dx = xwrap ? part - 1 : cell_x(pj.w) - cx;
+      const float ox = (float)dx * geom.lx;            // exact: dx is -1, 0 or 1
+      const float ddx = pj.x - pi.x + ox, ddy = pj.y - pi.y + oy, ddz = pj.z - pi.z + oz;
+      const bool ok = inr && j != i && nb_r2(ddx, ddy, ddz) < B.b4;
+      const uint32_t ent = (uint32_t)j | ((uint32_t)((dx + 1) + shb) << J_BITS);
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      const int slot = acc + __popc(m & lower);
+      if (ok && slot < NB_STAGE) stage[slot] = make_float4(ddx, ddy, ddz, __uint_as_float(ent));
+      acc += __popc(m);
     }
   }
   __syncwarp();
@@ -327,8 +325,8 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
   for (int s0 = 0; s0 < ms; s0 += 32) {
     int key = NB_SEG;
     if (s0 + lane < ms) {
-      const float ddx = sdd[s0 + lane], ddy = sdd[NB_STAGE + s0 + lane], ddz = sdd[2 * NB_STAGE + s0 + lane];
-      key = segment_of(ddx, ddy, ddz, nb_r2(ddx, ddy, ddz), B);
+      const float4 sd = stage[s0 + lane];
+      key = segment_of(sd.x, sd.y, sd.z, nb_r2(sd.x, sd.y, sd.z), B);
       skey[s0 + lane] = (uint8_t)key;
     }
     mycnt += segment_counts(key, lane, fsh);
@@ -345,7 +343,7 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
   for (int s0 = 0; s0 < ms; s0 += 32) {
     const bool valid = s0 + lane < ms;
     const int key = valid ? (int)skey[s0 + lane] : NB_SEG;
-    const uint32_t ent = valid ? stage[s0 + lane] : 0u;
+    const uint32_t ent = valid ? __float_as_uint(stage[s0 + lane].w) : 0u;
     const unsigned grp = __match_any_sync(0xffffffffu, key);
     const int k = __shfl_sync(0xffffffffu, myrun, key) + __popc(grp & lower);
     if (valid && k < limit) nbr[(size_t)k * n + i] = (int32_t)ent;
@@ -372,7 +370,8 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
 // own position broadcast): for each of the 9 (dy, dz) rows of the 27-cell stencil the three cells
 // x-1, x, x+1 are consecutive in the cell-sorted arrays, so the row is one contiguous range and a
 // candidate's x offset comes from its packed cell coordinate (rows that wrap around the periodic x
-// boundary are walked cell by cell).  Accepted entries go to a per-warp shared-memory stage in
+// boundary are walked cell by cell; the bounds of all ranges are read up front, one lane each).
+// Accepted entries go to a per-warp shared-memory stage in
 // candidate order (ballot + popc), then are placed by segment: [owned | not owned] x band, candidate
 // order inside a segment -- the same row as the thread-per-atom formulation, with 32-wide work
 // instead of divergent per-thread cell loops.
@@ -381,9 +380,8 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
             Bands B, int32_t *__restrict__ nbr, int32_t *__restrict__ nnum, int32_t *__restrict__ nang,
             int32_t *__restrict__ nown, int32_t *__restrict__ nband0, int32_t *__restrict__ nfar, Control *ctrl) {
   if (!ctrl->do_rebuild) return;
-  __shared__ uint32_t stage[NB_WARPS][NB_STAGE];
+  __shared__ float4 stage[NB_WARPS][NB_STAGE];         // staged (displacement, entry)
   __shared__ uint8_t skey[NB_WARPS][NB_STAGE];
-  __shared__ float sdd[NB_WARPS][3 * NB_STAGE];        // staged displacements (x | y | z)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // The grid is capped at the resident blocks (a launch on a step without a rebuild then costs a few
   // microseconds whatever the atom count); each block takes the next group of NB_WARPS consecutive
@@ -398,7 +396,7 @@ k_neighbors(int n, const float4 *__restrict__ pos, const int *__restrict__ cell_
     if ((long long)g * NB_WARPS >= n) break;           // block-uniform
     const int i = g * NB_WARPS + w;                    // warp-uniform
     if (i < n)
-      neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], sdd[w], skey[w], lane, nbr, nnum,
+      neighbors_of_atom(i, n, pos, cell_start, geom, B, min(cap, NB_STAGE), stage[w], skey[w], lane, nbr, nnum,
                         nang, nown, nband0, nfar, ctrl);
     __syncwarp();                                      // the stage is reused by the warp's next atom
   }

@@ -261,8 +261,13 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
   // wraps is three; rows whose (y, z) slab lies beyond the list radius are empty.  The 1e-4 margin
   // keeps every candidate a float32 distance test could accept, so the lists are unchanged.
   int rb = 0, rlen = 0;
+  float roy = 0.f, roz = 0.f;
+  int rcode = 0;                                       // shift-table base (dy, dz) | x part << 8
   if (lane < 27) {
     const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, part = lane % 3;
+    roz = dz < 0 ? -geom.lz : (dz > 0 ? geom.lz : 0.f);   // the shift table's offsets
+    roy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
+    rcode = (3 * (dy + 1) + 9 * (dz + 1)) | (part << 8);
     int zz = cz + dz;
     zz += zz < 0 ? geom.ncz : (zz >= geom.ncz ? -geom.ncz : 0);
     int yy = cy + dy;
@@ -294,10 +299,9 @@ __device__ __forceinline__ void neighbors_of_atom(int i, int n, const float4 *__
     const int L = __ffs(ne) - 1;                       // warp-uniform
     ne &= ne - 1u;
     const int b = __shfl_sync(0xffffffffu, rb, L), e = b + __shfl_sync(0xffffffffu, rlen, L);
-    const int dz = L / 9 - 1, dy = (L / 3) % 3 - 1, part = L % 3;
-    const float oz = dz < 0 ? -geom.lz : (dz > 0 ? geom.lz : 0.f);   // the shift table's offsets
-    const float oy = dy < 0 ? -geom.ly : (dy > 0 ? geom.ly : 0.f);
-    const int shb = 3 * (dy + 1) + 9 * (dz + 1);
+    const float oz = __shfl_sync(0xffffffffu, roz, L), oy = __shfl_sync(0xffffffffu, roy, L);
+    const int code = __shfl_sync(0xffffffffu, rcode, L);
+    const int shb = code & 255, part = code >> 8;
     for (int j0 = b; j0 < e; j0 += 32) {
       const int j = j0 + lane;
       const bool inr = j < e;

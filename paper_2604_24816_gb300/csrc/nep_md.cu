@@ -165,10 +165,13 @@ __global__ void k_kinetic(int n, const double *__restrict__ vx, const double *__
 // counters[v - 11] += sums[v] for v >= 11, counters[8] += 1 per evaluation.
 constexpr int N_SUMS = 19;
 
-__global__ void __launch_bounds__(256)
+constexpr int FIN_THREADS = 1024;   // one block per sum; the partials are 8-byte integers, so the
+                                    // order of the additions does not change the result
+__global__ void __launch_bounds__(FIN_THREADS)
 k_finalize(const long long *__restrict__ pd, int nbd, const long long *__restrict__ pf, int nbf,
            const long long *__restrict__ pk, int nbk, double *__restrict__ sums, long long *__restrict__ counters) {
-  __shared__ long long red[256];
+  static_assert(FIN_THREADS == 1024, "32 warp sums, reduced by one warp");
+  __shared__ long long red[FIN_THREADS / 32];
   const int v = blockIdx.x;
   const long long *src;
   int nb, stride, off;
@@ -180,14 +183,17 @@ k_finalize(const long long *__restrict__ pd, int nbd, const long long *__restric
   if (src == nullptr) return;
   long long t = 0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) t += src[(size_t)b * stride + off];
-  red[threadIdx.x] = t;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    t = red[threadIdx.x];                              // FIN_THREADS / 32 == 32 warp sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   }
   if (threadIdx.x == 0) {
-    const long long tot = red[0];
+    const long long tot = t;
     sums[v] = v <= 10 ? (double)tot * FIX_INV : (double)tot;       // energies/virial are fixed point
     if (counters != nullptr && v >= 11) counters[v - 11] += tot;
     if (counters != nullptr && v == 0) counters[8] += 1;
@@ -393,7 +399,7 @@ cudaError_t launch_kinetic(int n, const double *vx, const double *vy, const doub
 
 cudaError_t launch_finalize(const long long *pd, int nbd, const long long *pf, int nbf, const long long *pk, int nbk,
                             double *sums, long long *counters, cudaStream_t st) {
-  k_finalize<<<N_SUMS, 256, 0, st>>>(pd, nbd, pf, nbf, pk, nbk, sums, counters);
+  k_finalize<<<N_SUMS, FIN_THREADS, 0, st>>>(pd, nbd, pf, nbf, pk, nbk, sums, counters);
   return cudaGetLastError();
 }
 
